@@ -1,0 +1,282 @@
+"""FP64 CPU oracle for the CTrex projection / correction / backprojection path.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the product library
+never does.  The arithmetic lives in ``ctrex_oracle.c`` (plain C, FP64,
+OpenMP), which shares no code with the CUDA path; this module only marshals
+numpy arrays through ctypes and builds the shared object on first use.
+
+Each wrapper names the paper passage its C routine follows:
+
+* ``forward``/``forward_rays``  -- Sec. 4.1 projection operator (A), Sec. 3.4
+  angular sub-projections, Sec. 3.1 / 4.2.1 warped sampling.
+* ``correct``                   -- Sec. 4.1 correction kernel, Eq. (1) term 2.
+* ``backproject``               -- Sec. 4.1 backprojection operator with C and
+  alpha, Eq. (1) term 3; Sec. 3.2 / 4.3.2 voxel weights.
+* ``adjoint``, ``motion_grad``  -- transpose and chain rule of ``forward``
+  (Sec. 5 motivates geometry refinement; no formula is printed).
+* ``sirt``                      -- Eq. (1) iterated, all views in one subset.
+
+Parity status: every routine is pinned by ``tests/test_oracle_pins.py``
+(closed forms, analytic phantoms, adjointness, invariances, brute force and
+finite differences); none is "parity unpinned".
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ctrex_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+EPS_C = 1e-6
+
+
+def build(force: bool = False) -> str:
+    """Compile ctrex_oracle.c into liboracle.so (gcc, OpenMP, IEEE FP64)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC", "-std=c11",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = ctypes.CDLL(_LIB)
+            _declare(_lib)
+    return _lib
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_lp = ctypes.POINTER(ctypes.c_long)
+
+
+class _CProblem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("vox", ctypes.c_double * 3), ("origin", ctypes.c_double * 3),
+        ("nu", ctypes.c_int), ("nv", ctypes.c_int),
+        ("n_views", ctypes.c_int), ("n_sub", ctypes.c_int),
+        ("step_vox", ctypes.c_double),
+        ("P", _dp), ("theta", _dp), ("coef", _dp), ("s_view", _dp),
+        ("margin", ctypes.c_double),
+    ]
+
+
+def _declare(lib):
+    pp = ctypes.POINTER(_CProblem)
+    lib.or_setup_views.argtypes = [pp, _dp, _dp, _dp]
+    lib.or_forward.argtypes = [pp, _dp, _ip, ctypes.c_int, _dp, _dp]
+    lib.or_forward_rays.argtypes = [pp, _dp, _ip, _dp, _dp, ctypes.c_long, _dp, _dp]
+    lib.or_count_samples.argtypes = [pp, _ip, ctypes.c_int]
+    lib.or_count_samples.restype = ctypes.c_long
+    lib.or_correct.argtypes = [ctypes.c_long, _dp, _dp, _dp, ctypes.c_double, _dp, _dp]
+    lib.or_backproject.argtypes = [pp, _dp, _ip, ctypes.c_int, _dp, ctypes.c_double,
+                                   ctypes.c_double, _dp, _dp, _dp]
+    lib.or_backproject_voxels.argtypes = [pp, _dp, _ip, ctypes.c_int, _lp, ctypes.c_long, _dp, _dp]
+    lib.or_adjoint.argtypes = [pp, _dp, _ip, ctypes.c_int, _dp]
+    lib.or_motion_grad.argtypes = [pp, _dp, _dp, _ip, ctypes.c_int, _dp, _dp]
+    lib.or_sirt.argtypes = [pp, _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_double,
+                            ctypes.c_double, ctypes.c_double, _dp, _ip]
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a, typ=_dp):
+    if a is None:
+        return ctypes.cast(None, typ)
+    return a.ctypes.data_as(typ)
+
+
+class Problem:
+    """Geometry (and optional motion) of one projection problem, FP64.
+
+    P: [n_views, n_sub, 3, 4]; vol_shape (nz, ny, nx); vox, origin in (x, y, z)
+    order, mm; det (nu, nv); theta [n_views, 15]; coef [8, 8, 8, 3]; s_view
+    [n_views].
+    """
+
+    def __init__(self, P, vol_shape, vox, origin, det, step_vox=0.5, theta=None, coef=None,
+                 s_view=None, margin=0.0):
+        P = _f64(P)
+        if P.ndim == 3:
+            P = P[:, None]
+        self.P = P
+        self.n_views, self.n_sub = P.shape[0], P.shape[1]
+        self.nz, self.ny, self.nx = (int(s) for s in vol_shape)
+        self.vox = tuple(float(v) for v in vox)
+        self.origin = tuple(float(v) for v in origin)
+        self.nu, self.nv = (int(d) for d in det)
+        self.step_vox = float(step_vox)
+        self.theta = None if theta is None else _f64(theta)
+        self.coef = None if coef is None else _f64(coef)
+        self.s_view = None if s_view is None else _f64(s_view)
+        self.margin = float(margin)
+        self._c = _CProblem(self.nx, self.ny, self.nz, (ctypes.c_double * 3)(*self.vox),
+                            (ctypes.c_double * 3)(*self.origin), self.nu, self.nv, self.n_views,
+                            self.n_sub, self.step_vox, _ptr(self.P), _ptr(self.theta),
+                            _ptr(self.coef), _ptr(self.s_view), self.margin)
+
+    @property
+    def vol_shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def min_vox(self):
+        return min(self.vox)
+
+    @property
+    def eps_R(self):
+        return 1e-6 * self.min_vox
+
+    def with_motion(self, theta=None, coef=None, s_view=None, margin=0.0):
+        return Problem(self.P, self.vol_shape, self.vox, self.origin, (self.nu, self.nv),
+                       self.step_vox, theta, coef, s_view, margin)
+
+    def with_P(self, P):
+        return Problem(P, self.vol_shape, self.vox, self.origin, (self.nu, self.nv), self.step_vox,
+                       self.theta, self.coef, self.s_view, self.margin)
+
+
+def _views(pb, views):
+    if views is None:
+        return None, pb.n_views
+    v = np.ascontiguousarray(views, dtype=np.int32)
+    return v, len(v)
+
+
+def _check(ret):
+    if ret != 0:
+        raise ValueError(f"oracle error {ret}")
+
+
+def setup_views(pb):
+    lib = _load()
+    n = pb.n_views * pb.n_sub
+    Pn, src, Minv = np.zeros((n, 12)), np.zeros((n, 3)), np.zeros((n, 9))
+    _check(lib.or_setup_views(ctypes.byref(pb._c), _ptr(Pn), _ptr(src), _ptr(Minv)))
+    return Pn.reshape(pb.n_views, pb.n_sub, 3, 4), src.reshape(pb.n_views, pb.n_sub, 3), \
+        Minv.reshape(pb.n_views, pb.n_sub, 3, 3)
+
+
+def forward(pb, vol, views=None):
+    """(A x, A 1) for the listed views: two arrays [n_sel, nv, nu]."""
+    lib = _load()
+    vol = _f64(vol)
+    assert vol.shape == pb.vol_shape
+    v, n = _views(pb, views)
+    proj = np.zeros((n, pb.nv, pb.nu))
+    rs = np.zeros((n, pb.nv, pb.nu))
+    _check(lib.or_forward(ctypes.byref(pb._c), _ptr(vol), _ptr(v, _ip), n, _ptr(proj), _ptr(rs)))
+    return proj, rs
+
+
+def forward_rays(pb, vol, view, u, v):
+    """Ray integrals at arbitrary detector points (view[i], u[i], v[i])."""
+    lib = _load()
+    vol = _f64(vol)
+    view = np.ascontiguousarray(view, dtype=np.int32)
+    u, v = _f64(u), _f64(v)
+    n = len(view)
+    val, rs = np.zeros(n), np.zeros(n)
+    _check(lib.or_forward_rays(ctypes.byref(pb._c), _ptr(vol), _ptr(view, _ip), _ptr(u), _ptr(v), n,
+                               _ptr(val), _ptr(rs)))
+    return val, rs
+
+
+def count_samples(pb, views=None):
+    lib = _load()
+    v, n = _views(pb, views)
+    return int(lib.or_count_samples(ctypes.byref(pb._c), _ptr(v, _ip), n))
+
+
+def correct(p, q, rowsum, eps_R):
+    """(r, sum (p-q)^2, sum p^2) of Eq. (1) term 2."""
+    lib = _load()
+    p, q, rowsum = _f64(p), _f64(q), _f64(rowsum)
+    r = np.zeros_like(p)
+    sums = np.zeros(2)
+    _check(lib.or_correct(p.size, _ptr(p), _ptr(q), _ptr(rowsum), eps_R, _ptr(r), _ptr(sums)))
+    return r, sums[0], sums[1]
+
+
+def backproject(pb, r, views=None, w=None, alpha=1.0, x=None, eps_C=EPS_C):
+    """(x_new, b, c): Eq. (1) term 3 on x (zeros if None) from r [n_sel, nv, nu]."""
+    lib = _load()
+    r = _f64(r)
+    v, n = _views(pb, views)
+    assert r.shape == (n, pb.nv, pb.nu)
+    x = np.zeros(pb.vol_shape) if x is None else _f64(x).copy()
+    w = None if w is None else _f64(w)
+    b = np.zeros(pb.vol_shape)
+    c = np.zeros(pb.vol_shape)
+    _check(lib.or_backproject(ctypes.byref(pb._c), _ptr(r), _ptr(v, _ip), n, _ptr(w), alpha, eps_C,
+                              _ptr(x), _ptr(b), _ptr(c)))
+    return x, b, c
+
+
+def backproject_voxels(pb, r, vox_flat, views=None):
+    """(b, c) at the listed flat voxel indices."""
+    lib = _load()
+    r = _f64(r)
+    v, n = _views(pb, views)
+    vox_flat = np.ascontiguousarray(vox_flat, dtype=np.int64)
+    b = np.zeros(len(vox_flat))
+    c = np.zeros(len(vox_flat))
+    _check(lib.or_backproject_voxels(ctypes.byref(pb._c), _ptr(r), _ptr(v, _ip), n,
+                                     _ptr(vox_flat, _lp), len(vox_flat), _ptr(b), _ptr(c)))
+    return b, c
+
+
+def adjoint(pb, y, views=None):
+    """A^T y for y [n_sel, nv, nu] (matched transpose of ``forward``)."""
+    lib = _load()
+    y = _f64(y)
+    v, n = _views(pb, views)
+    out = np.zeros(pb.vol_shape)
+    _check(lib.or_adjoint(ctypes.byref(pb._c), _ptr(y), _ptr(v, _ip), n, _ptr(out)))
+    return out
+
+
+def motion_grad(pb, vol, g, views=None):
+    """(dL/dtheta [n_views, 15], dL/dcoef [8, 8, 8, 3]) for L = <g, A x>."""
+    lib = _load()
+    vol, g = _f64(vol), _f64(g)
+    v, n = _views(pb, views)
+    gt = np.zeros((pb.n_views, 15))
+    gc = np.zeros((8, 8, 8, 3))
+    _check(lib.or_motion_grad(ctypes.byref(pb._c), _ptr(vol), _ptr(g), _ptr(v, _ip), n, _ptr(gt),
+                              _ptr(gc)))
+    return gt, gc
+
+
+def sirt(pb, p, max_iter, alpha=1.0, w=None, tol=0.0, x0=None, eps_C=EPS_C):
+    """(x, residual history, iterations done) of Eq. (1) with all views."""
+    lib = _load()
+    p = _f64(p)
+    x = np.zeros(pb.vol_shape) if x0 is None else _f64(x0).copy()
+    w = None if w is None else _f64(w)
+    hist = np.full(max_iter, np.nan)
+    done = ctypes.c_int(0)
+    ret = lib.or_sirt(ctypes.byref(pb._c), _ptr(x), _ptr(p), max_iter, alpha, _ptr(w), tol, pb.eps_R,
+                      eps_C, _ptr(hist), ctypes.byref(done))
+    if ret < 0:
+        raise ValueError(f"oracle error {ret}")
+    return x, hist, done.value, ret

@@ -1,0 +1,348 @@
+"""Seeded synthetic inputs: configurations, trajectories, phantoms, motion.
+
+This module holds none of the reconstruction arithmetic.  It builds the
+*inputs* that the CUDA path and the FP64 oracle both consume: per-view 3x4
+projection matrices (the "Trajectory" of Sec. 2.1 / 2.2.2), volumes of
+analytic objects, and motion parameters.  Random numbers come from
+``numpy.random.Generator(PCG64(seed))``, drawn in the order documented in each
+builder, so every input is reproducible from its seed.
+
+Shared physical set-up (all configurations): source-object distance 200 mm,
+source-detector distance 400 mm, a 32 mm cubic field of view centred at the
+world origin (voxel = 32/N mm), a 96 mm wide detector (pitch = 96/nu mm, rows
+with the same pitch), circular view v at angle 2*pi*v/V about z.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+SOD = 200.0
+SDD = 400.0
+BOX = 32.0
+DET_WIDTH = 96.0
+
+
+@dataclasses.dataclass(frozen=True)
+class Config:
+    """One workload: volume edge n, detector nu x nv, views, sub-angles."""
+
+    name: str
+    n: int
+    nu: int
+    nv: int
+    n_views: int
+    n_sub: int = 1
+    trajectory: str = "circular"      # circular | perturbed | helical
+    seed: int = 1
+    helical_turns: float = 0.0
+    z_span: float = 0.0               # helical: source z runs -z_span .. +z_span (mm)
+    step_vox: float = 0.5
+    n_ellipsoids: int = 10
+    n_blobs: int = 0
+    textured: bool = False
+    motion: bool = False
+    margin: float = 0.0               # mm, clip-box dilation with motion
+    sirt_iters: int = 10
+    box: float = BOX
+    det_width: float = DET_WIDTH
+
+    @property
+    def vox(self) -> float:
+        return self.box / self.n
+
+    @property
+    def pitch(self) -> float:
+        return self.det_width / self.nu
+
+    @property
+    def origin(self) -> tuple:
+        o = -0.5 * self.box + 0.5 * self.vox
+        return (o, o, o)
+
+    @property
+    def vol_shape(self) -> tuple:
+        return (self.n, self.n, self.n)
+
+    def scaled(self, **kw) -> "Config":
+        return dataclasses.replace(self, **kw)
+
+
+# Workloads (names describe them; sizes as stated).
+CIRCULAR_64 = Config("circular-64^3-96^2-90v", n=64, nu=96, nv=96, n_views=90, seed=1,
+                     sirt_iters=10)
+PERTURBED_512 = Config("perturbed-512^3-768^2-720v", n=512, nu=768, nv=768, n_views=720,
+                       trajectory="perturbed", seed=2, n_blobs=40, sirt_iters=50)
+HELICAL_256 = Config("helical-256^3-512x384-1440v-S4", n=256, nu=512, nv=384, n_views=1440,
+                     n_sub=4, trajectory="helical", seed=3, helical_turns=2.0, z_span=36.0)
+MOTION_256 = Config("motion-256^3-384^2-360v", n=256, nu=384, nv=384, n_views=360, seed=4,
+                    motion=True, margin=0.5)
+MOTION_FD_32 = Config("motion-fd-32^3-48^2-24v", n=32, nu=48, nv=48, n_views=24, seed=4,
+                      motion=True, margin=0.5)
+SPARSE_128 = Config("sparse-128^3-192^2-60v", n=128, nu=192, nv=192, n_views=60, seed=0,
+                    textured=True)
+
+CONFIGS = {c.name: c for c in (CIRCULAR_64, PERTURBED_512, HELICAL_256, MOTION_256, MOTION_FD_32,
+                               SPARSE_128)}
+
+
+# ---------------------------------------------------------------------------
+# Trajectories: per-view projection matrices (inputs to both sides)
+# ---------------------------------------------------------------------------
+
+def rot_z(a: float) -> np.ndarray:
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def cone_matrix(src, det_centre, u_axis, v_axis, nu, nv) -> np.ndarray:
+    """3x4 matrix mapping world mm to homogeneous pixel indices.
+
+    Pixel (iu, iv) centre sits at d0 + iu*u_axis + iv*v_axis with
+    d0 = det_centre - (nu-1)/2 u_axis - (nv-1)/2 v_axis; the matrix is
+    Mc^{-1} [I | -src] with Mc = [u_axis | v_axis | d0 - src].
+    """
+    src = np.asarray(src, float)
+    u_axis = np.asarray(u_axis, float)
+    v_axis = np.asarray(v_axis, float)
+    d0 = np.asarray(det_centre, float) - 0.5 * (nu - 1) * u_axis - 0.5 * (nv - 1) * v_axis
+    Mc = np.stack([u_axis, v_axis, d0 - src], axis=1)
+    Mi = np.linalg.inv(Mc)
+    return np.concatenate([Mi, -(Mi @ src)[:, None]], axis=1)
+
+
+def _circular_pose(angle: float, z: float, cfg: Config):
+    R = rot_z(angle)
+    src = R @ np.array([-SOD, 0.0, 0.0]) + np.array([0.0, 0.0, z])
+    ctr = R @ np.array([SDD - SOD, 0.0, 0.0]) + np.array([0.0, 0.0, z])
+    u = R @ np.array([0.0, cfg.pitch, 0.0])
+    v = np.array([0.0, 0.0, cfg.pitch])
+    return src, ctr, u, v
+
+
+def detector_frames(cfg: Config):
+    """Per (view, sub) source, detector centre, u axis, v axis: arrays [V, S, 3].
+
+    circular:  angle 2*pi*v/V, z = 0.
+    perturbed: circular, then per view (draw order: du, dv in pixels U[-2, 2];
+               tilt U[-0.5, 0.5] deg about the detector normal; source jitter
+               3 x U[-0.2, 0.2] mm) the detector is offset by du*u + dv*v,
+               its u/v axes are rotated in-plane by the tilt and the source is
+               displaced.
+    helical:   V views over ``helical_turns`` turns, angle a_v = 2*pi*turns*v/V,
+               z = -z_span + p*a_v with p = 2*z_span / (2*pi*turns) (mm/rad);
+               sub-angle s of view v at a_v + (s + 1/2 - S/2) * da / S with da
+               the view increment, z interpolated the same way.
+    The sub-angle rule is also used by circular trajectories with n_sub > 1.
+    """
+    V, S = cfg.n_views, cfg.n_sub
+    srcs = np.zeros((V, S, 3))
+    ctrs = np.zeros((V, S, 3))
+    us = np.zeros((V, S, 3))
+    vs = np.zeros((V, S, 3))
+    if cfg.trajectory == "helical":
+        total = 2.0 * math.pi * cfg.helical_turns
+        da = total / V
+        p = 2.0 * cfg.z_span / total
+    else:
+        da = 2.0 * math.pi / V
+        p = 0.0
+    rng = np.random.Generator(np.random.PCG64(cfg.seed)) if cfg.trajectory == "perturbed" else None
+    for v in range(V):
+        if rng is not None:
+            du, dv = rng.uniform(-2.0, 2.0, size=2)
+            tilt = math.radians(rng.uniform(-0.5, 0.5))
+            jitter = rng.uniform(-0.2, 0.2, size=3)
+        for s in range(S):
+            a = v * da + (s + 0.5 - 0.5 * S) * da / S
+            z = (-cfg.z_span + p * a) if cfg.trajectory == "helical" else 0.0
+            src, ctr, u, w = _circular_pose(a, z, cfg)
+            if rng is not None:
+                n = np.cross(u, w)
+                n /= np.linalg.norm(n)
+                ctr = ctr + du * u + dv * w
+                c, sn = math.cos(tilt), math.sin(tilt)
+                u, w = c * u + sn * np.cross(n, u), c * w + sn * np.cross(n, w)
+                src = src + jitter
+            srcs[v, s], ctrs[v, s], us[v, s], vs[v, s] = src, ctr, u, w
+    return srcs, ctrs, us, vs
+
+
+def projection_matrices(cfg: Config) -> np.ndarray:
+    """P [V, S, 3, 4] (float64) for the configuration's trajectory."""
+    srcs, ctrs, us, vs = detector_frames(cfg)
+    V, S = cfg.n_views, cfg.n_sub
+    P = np.zeros((V, S, 3, 4))
+    for v in range(V):
+        for s in range(S):
+            P[v, s] = cone_matrix(srcs[v, s], ctrs[v, s], us[v, s], vs[v, s], cfg.nu, cfg.nv)
+    return P
+
+
+# ---------------------------------------------------------------------------
+# Phantoms
+# ---------------------------------------------------------------------------
+
+def random_rotation(rng) -> np.ndarray:
+    """Uniform rotation from a random unit quaternion (4 normal draws)."""
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+@dataclasses.dataclass
+class Ellipsoid:
+    centre: np.ndarray     # mm
+    semi_axes: np.ndarray  # mm
+    rot: np.ndarray        # columns = principal axes
+    density: float
+    texture: Optional[np.ndarray] = None  # [8, 4]: kx, ky, kz (1/mm), phase
+
+
+@dataclasses.dataclass
+class Blob:
+    centre: np.ndarray
+    sigma: float
+    amplitude: float
+
+
+def draw_objects(cfg: Config, seed: Optional[int] = None):
+    """Ellipsoids then blobs, drawn from PCG64(seed or cfg.seed) in this order.
+
+    Ellipsoid: full axes U[3, 20] mm (3 draws), rotation (4 normals), centre
+    uniform in the box shrunk by the largest semi-axis (3 draws), density
+    U[0.1, 1]; textured phantoms add 8 sinusoids (direction 3 normals,
+    |k| U[0.2, 1] 1/mm, phase U[0, 2 pi]).  Blob: sigma U[0.3, 2] mm,
+    amplitude U[0.05, 0.5], centre uniform in the box shrunk by 3 sigma.
+    """
+    rng = np.random.Generator(np.random.PCG64(cfg.seed if seed is None else seed))
+    half = 0.5 * cfg.box
+    ells = []
+    for _ in range(cfg.n_ellipsoids):
+        semi = 0.5 * rng.uniform(3.0, 20.0, size=3)
+        rot = random_rotation(rng)
+        r = float(semi.max())
+        centre = rng.uniform(-half + r, half - r, size=3)
+        dens = float(rng.uniform(0.1, 1.0))
+        tex = None
+        if cfg.textured:
+            tex = np.zeros((8, 4))
+            for k in range(8):
+                d = rng.normal(size=3)
+                d /= np.linalg.norm(d)
+                tex[k, :3] = d * rng.uniform(0.2, 1.0)
+                tex[k, 3] = rng.uniform(0.0, 2.0 * math.pi)
+        ells.append(Ellipsoid(centre, semi, rot, dens, tex))
+    blobs = []
+    for _ in range(cfg.n_blobs):
+        sigma = float(rng.uniform(0.3, 2.0))
+        amp = float(rng.uniform(0.05, 0.5))
+        centre = rng.uniform(-half + 3 * sigma, half - 3 * sigma, size=3)
+        blobs.append(Blob(centre, sigma, amp))
+    return ells, blobs
+
+
+def _axis_coords(cfg: Config, sub: int, torch_mod, device):
+    """Sub-sample coordinates along one axis: [n, sub] (mm)."""
+    off = (torch_mod.arange(sub, dtype=torch_mod.float64, device=device) + 0.5) / sub - 0.5
+    i = torch_mod.arange(cfg.n, dtype=torch_mod.float64, device=device)
+    return cfg.origin[0] + (i[:, None] + off[None, :]) * cfg.vox
+
+
+def voxelize(cfg: Config, ells, blobs, sub: int = 4, device: str = "cpu", dtype=None):
+    """Volume [n, n, n] (z, y, x): mean of the object sum over sub^3 sub-samples.
+
+    Overlapping objects add.  Ellipsoid indicator (times its density, times
+    1 + 0.3 * mean of its sinusoids if textured) is evaluated on the sub-sample
+    grid inside its bounding box; an isotropic Gaussian blob is separable, so
+    its sub-sample mean is the product of three per-axis means.
+    """
+    import torch
+
+    vol = torch.zeros(cfg.vol_shape, dtype=torch.float64, device=device)
+    ax = _axis_coords(cfg, sub, torch, device)          # [n, sub]
+    n = cfg.n
+    for e in ells:
+        r = float(e.semi_axes.max())
+        lo = [max(0, int(math.floor((e.centre[a] - r - cfg.origin[0]) / cfg.vox)) - 1) for a in range(3)]
+        hi = [min(n, int(math.ceil((e.centre[a] + r - cfg.origin[0]) / cfg.vox)) + 2) for a in range(3)]
+        Q = torch.tensor((e.rot / e.semi_axes[None, :]).T, dtype=torch.float64, device=device)
+        c = torch.tensor(e.centre, dtype=torch.float64, device=device)
+        xs = ax[lo[0]:hi[0]] - c[0]
+        ys = ax[lo[1]:hi[1]] - c[1]
+        for z0 in range(lo[2], hi[2], 16):
+            z1 = min(hi[2], z0 + 16)
+            zs = ax[z0:z1] - c[2]
+            # local coordinates: q = Q (x - c); broadcast [z, sz, y, sy, x, sx]
+            Z = zs[:, :, None, None, None, None]
+            Y = ys[None, None, :, :, None, None]
+            X = xs[None, None, None, None, :, :]
+            q2 = 0.0
+            for row in range(3):
+                qr = Q[row, 0] * X + Q[row, 1] * Y + Q[row, 2] * Z
+                q2 = q2 + qr * qr
+            inside = (q2 <= 1.0).to(torch.float64)
+            if e.texture is not None:
+                tex = 0.0
+                for k in range(8):
+                    kx, ky, kz, ph = (float(t) for t in e.texture[k])
+                    tex = tex + torch.sin(kx * (X + c[0]) + ky * (Y + c[1]) + kz * (Z + c[2]) + ph)
+                inside = inside * (1.0 + 0.3 * tex / 8.0)
+            val = inside.mean(dim=(1, 3, 5)) * e.density
+            vol[z0:z1, lo[1]:hi[1], lo[0]:hi[0]] += val
+    for b in blobs:
+        g = []
+        for a in range(3):
+            d = ax - float(b.centre[a])
+            g.append(torch.exp(-0.5 * d * d / (b.sigma * b.sigma)).mean(dim=1))
+        vol += b.amplitude * g[2][:, None, None] * g[1][None, :, None] * g[0][None, None, :]
+    if dtype is not None:
+        vol = vol.to(dtype)
+    return vol
+
+
+def phantom(cfg: Config, seed: Optional[int] = None, device: str = "cpu", sub: int = 4):
+    """Voxelised phantom of the configuration (float64 torch tensor)."""
+    ells, blobs = draw_objects(cfg, seed)
+    return voxelize(cfg, ells, blobs, sub=sub, device=device)
+
+
+# ---------------------------------------------------------------------------
+# Motion parameters
+# ---------------------------------------------------------------------------
+
+def motion_params(cfg: Config, seed: Optional[int] = None):
+    """theta [V, 15] = (omega, t, A row-major), coef [8, 8, 8, 3], s_view [V].
+
+    Draw order from PCG64(seed or cfg.seed + 1000): per view omega 3 x U[-1, 1]
+    deg, t 3 x U[-0.5, 0.5] mm, A = I + 9 x U[-0.01, 0.01]; then coefficients
+    8*8*8*3 x U[-1, 1], rescaled so that the largest control-point vector has
+    length 3 voxels (a B-spline is a convex combination of its coefficients, so
+    the displacement never exceeds that).  s_v = v / (V - 1).
+    """
+    rng = np.random.Generator(np.random.PCG64((cfg.seed if seed is None else seed) + 1000))
+    V = cfg.n_views
+    theta = np.zeros((V, 15))
+    for v in range(V):
+        theta[v, 0:3] = np.radians(rng.uniform(-1.0, 1.0, size=3))
+        theta[v, 3:6] = rng.uniform(-0.5, 0.5, size=3)
+        theta[v, 6:15] = (np.eye(3) + rng.uniform(-0.01, 0.01, size=(3, 3))).reshape(9)
+    coef = rng.uniform(-1.0, 1.0, size=(8, 8, 8, 3))
+    coef *= 3.0 * cfg.vox / np.linalg.norm(coef, axis=-1).max()
+    s_view = np.arange(V, dtype=np.float64) / max(V - 1, 1)
+    return theta, coef, s_view
+
+
+def identity_theta(n_views: int) -> np.ndarray:
+    th = np.zeros((n_views, 15))
+    th[:, 6:15] = np.eye(3).reshape(9)
+    return th

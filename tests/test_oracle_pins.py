@@ -1,0 +1,530 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself: each check is a closed form, an
+analytic line integral, an identity of the operators (adjointness, partition of
+unity, linearity), an invariance of the projection-matrix formulation
+(Sec. 2.2), brute force on an 8^3 grid, or finite differences.  A plausible
+slip in the oracle (dropped term, wrong sign, swapped axis, transposed matrix)
+fails at least one of them.
+"""
+
+import math
+
+import numpy as np
+import pytest
+from scipy.special import erf
+
+import oracle
+from paper_2609_30166_gb300 import inputs
+from tests.helpers import oracle_problem, ray_points, rel_l2
+
+
+def small(cfg=None, **kw):
+    base = inputs.CIRCULAR_64 if cfg is None else cfg
+    return base.scaled(**kw)
+
+
+# ---------------------------------------------------------------------------
+# P1: closed form for axis-aligned rays through a row of voxel centres
+# ---------------------------------------------------------------------------
+
+def _row_closed_form(row, vox):
+    # truncated-midpoint samples at index -1/4, 1/4, ..., N - 3/4 with weight vox/2
+    return vox * (row.sum() - (row[0] + row[-1]) / 8.0)
+
+
+@pytest.mark.parametrize("n", [9, 13])
+def test_p1_axis_rays_closed_form(n):
+    cfg = small(n=n, nu=n, nv=n, n_views=4)
+    pb = oracle_problem(cfg)
+    rng = np.random.default_rng(11)
+    vol = rng.uniform(0.0, 1.0, size=cfg.vol_shape)
+    proj, rs = oracle.forward(pb, vol)
+    c = (n - 1) // 2
+    # view 0: source on -x, central ray along +x through row (z=c, y=c)
+    assert proj[0, c, c] == pytest.approx(_row_closed_form(vol[c, c, :], cfg.vox), rel=1e-13)
+    # view 1: angle 90 deg, central ray along +y through column (z=c, x=c)
+    assert proj[1, c, c] == pytest.approx(_row_closed_form(vol[c, :, c], cfg.vox), rel=1e-13)
+    # all-ones volume: row sum = vox (N - 1/4)
+    assert rs[0, c, c] == pytest.approx(cfg.vox * (n - 0.25), rel=1e-13)
+    # off-centre detector rows through voxel-centre rows are not axis aligned;
+    # the central column of view 0 with an all-ones volume obeys the same rule
+    ones_proj, _ = oracle.forward(pb, np.ones(cfg.vol_shape))
+    assert ones_proj[0, c, c] == pytest.approx(cfg.vox * (n - 0.25), rel=1e-13)
+
+
+def test_p1_z_ray_closed_form():
+    n = 11
+    cfg = small(n=n, nu=n, nv=n, n_views=1)
+    pitch = cfg.pitch
+    P = inputs.cone_matrix([0.0, 0.0, -inputs.SOD], [0.0, 0.0, inputs.SDD - inputs.SOD],
+                           [pitch, 0.0, 0.0], [0.0, pitch, 0.0], n, n)
+    pb = oracle_problem(cfg, P=P[None, None])
+    rng = np.random.default_rng(12)
+    vol = rng.uniform(0.0, 1.0, size=cfg.vol_shape)
+    proj, _ = oracle.forward(pb, vol)
+    c = (n - 1) // 2
+    assert proj[0, c, c] == pytest.approx(_row_closed_form(vol[:, c, c], cfg.vox), rel=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# P2: analytic ellipsoid line integrals (chord length x density)
+# ---------------------------------------------------------------------------
+
+def _analytic_ellipsoids(cfg, ells, views):
+    out = []
+    for view in views:
+        s, pix = ray_points(cfg, view)
+        d = pix - s
+        d /= np.linalg.norm(d, axis=-1, keepdims=True)
+        tot = np.zeros(pix.shape[:2])
+        for e in ells:
+            Q = (e.rot / e.semi_axes[None, :]).T       # q = Q (x - c)
+            a0 = (s - e.centre) @ Q.T                   # [3]
+            a1 = d @ Q.T                                # [nv, nu, 3]
+            A = (a1 * a1).sum(-1)
+            B = 2.0 * (a1 * a0).sum(-1)
+            C = (a0 * a0).sum() - 1.0
+            disc = B * B - 4 * A * C
+            chord = np.where(disc > 0, np.sqrt(np.maximum(disc, 0)) / A, 0.0)
+            tot += e.density * chord
+        out.append(tot)
+    return np.stack(out)
+
+
+def test_p2_ellipsoid_chords_converge():
+    errs = []
+    for n in (64, 128):
+        cfg = small(n=n, n_views=6)
+        ells, blobs = inputs.draw_objects(cfg)
+        vol = inputs.voxelize(cfg, ells, blobs).numpy()
+        pb = oracle_problem(cfg)
+        proj, _ = oracle.forward(pb, vol)
+        ref = _analytic_ellipsoids(cfg, ells, range(cfg.n_views))
+        errs.append(rel_l2(proj, ref))
+    assert errs[0] <= 2e-2, errs
+    assert errs[0] / errs[1] >= 1.7, errs
+
+
+# ---------------------------------------------------------------------------
+# P3: analytic Gaussian line integral (erf), second-order convergence
+# ---------------------------------------------------------------------------
+
+def _gauss_line(s, d, blob, t0, t1):
+    c = blob.centre
+    tc = (c - s) @ d
+    b2 = ((c - s) ** 2).sum() - tc * tc
+    sg = blob.sigma
+    k = blob.amplitude * math.exp(-0.5 * b2 / (sg * sg)) * sg * math.sqrt(math.pi / 2)
+    return k * (erf((t1 - tc) / (sg * math.sqrt(2))) - erf((t0 - tc) / (sg * math.sqrt(2))))
+
+
+def test_p3_gaussian_blob_second_order():
+    """Ray through the centre of an isotropic Gaussian, nearly along x.
+
+    Leading-order error of (voxel average over 4^3 sub-samples) + (trilinear
+    interpolation) + (truncated-midpoint quadrature) relative to the exact erf
+    integral: along the ray both the voxel smoothing and the quadrature of the
+    piecewise-linear interpolant integrate to zero; across the ray the
+    projected Gaussian G is box-smoothed in y and z (factor 1 - 2 h^2 / 24 s^2)
+    and bilinearly interpolated at fractional offsets (fy, fz) (error
+    -fy(1-fy) h^2 / 2s^2 - fz(1-fz) h^2 / 2s^2).  So
+        rel.err = -(h/s)^2 [1/12 + (fy(1-fy) + fz(1-fz)) / 2] + O(h^4).
+    """
+    blob = inputs.Blob(np.array([0.7, -0.4, 0.3]), 3.0, 1.0)
+    for n in (32, 64, 128):
+        cfg = small(n=n, nu=48, nv=48, n_views=1, n_ellipsoids=0)
+        vol = inputs.voxelize(cfg, [], [blob]).numpy()
+        pb = oracle_problem(cfg)
+        srcs, ctrs, ua, va = inputs.detector_frames(cfg)
+        s = srcs[0, 0]
+        # detector point on the line source -> blob centre (trajectory definition)
+        d = blob.centre - s
+        d /= np.linalg.norm(d)
+        nrm = np.cross(ua[0, 0], va[0, 0])
+        d0 = ctrs[0, 0] - 0.5 * (cfg.nu - 1) * ua[0, 0] - 0.5 * (cfg.nv - 1) * va[0, 0]
+        hit = s + d * (((d0 - s) @ nrm) / (d @ nrm)) - d0
+        u = hit @ ua[0, 0] / (ua[0, 0] @ ua[0, 0])
+        v = hit @ va[0, 0] / (va[0, 0] @ va[0, 0])
+        val, _ = oracle.forward_rays(pb, vol, [0], [u], [v])
+        exact = _gauss_line(s, d, blob, -1e3, 1e3)
+        err = val[0] / exact - 1.0
+        g = (blob.centre - np.array(cfg.origin)) / cfg.vox
+        fy, fz = g[1] - math.floor(g[1]), g[2] - math.floor(g[2])
+        pred = -(cfg.vox / blob.sigma) ** 2 * (1.0 / 12.0 + 0.5 * (fy * (1 - fy) + fz * (1 - fz)))
+        assert abs(err - pred) <= 0.1 * abs(pred), (n, err, pred)
+
+
+def test_p3_gaussian_blob_detector():
+    """Whole detector, sigma = 6 voxels: second-order error below 1e-2."""
+    cfg = small(n=64, nu=48, nv=48, n_views=2, n_ellipsoids=0)
+    blob = inputs.Blob(np.array([0.7, -0.4, 0.3]), 3.0, 1.0)
+    vol = inputs.voxelize(cfg, [], [blob]).numpy()
+    proj, _ = oracle.forward(oracle_problem(cfg), vol)
+    ref = np.zeros_like(proj)
+    for view in range(cfg.n_views):
+        s, pix = ray_points(cfg, view)
+        for iv in range(cfg.nv):
+            for iu in range(cfg.nu):
+                d = pix[iv, iu] - s
+                d /= np.linalg.norm(d)
+                ref[view, iv, iu] = _gauss_line(s, d, blob, -1e3, 1e3)
+    assert rel_l2(proj, ref) <= 1e-2
+
+
+# ---------------------------------------------------------------------------
+# P4: adjoint dot-product test <Ax, y> = <x, A^T y>
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", ["plain", "subangles", "motion", "perturbed"])
+def test_p4_adjoint_dot_product(variant):
+    rng = np.random.default_rng(4)
+    if variant == "plain":
+        cfg = small(n=16, nu=20, nv=18, n_views=5)
+        pb = oracle_problem(cfg)
+    elif variant == "subangles":
+        cfg = small(n=16, nu=20, nv=18, n_views=5, n_sub=3)
+        pb = oracle_problem(cfg)
+    elif variant == "perturbed":
+        cfg = small(n=16, nu=20, nv=18, n_views=5, trajectory="perturbed", seed=7)
+        pb = oracle_problem(cfg)
+    else:
+        cfg = small(inputs.MOTION_FD_32, n=16, nu=20, nv=18, n_views=5)
+        th, co, sv = inputs.motion_params(cfg)
+        pb = oracle_problem(cfg, theta=th, coef=co, s_view=sv)
+    x = rng.normal(size=cfg.vol_shape)
+    y = rng.normal(size=(cfg.n_views, cfg.nv, cfg.nu))
+    Ax, _ = oracle.forward(pb, x)
+    ATy = oracle.adjoint(pb, y)
+    lhs, rhs = float((Ax * y).sum()), float((x * ATy).sum())
+    scale = np.linalg.norm(Ax) * np.linalg.norm(y)
+    assert abs(lhs - rhs) <= 1e-12 * scale
+
+
+# ---------------------------------------------------------------------------
+# P5: brute force on an 8^3 grid
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def dense8():
+    cfg = small(n=8, nu=10, nv=9, n_views=4, trajectory="perturbed", seed=5)
+    pb = oracle_problem(cfg)
+    nvox = 8 ** 3
+    nray = cfg.n_views * cfg.nv * cfg.nu
+    A = np.zeros((nray, nvox))
+    for j in range(nvox):
+        e = np.zeros(nvox)
+        e[j] = 1.0
+        A[:, j] = oracle.forward(pb, e.reshape(cfg.vol_shape))[0].ravel()
+    B = np.zeros((nvox, nray))
+    for i in range(nray):
+        e = np.zeros(nray)
+        e[i] = 1.0
+        B[:, i] = oracle.backproject(pb, e.reshape(cfg.n_views, cfg.nv, cfg.nu))[1].ravel()
+    return cfg, pb, A, B
+
+
+def test_p5_dense_adjoint_is_transpose(dense8):
+    cfg, pb, A, _ = dense8
+    nray = A.shape[0]
+    AT = np.zeros((A.shape[1], nray))
+    for i in range(0, nray, 1):
+        e = np.zeros(nray)
+        e[i] = 1.0
+        AT[:, i] = oracle.adjoint(pb, e.reshape(cfg.n_views, cfg.nv, cfg.nu)).ravel()
+    assert np.max(np.abs(AT - A.T)) <= 1e-14 * np.max(np.abs(A))
+    assert (A >= 0).all() and A.sum() > 0
+
+
+def test_p5_linearity_and_rowsum(dense8):
+    cfg, pb, A, _ = dense8
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=cfg.vol_shape)
+    Ax, rs = oracle.forward(pb, x)
+    assert np.allclose(Ax.ravel(), A @ x.ravel(), rtol=0, atol=1e-12 * np.abs(Ax).max())
+    assert np.allclose(rs.ravel(), A.sum(axis=1), rtol=0, atol=1e-13)
+
+
+def test_p5_backprojector_column_sums(dense8):
+    cfg, pb, _, B = dense8
+    _, _, c = oracle.backproject(pb, np.ones((cfg.n_views, cfg.nv, cfg.nu)))
+    assert np.allclose(c.ravel(), B.sum(axis=1), atol=1e-13)
+    assert (B >= 0).all()
+
+
+def test_p5_sirt_step_is_dense_formula(dense8):
+    cfg, pb, A, B = dense8
+    rng = np.random.default_rng(6)
+    x0 = rng.uniform(0, 1, size=cfg.vol_shape)
+    p = A @ rng.uniform(0, 1, size=A.shape[1])
+    w = rng.uniform(0.2, 1.0, size=cfg.vol_shape)
+    alpha = 0.7
+    rowsum = A.sum(axis=1)
+    R = np.where(rowsum > pb.eps_R, 1.0 / np.where(rowsum > 0, rowsum, 1), 0.0)
+    colsum = B.sum(axis=1)
+    C = np.where(colsum > oracle.EPS_C, 1.0 / np.where(colsum > 0, colsum, 1), 0.0)
+    expect = x0.ravel() + alpha * w.ravel() * C * (B @ (R * (p - A @ x0.ravel())))
+    x1, hist, done, ret = oracle.sirt(pb, p.reshape(cfg.n_views, cfg.nv, cfg.nu), 1, alpha=alpha,
+                                      w=w, x0=x0)
+    assert done == 1 and ret == 0
+    assert np.allclose(x1.ravel(), expect, rtol=0, atol=1e-12)
+    rho = np.linalg.norm(p - A @ x0.ravel()) / np.linalg.norm(p)
+    assert hist[0] == pytest.approx(rho, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# P6: invariances of the projection-matrix formulation (Sec. 2.2)
+# ---------------------------------------------------------------------------
+
+def test_p6_scale_invariance_and_sign():
+    cfg = small(n=16, nu=20, nv=20, n_views=4, trajectory="perturbed", seed=3)
+    pb = oracle_problem(cfg)
+    rng = np.random.default_rng(7)
+    vol = rng.uniform(size=cfg.vol_shape)
+    ref, rs = oracle.forward(pb, vol)
+    for kappa in (-2.5, 3.0, -1e-3):
+        got, rs2 = oracle.forward(pb.with_P(pb.P * kappa), vol)
+        assert np.allclose(got, ref, rtol=0, atol=1e-12 * ref.max())
+        assert np.allclose(rs2, rs, rtol=0, atol=1e-12 * rs.max())
+    r = rng.normal(size=ref.shape)
+    _, b1, c1 = oracle.backproject(pb, r)
+    _, b2, c2 = oracle.backproject(pb.with_P(pb.P * -4.0), r)
+    assert np.allclose(b1, b2, atol=1e-12) and np.allclose(c1, c2, atol=1e-12)
+
+
+def test_p6_rotation_about_z():
+    cfg = small(n=16, nu=24, nv=20, n_views=3, trajectory="perturbed", seed=9)
+    pb = oracle_problem(cfg)
+    rng = np.random.default_rng(8)
+    vol = rng.uniform(size=cfg.vol_shape)
+    # rotate content by +90 deg about z: new(x, y) = old(y, -x)
+    vol_r = np.ascontiguousarray(vol[:, ::-1, :].transpose(0, 2, 1))
+    Rz = inputs.rot_z(math.pi / 2)
+    P2 = pb.P.copy()
+    P2[..., :3] = pb.P[..., :3] @ Rz.T
+    ref, _ = oracle.forward(pb, vol)
+    got, _ = oracle.forward(pb.with_P(P2), vol_r)
+    assert np.allclose(got, ref, rtol=0, atol=1e-11 * ref.max())
+    # the backprojector commutes with the same rotation
+    r = rng.normal(size=ref.shape)
+    _, b1, _ = oracle.backproject(pb, r)
+    _, b2, _ = oracle.backproject(pb.with_P(P2), r)
+    b1_r = b1[:, ::-1, :].transpose(0, 2, 1)
+    assert np.allclose(b2, b1_r, rtol=0, atol=1e-11 * np.abs(b1).max())
+
+
+def test_p6_view_order_and_linearity():
+    cfg = small(n=16, nu=20, nv=20, n_views=5, trajectory="perturbed", seed=10)
+    pb = oracle_problem(cfg)
+    rng = np.random.default_rng(9)
+    x, y = rng.uniform(size=cfg.vol_shape), rng.uniform(size=cfg.vol_shape)
+    ref, _ = oracle.forward(pb, x)
+    perm = np.array([3, 0, 4, 1, 2])
+    got, _ = oracle.forward(pb, x, views=perm)
+    assert np.array_equal(got, ref[perm])
+    ay, _ = oracle.forward(pb, y)
+    axy, _ = oracle.forward(pb, 2.0 * x - 3.0 * y)
+    assert np.allclose(axy, 2.0 * ref - 3.0 * ay, atol=1e-12 * np.abs(axy).max())
+
+
+# ---------------------------------------------------------------------------
+# P7: special cases of the motion model (Sec. 2.2.2, Sec. 3.1, Sec. 3.4)
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def motion_case():
+    cfg = small(inputs.MOTION_FD_32, n=16, nu=20, nv=20, n_views=4)
+    rng = np.random.default_rng(10)
+    vol = np.zeros(cfg.vol_shape)
+    vol[4:12, 4:12, 4:12] = rng.uniform(size=(8, 8, 8))  # interior content
+    return cfg, vol
+
+
+def test_p7_identity_motion_is_static(motion_case):
+    cfg, vol = motion_case
+    ref, rs = oracle.forward(oracle_problem(cfg), vol)
+    pb = oracle_problem(cfg, theta=inputs.identity_theta(cfg.n_views), coef=np.zeros((8, 8, 8, 3)),
+                        s_view=np.ones(cfg.n_views))
+    pb0 = pb.with_motion(pb.theta, pb.coef, pb.s_view, margin=0.0)
+    got, rs2 = oracle.forward(pb0, vol)
+    assert np.array_equal(got, ref) and np.array_equal(rs2, rs)
+
+
+def test_p7_constant_coefficients_are_translation(motion_case):
+    cfg, vol = motion_case
+    shift = np.array([2.0, -1.0, 1.0]) * cfg.vox          # whole voxels (x, y, z)
+    coef = np.broadcast_to(shift, (8, 8, 8, 3)).copy()
+    th = inputs.identity_theta(cfg.n_views)
+    pb_c = oracle_problem(cfg, theta=th, coef=coef, s_view=np.ones(cfg.n_views))
+    th_t = th.copy()
+    th_t[:, 3:6] = shift
+    pb_t = oracle_problem(cfg, theta=th_t, coef=np.zeros((8, 8, 8, 3)), s_view=np.ones(cfg.n_views))
+    a, _ = oracle.forward(pb_c, vol)
+    b, _ = oracle.forward(pb_t, vol)
+    assert np.allclose(a, b, rtol=0, atol=1e-12 * a.max())
+    # sampling mu(x + shift) equals sampling the volume shifted by -shift
+    shifted = np.zeros_like(vol)
+    shifted[3:11, 5:13, 2:10] = vol[4:12, 4:12, 4:12]      # z-1, y+1, x-2 voxels
+    pb_s = oracle_problem(cfg, theta=th, coef=np.zeros((8, 8, 8, 3)), s_view=np.ones(cfg.n_views))
+    c, _ = oracle.forward(pb_s, shifted)
+    assert np.allclose(a, c, rtol=0, atol=1e-12 * a.max())
+
+
+def test_p7_rotation_and_affine_conventions(motion_case):
+    cfg, vol = motion_case
+    zero = np.zeros((8, 8, 8, 3))
+    # omega = (0, 0, pi/2): sampling mu(R x) equals sampling a rotated copy
+    th = inputs.identity_theta(cfg.n_views)
+    th[:, 2] = math.pi / 2
+    a, _ = oracle.forward(oracle_problem(cfg, theta=th, coef=zero, s_view=np.zeros(cfg.n_views)), vol)
+    # R (x, y) = (-y, x): new[z, iy, ix] = old at (-y, x) = old[z, ix, N-1-iy]
+    vol_r = np.ascontiguousarray(vol[:, :, ::-1].transpose(0, 2, 1))
+    pb_s = oracle_problem(cfg, theta=inputs.identity_theta(cfg.n_views), coef=zero,
+                          s_view=np.zeros(cfg.n_views))
+    b, _ = oracle.forward(pb_s, vol_r)
+    assert np.allclose(a, b, rtol=0, atol=1e-11 * a.max())
+    # A = permutation swapping x and y: mu(A x) = transposed volume
+    th2 = inputs.identity_theta(cfg.n_views)
+    th2[:, 6:15] = np.array([[0, 1, 0], [1, 0, 0], [0, 0, 1]], float).reshape(9)
+    c, _ = oracle.forward(oracle_problem(cfg, theta=th2, coef=zero, s_view=np.zeros(cfg.n_views)), vol)
+    d, _ = oracle.forward(pb_s, np.ascontiguousarray(vol.transpose(0, 2, 1)))
+    assert np.allclose(c, d, rtol=0, atol=1e-12 * c.max())
+
+
+def test_p7_repeated_subangles_equal_single():
+    cfg = small(n=16, nu=20, nv=20, n_views=3)
+    P1 = inputs.projection_matrices(cfg)
+    P3 = np.repeat(P1, 3, axis=1)
+    rng = np.random.default_rng(12)
+    vol = rng.uniform(size=cfg.vol_shape)
+    a, ra = oracle.forward(oracle_problem(cfg, P=P1), vol)
+    b, rb = oracle.forward(oracle_problem(cfg.scaled(n_sub=3), P=P3), vol)
+    assert np.allclose(a, b, rtol=1e-14) and np.allclose(ra, rb, rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# P8: backprojector special cases (Sec. 4.1, Sec. 4.3.2)
+# ---------------------------------------------------------------------------
+
+def _projected_points(cfg, view, X):
+    """Detector coordinates of points X [..., 3] by line/plane intersection,
+    from the trajectory definition (no projection matrix)."""
+    srcs, ctrs, us, vs = inputs.detector_frames(cfg)
+    s, c, u, v = srcs[view, 0], ctrs[view, 0], us[view, 0], vs[view, 0]
+    d0 = c - 0.5 * (cfg.nu - 1) * u - 0.5 * (cfg.nv - 1) * v
+    nrm = np.cross(u, v)
+    t = ((d0 - s) @ nrm) / ((X - s) @ nrm)
+    hit = s + t[..., None] * (X - s)
+    rel = hit - d0
+    G = np.array([[u @ u, u @ v], [u @ v, v @ v]])
+    coords = np.linalg.solve(G, np.stack([rel @ u, rel @ v], axis=-1)[..., None])[..., 0]
+    return coords[..., 0], coords[..., 1]
+
+
+def test_p8_interior_colsum_and_affine_images():
+    cfg = small(n=16, nu=40, nv=40, n_views=5, trajectory="perturbed", seed=13)
+    pb = oracle_problem(cfg)
+    n = cfg.n
+    idx = np.arange(n)
+    Z, Y, X = np.meshgrid(idx, idx, idx, indexing="ij")
+    pts = np.stack([cfg.origin[0] + X * cfg.vox, cfg.origin[1] + Y * cfg.vox,
+                    cfg.origin[2] + Z * cfg.vox], axis=-1)
+    rng = np.random.default_rng(13)
+    coef = rng.normal(size=(cfg.n_views, 3))
+    iu = np.arange(cfg.nu)[None, :]
+    iv = np.arange(cfg.nv)[:, None]
+    r = np.stack([coef[k, 0] + coef[k, 1] * iu + coef[k, 2] * iv for k in range(cfg.n_views)])
+    _, b, c = oracle.backproject(pb, r)
+    expect = np.zeros(cfg.vol_shape)
+    interior = np.ones(cfg.vol_shape, bool)
+    for k in range(cfg.n_views):
+        u, v = _projected_points(cfg, k, pts)
+        expect += coef[k, 0] + coef[k, 1] * u + coef[k, 2] * v
+        interior &= (u >= 0) & (u <= cfg.nu - 1) & (v >= 0) & (v <= cfg.nv - 1)
+    assert interior.sum() > 1000
+    # bilinear interpolation reproduces affine images exactly
+    assert np.allclose(b[interior], expect[interior], rtol=0, atol=1e-9)
+    # interior voxels: column sum = number of views exactly
+    assert np.allclose(c[interior], cfg.n_views, rtol=0, atol=1e-12)
+
+
+def test_p8_weights_special_cases():
+    cfg = small(n=16, nu=24, nv=24, n_views=4)
+    pb = oracle_problem(cfg)
+    rng = np.random.default_rng(14)
+    r = rng.normal(size=(cfg.n_views, cfg.nv, cfg.nu))
+    x0 = rng.uniform(size=cfg.vol_shape)
+    xa, _, _ = oracle.backproject(pb, r, x=x0)
+    xb, _, _ = oracle.backproject(pb, r, x=x0, w=np.ones(cfg.vol_shape))
+    xc, _, _ = oracle.backproject(pb, r, x=x0, w=np.zeros(cfg.vol_shape))
+    assert np.array_equal(xa, xb)
+    assert np.array_equal(xc, x0)
+    w = rng.uniform(size=cfg.vol_shape)
+    xd, _, _ = oracle.backproject(pb, r, x=x0, w=w, alpha=0.5)
+    assert np.allclose(xd - x0, 0.5 * w * (xa - x0), atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# P9: finite differences of the motion-aware forward (FP64)
+# ---------------------------------------------------------------------------
+
+def test_p9_motion_gradient_finite_differences():
+    cfg = inputs.MOTION_FD_32.scaled(nu=24, nv=24, n_views=6)
+    th, co, sv = inputs.motion_params(cfg)
+    vol = inputs.phantom(cfg).numpy()
+    pb = oracle_problem(cfg, theta=th, coef=co, s_view=sv)
+    rng = np.random.default_rng(15)
+    g = rng.normal(size=(cfg.n_views, cfg.nv, cfg.nu))
+    gt, gc = oracle.motion_grad(pb, vol, g)
+    h = 1e-6
+
+    def loss(theta=th, coef=co, views=None):
+        p = oracle_problem(cfg, theta=theta, coef=coef, s_view=sv)
+        proj, _ = oracle.forward(p, vol, views=views)
+        gg = g if views is None else g[views]
+        return float((proj * gg).sum())
+
+    fd_t, an_t = [], []
+    for view in (1, 4):
+        for q in range(15):
+            tp, tm = th.copy(), th.copy()
+            tp[view, q] += h
+            tm[view, q] -= h
+            fd_t.append((loss(theta=tp, views=[view]) - loss(theta=tm, views=[view])) / (2 * h))
+            an_t.append(gt[view, q])
+    assert rel_l2(an_t, fd_t) <= 1e-5
+    fd_c, an_c = [], []
+    for (k, j, i, comp) in [(3, 3, 3, 0), (4, 3, 5, 1), (2, 5, 4, 2), (5, 4, 2, 0)]:
+        cp, cm = co.copy(), co.copy()
+        cp[k, j, i, comp] += h
+        cm[k, j, i, comp] -= h
+        fd_c.append((loss(coef=cp) - loss(coef=cm)) / (2 * h))
+        an_c.append(gc[k, j, i, comp])
+    assert rel_l2(an_c, fd_c) <= 1e-5
+    # volume gradient of <g, A x> is A^T g: finite differences along a random direction
+    dx = rng.normal(size=cfg.vol_shape)
+    ATg = oracle.adjoint(pb, g)
+    fd = (float((oracle.forward(pb, vol + dx)[0] * g).sum()) -
+          float((oracle.forward(pb, vol - dx)[0] * g).sum())) / 2.0
+    assert fd == pytest.approx(float((ATg * dx).sum()), rel=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Geometry reading R1: rejection of degenerate matrices
+# ---------------------------------------------------------------------------
+
+def test_geometry_rejects_singular_and_zero_depth():
+    cfg = small(n=8, nu=8, nv=8, n_views=1)
+    P = inputs.projection_matrices(cfg)
+    bad = P.copy()
+    bad[0, 0, :, 0] = 0.0  # singular left block
+    with pytest.raises(ValueError):
+        oracle.setup_views(oracle_problem(cfg, P=bad))
+    bad2 = P.copy()
+    bad2[0, 0, 2, :] = 0.0
+    bad2[0, 0, 2, 0] = 1.0  # depth = x, zero at the volume centre
+    with pytest.raises(ValueError):
+        oracle.setup_views(oracle_problem(cfg, P=bad2))
+    Pn, src, _ = oracle.setup_views(oracle_problem(cfg, P=-P))
+    assert np.allclose(src[0, 0], [-inputs.SOD, 0, 0])
+    assert np.allclose(Pn, P)
