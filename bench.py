@@ -1,0 +1,335 @@
+"""Benchmark: one SIRT iteration (fused forward projection + correction, then
+voxel-driven weighted backprojection with normalisation and update) of the
+perturbed circular cone-beam workload: 512^3 volume, 768 x 768 detector,
+720 views, FP32 storage (``--dtype bf16`` for BF16 storage).
+
+Metric: GUPS = (ray samples + voxel-view updates) per second / 1e9, whole job
+(sum over ranks / max time over ranks).  Inputs (volume 0.5 GiB, projections
+1.7 GB, correction images 1.7 GB) are larger than L2, so no flush is needed
+between steps.  ``--impl reference`` times the FP64 CPU oracle (the only
+reference this method has) on a bounded sample of the same workload.
+
+Prints ONE JSON line on rank 0.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GUPS (ray samples + voxel updates/s) & SIRT iters/s at 512³; time to residual 1e-3"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="64^3 workload (quick check)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+
+def oracle_sample_run(cfg, P, vol_np, n_fwd_views=2, bp_edge=32, bp_views=90):
+    """Time the oracle: forward of n_fwd_views complete views + backprojection
+    of the central bp_edge^3 sub-volume over bp_views views.  Returns
+    (units, seconds, description)."""
+    import numpy as np
+
+    import oracle
+
+    pb = oracle.Problem(P, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin, (cfg.nu, cfg.nv), cfg.step_vox)
+    fwd_views = np.linspace(0, cfg.n_views - 1, n_fwd_views).astype(np.int32)
+    bp_sel = np.linspace(0, cfg.n_views - 1, bp_views).astype(np.int32)
+    n_samples = oracle.count_samples(pb, fwd_views) * 1  # counted outside the timed region
+    lo = cfg.n // 2 - bp_edge // 2
+    idx = np.arange(lo, lo + bp_edge)
+    zz, yy, xx = np.meshgrid(idx, idx, idx, indexing="ij")
+    vox_flat = ((zz * cfg.n + yy) * cfg.n + xx).ravel().astype(np.int64)
+    r = np.ones((bp_views, cfg.nv, cfg.nu))
+    t0 = time.perf_counter()
+    oracle.forward(pb, vol_np, views=fwd_views)
+    oracle.backproject_voxels(pb, r, vox_flat, views=bp_sel)
+    dt = time.perf_counter() - t0
+    units = n_samples + len(vox_flat) * bp_views * cfg.n_sub
+    desc = (f"oracle FP64: forward of {n_fwd_views} complete views ({n_samples} samples) + backprojection of the "
+            f"central {bp_edge}^3 sub-volume over {bp_views} views ({len(vox_flat) * bp_views} updates)")
+    return units, dt, desc
+
+
+def omp_threads():
+    try:
+        return int(os.environ.get("OMP_NUM_THREADS", "")) or os.cpu_count()
+    except ValueError:
+        return os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+
+def build_workload(cfg, device, dtype):
+    import torch
+
+    from paper_2609_30166_gb300 import ctrex, inputs
+
+    P = inputs.projection_matrices(cfg)
+    ctx = ctrex.context_for(cfg, P=P, device=device)
+    phantom = inputs.phantom(cfg, device=str(device)).to(torch.float32).contiguous()
+    p32 = ctx.fwd_project(phantom)  # inverse-crime measured data
+    torch.cuda.synchronize(device)
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    p = p32.to(tdt).contiguous()
+    del p32
+    return ctx, P, phantom, p, tdt
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2609_30166_gb300 import inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    cfg = inputs.CIRCULAR_64 if args.small else inputs.PERTURBED_512
+    ctx, P, phantom, p, tdt = build_workload(cfg, device, args.dtype)
+    n_samples = ctx.count_samples()
+    n_updates = cfg.n ** 3 * cfg.n_views * cfg.n_sub
+    units = n_samples + n_updates
+
+    x = torch.zeros(cfg.vol_shape, dtype=tdt, device=device)
+    r = torch.empty_like(p)
+    sums = torch.zeros(2, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        ctx.fwd_correct(x, p, r=r, sums=sums)
+        if ev is not None:
+            ev[1].record(stream)
+        ctx.back_project(r, vol=x, alpha=1.0, normalize=True, accumulate=True)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(device)
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    bp_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    res = float((sums[0] / sums[1]).sqrt())
+    if world > 1:
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sec = ms / 1e3
+    value = units * args.steps * world / sec / 1e9
+
+    # end to end through the host-buffer C ABI entry point
+    e2e = None
+    if args.e2e_steps > 0:
+        xh = torch.zeros(cfg.vol_shape, dtype=tdt).pin_memory()
+        ph = p.cpu().pin_memory()
+        ctx.sirt_host(xh, ph, 1)  # warm-up (allocates the context's host-path buffers)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.sirt_host(xh, ph, 1)
+        e2e_s = time.perf_counter() - t0
+        elt = 2 if tdt == torch.bfloat16 else 4
+        e2e = {"value": units * args.e2e_steps * world / e2e_s / 1e9, "unit": "GUPS",
+               "h2d_bytes_per_step": int(xh.numel() * elt + ph.numel() * elt),
+               "d2h_bytes_per_step": int(xh.numel() * elt + 16)}
+        del ph, xh
+
+    elt = 2 if tdt == torch.bfloat16 else 4
+    fwd_avg = statistics.mean(fwd_ms) / 1e3
+    alg_bytes = n_samples * 8 * elt
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / fwd_avg / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": "GUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.dtype == "f32" else "bf16",
+        "data": "synthetic (seeded ellipsoid + Gaussian-blob phantom, projections simulated by the projector)",
+        "config": {"workload": cfg.name, "volume": list(cfg.vol_shape), "detector": [cfg.nv, cfg.nu],
+                   "views": cfg.n_views, "sub_angles": cfg.n_sub, "step_vox": cfg.step_vox,
+                   "storage": args.dtype, "accumulation": "f32",
+                   "l2": "inputs larger than L2 (volume, projections and correction images > 129 MB); no flush",
+                   "parallelism": f"replicas x{world}", "samples_per_step": n_samples,
+                   "updates_per_step": n_updates},
+        "sirt_iters_per_s": args.steps * world / sec,
+        "kernel_ms": {"fwd_correct": statistics.mean(fwd_ms), "back_project": statistics.mean(bp_ms)},
+        "residual_after": res,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "fwd_kernel (fused forward + correction)",
+                     "note": f"algorithmic gather bytes = 8 taps x {elt} B per sample; peak = HBM copy "
+                             f"bandwidth ({peak_kind}); the gather is served mostly from L1/L2"},
+        "gpu_launches": 3 * args.steps,
+        "e2e": e2e,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        vol_np = phantom.double().cpu().numpy()
+        ncpu_units, ncpu_s, desc = oracle_sample_run(cfg, P, vol_np, n_fwd_views=1 if not args.small else 8,
+                                                     bp_edge=32 if not args.small else 16,
+                                                     bp_views=45 if not args.small else 90)
+        out["cpu_baseline"] = {"value": ncpu_units / ncpu_s / 1e9, "unit": "GUPS", "cores": omp_threads(),
+                               "kind": "oracle", "sample": desc}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores, on bounded samples of the workload."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    from paper_2609_30166_gb300 import inputs
+
+    cfg = inputs.CIRCULAR_64 if args.small else inputs.PERTURBED_512
+    P = inputs.projection_matrices(cfg)
+    vol_np = inputs.phantom(cfg).numpy() if args.small else inputs.phantom(cfg, sub=1).numpy()
+    kw = dict(n_fwd_views=1, bp_edge=16, bp_views=45) if not args.small else dict(n_fwd_views=4, bp_edge=16,
+                                                                                   bp_views=90)
+    for _ in range(args.warmup):
+        oracle_sample_run(cfg, P, vol_np, **dict(kw, n_fwd_views=1, bp_edge=8, bp_views=4))
+    units_total, secs, desc = 0, 0.0, ""
+    for _ in range(args.steps):
+        u, s, desc = oracle_sample_run(cfg, P, vol_np, **kw)
+        units_total += u
+        secs += s
+    value = units_total / secs / 1e9
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": cfg.name, "volume": list(cfg.vol_shape),
+                                        "detector": [cfg.nv, cfg.nu], "views": cfg.n_views},
+        "cpu_baseline": {"value": value, "unit": "GUPS", "cores": omp_threads(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "GUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    _ = np
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,244 @@
+/*
+ * ctrex.h -- C ABI of the GB300 (sm_103a) CTrex projection library.
+ *
+ * The library implements the projection-correction-backprojection loop of
+ * ordered-subset SIRT, Eq. (1) of the CTrex paper (arxiv 2609.30166):
+ *
+ *     mu_{k+1} = mu_k + alpha C A^T R (p - A mu_k)
+ *
+ * with A the ray-driven cone-beam projector (Sec. 4.1 "Projection operator"),
+ * R the detector-space correction (Sec. 4.1 "Correction kernel") and C A^T the
+ * voxel-driven, voxel-weighted backprojector (Sec. 4.1 "Backprojection
+ * operator", Sec. 4.3.2).  Geometry is one 3x4 projection matrix per view and
+ * angular sub-sample (Sec. 2.2.1, Sec. 3.4); motion is a per-view rigid+affine
+ * pose plus a smooth deformation applied during ray traversal (Sec. 2.2.2,
+ * Sec. 3.1.1, Sec. 4.2.1).
+ *
+ * Conventions
+ *   volume   vol[nz][ny][nx], x fastest; voxel (ix,iy,iz) centred at
+ *            origin + (ix,iy,iz) * vox (mm).
+ *   images   proj[k][nv][nu], u fastest; k indexes the views of the call's
+ *            view list (all views in order when the list is NULL).  Pixel
+ *            (iu,iv) is centred at detector coordinate (iu,iv).
+ *   P        double P[n_views][n_sub][3][4], row-major; maps homogeneous
+ *            world mm to homogeneous detector coordinates.  P and kappa*P
+ *            (kappa != 0) describe the same projection.
+ *   dtypes   CTREX_F32 or CTREX_BF16 storage; every sum is accumulated in FP32.
+ *
+ * Ownership and execution
+ *   Every data pointer (volumes, images, weights, gradients, view lists) is a
+ *   DEVICE pointer owned by the caller, unless a comment says host.  The
+ *   context owns copies of the geometry and motion parameters and its own
+ *   scratch buffers.  Calls enqueue work on the context's stream and return
+ *   without synchronising, except where stated (sirt_iterate reads one
+ *   residual per iteration; the *_host entry points copy their results back).
+ *   A context must not be used from two host threads at once.
+ *
+ * Errors
+ *   Every call returns CTREX_OK (0) or a negative CTREX_E_* code; the message
+ *   of the last failure is in ctrex_last_error(ctx).  No C++ exception crosses
+ *   this interface.  A call that fails argument validation enqueues no work.
+ */
+#ifndef CTREX_H
+#define CTREX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ctrex_ctx ctrex_ctx;
+
+typedef enum { CTREX_F32 = 0, CTREX_BF16 = 1 } ctrex_dtype;
+
+enum {
+    CTREX_OK = 0,
+    CTREX_E_ARG = -1,          /* NULL pointer, bad enum, bad scalar         */
+    CTREX_E_SHAPE = -2,        /* size out of range, view index out of range */
+    CTREX_E_DTYPE = -3,        /* dtype not supported for this operation     */
+    CTREX_E_GEOMETRY = -4,     /* singular P, or depth <= 0 at volume centre */
+    CTREX_E_CUDA = -5,         /* CUDA runtime error (message in last_error) */
+    CTREX_E_DIVERGED = -6,     /* non-finite residual in sirt_iterate        */
+    CTREX_E_DEVICE_CHECK = -7, /* a kernel's own bounds check fired          */
+    CTREX_E_NOMEM = -8,        /* device allocation failed                   */
+    CTREX_E_STATE = -9         /* call needs set_geometry / set_motion first */
+};
+
+/* Volume grid: sizes, voxel pitch (mm) and centre of voxel (0,0,0) (mm). */
+typedef struct {
+    int nx, ny, nz;
+    double vox[3];
+    double origin[3];
+} ctrex_vol_grid;
+
+/* Detector grid: nu columns (u fastest), nv rows. */
+typedef struct {
+    int nu, nv;
+} ctrex_det_grid;
+
+/* Library version string (static storage). */
+const char *ctrex_version(void);
+
+/*
+ * Create a context on CUDA device `device` that enqueues work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * *out receives the context; destroy it with ctrex_destroy.
+ */
+int ctrex_create(ctrex_ctx **out, int device, void *cuda_stream);
+
+/* Free the context and every buffer it owns (synchronises its stream). */
+int ctrex_destroy(ctrex_ctx *ctx);
+
+/* Change the stream later calls enqueue on. */
+int ctrex_set_stream(ctrex_ctx *ctx, void *cuda_stream);
+
+/* Message of the last failed call on ctx (static text if ctx is NULL). */
+const char *ctrex_last_error(const ctrex_ctx *ctx);
+
+/*
+ * Synchronise the context's stream and report whether a kernel's own bounds
+ * check fired since the last call (a view index outside [0, n_views) in a
+ * view list): CTREX_E_DEVICE_CHECK, and the flag is cleared; else CTREX_OK.
+ * Kernels never trap: an out-of-range view is skipped (its output is zero).
+ */
+int ctrex_device_status(ctrex_ctx *ctx);
+
+/*
+ * Sec. 2.2.1 single-projection geometry, Sec. 2.2.2 trajectory as a sequence
+ * of matrices, Sec. 3.4 angular sub-projections.
+ *   P         HOST double [n_views][n_sub][3][4]; copied, may be freed after.
+ *   n_views   >= 1; n_sub >= 1 sub-angle matrices per view (motion blur:
+ *             a pixel is the mean of its n_sub sub-projections).
+ *   vol, det  grids (HOST structs); sizes >= 1, pitches > 0.
+ *   step_vox  ray step as a fraction of the smallest voxel pitch, in [0.01, 100].
+ * Each P is sign-normalised so that the volume centre has positive depth.
+ * Fails with CTREX_E_GEOMETRY if a left 3x3 block is singular
+ * (|det| <= 1e-12 |M|_F^3) or the volume centre lies on a source plane.
+ * Clears any motion set earlier.
+ */
+int ctrex_set_geometry(ctrex_ctx *ctx, const double *P, int n_views, int n_sub,
+                       const ctrex_vol_grid *vol, const ctrex_det_grid *det, double step_vox);
+
+/*
+ * Sec. 2.2.2 affine volume pose (rigid then affine) and Sec. 3.1.1 / 4.2.1
+ * sample-point warping.  Sample point x (mm, volume frame) of view v is
+ * mapped to y = x' + s_v u(x'), x' = A_v (R(omega_v) x + t_v), before the
+ * volume lookup; u is a uniform cubic B-spline on an 8^3 control grid whose
+ * points i = 0..7 sit at box_min + (i - 1) * box_len / 5 per axis (spline
+ * coordinate clamped to [1, 6]).
+ *   theta   DEVICE float [n_views][15] = (omega(3) Rodrigues, t(3) mm,
+ *           A(9) row-major), or NULL for no pose change.
+ *   coef    DEVICE float [8][8][8][3] (z, y, x, component; mm), or NULL.
+ *   s_view  DEVICE float [n_views] time scale of the deformation, or NULL
+ *           (then s_v = 0).
+ *   margin  mm in [0, largest box edge]; the ray clip box is the volume box
+ *           dilated by this much (fixed, so sample positions do not depend
+ *           on theta).
+ * The arrays are copied (device to device, on the stream).  Passing all
+ * three as NULL switches motion off.
+ */
+int ctrex_set_motion(ctrex_ctx *ctx, const float *theta, const float *coef, const float *s_view,
+                     double margin_mm);
+
+/*
+ * A x (Sec. 4.1 projection operator; Sec. 3.4 mean over sub-angles; motion
+ * if set).  Ray from the source through the pixel centre, clipped to the
+ * box, fixed-step truncated-midpoint quadrature with trilinear interpolation
+ * (zero outside the grid), weights = segment lengths in mm.
+ *   vol      DEVICE [nz][ny][nx] of vol_dtype.
+ *   proj     DEVICE [n_idx][nv][nu] of proj_dtype (overwritten).
+ *   view_idx DEVICE int32 [n_idx] (each in [0, n_views)), or NULL = all.
+ *   rowsum   DEVICE float [n_idx][nv][nu] receiving A 1, or NULL.
+ */
+int ctrex_fwd_project(ctrex_ctx *ctx, const void *vol, int vol_dtype, void *proj, int proj_dtype,
+                      float *rowsum, const int *view_idx, int n_idx);
+
+/*
+ * Fused A x and correction (Eq. (1) terms 1 and 2, Sec. 4.1 correction
+ * kernel): r_i = R_i (p_i - (A x)_i) with R_i = 1 / (A 1)_i if that row sum
+ * exceeds 1e-6 * (smallest voxel pitch), else 0.  A x is never stored.
+ *   p        DEVICE measured images [n_idx][nv][nu] of p_dtype.
+ *   r        DEVICE output [n_idx][nv][nu] of r_dtype (may alias nothing).
+ *   sums     DEVICE double [2] receiving (sum (p - Ax)^2, sum p^2) over all
+ *            pixels of the listed views (fixed-order reduction: bitwise
+ *            reproducible), or NULL.
+ */
+int ctrex_fwd_correct(ctrex_ctx *ctx, const void *vol, int vol_dtype, const void *p, int p_dtype,
+                      void *r, int r_dtype, double *sums, const int *view_idx, int n_idx);
+
+/*
+ * Voxel-driven backprojection with normalisation and update (Eq. (1) term
+ * 3, Sec. 4.1 backprojection operator, Sec. 4.3.2 weighted BP).  For voxel j,
+ * b_j = sum over listed views of (1/n_sub) sum over sub-angles of the
+ * bilinear sample of r at the projected voxel centre (zero outside the
+ * detector, skipped where the depth is <= 0), c_j = the same sum with r = 1.
+ *   out_j = (accumulate ? vol_j : 0) + alpha * w_j * (normalize ? C_j : 1) * b_j
+ * with C_j = 1 / c_j if c_j > 1e-6 else 0.
+ *   r        DEVICE [n_idx][nv][nu] of r_dtype.
+ *   vol      DEVICE [nz][ny][nx] of vol_dtype, read (if accumulate) and written.
+ *   w        DEVICE float [nz][ny][nx] voxel weights, or NULL (= 1).
+ */
+int ctrex_back_project(ctrex_ctx *ctx, const void *r, int r_dtype, void *vol, int vol_dtype,
+                       const float *w, float alpha, int normalize, int accumulate,
+                       const int *view_idx, int n_idx);
+
+/*
+ * Matched adjoint of ctrex_fwd_project (exact transpose, motion included):
+ * vol += A^T proj, scattered with FP32 atomics (summation order is not
+ * reproducible bit for bit).  The paper has no such operator; it is the
+ * transpose of its Sec. 4.1 projector, used for gradients.
+ *   proj     DEVICE float [n_idx][nv][nu];  vol  DEVICE float [nz][ny][nx].
+ */
+int ctrex_adjoint_project(ctrex_ctx *ctx, const float *proj, float *vol, const int *view_idx,
+                          int n_idx);
+
+/*
+ * Gradient of L = sum_i g_i (A x)_i with respect to the motion parameters
+ * set by ctrex_set_motion (chain rule through the warp; the deformation is
+ * recomputed, never stored).  Requires motion to be set.
+ *   grad_proj   DEVICE float [n_idx][nv][nu] (= g).
+ *   grad_theta  DEVICE float [n_views][15], accumulated (+=), or NULL.
+ *   grad_coef   DEVICE float [8][8][8][3], accumulated (+=), or NULL.
+ */
+int ctrex_motion_grad(ctrex_ctx *ctx, const void *vol, int vol_dtype, const float *grad_proj,
+                      float *grad_theta, float *grad_coef, const int *view_idx, int n_idx);
+
+/*
+ * SIRT (Eq. (1) with one subset holding every view, Sec. 2.3.2).  Iteration
+ * k: fused A x_k / correction, rho_k = ||p - A x_k|| / ||p|| (one 16-byte
+ * device-to-host read); stop if rho_k <= tol; else backproject with
+ * normalisation and update x.  At most max_iter updates.
+ *   vol                 DEVICE x_0 in, result out.
+ *   p                   DEVICE [n_views][nv][nu] measured images.
+ *   w                   DEVICE float voxel weights or NULL.
+ *   residual_history    HOST float [max_iter] (entries past the stop are
+ *                       left untouched), or NULL.
+ *   iters_done          HOST, number of updates applied (may be NULL).
+ * Returns CTREX_E_DIVERGED if a residual is not finite.
+ */
+int ctrex_sirt_iterate(ctrex_ctx *ctx, void *vol, int vol_dtype, const void *p, int p_dtype,
+                       int max_iter, float alpha, const float *w, float tol,
+                       float *residual_history, int *iters_done);
+
+/*
+ * Same as ctrex_sirt_iterate with HOST buffers: copies vol (x_0) and p to
+ * device buffers owned by the context, iterates, and copies the volume back
+ * into vol.  vol_dtype / p_dtype describe the host arrays.  Synchronous.
+ */
+int ctrex_sirt_host(ctrex_ctx *ctx, void *vol_host, int vol_dtype, const void *p_host, int p_dtype,
+                    int max_iter, float alpha, const float *w_host, float tol,
+                    float *residual_history, int *iters_done);
+
+/*
+ * Exact number of ray samples (segments) of the listed views, summed over
+ * all pixels and sub-angles, as the projector kernels count them; result in
+ * HOST *out.  Synchronous.
+ */
+int ctrex_count_samples(ctrex_ctx *ctx, const int *view_idx, int n_idx, long long *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTREX_H */

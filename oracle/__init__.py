@@ -26,6 +26,8 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
+import struct
 import subprocess
 import threading
 
@@ -40,9 +42,20 @@ _lib = None
 EPS_C = 1e-6
 
 
+def _native(path):
+    machine = {"x86_64": 62, "aarch64": 183, "arm64": 183}.get(platform.machine())
+    try:
+        with open(path, "rb") as f:
+            head = f.read(20)
+        return head[:4] == b"\x7fELF" and struct.unpack("<H", head[18:20])[0] == machine
+    except OSError:
+        return False
+
+
 def build(force: bool = False) -> str:
     """Compile ctrex_oracle.c into liboracle.so (gcc, OpenMP, IEEE FP64)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if (force or not os.path.exists(_LIB) or not _native(_LIB)
+            or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)):
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC", "-std=c11",
                "-o", tmp, _SRC, "-lm"]

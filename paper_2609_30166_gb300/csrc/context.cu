@@ -1,0 +1,614 @@
+// context.cu -- the C ABI of libctrex: context, geometry and motion set-up,
+// operator entry points and the SIRT driver (the paper's Rex / Trajectory
+// split, Sec. 2.1-2.3, as a native library).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ctrex_internal.cuh"
+
+using namespace ctrex;
+
+struct ctrex_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // geometry
+    bool has_geom = false;
+    Grid grid{};
+    double vox[3] = {1, 1, 1}, origin[3] = {0, 0, 0};
+    double step_vox = 0.5;
+    ViewGPU *d_views = nullptr;
+    // motion
+    bool has_motion = false;
+    double margin = 0.0;
+    MotionGPU *d_motion = nullptr;
+    float *d_theta = nullptr;     // [n_views][15] copy (or null)
+    float *d_coef = nullptr;      // [8][8][8][3] mm
+    float *d_coef_idx = nullptr;  // [8][8][8][3] voxels
+    float *d_dRdw = nullptr;      // [n_views][27]
+    float *d_gM = nullptr, *d_gb = nullptr, *d_gcoef = nullptr;  // gradient scratch
+    bool coef_valid = false, theta_valid = false;
+    // scratch
+    float *d_partials = nullptr;
+    int partials_cap = 0;
+    double *d_sums = nullptr;
+    unsigned *d_devcheck = nullptr;
+    unsigned long long *d_count = nullptr;
+    void *d_r = nullptr;  // SIRT correction images
+    size_t r_bytes = 0;
+    // host-buffer entry point scratch
+    void *d_hvol = nullptr, *d_hp = nullptr;
+    float *d_hw = nullptr;
+    size_t hvol_bytes = 0, hp_bytes = 0, hw_bytes = 0;
+};
+
+namespace {
+
+const char *g_static_err = "ctrex: invalid context";
+
+int fail(ctrex_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+int cuda_fail(ctrex_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? CTREX_E_NOMEM : CTREX_E_CUDA, "%s: %s (%s)", where,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define CT_CUDA(c, call)                                  \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename T> void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+int ensure(ctrex_ctx *c, void **p, size_t *have, size_t need, const char *what)
+{
+    if (*have >= need && *p) return CTREX_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc(p, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, CTREX_E_NOMEM, "cannot allocate %zu bytes for %s: %s", need, what, cudaGetErrorString(e));
+    }
+    *have = need;
+    return CTREX_OK;
+}
+
+size_t dtype_size(int dt) { return dt == CTREX_BF16 ? 2 : 4; }
+bool dtype_ok(int dt) { return dt == CTREX_F32 || dt == CTREX_BF16; }
+
+int check_ctx(ctrex_ctx *c)
+{
+    if (!c) return CTREX_E_ARG;
+    return CTREX_OK;
+}
+
+int check_views(ctrex_ctx *c, const int *view_idx, int n_idx)
+{
+    if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_geometry has not been called");
+    if (n_idx < 0 || n_idx > 65535) return fail(c, CTREX_E_SHAPE, "n_idx %d outside [0, 65535]", n_idx);
+    if (!view_idx && n_idx != c->grid.n_views)
+        return fail(c, CTREX_E_SHAPE, "view_idx is NULL but n_idx (%d) != n_views (%d)", n_idx, c->grid.n_views);
+    return CTREX_OK;
+}
+
+FwdArgs fwd_args(ctrex_ctx *c, const void *vol, int vdt, const int *view_idx, int n_idx)
+{
+    FwdArgs a;
+    a.grid = &c->grid;
+    a.views = c->d_views;
+    a.motion = c->has_motion ? c->d_motion : nullptr;
+    a.coef_idx = (c->has_motion && c->coef_valid) ? c->d_coef_idx : nullptr;
+    a.vol = vol;
+    a.vol_dtype = vdt;
+    a.view_idx = view_idx;
+    a.n_idx = n_idx;
+    a.stream = c->stream;
+    a.devcheck = c->d_devcheck;
+    return a;
+}
+
+// 3x3 helpers (FP64, host)
+double det3(const double *m)
+{
+    return m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) + m[2] * (m[3] * m[7] - m[4] * m[6]);
+}
+
+void inv3(const double *m, double *r)
+{
+    const double d = det3(m);
+    r[0] = (m[4] * m[8] - m[5] * m[7]) / d;
+    r[1] = (m[2] * m[7] - m[1] * m[8]) / d;
+    r[2] = (m[1] * m[5] - m[2] * m[4]) / d;
+    r[3] = (m[5] * m[6] - m[3] * m[8]) / d;
+    r[4] = (m[0] * m[8] - m[2] * m[6]) / d;
+    r[5] = (m[2] * m[3] - m[0] * m[5]) / d;
+    r[6] = (m[3] * m[7] - m[4] * m[6]) / d;
+    r[7] = (m[1] * m[6] - m[0] * m[7]) / d;
+    r[8] = (m[0] * m[4] - m[1] * m[3]) / d;
+}
+
+void set_clip_box(ctrex_ctx *c)
+{
+    const int n[3] = {c->grid.nx, c->grid.ny, c->grid.nz};
+    const double m = c->has_motion ? c->margin : 0.0;
+    for (int a = 0; a < 3; ++a) {
+        c->grid.lo[a] = (float)(-0.5 - m / c->vox[a]);
+        c->grid.hi[a] = (float)(n[a] - 0.5 + m / c->vox[a]);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ctrex_version(void) { return "ctrex-gb300 0.1 (sm_103a)"; }
+
+const char *ctrex_last_error(const ctrex_ctx *c) { return c ? c->err.c_str() : g_static_err; }
+
+int ctrex_create(ctrex_ctx **out, int device, void *stream)
+{
+    if (!out) return CTREX_E_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return CTREX_E_CUDA;
+    }
+    ctrex_ctx *c = new (std::nothrow) ctrex_ctx();
+    if (!c) return CTREX_E_NOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    DeviceGuard g(device);
+    if (cudaMalloc((void **)&c->d_sums, 2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_devcheck, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_count, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        ctrex_destroy(c);
+        return CTREX_E_NOMEM;
+    }
+    cudaMemset(c->d_devcheck, 0, sizeof(unsigned));
+    *out = c;
+    return CTREX_OK;
+}
+
+int ctrex_destroy(ctrex_ctx *c)
+{
+    if (!c) return CTREX_E_ARG;
+    {
+        DeviceGuard g(c->device);
+        cudaStreamSynchronize(c->stream);
+        dfree(c->d_views);
+        dfree(c->d_motion);
+        dfree(c->d_theta);
+        dfree(c->d_coef);
+        dfree(c->d_coef_idx);
+        dfree(c->d_dRdw);
+        dfree(c->d_gM);
+        dfree(c->d_gb);
+        dfree(c->d_gcoef);
+        dfree(c->d_partials);
+        dfree(c->d_sums);
+        dfree(c->d_devcheck);
+        dfree(c->d_count);
+        dfree(c->d_r);
+        dfree(c->d_hvol);
+        dfree(c->d_hp);
+        dfree(c->d_hw);
+    }
+    delete c;
+    return CTREX_OK;
+}
+
+int ctrex_set_stream(ctrex_ctx *c, void *stream)
+{
+    if (!c) return CTREX_E_ARG;
+    c->stream = (cudaStream_t)stream;
+    return CTREX_OK;
+}
+
+int ctrex_device_status(ctrex_ctx *c)
+{
+    if (!c) return CTREX_E_ARG;
+    DeviceGuard g(c->device);
+    unsigned h = 0;
+    CT_CUDA(c, cudaMemcpyAsync(&h, c->d_devcheck, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h) {
+        CT_CUDA(c, cudaMemsetAsync(c->d_devcheck, 0, sizeof(unsigned), c->stream));
+        return fail(c, CTREX_E_DEVICE_CHECK, "a kernel bounds check fired (flags 0x%x): view index out of range", h);
+    }
+    return CTREX_OK;
+}
+
+int ctrex_set_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, const ctrex_vol_grid *vol,
+                       const ctrex_det_grid *det, double step_vox)
+{
+    if (!c) return CTREX_E_ARG;
+    if (!P || !vol || !det) return fail(c, CTREX_E_ARG, "set_geometry: NULL argument");
+    if (n_views < 1 || n_sub < 1 || (long long)n_views * n_sub > (1 << 24))
+        return fail(c, CTREX_E_SHAPE, "set_geometry: bad n_views %d / n_sub %d", n_views, n_sub);
+    if (vol->nx < 1 || vol->ny < 1 || vol->nz < 1 || (long long)vol->nx * vol->ny * vol->nz >= (1LL << 31))
+        return fail(c, CTREX_E_SHAPE, "set_geometry: volume %d x %d x %d unsupported", vol->nx, vol->ny, vol->nz);
+    if (det->nu < 1 || det->nv < 1 || det->nv > 4 * 65535 || (long long)det->nu * det->nv >= (1LL << 31))
+        return fail(c, CTREX_E_SHAPE, "set_geometry: detector %d x %d unsupported", det->nu, det->nv);
+    for (int a = 0; a < 3; ++a)
+        if (!(vol->vox[a] > 0.0) || !isfinite(vol->origin[a]))
+            return fail(c, CTREX_E_ARG, "set_geometry: voxel pitch must be > 0 and origin finite");
+    // bounded step keeps every ray's sample count (and kernel run time) bounded
+    if (!(step_vox >= 1e-2 && step_vox <= 100.0))
+        return fail(c, CTREX_E_ARG, "set_geometry: step_vox must lie in [0.01, 100]");
+    DeviceGuard g(c->device);
+    const int nvs = n_views * n_sub;
+    std::vector<ViewGPU> hv((size_t)nvs);
+    const int n[3] = {vol->nx, vol->ny, vol->nz};
+    double ctr[3];
+    for (int a = 0; a < 3; ++a) ctr[a] = vol->origin[a] + 0.5 * (n[a] - 1) * vol->vox[a];
+    const double uc = 0.5 * (det->nu - 1), vc = 0.5 * (det->nv - 1);
+    for (int q = 0; q < nvs; ++q) {
+        const double *Pi = P + 12 * (size_t)q;
+        double M[9], fro = 0.0;
+        for (int k = 0; k < 12; ++k)
+            if (!isfinite(Pi[k])) return fail(c, CTREX_E_GEOMETRY, "view %d sub %d: non-finite matrix", q / n_sub, q % n_sub);
+        for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc) {
+                M[3 * r + cc] = Pi[4 * r + cc];
+                fro += M[3 * r + cc] * M[3 * r + cc];
+            }
+        fro = sqrt(fro);
+        if (!(fabs(det3(M)) > 1e-12 * fro * fro * fro))
+            return fail(c, CTREX_E_GEOMETRY, "view %d sub %d: singular projection matrix", q / n_sub, q % n_sub);
+        const double depth = Pi[8] * ctr[0] + Pi[9] * ctr[1] + Pi[10] * ctr[2] + Pi[11];
+        if (!(depth != 0.0))
+            return fail(c, CTREX_E_GEOMETRY, "view %d sub %d: volume centre on the source plane", q / n_sub, q % n_sub);
+        const double sgn = depth > 0 ? 1.0 : -1.0;
+        double Pn[12];
+        for (int k = 0; k < 12; ++k) Pn[k] = sgn * Pi[k];
+        for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc) M[3 * r + cc] = Pn[4 * r + cc];
+        double Mi[9];
+        inv3(M, Mi);
+        double src[3];
+        for (int r = 0; r < 3; ++r) src[r] = -(Mi[3 * r] * Pn[3] + Mi[3 * r + 1] * Pn[7] + Mi[3 * r + 2] * Pn[11]);
+        const double lam = sgn * depth;  // depth of the volume centre, > 0
+        ViewGPU &V = hv[(size_t)q];
+        for (int a = 0; a < 3; ++a) {
+            const double mc = Mi[3 * a] * uc + Mi[3 * a + 1] * vc + Mi[3 * a + 2];
+            const double dref = lam * mc;  // X(uc,vc) - source, mm
+            V.dref[a] = (float)(dref / vol->vox[a]);
+            V.ref[a] = (float)((src[a] + dref - vol->origin[a]) / vol->vox[a]);
+            V.qu[a] = (float)(lam * Mi[3 * a] / vol->vox[a]);
+            V.qv[a] = (float)(lam * Mi[3 * a + 1] / vol->vox[a]);
+        }
+        // h = Pn [origin + vox * i; 1]
+        for (int r = 0; r < 3; ++r) {
+            double acc = Pn[4 * r + 3];
+            for (int a = 0; a < 3; ++a) {
+                V.P[4 * r + a] = (float)(Pn[4 * r + a] * vol->vox[a]);
+                acc += Pn[4 * r + a] * vol->origin[a];
+            }
+            V.P[4 * r + 3] = (float)acc;
+        }
+    }
+    dfree(c->d_views);
+    // motion buffers are sized by n_views: drop them with the old geometry
+    dfree(c->d_motion);
+    dfree(c->d_dRdw);
+    dfree(c->d_theta);
+    dfree(c->d_coef);
+    dfree(c->d_coef_idx);
+    dfree(c->d_gM);
+    dfree(c->d_gb);
+    dfree(c->d_gcoef);
+    c->coef_valid = c->theta_valid = false;
+    CT_CUDA(c, cudaMalloc((void **)&c->d_views, sizeof(ViewGPU) * (size_t)nvs));
+    CT_CUDA(c, cudaMemcpy(c->d_views, hv.data(), sizeof(ViewGPU) * (size_t)nvs, cudaMemcpyHostToDevice));
+    Grid &G = c->grid;
+    G.nx = vol->nx;
+    G.ny = vol->ny;
+    G.nz = vol->nz;
+    G.nu = det->nu;
+    G.nv = det->nv;
+    G.n_views = n_views;
+    G.n_sub = n_sub;
+    double minv = vol->vox[0];
+    for (int a = 0; a < 3; ++a) {
+        c->vox[a] = vol->vox[a];
+        c->origin[a] = vol->origin[a];
+        G.vox[a] = (float)vol->vox[a];
+        G.spl_scale[a] = (float)(5.0 / n[a]);
+        if (vol->vox[a] < minv) minv = vol->vox[a];
+    }
+    c->step_vox = step_vox;
+    G.step_mm = (float)(step_vox * minv);
+    G.uc = (float)uc;
+    G.vc = (float)vc;
+    G.eps_R = (float)(1e-6 * minv);
+    G.inv_sub = (float)(1.0 / n_sub);
+    c->has_motion = false;
+    c->has_geom = true;
+    set_clip_box(c);
+    return CTREX_OK;
+}
+
+int ctrex_set_motion(ctrex_ctx *c, const float *theta, const float *coef, const float *s_view, double margin_mm)
+{
+    if (!c) return CTREX_E_ARG;
+    if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_motion before set_geometry");
+    double box = 0.0;
+    const int nn[3] = {c->grid.nx, c->grid.ny, c->grid.nz};
+    for (int a = 0; a < 3; ++a) box = fmax(box, nn[a] * c->vox[a]);
+    if (!(margin_mm >= 0.0 && margin_mm <= box))
+        return fail(c, CTREX_E_ARG, "set_motion: margin must lie in [0, largest box edge]");
+    DeviceGuard g(c->device);
+    if (!theta && !coef && !s_view) {
+        c->has_motion = false;
+        set_clip_box(c);
+        return CTREX_OK;
+    }
+    const int V = c->grid.n_views;
+    if (!c->d_motion) {
+        CT_CUDA(c, cudaMalloc((void **)&c->d_motion, sizeof(MotionGPU) * (size_t)V));
+        CT_CUDA(c, cudaMalloc((void **)&c->d_dRdw, sizeof(float) * 27 * (size_t)V));
+        CT_CUDA(c, cudaMalloc((void **)&c->d_theta, sizeof(float) * 15 * (size_t)V));
+        CT_CUDA(c, cudaMalloc((void **)&c->d_coef, sizeof(float) * 1536));
+        CT_CUDA(c, cudaMalloc((void **)&c->d_coef_idx, sizeof(float) * 1536));
+        CT_CUDA(c, cudaMalloc((void **)&c->d_gM, sizeof(float) * 9 * (size_t)V));
+        CT_CUDA(c, cudaMalloc((void **)&c->d_gb, sizeof(float) * 3 * (size_t)V));
+        CT_CUDA(c, cudaMalloc((void **)&c->d_gcoef, sizeof(float) * 1536));
+    }
+    const float *th = nullptr;
+    if (theta) {
+        CT_CUDA(c, cudaMemcpyAsync(c->d_theta, theta, sizeof(float) * 15 * (size_t)V, cudaMemcpyDeviceToDevice, c->stream));
+        th = c->d_theta;
+    }
+    const float *co = nullptr;
+    if (coef) {
+        CT_CUDA(c, cudaMemcpyAsync(c->d_coef, coef, sizeof(float) * 1536, cudaMemcpyDeviceToDevice, c->stream));
+        co = c->d_coef;
+    }
+    const float *sv = nullptr;
+    // s_view is consumed by the set-up kernel straight from the caller's buffer
+    if (s_view) sv = s_view;
+    c->margin = margin_mm;
+    c->has_motion = true;
+    cudaError_t e = launch_motion_setup(th, co, sv, V, c->grid, c->vox, c->origin, c->d_motion, c->d_coef_idx,
+                                        c->d_dRdw, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "motion set-up");
+    c->coef_valid = co != nullptr;
+    c->theta_valid = th != nullptr;
+    set_clip_box(c);
+    return CTREX_OK;
+}
+
+int ctrex_fwd_project(ctrex_ctx *c, const void *vol, int vdt, void *proj, int pdt, float *rowsum,
+                      const int *view_idx, int n_idx)
+{
+    if (!c) return CTREX_E_ARG;
+    int e = check_views(c, view_idx, n_idx);
+    if (e) return e;
+    if (!vol || !proj) return fail(c, CTREX_E_ARG, "fwd_project: NULL buffer");
+    if (!dtype_ok(vdt) || !dtype_ok(pdt)) return fail(c, CTREX_E_DTYPE, "fwd_project: bad dtype");
+    DeviceGuard g(c->device);
+    cudaError_t ce = launch_forward(fwd_args(c, vol, vdt, view_idx, n_idx), proj, pdt, rowsum);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "fwd_project launch");
+    return CTREX_OK;
+}
+
+static int ensure_partials(ctrex_ctx *c, int n_idx)
+{
+    const int need = forward_partials_needed(c->grid, n_idx);
+    if (need <= c->partials_cap) return CTREX_OK;
+    size_t have = (size_t)c->partials_cap * 2 * sizeof(float);
+    int e = ensure(c, (void **)&c->d_partials, &have, (size_t)need * 2 * sizeof(float), "residual partials");
+    if (e) return e;
+    c->partials_cap = need;
+    return CTREX_OK;
+}
+
+int ctrex_fwd_correct(ctrex_ctx *c, const void *vol, int vdt, const void *p, int pdt, void *r, int rdt,
+                      double *sums, const int *view_idx, int n_idx)
+{
+    if (!c) return CTREX_E_ARG;
+    int e = check_views(c, view_idx, n_idx);
+    if (e) return e;
+    if (!vol || !p || !r) return fail(c, CTREX_E_ARG, "fwd_correct: NULL buffer");
+    if (!dtype_ok(vdt) || !dtype_ok(pdt) || !dtype_ok(rdt)) return fail(c, CTREX_E_DTYPE, "fwd_correct: bad dtype");
+    if (pdt != rdt) return fail(c, CTREX_E_DTYPE, "fwd_correct: p and r must share one dtype");
+    DeviceGuard g(c->device);
+    e = ensure_partials(c, n_idx);
+    if (e) return e;
+    cudaError_t ce = launch_forward_correct(fwd_args(c, vol, vdt, view_idx, n_idx), p, pdt, r, rdt, c->d_partials,
+                                            c->partials_cap, sums);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "fwd_correct launch");
+    return CTREX_OK;
+}
+
+int ctrex_back_project(ctrex_ctx *c, const void *r, int rdt, void *vol, int vdt, const float *w, float alpha,
+                       int normalize, int accumulate, const int *view_idx, int n_idx)
+{
+    if (!c) return CTREX_E_ARG;
+    int e = check_views(c, view_idx, n_idx);
+    if (e) return e;
+    if (!r || !vol) return fail(c, CTREX_E_ARG, "back_project: NULL buffer");
+    if (!dtype_ok(vdt) || !dtype_ok(rdt)) return fail(c, CTREX_E_DTYPE, "back_project: bad dtype");
+    if (!isfinite(alpha)) return fail(c, CTREX_E_ARG, "back_project: alpha not finite");
+    DeviceGuard g(c->device);
+    BpArgs a;
+    a.grid = &c->grid;
+    a.views = c->d_views;
+    a.view_idx = view_idx;
+    a.n_idx = n_idx;
+    a.r = r;
+    a.r_dtype = rdt;
+    a.vol = vol;
+    a.vol_dtype = vdt;
+    a.w = w;
+    a.alpha = alpha;
+    a.normalize = normalize ? 1 : 0;
+    a.accumulate = accumulate ? 1 : 0;
+    a.stream = c->stream;
+    cudaError_t ce = launch_backproject(a);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "back_project launch");
+    return CTREX_OK;
+}
+
+int ctrex_adjoint_project(ctrex_ctx *c, const float *proj, float *vol, const int *view_idx, int n_idx)
+{
+    if (!c) return CTREX_E_ARG;
+    int e = check_views(c, view_idx, n_idx);
+    if (e) return e;
+    if (!proj || !vol) return fail(c, CTREX_E_ARG, "adjoint_project: NULL buffer");
+    DeviceGuard g(c->device);
+    cudaError_t ce = launch_adjoint(fwd_args(c, nullptr, CTREX_F32, view_idx, n_idx), proj, vol);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "adjoint_project launch");
+    return CTREX_OK;
+}
+
+int ctrex_motion_grad(ctrex_ctx *c, const void *vol, int vdt, const float *gproj, float *grad_theta,
+                      float *grad_coef, const int *view_idx, int n_idx)
+{
+    if (!c) return CTREX_E_ARG;
+    int e = check_views(c, view_idx, n_idx);
+    if (e) return e;
+    if (!c->has_motion) return fail(c, CTREX_E_STATE, "motion_grad: set_motion has not been called");
+    if (!vol || !gproj) return fail(c, CTREX_E_ARG, "motion_grad: NULL buffer");
+    if (!dtype_ok(vdt)) return fail(c, CTREX_E_DTYPE, "motion_grad: bad dtype");
+    if (grad_theta && !c->theta_valid)
+        return fail(c, CTREX_E_STATE, "motion_grad: grad_theta requested but no theta was set");
+    if (grad_coef && !c->coef_valid)
+        return fail(c, CTREX_E_STATE, "motion_grad: grad_coef requested but no coefficients were set");
+    DeviceGuard g(c->device);
+    const int V = c->grid.n_views;
+    CT_CUDA(c, cudaMemsetAsync(c->d_gM, 0, sizeof(float) * 9 * (size_t)V, c->stream));
+    CT_CUDA(c, cudaMemsetAsync(c->d_gb, 0, sizeof(float) * 3 * (size_t)V, c->stream));
+    CT_CUDA(c, cudaMemsetAsync(c->d_gcoef, 0, sizeof(float) * 1536, c->stream));
+    cudaError_t ce = launch_motion_grad(fwd_args(c, vol, vdt, view_idx, n_idx), gproj, c->d_gM, c->d_gb,
+                                        grad_coef ? c->d_gcoef : nullptr);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "motion_grad launch");
+    ce = launch_motion_grad_finish(c->theta_valid ? c->d_theta : nullptr, c->d_dRdw, c->d_gM, c->d_gb, c->d_gcoef, V,
+                                   c->vox, c->origin, grad_theta, grad_coef, c->stream);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "motion_grad finish");
+    return CTREX_OK;
+}
+
+int ctrex_sirt_iterate(ctrex_ctx *c, void *vol, int vdt, const void *p, int pdt, int max_iter, float alpha,
+                       const float *w, float tol, float *hist, int *iters_done)
+{
+    if (!c) return CTREX_E_ARG;
+    if (iters_done) *iters_done = 0;
+    int e = check_views(c, nullptr, c->has_geom ? c->grid.n_views : 0);
+    if (e) return e;
+    if (!vol || !p) return fail(c, CTREX_E_ARG, "sirt_iterate: NULL buffer");
+    if (!dtype_ok(vdt) || !dtype_ok(pdt)) return fail(c, CTREX_E_DTYPE, "sirt_iterate: bad dtype");
+    if (max_iter < 0) return fail(c, CTREX_E_ARG, "sirt_iterate: max_iter < 0");
+    DeviceGuard g(c->device);
+    const int V = c->grid.n_views;
+    const size_t rb = (size_t)V * c->grid.nu * c->grid.nv * dtype_size(pdt);
+    e = ensure(c, &c->d_r, &c->r_bytes, rb, "SIRT correction images");
+    if (e) return e;
+    e = ensure_partials(c, V);
+    if (e) return e;
+    for (int k = 0; k < max_iter; ++k) {
+        cudaError_t ce = launch_forward_correct(fwd_args(c, vol, vdt, nullptr, V), p, pdt, c->d_r, pdt,
+                                                c->d_partials, c->partials_cap, c->d_sums);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "sirt: fwd_correct");
+        double s[2];
+        CT_CUDA(c, cudaMemcpyAsync(s, c->d_sums, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+        CT_CUDA(c, cudaStreamSynchronize(c->stream));
+        const double rho = s[1] > 0.0 ? sqrt(s[0] / s[1]) : sqrt(s[0]);
+        if (hist) hist[k] = (float)rho;
+        if (!isfinite(rho)) return fail(c, CTREX_E_DIVERGED, "sirt: residual not finite at iteration %d", k);
+        if (rho <= (double)tol) break;
+        int be = ctrex_back_project(c, c->d_r, pdt, vol, vdt, w, alpha, 1, 1, nullptr, V);
+        if (be) return be;
+        if (iters_done) *iters_done = k + 1;
+    }
+    return ctrex_device_status(c);
+}
+
+int ctrex_sirt_host(ctrex_ctx *c, void *vol_h, int vdt, const void *p_h, int pdt, int max_iter, float alpha,
+                    const float *w_h, float tol, float *hist, int *iters_done)
+{
+    if (!c) return CTREX_E_ARG;
+    if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_geometry has not been called");
+    if (!vol_h || !p_h) return fail(c, CTREX_E_ARG, "sirt_host: NULL buffer");
+    if (!dtype_ok(vdt) || !dtype_ok(pdt)) return fail(c, CTREX_E_DTYPE, "sirt_host: bad dtype");
+    DeviceGuard g(c->device);
+    const Grid &G = c->grid;
+    const size_t nvox = (size_t)G.nx * G.ny * G.nz;
+    const size_t vb = nvox * dtype_size(vdt);
+    const size_t pb = (size_t)G.n_views * G.nu * G.nv * dtype_size(pdt);
+    int e = ensure(c, &c->d_hvol, &c->hvol_bytes, vb, "host-SIRT volume");
+    if (e) return e;
+    e = ensure(c, &c->d_hp, &c->hp_bytes, pb, "host-SIRT projections");
+    if (e) return e;
+    const float *dw = nullptr;
+    if (w_h) {
+        e = ensure(c, (void **)&c->d_hw, &c->hw_bytes, nvox * sizeof(float), "host-SIRT weights");
+        if (e) return e;
+        CT_CUDA(c, cudaMemcpyAsync(c->d_hw, w_h, nvox * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        dw = c->d_hw;
+    }
+    CT_CUDA(c, cudaMemcpyAsync(c->d_hvol, vol_h, vb, cudaMemcpyHostToDevice, c->stream));
+    CT_CUDA(c, cudaMemcpyAsync(c->d_hp, p_h, pb, cudaMemcpyHostToDevice, c->stream));
+    e = ctrex_sirt_iterate(c, c->d_hvol, vdt, c->d_hp, pdt, max_iter, alpha, dw, tol, hist, iters_done);
+    if (e) return e;
+    CT_CUDA(c, cudaMemcpyAsync(vol_h, c->d_hvol, vb, cudaMemcpyDeviceToHost, c->stream));
+    CT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CTREX_OK;
+}
+
+int ctrex_count_samples(ctrex_ctx *c, const int *view_idx, int n_idx, long long *out)
+{
+    if (!c) return CTREX_E_ARG;
+    int e = check_views(c, view_idx, n_idx);
+    if (e) return e;
+    if (!out) return fail(c, CTREX_E_ARG, "count_samples: NULL output");
+    DeviceGuard g(c->device);
+    cudaError_t ce = launch_count_samples(fwd_args(c, nullptr, CTREX_F32, view_idx, n_idx), c->d_count);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "count_samples launch");
+    unsigned long long h = 0;
+    CT_CUDA(c, cudaMemcpyAsync(&h, c->d_count, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CT_CUDA(c, cudaStreamSynchronize(c->stream));
+    *out = (long long)h;
+    return CTREX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// ctrex_internal.cuh -- device-side data layout shared by the CUDA kernels of
+// libctrex (sm_103a).  Nothing here is visible through the C ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ctrex.h"
+
+namespace ctrex {
+
+// Per (view, sub-angle) ray parameters, FP32, in voxel-index coordinates
+// (g = (x - origin) / vox).  Derived on the host in FP64 from the
+// sign-normalised projection matrix (Sec. 2.2.1):
+//   ray through detector point (u, v) meets the plane of constant depth
+//   through the volume centre at  X(u,v) = ref + (u-uc) qu + (v-vc) qv,
+//   and X(u,v) - source = dref + (u-uc) qu + (v-vc) qv   (no cancellation),
+// so every sample position is formed relative to a point near the volume,
+// never relative to the distant source.
+//   P: the projection matrix composed with index -> mm, h = P [ix iy iz 1].
+struct ViewGPU {
+    float ref[3];
+    float dref[3];
+    float qu[3];
+    float qv[3];
+    float P[12];
+};
+static_assert(sizeof(ViewGPU) == 96, "ViewGPU layout");
+
+// Per-view motion, voxel-index coordinates: g' = M g + b (pose), then
+// y = g' + s * u(g') with u in voxels (coefficients pre-divided by vox).
+struct MotionGPU {
+    float M[9];
+    float b[3];
+    float s;
+    float pad[3];
+};
+static_assert(sizeof(MotionGPU) == 64, "MotionGPU layout");
+
+struct Grid {
+    int nx, ny, nz;
+    int nu, nv;
+    int n_views, n_sub;
+    float step_mm;       // ray step (mm)
+    float vox[3];        // mm
+    float uc, vc;        // detector centre coordinates
+    float lo[3], hi[3];  // clip box, index coordinates (dilated when motion is on)
+    float eps_R;         // row-sum threshold of the correction (mm)
+    float inv_sub;       // 1 / n_sub
+    float spl_scale[3];  // B-spline coordinate: xi = (g + 1/2) * spl_scale + 1
+};
+
+template <typename T> struct Storage;
+template <> struct Storage<float> {
+    static __device__ __forceinline__ float load(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ void store(float *p, float v) { *p = v; }
+};
+template <> struct Storage<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16 *p)
+    {
+        return __bfloat162float(__ldg(p));
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// Status word written by kernels whose own bounds checks fire (never trap).
+enum : unsigned { DEVCHECK_OOB = 1u };
+
+// ---- host-side launchers (defined in project.cu / backproject.cu / ...) ----
+
+struct FwdArgs {
+    const Grid *grid;           // host copy
+    const ViewGPU *views;       // device [n_views * n_sub]
+    const MotionGPU *motion;    // device [n_views] or nullptr
+    const float *coef_idx;      // device [8][8][8][3] voxels, or nullptr
+    const void *vol;
+    int vol_dtype;
+    const int *view_idx;        // device or nullptr
+    int n_idx;
+    cudaStream_t stream;
+    unsigned *devcheck;         // device status word
+};
+
+cudaError_t launch_forward(const FwdArgs &a, void *proj, int proj_dtype, float *rowsum);
+cudaError_t launch_forward_correct(const FwdArgs &a, const void *p, int p_dtype, void *r,
+                                   int r_dtype, float *partials, int n_partials_cap,
+                                   double *sums);
+int forward_partials_needed(const Grid &g, int n_idx);
+cudaError_t launch_count_samples(const FwdArgs &a, unsigned long long *out);
+
+struct BpArgs {
+    const Grid *grid;
+    const ViewGPU *views;
+    const int *view_idx;
+    int n_idx;
+    const void *r;
+    int r_dtype;
+    void *vol;
+    int vol_dtype;
+    const float *w;
+    float alpha;
+    int normalize;
+    int accumulate;
+    cudaStream_t stream;
+};
+cudaError_t launch_backproject(const BpArgs &a);
+
+cudaError_t launch_adjoint(const FwdArgs &a, const float *proj, float *vol);
+cudaError_t launch_motion_grad(const FwdArgs &a, const float *gproj, float *grad_M, float *grad_b,
+                               float *grad_coef_idx);
+cudaError_t launch_motion_setup(const float *theta, const float *coef, const float *s_view,
+                                int n_views, const Grid &g, const double vox[3],
+                                const double origin[3], MotionGPU *motion, float *coef_idx,
+                                float *dRdw, cudaStream_t stream);
+cudaError_t launch_motion_grad_finish(const float *theta, const float *dRdw, const float *grad_M,
+                                      const float *grad_b, const float *grad_coef_idx,
+                                      int n_views, const double vox[3], const double origin[3],
+                                      float *grad_theta, float *grad_coef, cudaStream_t stream);
+
+}  // namespace ctrex

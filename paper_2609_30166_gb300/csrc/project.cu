@@ -1,0 +1,273 @@
+// project.cu -- ray-driven cone-beam forward projector A (Sec. 4.1
+// "Projection operator"), its angular sub-sample loop (Sec. 3.4, Sec. 4.2.2),
+// the per-sample motion warp (Sec. 3.1.1, Sec. 4.2.1) and the fused
+// detector-space correction R (p - A x) with residual norms (Sec. 4.1
+// "Correction kernel", Eq. (1) terms 1-2).
+//
+// Launch shape: one thread per detector pixel, 32 x 4 pixels per CTA so that
+// a warp covers 32 neighbouring pixels of one detector row (neighbouring rays
+// sample neighbouring voxels at every step).  Grid = (u tiles, views, v
+// tiles): the CTAs resident at one time cover a band of detector rows across
+// many views, whose rays all cross the same z-slab of the volume, so that
+// slab stays in L2 while it is being sampled.
+#include "ray.cuh"
+
+namespace ctrex {
+
+constexpr int FWD_TX = 32;
+constexpr int FWD_TY = 4;
+
+enum FwdMode { MODE_PROJECT = 0, MODE_CORRECT = 1 };
+
+// Integral of one pixel (mean over its sub-angle rays): value and row sum.
+template <typename TV, bool MOTION>
+__device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__restrict__ views,
+                                               const MotionGPU &mo, const float *coef,
+                                               const TV *__restrict__ vol, int view, float u,
+                                               float v, float &val, float &rs)
+{
+    float acc = 0.0f, acc_rs = 0.0f;
+    for (int s = 0; s < G.n_sub; ++s) {
+        const ViewGPU V = views[view * G.n_sub + s];
+        Ray R;
+        if (!setup_ray(G, V, u, v, R)) continue;
+        float a = 0.0f, ars = 0.0f;
+        const int Km1 = R.K - 1;
+        for (int k = 0; k < Km1; ++k) {
+            float g[3];
+            g[0] = fmaf((float)k, R.sg[0], R.g0[0]);
+            g[1] = fmaf((float)k, R.sg[1], R.g0[1]);
+            g[2] = fmaf((float)k, R.sg[2], R.g0[2]);
+            if (MOTION) {
+                float y[3];
+                warp_sample(G, mo, coef, g, y);
+                g[0] = y[0];
+                g[1] = y[1];
+                g[2] = y[2];
+            }
+            float ws;
+            a += trilinear(vol, G.nx, G.ny, G.nz, g[0], g[1], g[2], ws);
+            ars += ws;
+        }
+        a *= G.step_mm;
+        ars *= G.step_mm;
+        if (R.w_last > 0.0f) {
+            float g[3] = {R.g_last[0], R.g_last[1], R.g_last[2]};
+            if (MOTION) {
+                float y[3];
+                warp_sample(G, mo, coef, g, y);
+                g[0] = y[0];
+                g[1] = y[1];
+                g[2] = y[2];
+            }
+            float ws;
+            a = fmaf(R.w_last, trilinear(vol, G.nx, G.ny, G.nz, g[0], g[1], g[2], ws), a);
+            ars = fmaf(R.w_last, ws, ars);
+        }
+        acc += a;
+        acc_rs += ars;
+    }
+    val = acc * G.inv_sub;
+    rs = acc_rs * G.inv_sub;
+}
+
+template <typename TV, typename TP, int MODE, bool MOTION>
+__global__ void __launch_bounds__(FWD_TX *FWD_TY)
+    fwd_kernel(Grid G, const ViewGPU *__restrict__ views, const MotionGPU *__restrict__ motion,
+               const float *__restrict__ coef_g, const TV *__restrict__ vol,
+               const int *__restrict__ view_idx, TP *__restrict__ out, float *__restrict__ rowsum_out,
+               const TP *__restrict__ p, float *__restrict__ partials, unsigned *devcheck)
+{
+    __shared__ float s_coef[MOTION ? 8 * 8 * 8 * 3 : 1];
+    __shared__ float s_red[2][FWD_TX * FWD_TY / 32];
+    const int k = blockIdx.y;
+    int view = view_idx ? view_idx[k] : k;
+    bool ok = true;
+    if (view < 0 || view >= G.n_views) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(devcheck, (unsigned)DEVCHECK_OOB);
+        ok = false;
+        view = 0;
+    }
+    MotionGPU mo;
+    const float *coef = nullptr;
+    if (MOTION) {
+        mo = motion[view];
+        if (coef_g != nullptr) {
+            for (int i = threadIdx.y * FWD_TX + threadIdx.x; i < 8 * 8 * 8 * 3; i += FWD_TX * FWD_TY)
+                s_coef[i] = coef_g[i];
+            coef = s_coef;
+        }
+        __syncthreads();
+    }
+    const int iu = blockIdx.x * FWD_TX + threadIdx.x;
+    const int iv = blockIdx.z * FWD_TY + threadIdx.y;
+    const bool inside = ok && iu < G.nu && iv < G.nv;
+    float val = 0.0f, rs = 0.0f;
+    if (inside) pixel_integral<TV, MOTION>(G, views, mo, coef, vol, view, (float)iu, (float)iv, val, rs);
+    const size_t pix = ((size_t)k * G.nv + iv) * G.nu + iu;
+    if (MODE == MODE_PROJECT) {
+        if (inside) {
+            Storage<TP>::store(out + pix, val);
+            if (rowsum_out) rowsum_out[pix] = rs;
+        }
+        return;
+    } else {
+        float e2 = 0.0f, p2 = 0.0f;
+        if (inside) {
+            const float pm = Storage<TP>::load(p + pix);
+            const float e = pm - val;
+            const float Rw = rs > G.eps_R ? 1.0f / rs : 0.0f;
+            Storage<TP>::store(out + pix, Rw * e);
+            e2 = e * e;
+            p2 = pm * pm;
+        }
+        // warp-shuffle then fixed-order CTA reduction of the residual norms
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            e2 += __shfl_xor_sync(0xffffffffu, e2, off);
+            p2 += __shfl_xor_sync(0xffffffffu, p2, off);
+        }
+        const int lane = threadIdx.x & 31;
+        const int warp = (threadIdx.y * FWD_TX + threadIdx.x) >> 5;
+        if (lane == 0) {
+            s_red[0][warp] = e2;
+            s_red[1][warp] = p2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            float a = 0.0f, b = 0.0f;
+#pragma unroll
+            for (int w = 0; w < FWD_TX * FWD_TY / 32; ++w) {
+                a += s_red[0][w];
+                b += s_red[1][w];
+            }
+            const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            partials[2 * bid] = a;
+            partials[2 * bid + 1] = b;
+        }
+    }
+}
+
+// Second pass of the residual reduction: one CTA, fixed order, FP64.
+__global__ void __launch_bounds__(1024) finish_sums_kernel(const float *__restrict__ partials, size_t n,
+                                                           double *__restrict__ sums)
+{
+    __shared__ double s[2][1024];
+    double a = 0.0, b = 0.0;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+        a += (double)partials[2 * i];
+        b += (double)partials[2 * i + 1];
+    }
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + off];
+            s[1][threadIdx.x] += s[1][threadIdx.x + off];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sums[0] = s[0][0];
+        sums[1] = s[1][0];
+    }
+}
+
+// Exact sample count (same set-up arithmetic as the projector).
+__global__ void __launch_bounds__(FWD_TX *FWD_TY)
+    count_kernel(Grid G, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx,
+                 unsigned long long *out)
+{
+    const int k = blockIdx.y;
+    const int view = view_idx ? view_idx[k] : k;
+    if (view < 0 || view >= G.n_views) return;
+    const int iu = blockIdx.x * FWD_TX + threadIdx.x;
+    const int iv = blockIdx.z * FWD_TY + threadIdx.y;
+    unsigned long long n = 0;
+    if (iu < G.nu && iv < G.nv) {
+        for (int s = 0; s < G.n_sub; ++s) {
+            Ray R;
+            if (setup_ray(G, views[view * G.n_sub + s], (float)iu, (float)iv, R)) n += (unsigned long long)R.K;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) n += __shfl_xor_sync(0xffffffffu, n, off);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(out, n);
+}
+
+static dim3 fwd_grid(const Grid &G, int n_idx)
+{
+    return dim3((G.nu + FWD_TX - 1) / FWD_TX, n_idx, (G.nv + FWD_TY - 1) / FWD_TY);
+}
+
+int forward_partials_needed(const Grid &G, int n_idx)
+{
+    const dim3 g = fwd_grid(G, n_idx);
+    return (int)(g.x * g.y * g.z);
+}
+
+template <typename TV, typename TP, int MODE>
+static cudaError_t fwd_dispatch_motion(const FwdArgs &a, TP *out, float *rowsum, const TP *p,
+                                       float *partials)
+{
+    const Grid &G = *a.grid;
+    const dim3 grid = fwd_grid(G, a.n_idx), block(FWD_TX, FWD_TY);
+    const TV *vol = static_cast<const TV *>(a.vol);
+    if (a.motion)
+        fwd_kernel<TV, TP, MODE, true><<<grid, block, 0, a.stream>>>(
+            G, a.views, a.motion, a.coef_idx, vol, a.view_idx, out, rowsum, p, partials, a.devcheck);
+    else
+        fwd_kernel<TV, TP, MODE, false><<<grid, block, 0, a.stream>>>(
+            G, a.views, nullptr, nullptr, vol, a.view_idx, out, rowsum, p, partials, a.devcheck);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t fwd_dispatch(const FwdArgs &a, int pdt, void *out, float *rowsum, const void *p,
+                                float *partials)
+{
+    if (a.vol_dtype == CTREX_F32) {
+        if (pdt == CTREX_F32)
+            return fwd_dispatch_motion<float, float, MODE>(a, (float *)out, rowsum, (const float *)p, partials);
+        return fwd_dispatch_motion<float, __nv_bfloat16, MODE>(a, (__nv_bfloat16 *)out, rowsum,
+                                                                (const __nv_bfloat16 *)p, partials);
+    }
+    if (pdt == CTREX_F32)
+        return fwd_dispatch_motion<__nv_bfloat16, float, MODE>(a, (float *)out, rowsum, (const float *)p, partials);
+    return fwd_dispatch_motion<__nv_bfloat16, __nv_bfloat16, MODE>(a, (__nv_bfloat16 *)out, rowsum,
+                                                                    (const __nv_bfloat16 *)p, partials);
+}
+
+cudaError_t launch_forward(const FwdArgs &a, void *proj, int proj_dtype, float *rowsum)
+{
+    if (a.n_idx == 0) return cudaSuccess;
+    return fwd_dispatch<MODE_PROJECT>(a, proj_dtype, proj, rowsum, nullptr, nullptr);
+}
+
+cudaError_t launch_forward_correct(const FwdArgs &a, const void *p, int p_dtype, void *r, int r_dtype,
+                                   float *partials, int n_partials_cap, double *sums)
+{
+    if (p_dtype != r_dtype) return cudaErrorInvalidValue;
+    if (a.n_idx == 0) {
+        if (sums) return cudaMemsetAsync(sums, 0, 2 * sizeof(double), a.stream);
+        return cudaSuccess;
+    }
+    const int n = forward_partials_needed(*a.grid, a.n_idx);
+    if (n > n_partials_cap) return cudaErrorInvalidValue;
+    cudaError_t e = fwd_dispatch<MODE_CORRECT>(a, p_dtype, r, nullptr, p, partials);
+    if (e != cudaSuccess || sums == nullptr) return e;
+    finish_sums_kernel<<<1, 1024, 0, a.stream>>>(partials, (size_t)n, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_samples(const FwdArgs &a, unsigned long long *out)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), a.stream);
+    if (e != cudaSuccess || a.n_idx == 0) return e;
+    count_kernel<<<fwd_grid(*a.grid, a.n_idx), dim3(FWD_TX, FWD_TY), 0, a.stream>>>(*a.grid, a.views,
+                                                                                 a.view_idx, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ctrex

@@ -1,0 +1,178 @@
+// ray.cuh -- per-ray set-up, sampling and interpolation shared by the
+// ray-driven kernels (forward, fused correction, adjoint, motion gradient).
+#pragma once
+
+#include "ctrex_internal.cuh"
+
+namespace ctrex {
+
+// Geometry of one ray in voxel-index coordinates.  Samples k = 0..K-2 sit at
+// g0 + k * sg with weight step_mm; the last one at g_last with weight w_last
+// (truncated-midpoint rule of the clipped segment, Sec. 4.1 "weighted by
+// their path lengths").
+struct Ray {
+    float g0[3];
+    float sg[3];
+    float g_last[3];
+    float w_last;
+    int K;
+};
+
+// Sets up the ray of view parameters V through detector point (u, v).
+// Returns false if the half line from the source misses the clip box.
+__device__ __forceinline__ bool setup_ray(const Grid &G, const ViewGPU &V, float u, float v, Ray &R)
+{
+    const float du = u - G.uc, dv = v - G.vc;
+    float X[3], D[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        X[a] = fmaf(dv, V.qv[a], fmaf(du, V.qu[a], V.ref[a]));
+        D[a] = fmaf(dv, V.qv[a], fmaf(du, V.qu[a], V.dref[a]));
+    }
+    const float m0 = D[0] * G.vox[0], m1 = D[1] * G.vox[1], m2 = D[2] * G.vox[2];
+    const float len = sqrtf(fmaf(m0, m0, fmaf(m1, m1, m2 * m2)));
+    const float il = 1.0f / len;
+    float dg[3] = {D[0] * il, D[1] * il, D[2] * il};  // voxels per mm along the ray
+    // t: mm along the ray measured from X; the source sits at t = -len.
+    float t0 = -len, t1 = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (dg[a] != 0.0f) {
+            const float inv = 1.0f / dg[a];
+            const float ta = (G.lo[a] - X[a]) * inv, tb = (G.hi[a] - X[a]) * inv;
+            t0 = fmaxf(t0, fminf(ta, tb));
+            t1 = fminf(t1, fmaxf(ta, tb));
+        } else if (X[a] < G.lo[a] || X[a] > G.hi[a]) {
+            return false;
+        }
+    }
+    if (!(t1 > t0)) return false;
+    const float step = G.step_mm;
+    const float L = t1 - t0;
+    int K = (int)ceilf(L / step);
+    if (K < 1) K = 1;
+    const float th = t0 + 0.5f * step;
+    const float a_last = fmaf((float)(K - 1), step, t0);
+    const float t_last = 0.5f * (a_last + t1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R.g0[a] = fmaf(th, dg[a], X[a]);
+        R.sg[a] = step * dg[a];
+        R.g_last[a] = fmaf(t_last, dg[a], X[a]);
+    }
+    R.w_last = t1 - a_last;
+    R.K = K;
+    return true;
+}
+
+// Zero-padded trilinear interpolation at index coordinate g (reading: taps
+// outside [0, n-1] contribute nothing).  wsum receives the summed weight of
+// the in-range taps (the interpolant of an all-ones volume, for row sums).
+template <typename TV>
+__device__ __forceinline__ float trilinear(const TV *__restrict__ vol, int nx, int ny, int nz,
+                                           float gx, float gy, float gz, float &wsum)
+{
+    const float fx = floorf(gx), fy = floorf(gy), fz = floorf(gz);
+    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+    const float ax = gx - fx, ay = gy - fy, az = gz - fz;
+    const float wx0 = ((unsigned)ix < (unsigned)nx) ? 1.0f - ax : 0.0f;
+    const float wx1 = ((unsigned)(ix + 1) < (unsigned)nx) ? ax : 0.0f;
+    const float wy0 = ((unsigned)iy < (unsigned)ny) ? 1.0f - ay : 0.0f;
+    const float wy1 = ((unsigned)(iy + 1) < (unsigned)ny) ? ay : 0.0f;
+    const float wz0 = ((unsigned)iz < (unsigned)nz) ? 1.0f - az : 0.0f;
+    const float wz1 = ((unsigned)(iz + 1) < (unsigned)nz) ? az : 0.0f;
+    const int x0 = min(max(ix, 0), nx - 1), x1 = min(max(ix + 1, 0), nx - 1);
+    const int y0 = min(max(iy, 0), ny - 1), y1 = min(max(iy + 1, 0), ny - 1);
+    const int z0 = min(max(iz, 0), nz - 1), z1 = min(max(iz + 1, 0), nz - 1);
+    const TV *r00 = vol + (z0 * ny + y0) * nx;
+    const TV *r01 = vol + (z0 * ny + y1) * nx;
+    const TV *r10 = vol + (z1 * ny + y0) * nx;
+    const TV *r11 = vol + (z1 * ny + y1) * nx;
+    const float v000 = Storage<TV>::load(r00 + x0), v001 = Storage<TV>::load(r00 + x1);
+    const float v010 = Storage<TV>::load(r01 + x0), v011 = Storage<TV>::load(r01 + x1);
+    const float v100 = Storage<TV>::load(r10 + x0), v101 = Storage<TV>::load(r10 + x1);
+    const float v110 = Storage<TV>::load(r11 + x0), v111 = Storage<TV>::load(r11 + x1);
+    const float c00 = fmaf(wx0, v000, wx1 * v001), c01 = fmaf(wx0, v010, wx1 * v011);
+    const float c10 = fmaf(wx0, v100, wx1 * v101), c11 = fmaf(wx0, v110, wx1 * v111);
+    const float c0 = fmaf(wy0, c00, wy1 * c01), c1 = fmaf(wy0, c10, wy1 * c11);
+    wsum = (wx0 + wx1) * (wy0 + wy1) * (wz0 + wz1);
+    return fmaf(wz0, c0, wz1 * c1);
+}
+
+// Uniform cubic B-spline weights of control points i0-1 .. i0+2 at fractional
+// offset f in [0, 1) (i0 = floor of the spline coordinate), and derivatives.
+__device__ __forceinline__ void bspline_weights(float f, float w[4])
+{
+    const float f2 = f * f, f3 = f2 * f, g = 1.0f - f;
+    w[0] = g * g * g * (1.0f / 6.0f);
+    w[1] = fmaf(0.5f, f3, fmaf(-1.0f, f2, 2.0f / 3.0f));
+    w[2] = fmaf(-0.5f, f3, fmaf(0.5f, f2, fmaf(0.5f, f, 1.0f / 6.0f)));
+    w[3] = f3 * (1.0f / 6.0f);
+}
+
+__device__ __forceinline__ void bspline_dweights(float f, float d[4])
+{
+    const float f2 = f * f, g = 1.0f - f;
+    d[0] = -0.5f * g * g;
+    d[1] = fmaf(1.5f, f2, -2.0f * f);
+    d[2] = fmaf(-1.5f, f2, fmaf(1.0f, f, 0.5f));
+    d[3] = 0.5f * f2;
+}
+
+// Spline coordinate of index coordinate gp along one axis (clamped to [1, 6]);
+// i0 in [1, 6], f in [0, 1); `active` is false where the clamp holds.
+__device__ __forceinline__ void spline_coord(float gp, float scale, int &i0, float &f, bool &active)
+{
+    float xi = fmaf(gp + 0.5f, scale, 1.0f);
+    active = (xi > 1.0f) && (xi < 6.0f);
+    xi = fminf(fmaxf(xi, 1.0f), 6.0f);
+    const float fl = floorf(xi);
+    i0 = (int)fl;
+    f = xi - fl;
+}
+
+// Warp of one sample (Sec. 2.2.2 pose, then Sec. 3.1 displacement): index
+// coordinates in, index coordinates out.  coef: shared-memory copy of the
+// [8][8][8][3] coefficients in voxels, or nullptr.
+__device__ __forceinline__ void warp_sample(const Grid &G, const MotionGPU &m, const float *coef,
+                                            const float g[3], float y[3])
+{
+    float gp[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        gp[r] = fmaf(m.M[3 * r], g[0], fmaf(m.M[3 * r + 1], g[1], fmaf(m.M[3 * r + 2], g[2], m.b[r])));
+    float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
+    if (coef != nullptr && m.s != 0.0f) {
+        int i0[3];
+        float f[3], wx[4], wy[4], wz[4];
+        bool act[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) spline_coord(gp[a], G.spl_scale[a], i0[a], f[a], act[a]);
+        bspline_weights(f[0], wx);
+        bspline_weights(f[1], wy);
+        bspline_weights(f[2], wz);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int cz = min(i0[2] - 1 + k, 7);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int cy = min(i0[1] - 1 + j, 7);
+                const float wyz = wz[k] * wy[j];
+                const float *row = coef + 3 * ((cz * 8 + cy) * 8);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int cx = min(i0[0] - 1 + i, 7);
+                    const float wt = wyz * wx[i];
+                    u0 = fmaf(wt, row[3 * cx + 0], u0);
+                    u1 = fmaf(wt, row[3 * cx + 1], u1);
+                    u2 = fmaf(wt, row[3 * cx + 2], u2);
+                }
+            }
+        }
+    }
+    y[0] = fmaf(m.s, u0, gp[0]);
+    y[1] = fmaf(m.s, u1, gp[1]);
+    y[2] = fmaf(m.s, u2, gp[2]);
+}
+
+}  // namespace ctrex

@@ -1,0 +1,70 @@
+"""C ABI: the library builds, loads and exports every symbol include/ctrex.h
+declares; host-side argument checks answer without a GPU."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ctrex.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ctrex_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2609_30166_gb300 import _build, ctrex
+
+    _build.build_library()
+    return ctrex.load_library()
+
+
+def test_header_declares_the_binding_exports():
+    from paper_2609_30166_gb300 import ctrex
+
+    assert declared_symbols() == sorted(ctrex.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(os.path.join(ROOT, "paper_2609_30166_gb300", "libctrex.so"))
+    for name in declared_symbols():
+        assert hasattr(raw, name), name
+
+
+def test_null_context_is_rejected_without_gpu(lib):
+    assert lib.ctrex_destroy(None) == -1
+    assert lib.ctrex_device_status(None) == -1
+    assert lib.ctrex_set_geometry(None, None, 1, 1, None, None, 0.5) == -1
+    assert lib.ctrex_fwd_project(None, None, 0, None, 0, None, None, 0) == -1
+    assert lib.ctrex_sirt_iterate(None, None, 0, None, 0, 1, 1.0, None, 0.0, None, None) == -1
+    assert b"invalid context" in lib.ctrex_last_error(None)
+    assert lib.ctrex_version().startswith(b"ctrex-gb300")
+    assert lib.ctrex_create(None, 0, None) == -1
+
+
+def test_create_without_device_fails_cleanly(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.ctrex_create(ctypes.byref(h), 0, None) == -5
+    assert not h.value
+
+
+def test_binding_refuses_to_run_without_library(tmp_path):
+    from paper_2609_30166_gb300 import ctrex
+
+    saved = ctrex._lib
+    ctrex._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="no CPU fallback"):
+            ctrex.load_library(str(tmp_path / "missing.so"))
+    finally:
+        ctrex._lib = saved
