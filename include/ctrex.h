@@ -148,7 +148,8 @@ int ctrex_set_motion(ctrex_ctx *ctx, const float *theta, const float *coef, cons
  * (zero outside the grid), weights = segment lengths in mm.
  *   vol      DEVICE [nz][ny][nx] of vol_dtype.
  *   proj     DEVICE [n_idx][nv][nu] of proj_dtype (overwritten).
- *   view_idx DEVICE int32 [n_idx] (each in [0, n_views)), or NULL = all.
+ *   view_idx DEVICE int32 [n_idx] (each in [0, n_views)), or NULL = all
+ *            views (then n_idx must be n_views, or 0 for an empty call).
  *   rowsum   DEVICE float [n_idx][nv][nu] receiving A 1, or NULL.
  */
 int ctrex_fwd_project(ctrex_ctx *ctx, const void *vol, int vol_dtype, void *proj, int proj_dtype,

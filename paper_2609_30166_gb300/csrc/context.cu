@@ -122,7 +122,7 @@ int check_views(ctrex_ctx *c, const int *view_idx, int n_idx)
 {
     if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_geometry has not been called");
     if (n_idx < 0 || n_idx > 65535) return fail(c, CTREX_E_SHAPE, "n_idx %d outside [0, 65535]", n_idx);
-    if (!view_idx && n_idx != c->grid.n_views)
+    if (!view_idx && n_idx != 0 && n_idx != c->grid.n_views)
         return fail(c, CTREX_E_SHAPE, "view_idx is NULL but n_idx (%d) != n_views (%d)", n_idx, c->grid.n_views);
     return CTREX_OK;
 }
@@ -423,6 +423,7 @@ int ctrex_fwd_project(ctrex_ctx *c, const void *vol, int vdt, void *proj, int pd
     if (!c) return CTREX_E_ARG;
     int e = check_views(c, view_idx, n_idx);
     if (e) return e;
+    if (n_idx == 0) return CTREX_OK;  // nothing to project
     if (!vol || !proj) return fail(c, CTREX_E_ARG, "fwd_project: NULL buffer");
     if (!dtype_ok(vdt) || !dtype_ok(pdt)) return fail(c, CTREX_E_DTYPE, "fwd_project: bad dtype");
     DeviceGuard g(c->device);
@@ -448,6 +449,10 @@ int ctrex_fwd_correct(ctrex_ctx *c, const void *vol, int vdt, const void *p, int
     if (!c) return CTREX_E_ARG;
     int e = check_views(c, view_idx, n_idx);
     if (e) return e;
+    if (n_idx == 0) {  // empty view list: zero norms, no images
+        if (sums) CT_CUDA(c, cudaMemsetAsync(sums, 0, 2 * sizeof(double), c->stream));
+        return CTREX_OK;
+    }
     if (!vol || !p || !r) return fail(c, CTREX_E_ARG, "fwd_correct: NULL buffer");
     if (!dtype_ok(vdt) || !dtype_ok(pdt) || !dtype_ok(rdt)) return fail(c, CTREX_E_DTYPE, "fwd_correct: bad dtype");
     if (pdt != rdt) return fail(c, CTREX_E_DTYPE, "fwd_correct: p and r must share one dtype");
@@ -466,7 +471,7 @@ int ctrex_back_project(ctrex_ctx *c, const void *r, int rdt, void *vol, int vdt,
     if (!c) return CTREX_E_ARG;
     int e = check_views(c, view_idx, n_idx);
     if (e) return e;
-    if (!r || !vol) return fail(c, CTREX_E_ARG, "back_project: NULL buffer");
+    if (!vol || (!r && n_idx > 0)) return fail(c, CTREX_E_ARG, "back_project: NULL buffer");
     if (!dtype_ok(vdt) || !dtype_ok(rdt)) return fail(c, CTREX_E_DTYPE, "back_project: bad dtype");
     if (!isfinite(alpha)) return fail(c, CTREX_E_ARG, "back_project: alpha not finite");
     DeviceGuard g(c->device);
@@ -494,6 +499,7 @@ int ctrex_adjoint_project(ctrex_ctx *c, const float *proj, float *vol, const int
     if (!c) return CTREX_E_ARG;
     int e = check_views(c, view_idx, n_idx);
     if (e) return e;
+    if (n_idx == 0) return CTREX_OK;
     if (!proj || !vol) return fail(c, CTREX_E_ARG, "adjoint_project: NULL buffer");
     DeviceGuard g(c->device);
     cudaError_t ce = launch_adjoint(fwd_args(c, nullptr, CTREX_F32, view_idx, n_idx), proj, vol);
@@ -508,6 +514,7 @@ int ctrex_motion_grad(ctrex_ctx *c, const void *vol, int vdt, const float *gproj
     int e = check_views(c, view_idx, n_idx);
     if (e) return e;
     if (!c->has_motion) return fail(c, CTREX_E_STATE, "motion_grad: set_motion has not been called");
+    if (n_idx == 0) return CTREX_OK;
     if (!vol || !gproj) return fail(c, CTREX_E_ARG, "motion_grad: NULL buffer");
     if (!dtype_ok(vdt)) return fail(c, CTREX_E_DTYPE, "motion_grad: bad dtype");
     if (grad_theta && !c->theta_valid)

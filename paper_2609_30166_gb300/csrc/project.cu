@@ -101,18 +101,20 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
     }
     const int iu = blockIdx.x * FWD_TX + threadIdx.x;
     const int iv = blockIdx.z * FWD_TY + threadIdx.y;
-    const bool inside = ok && iu < G.nu && iv < G.nv;
+    const bool in_pix = iu < G.nu && iv < G.nv;
+    const bool inside = ok && in_pix;
     float val = 0.0f, rs = 0.0f;
     if (inside) pixel_integral<TV, MOTION>(G, views, mo, coef, vol, view, (float)iu, (float)iv, val, rs);
     const size_t pix = ((size_t)k * G.nv + iv) * G.nu + iu;
     if (MODE == MODE_PROJECT) {
-        if (inside) {
+        if (in_pix) {  // a skipped (out-of-range) view gets zeros
             Storage<TP>::store(out + pix, val);
             if (rowsum_out) rowsum_out[pix] = rs;
         }
         return;
     } else {
         float e2 = 0.0f, p2 = 0.0f;
+        if (in_pix && !ok) Storage<TP>::store(out + pix, 0.0f);
         if (inside) {
             const float pm = Storage<TP>::load(p + pix);
             const float e = pm - val;
