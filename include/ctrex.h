@@ -238,6 +238,35 @@ int ctrex_sirt_host(ctrex_ctx *ctx, void *vol_host, int vol_dtype, const void *p
  */
 int ctrex_count_samples(ctrex_ctx *ctx, const int *view_idx, int n_idx, long long *out);
 
+/*
+ * Detector-space correction without any allocation.  The paper has no
+ * counterpart: this is an extra entry point for callers that cannot let the
+ * library call cudaMalloc (a host whose caching allocator already reserved
+ * the device memory, an acquisition loop that must not stall in the driver's
+ * allocator, a plugin host that forbids allocation in its callback).
+ * It needs no context.  On the current CUDA device it computes, for
+ * i < n,  r_i = R_i (p_i - q_i)  with R_i = 1 / rowsum_i if rowsum_i > eps_R
+ * else 0, and sums = (sum (p - q)^2, sum p^2) in a fixed-order two-pass
+ * reduction -- the same correction ctrex_fwd_correct fuses into the
+ * projector, here fed with q = A x and rowsum = A 1 from ctrex_fwd_project.
+ *   p, q     DEVICE [n] of dtype (CTREX_F32 or CTREX_BF16); r DEVICE [n]
+ *            output of dtype; rowsum DEVICE float [n]; sums DEVICE double
+ *            [2] or NULL (then only r is written).
+ *   n        0 <= n <= 2^29 (536870912); larger n returns CTREX_E_SHAPE
+ *            before any work is enqueued.
+ *   stream   cudaStream_t to enqueue on (NULL = legacy default stream).
+ * The reduction's scratch is a 1 MiB static device array that every GPU
+ * loading the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * caches it, so make the first call on each device before any stream
+ * capture.  Every call shares the array: calls whose kernels overlap on the
+ * GPU race on it and must be serialised by the caller.  Errors:
+ * CTREX_E_SHAPE, CTREX_E_DTYPE, CTREX_E_ARG (NULL buffer, eps_R < 0 or NaN),
+ * CTREX_E_CUDA (address lookup or launch failed).
+ */
+int ctrex_correct_static(const void *p, const void *q, const float *rowsum, void *r, int dtype,
+                         long long n, float eps_R, double *sums, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

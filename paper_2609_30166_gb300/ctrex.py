@@ -30,8 +30,11 @@ EXPORTS = (
     "ctrex_version", "ctrex_create", "ctrex_destroy", "ctrex_set_stream", "ctrex_last_error",
     "ctrex_device_status", "ctrex_set_geometry", "ctrex_set_motion", "ctrex_fwd_project",
     "ctrex_fwd_correct", "ctrex_back_project", "ctrex_adjoint_project", "ctrex_motion_grad",
-    "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples",
+    "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples", "ctrex_correct_static",
 )
+
+# Largest n ctrex_correct_static accepts (its static scratch holds 65536 CTA partials of 8192 elements).
+CORRECT_STATIC_MAX_N = 1 << 29
 
 
 class CtrexError(RuntimeError):
@@ -81,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "ctrex_sirt_iterate": ([vp, vp, i, vp, i, i, f, vp, f, fp, ip], i),
         "ctrex_sirt_host": ([vp, vp, i, vp, i, i, f, vp, f, fp, ip], i),
         "ctrex_count_samples": ([vp, vp, i, ctypes.POINTER(ctypes.c_longlong)], i),
+        "ctrex_correct_static": ([vp, vp, vp, vp, i, ctypes.c_longlong, f, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -306,6 +310,35 @@ class Context:
     def device_status(self):
         self._sync_stream()
         self._check(self.lib.ctrex_device_status(self._h))
+
+
+def correct_static(p, q, rowsum, r=None, sums=None, eps_R=0.0):
+    """r = R (p - q) and (sum (p-q)^2, sum p^2) without any allocation in the
+    library (for callers that cannot let it call cudaMalloc); see
+    ``ctrex_correct_static`` in include/ctrex.h.  Runs on the device of p, on
+    the current torch stream.  Calls that overlap on the GPU share one static
+    scratch array and race: serialise them."""
+    lib = load_library()
+    dev = p.device
+    for t, name in ((p, "p"), (q, "q"), (rowsum, "rowsum")):
+        if not isinstance(t, torch.Tensor) or t.device != dev or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous tensor on {dev}")
+    if q.dtype != p.dtype or q.shape != p.shape or rowsum.shape != p.shape or rowsum.dtype != torch.float32:
+        raise ValueError("q must match p; rowsum must be float32 of p's shape")
+    n = p.numel()
+    if n > CORRECT_STATIC_MAX_N:
+        raise ValueError(f"correct_static: n = {n} exceeds the static scratch limit {CORRECT_STATIC_MAX_N}")
+    if r is None:
+        r = torch.empty_like(p)
+    if sums is None:
+        sums = torch.empty(2, dtype=torch.float64, device=dev)
+    with torch.cuda.device(dev):
+        stream = torch.cuda.current_stream(dev).cuda_stream
+        rc = lib.ctrex_correct_static(_ptr(p), _ptr(q), _ptr(rowsum), _ptr(r), _dt(p), n, float(eps_R),
+                                      _ptr(sums), ctypes.c_void_p(stream))
+    if rc != OK:
+        raise CtrexError(rc, f"ctrex_correct_static failed (n = {n})")
+    return r, sums
 
 
 def context_for(cfg, P=None, device=None):
