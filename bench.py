@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="64^3 workload (quick check)")
+    ap.add_argument("--views", type=int, default=0,
+                    help="override the number of views (small cases for ncu captures; not a bench line)")
     return ap.parse_args()
 
 
@@ -181,6 +183,8 @@ def run_ours(args):
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
     cfg = inputs.CIRCULAR_64 if args.small else inputs.PERTURBED_512
+    if args.views:
+        cfg = cfg.scaled(n_views=args.views, name=f"{cfg.name}-views{args.views}")
     ctx, P, phantom, p, tdt = build_workload(cfg, device, args.dtype)
     n_samples = ctx.count_samples()
     n_updates = cfg.n ** 3 * cfg.n_views * cfg.n_sub

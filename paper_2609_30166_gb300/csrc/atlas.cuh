@@ -1,0 +1,100 @@
+// atlas.cuh -- a stack of 2D slices (volume z-slices, or detector images)
+// laid out as tiles of one 2D cudaArray, read through the texture path.
+//
+// The array is block-linear: a 2x2 neighbourhood of one slice sits in one or
+// two cache lines whatever the direction a warp's rays travel in, which a
+// row-major volume cannot offer.  One tex2Dgather returns the four texels of
+// a bilinear footprint in a single instruction; the interpolation weights are
+// computed in FP32 registers by the caller (the texture unit's own filtering
+// uses low-precision fixed-point weights and is not used).  The footprint is
+// addressed at the exact corner shared by its four texels, an integer
+// coordinate, so the texture unit's coordinate rounding cannot move it.
+#pragma once
+
+#include "ctrex_internal.cuh"
+
+namespace ctrex {
+
+struct Atlas {
+    cudaTextureObject_t tex = 0;  // point sampling, border = 0, unnormalised coordinates
+    int w = 0, h = 0;             // slice width and height (texels)
+    int n = 0;                    // number of slices
+    int tshift = 0;               // tiles per atlas row = 1 << tshift
+    int bf16 = 0;                 // texels are raw BF16 bit patterns (16-bit unsigned)
+};
+
+// Four texels (x0,y0) (x0+1,y0) (x0,y0+1) (x0+1,y0+1) of slice s (clamped to a
+// valid slice; out-of-slice texels are the neighbouring tile's, so callers
+// give them zero weight).
+__device__ __forceinline__ void atlas_quad(const Atlas &A, int s, int x0, int y0, float &c00, float &c10,
+                                           float &c01, float &c11)
+{
+    s = min(max(s, 0), A.n - 1);
+    const float X = (float)(((s & ((1 << A.tshift) - 1)) * A.w) + x0) + 1.0f;
+    const float Y = (float)(((s >> A.tshift) * A.h) + y0) + 1.0f;
+    if (A.bf16) {
+        const ushort4 q = tex2Dgather<ushort4>(A.tex, X, Y, 0);
+        c01 = __uint_as_float((unsigned)q.x << 16);
+        c11 = __uint_as_float((unsigned)q.y << 16);
+        c10 = __uint_as_float((unsigned)q.z << 16);
+        c00 = __uint_as_float((unsigned)q.w << 16);
+    } else {
+        const float4 q = tex2Dgather<float4>(A.tex, X, Y, 0);
+        c01 = q.x;
+        c11 = q.y;
+        c10 = q.z;
+        c00 = q.w;
+    }
+}
+
+// Zero-padded trilinear interpolation of a volume atlas at index coordinate
+// (gx, gy, gz); same weights as the row-major sampler, two gathers.
+struct AtlasSampler {
+    Atlas A;
+    __device__ __forceinline__ float operator()(float gx, float gy, float gz, float &wsum) const
+    {
+        const float fx = floorf(gx), fy = floorf(gy), fz = floorf(gz);
+        const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+        const float ax = gx - fx, ay = gy - fy, az = gz - fz;
+        const float wx0 = ((unsigned)ix < (unsigned)A.w) ? 1.0f - ax : 0.0f;
+        const float wx1 = ((unsigned)(ix + 1) < (unsigned)A.w) ? ax : 0.0f;
+        const float wy0 = ((unsigned)iy < (unsigned)A.h) ? 1.0f - ay : 0.0f;
+        const float wy1 = ((unsigned)(iy + 1) < (unsigned)A.h) ? ay : 0.0f;
+        const float wz0 = ((unsigned)iz < (unsigned)A.n) ? 1.0f - az : 0.0f;
+        const float wz1 = ((unsigned)(iz + 1) < (unsigned)A.n) ? az : 0.0f;
+        // keep the gathered footprint inside the tile's neighbourhood
+        const int x0 = min(max(ix, -1), A.w - 1), y0 = min(max(iy, -1), A.h - 1);
+        float a00, a10, a01, a11, b00, b10, b01, b11;
+        atlas_quad(A, iz, x0, y0, a00, a10, a01, a11);
+        atlas_quad(A, iz + 1, x0, y0, b00, b10, b01, b11);
+        const float c0 = fmaf(wy0, fmaf(wx0, a00, wx1 * a10), wy1 * fmaf(wx0, a01, wx1 * a11));
+        const float c1 = fmaf(wy0, fmaf(wx0, b00, wx1 * b10), wy1 * fmaf(wx0, b01, wx1 * b11));
+        wsum = (wx0 + wx1) * (wy0 + wy1) * (wz0 + wz1);
+        return fmaf(wz0, c0, wz1 * c1);
+    }
+};
+
+// Row-major (linear memory) sampler with the same semantics.
+template <typename TV>
+struct LinearSampler {
+    const TV *vol;
+    int nx, ny, nz;
+    __device__ __forceinline__ float operator()(float gx, float gy, float gz, float &wsum) const;
+};
+
+// Host side (atlas.cu).
+struct AtlasStore {
+    cudaArray_t array = nullptr;
+    cudaTextureObject_t tex = 0;
+    cudaSurfaceObject_t surf = 0;
+    int w = 0, h = 0, n = 0, tshift = 0, bf16 = -1;
+};
+// Creates (or keeps, if the shape matches) an atlas for n slices of w x h.
+// Returns cudaErrorInvalidValue if it cannot fit the device's 2D texture limits.
+cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int device);
+void atlas_release(AtlasStore &s);
+Atlas atlas_view(const AtlasStore &s);
+// Copies slices [n][h][w] (row-major, FP32 or BF16 as the atlas) into the atlas.
+cudaError_t atlas_upload(const AtlasStore &s, const void *src, cudaStream_t stream);
+
+}  // namespace ctrex

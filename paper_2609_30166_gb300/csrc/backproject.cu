@@ -9,6 +9,7 @@
 // resident CTAs at once (one image band at a time sits in L2).  Grid order
 // is x, y, then z: the CTAs resident together cover a z-slab of the volume,
 // whose detector footprint over all views is a band of rows.
+#include "atlas.cuh"
 #include "ctrex_internal.cuh"
 
 namespace ctrex {
@@ -17,11 +18,43 @@ constexpr int BP_TX = 32, BP_TY = 4, BP_TZ = 2;
 constexpr int BP_THREADS = BP_TX * BP_TY * BP_TZ;
 constexpr int BP_CHUNK = 128;
 
-template <typename TR, typename TV>
+// Bilinear sample of correction image k at (u, v), zero outside the detector
+// (taps outside get zero weight); returns the sample, wsum = in-range weight.
+template <typename TR>
+struct LinearImages {
+    const TR *r;
+    int nu, nv;
+    __device__ __forceinline__ float operator()(int k, int iu, int iv, float wu0, float wu1, float wv0,
+                                                float wv1) const
+    {
+        const int u0 = max(iu, 0), u1 = min(iu + 1, nu - 1);
+        const int v0 = max(iv, 0), v1 = min(iv + 1, nv - 1);
+        const TR *img = r + (size_t)k * nu * nv;
+        const float r00 = Storage<TR>::load(img + v0 * nu + u0);
+        const float r01 = Storage<TR>::load(img + v0 * nu + u1);
+        const float r10 = Storage<TR>::load(img + v1 * nu + u0);
+        const float r11 = Storage<TR>::load(img + v1 * nu + u1);
+        return fmaf(wv0, fmaf(wu0, r00, wu1 * r01), wv1 * fmaf(wu0, r10, wu1 * r11));
+    }
+};
+
+// The same sample from a texture atlas of the images: one gather.
+struct AtlasImages {
+    Atlas A;
+    __device__ __forceinline__ float operator()(int k, int iu, int iv, float wu0, float wu1, float wv0,
+                                                float wv1) const
+    {
+        float c00, c10, c01, c11;
+        atlas_quad(A, k, iu, iv, c00, c10, c01, c11);
+        return fmaf(wv0, fmaf(wu0, c00, wu1 * c10), wv1 * fmaf(wu0, c01, wu1 * c11));
+    }
+};
+
+template <typename Images, typename TV>
 __global__ void __launch_bounds__(BP_THREADS)
     bp_kernel(Grid G, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx, int n_idx,
-              const TR *__restrict__ r, TV *__restrict__ vol, const float *__restrict__ w, float alpha,
-              int normalize, int accumulate)
+              const Images img, TV *__restrict__ vol, const float *__restrict__ w, float alpha, int normalize,
+              int accumulate)
 {
     __shared__ float4 sP[BP_CHUNK][3];
     __shared__ int sImg[BP_CHUNK];
@@ -32,7 +65,6 @@ __global__ void __launch_bounds__(BP_THREADS)
     const bool inside = ix < G.nx && iy < G.ny && iz < G.nz;
     const float fx = (float)ix, fy = (float)iy, fz = (float)iz;
     const int nu = G.nu, nv = G.nv;
-    const size_t npix = (size_t)nu * nv;
     float b = 0.0f, c = 0.0f;
     const int total = n_idx * G.n_sub;
     for (int base = 0; base < total; base += BP_CHUNK) {
@@ -70,14 +102,7 @@ __global__ void __launch_bounds__(BP_THREADS)
             const float wu1 = iu + 1 < nu ? au : 0.0f;
             const float wv0 = iv >= 0 ? 1.0f - av : 0.0f;
             const float wv1 = iv + 1 < nv ? av : 0.0f;
-            const int u0 = max(iu, 0), u1 = min(iu + 1, nu - 1);
-            const int v0 = max(iv, 0), v1 = min(iv + 1, nv - 1);
-            const TR *img = r + (size_t)sImg[m] * npix;
-            const float r00 = Storage<TR>::load(img + v0 * nu + u0);
-            const float r01 = Storage<TR>::load(img + v0 * nu + u1);
-            const float r10 = Storage<TR>::load(img + v1 * nu + u0);
-            const float r11 = Storage<TR>::load(img + v1 * nu + u1);
-            b += fmaf(wv0, fmaf(wu0, r00, wu1 * r01), wv1 * fmaf(wu0, r10, wu1 * r11));
+            b += img(sImg[m], iu, iv, wu0, wu1, wv0, wv1);
             c += (wu0 + wu1) * (wv0 + wv1);
         }
     }
@@ -93,26 +118,32 @@ __global__ void __launch_bounds__(BP_THREADS)
     Storage<TV>::store(vol + j, out);
 }
 
-template <typename TR, typename TV>
-static cudaError_t bp_launch(const BpArgs &a)
+template <typename Images, typename TV>
+static cudaError_t bp_launch(const BpArgs &a, const Images &img)
 {
     const Grid &G = *a.grid;
     const dim3 block(BP_TX, BP_TY, BP_TZ);
     const dim3 grid((G.nx + BP_TX - 1) / BP_TX, (G.ny + BP_TY - 1) / BP_TY, (G.nz + BP_TZ - 1) / BP_TZ);
-    bp_kernel<TR, TV><<<grid, block, 0, a.stream>>>(G, a.views, a.view_idx, a.n_idx,
-                                                   static_cast<const TR *>(a.r), static_cast<TV *>(a.vol),
-                                                   a.w, a.alpha, a.normalize, a.accumulate);
+    bp_kernel<Images, TV><<<grid, block, 0, a.stream>>>(G, a.views, a.view_idx, a.n_idx, img,
+                                                       static_cast<TV *>(a.vol), a.w, a.alpha, a.normalize,
+                                                       a.accumulate);
     return cudaGetLastError();
+}
+
+template <typename Images>
+static cudaError_t bp_dispatch_vol(const BpArgs &a, const Images &img)
+{
+    if (a.vol_dtype == CTREX_F32) return bp_launch<Images, float>(a, img);
+    return bp_launch<Images, __nv_bfloat16>(a, img);
 }
 
 cudaError_t launch_backproject(const BpArgs &a)
 {
-    if (a.r_dtype == CTREX_F32) {
-        if (a.vol_dtype == CTREX_F32) return bp_launch<float, float>(a);
-        return bp_launch<float, __nv_bfloat16>(a);
-    }
-    if (a.vol_dtype == CTREX_F32) return bp_launch<__nv_bfloat16, float>(a);
-    return bp_launch<__nv_bfloat16, __nv_bfloat16>(a);
+    const Grid &G = *a.grid;
+    if (a.atlas) return bp_dispatch_vol(a, AtlasImages{*a.atlas});
+    if (a.r_dtype == CTREX_F32)
+        return bp_dispatch_vol(a, LinearImages<float>{static_cast<const float *>(a.r), G.nu, G.nv});
+    return bp_dispatch_vol(a, LinearImages<__nv_bfloat16>{static_cast<const __nv_bfloat16 *>(a.r), G.nu, G.nv});
 }
 
 }  // namespace ctrex

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "atlas.cuh"
 #include "ctrex_internal.cuh"
 
 using namespace ctrex;
@@ -42,6 +43,14 @@ struct ctrex_ctx {
     unsigned long long *d_count = nullptr;
     void *d_r = nullptr;  // SIRT correction images
     size_t r_bytes = 0;
+    // texture atlas of the volume read by the forward projector
+    AtlasStore vol_atlas;
+    Atlas vol_atlas_view;
+    // texture atlas of the correction images read by the backprojector
+    AtlasStore img_atlas;
+    Atlas img_atlas_view;
+    bool img_atlas_unfit = false;
+    bool atlas_unfit = false;  // geometry exceeds the 2D texture limits: row-major sampling
     // host-buffer entry point scratch
     void *d_hvol = nullptr, *d_hp = nullptr;
     float *d_hw = nullptr;
@@ -143,6 +152,25 @@ FwdArgs fwd_args(ctrex_ctx *c, const void *vol, int vdt, const int *view_idx, in
     return a;
 }
 
+// Uploads vol into the context's texture atlas and points a.atlas at it; if
+// the volume does not fit the 2D texture limits the row-major path is used.
+int prepare_atlas(ctrex_ctx *c, FwdArgs &a, const void *vol, int vdt)
+{
+    if (c->atlas_unfit) return CTREX_OK;
+    cudaError_t e = atlas_ensure(c->vol_atlas, c->grid.nx, c->grid.ny, c->grid.nz, vdt == CTREX_BF16, c->device);
+    if (e == cudaErrorInvalidValue) {
+        cudaGetLastError();
+        c->atlas_unfit = true;
+        return CTREX_OK;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "volume atlas allocation");
+    e = atlas_upload(c->vol_atlas, vol, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "volume atlas upload");
+    c->vol_atlas_view = atlas_view(c->vol_atlas);
+    a.atlas = &c->vol_atlas_view;
+    return CTREX_OK;
+}
+
 // 3x3 helpers (FP64, host)
 double det3(const double *m)
 {
@@ -231,6 +259,8 @@ int ctrex_destroy(ctrex_ctx *c)
         dfree(c->d_hvol);
         dfree(c->d_hp);
         dfree(c->d_hw);
+        atlas_release(c->vol_atlas);
+        atlas_release(c->img_atlas);
     }
     delete c;
     return CTREX_OK;
@@ -363,6 +393,8 @@ int ctrex_set_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, co
     G.inv_sub = (float)(1.0 / n_sub);
     c->has_motion = false;
     c->has_geom = true;
+    c->atlas_unfit = false;
+    c->img_atlas_unfit = false;
     set_clip_box(c);
     return CTREX_OK;
 }
@@ -427,7 +459,10 @@ int ctrex_fwd_project(ctrex_ctx *c, const void *vol, int vdt, void *proj, int pd
     if (!vol || !proj) return fail(c, CTREX_E_ARG, "fwd_project: NULL buffer");
     if (!dtype_ok(vdt) || !dtype_ok(pdt)) return fail(c, CTREX_E_DTYPE, "fwd_project: bad dtype");
     DeviceGuard g(c->device);
-    cudaError_t ce = launch_forward(fwd_args(c, vol, vdt, view_idx, n_idx), proj, pdt, rowsum);
+    FwdArgs a = fwd_args(c, vol, vdt, view_idx, n_idx);
+    e = prepare_atlas(c, a, vol, vdt);
+    if (e) return e;
+    cudaError_t ce = launch_forward(a, proj, pdt, rowsum);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "fwd_project launch");
     return CTREX_OK;
 }
@@ -459,8 +494,10 @@ int ctrex_fwd_correct(ctrex_ctx *c, const void *vol, int vdt, const void *p, int
     DeviceGuard g(c->device);
     e = ensure_partials(c, n_idx);
     if (e) return e;
-    cudaError_t ce = launch_forward_correct(fwd_args(c, vol, vdt, view_idx, n_idx), p, pdt, r, rdt, c->d_partials,
-                                            c->partials_cap, sums);
+    FwdArgs a = fwd_args(c, vol, vdt, view_idx, n_idx);
+    e = prepare_atlas(c, a, vol, vdt);
+    if (e) return e;
+    cudaError_t ce = launch_forward_correct(a, p, pdt, r, rdt, c->d_partials, c->partials_cap, sums);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "fwd_correct launch");
     return CTREX_OK;
 }
@@ -489,6 +526,20 @@ int ctrex_back_project(ctrex_ctx *c, const void *r, int rdt, void *vol, int vdt,
     a.normalize = normalize ? 1 : 0;
     a.accumulate = accumulate ? 1 : 0;
     a.stream = c->stream;
+    if (n_idx > 0 && !c->img_atlas_unfit) {
+        cudaError_t ae = atlas_ensure(c->img_atlas, c->grid.nu, c->grid.nv, n_idx, rdt == CTREX_BF16, c->device);
+        if (ae == cudaErrorInvalidValue) {
+            cudaGetLastError();
+            c->img_atlas_unfit = true;
+        } else if (ae != cudaSuccess) {
+            return cuda_fail(c, ae, "image atlas allocation");
+        } else {
+            ae = atlas_upload(c->img_atlas, r, c->stream);
+            if (ae != cudaSuccess) return cuda_fail(c, ae, "image atlas upload");
+            c->img_atlas_view = atlas_view(c->img_atlas);
+            a.atlas = &c->img_atlas_view;
+        }
+    }
     cudaError_t ce = launch_backproject(a);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "back_project launch");
     return CTREX_OK;
@@ -553,8 +604,10 @@ int ctrex_sirt_iterate(ctrex_ctx *c, void *vol, int vdt, const void *p, int pdt,
     e = ensure_partials(c, V);
     if (e) return e;
     for (int k = 0; k < max_iter; ++k) {
-        cudaError_t ce = launch_forward_correct(fwd_args(c, vol, vdt, nullptr, V), p, pdt, c->d_r, pdt,
-                                                c->d_partials, c->partials_cap, c->d_sums);
+        FwdArgs a = fwd_args(c, vol, vdt, nullptr, V);
+        e = prepare_atlas(c, a, vol, vdt);
+        if (e) return e;
+        cudaError_t ce = launch_forward_correct(a, p, pdt, c->d_r, pdt, c->d_partials, c->partials_cap, c->d_sums);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "sirt: fwd_correct");
         double s[2];
         CT_CUDA(c, cudaMemcpyAsync(s, c->d_sums, sizeof s, cudaMemcpyDeviceToHost, c->stream));

@@ -69,8 +69,11 @@ enum : unsigned { DEVCHECK_OOB = 1u };
 
 // ---- host-side launchers (defined in project.cu / backproject.cu / ...) ----
 
+struct Atlas;
+
 struct FwdArgs {
     const Grid *grid;           // host copy
+    const Atlas *atlas = nullptr;  // volume uploaded into a texture atlas, or nullptr
     const ViewGPU *views;       // device [n_views * n_sub]
     const MotionGPU *motion;    // device [n_views] or nullptr
     const float *coef_idx;      // device [8][8][8][3] voxels, or nullptr
@@ -91,6 +94,7 @@ cudaError_t launch_count_samples(const FwdArgs &a, unsigned long long *out);
 
 struct BpArgs {
     const Grid *grid;
+    const Atlas *atlas = nullptr;  // correction images uploaded into a texture atlas, or nullptr
     const ViewGPU *views;
     const int *view_idx;
     int n_idx;

@@ -10,6 +10,7 @@
 // tiles): the CTAs resident at one time cover a band of detector rows across
 // many views, whose rays all cross the same z-slab of the volume, so that
 // slab stays in L2 while it is being sampled.
+#include "atlas.cuh"
 #include "ray.cuh"
 
 namespace ctrex {
@@ -19,11 +20,17 @@ constexpr int FWD_TY = 4;
 
 enum FwdMode { MODE_PROJECT = 0, MODE_CORRECT = 1 };
 
+template <typename TV>
+__device__ __forceinline__ float LinearSampler<TV>::operator()(float gx, float gy, float gz, float &wsum) const
+{
+    return trilinear(vol, nx, ny, nz, gx, gy, gz, wsum);
+}
+
 // Integral of one pixel (mean over its sub-angle rays): value and row sum.
-template <typename TV, bool MOTION>
+template <typename Sampler, bool MOTION>
 __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__restrict__ views,
                                                const MotionGPU &mo, const float *coef,
-                                               const TV *__restrict__ vol, int view, float u,
+                                               const Sampler &vol, int view, float u,
                                                float v, float &val, float &rs)
 {
     float acc = 0.0f, acc_rs = 0.0f;
@@ -46,7 +53,7 @@ __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__r
                 g[2] = y[2];
             }
             float ws;
-            a += trilinear(vol, G.nx, G.ny, G.nz, g[0], g[1], g[2], ws);
+            a += vol(g[0], g[1], g[2], ws);
             ars += ws;
         }
         a *= G.step_mm;
@@ -61,7 +68,7 @@ __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__r
                 g[2] = y[2];
             }
             float ws;
-            a = fmaf(R.w_last, trilinear(vol, G.nx, G.ny, G.nz, g[0], g[1], g[2], ws), a);
+            a = fmaf(R.w_last, vol(g[0], g[1], g[2], ws), a);
             ars = fmaf(R.w_last, ws, ars);
         }
         acc += a;
@@ -71,10 +78,10 @@ __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__r
     rs = acc_rs * G.inv_sub;
 }
 
-template <typename TV, typename TP, int MODE, bool MOTION>
+template <typename Sampler, typename TP, int MODE, bool MOTION>
 __global__ void __launch_bounds__(FWD_TX *FWD_TY)
     fwd_kernel(Grid G, const ViewGPU *__restrict__ views, const MotionGPU *__restrict__ motion,
-               const float *__restrict__ coef_g, const TV *__restrict__ vol,
+               const float *__restrict__ coef_g, const Sampler vol,
                const int *__restrict__ view_idx, TP *__restrict__ out, float *__restrict__ rowsum_out,
                const TP *__restrict__ p, float *__restrict__ partials, unsigned *devcheck)
 {
@@ -104,7 +111,7 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
     const bool in_pix = iu < G.nu && iv < G.nv;
     const bool inside = ok && in_pix;
     float val = 0.0f, rs = 0.0f;
-    if (inside) pixel_integral<TV, MOTION>(G, views, mo, coef, vol, view, (float)iu, (float)iv, val, rs);
+    if (inside) pixel_integral<Sampler, MOTION>(G, views, mo, coef, vol, view, (float)iu, (float)iv, val, rs);
     const size_t pix = ((size_t)k * G.nv + iv) * G.nu + iu;
     if (MODE == MODE_PROJECT) {
         if (in_pix) {  // a skipped (out-of-range) view gets zeros
@@ -209,36 +216,44 @@ int forward_partials_needed(const Grid &G, int n_idx)
     return (int)(g.x * g.y * g.z);
 }
 
-template <typename TV, typename TP, int MODE>
-static cudaError_t fwd_dispatch_motion(const FwdArgs &a, TP *out, float *rowsum, const TP *p,
-                                       float *partials)
+template <typename Sampler, typename TP, int MODE>
+static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, float *rowsum, const TP *p,
+                              float *partials)
 {
     const Grid &G = *a.grid;
     const dim3 grid = fwd_grid(G, a.n_idx), block(FWD_TX, FWD_TY);
-    const TV *vol = static_cast<const TV *>(a.vol);
     if (a.motion)
-        fwd_kernel<TV, TP, MODE, true><<<grid, block, 0, a.stream>>>(
-            G, a.views, a.motion, a.coef_idx, vol, a.view_idx, out, rowsum, p, partials, a.devcheck);
+        fwd_kernel<Sampler, TP, MODE, true><<<grid, block, 0, a.stream>>>(
+            G, a.views, a.motion, a.coef_idx, smp, a.view_idx, out, rowsum, p, partials, a.devcheck);
     else
-        fwd_kernel<TV, TP, MODE, false><<<grid, block, 0, a.stream>>>(
-            G, a.views, nullptr, nullptr, vol, a.view_idx, out, rowsum, p, partials, a.devcheck);
+        fwd_kernel<Sampler, TP, MODE, false><<<grid, block, 0, a.stream>>>(
+            G, a.views, nullptr, nullptr, smp, a.view_idx, out, rowsum, p, partials, a.devcheck);
     return cudaGetLastError();
+}
+
+// Texture-atlas sampling when the context has uploaded the volume into one;
+// row-major loads otherwise (volumes beyond the 2D texture limits).
+template <typename TP, int MODE>
+static cudaError_t fwd_dispatch_sampler(const FwdArgs &a, TP *out, float *rowsum, const TP *p, float *partials)
+{
+    if (a.atlas) return fwd_launch<AtlasSampler, TP, MODE>(a, AtlasSampler{*a.atlas}, out, rowsum, p, partials);
+    const Grid &G = *a.grid;
+    if (a.vol_dtype == CTREX_F32)
+        return fwd_launch<LinearSampler<float>, TP, MODE>(
+            a, LinearSampler<float>{static_cast<const float *>(a.vol), G.nx, G.ny, G.nz}, out, rowsum, p, partials);
+    return fwd_launch<LinearSampler<__nv_bfloat16>, TP, MODE>(
+        a, LinearSampler<__nv_bfloat16>{static_cast<const __nv_bfloat16 *>(a.vol), G.nx, G.ny, G.nz}, out, rowsum,
+        p, partials);
 }
 
 template <int MODE>
 static cudaError_t fwd_dispatch(const FwdArgs &a, int pdt, void *out, float *rowsum, const void *p,
                                 float *partials)
 {
-    if (a.vol_dtype == CTREX_F32) {
-        if (pdt == CTREX_F32)
-            return fwd_dispatch_motion<float, float, MODE>(a, (float *)out, rowsum, (const float *)p, partials);
-        return fwd_dispatch_motion<float, __nv_bfloat16, MODE>(a, (__nv_bfloat16 *)out, rowsum,
-                                                                (const __nv_bfloat16 *)p, partials);
-    }
     if (pdt == CTREX_F32)
-        return fwd_dispatch_motion<__nv_bfloat16, float, MODE>(a, (float *)out, rowsum, (const float *)p, partials);
-    return fwd_dispatch_motion<__nv_bfloat16, __nv_bfloat16, MODE>(a, (__nv_bfloat16 *)out, rowsum,
-                                                                    (const __nv_bfloat16 *)p, partials);
+        return fwd_dispatch_sampler<float, MODE>(a, (float *)out, rowsum, (const float *)p, partials);
+    return fwd_dispatch_sampler<__nv_bfloat16, MODE>(a, (__nv_bfloat16 *)out, rowsum, (const __nv_bfloat16 *)p,
+                                                     partials);
 }
 
 cudaError_t launch_forward(const FwdArgs &a, void *proj, int proj_dtype, float *rowsum)
