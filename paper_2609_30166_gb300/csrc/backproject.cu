@@ -18,18 +18,21 @@ constexpr int BP_TX = 32, BP_TY = 4, BP_TZ = 2;
 constexpr int BP_THREADS = BP_TX * BP_TY * BP_TZ;
 constexpr int BP_CHUNK = 128;
 
-// Bilinear sample of correction image k at (u, v), zero outside the detector
-// (taps outside get zero weight); returns the sample, wsum = in-range weight.
+// Bilinear sample of one correction image at (u, v) = (iu + au, iv + av),
+// zero outside the detector (taps outside get zero weight).  A Slot holds what
+// a view's image needs (its base pointer or atlas tile origin); slots are
+// computed once per view and staged in shared memory with the matrices.
 template <typename TR>
 struct LinearImages {
     const TR *r;
     int nu, nv;
-    __device__ __forceinline__ float operator()(int k, int iu, int iv, float wu0, float wu1, float wv0,
-                                                float wv1) const
+    typedef const TR *Slot;
+    __device__ __forceinline__ Slot slot(int k) const { return r + (size_t)k * nu * nv; }
+    __device__ __forceinline__ float operator()(Slot img, int iu, int iv, float, float, float wu0, float wu1,
+                                                float wv0, float wv1) const
     {
         const int u0 = max(iu, 0), u1 = min(iu + 1, nu - 1);
         const int v0 = max(iv, 0), v1 = min(iv + 1, nv - 1);
-        const TR *img = r + (size_t)k * nu * nv;
         const float r00 = Storage<TR>::load(img + v0 * nu + u0);
         const float r01 = Storage<TR>::load(img + v0 * nu + u1);
         const float r10 = Storage<TR>::load(img + v1 * nu + u0);
@@ -38,14 +41,33 @@ struct LinearImages {
     }
 };
 
-// The same sample from a texture atlas of the images: one gather.
+// The same sample from a texture atlas of the images: one gather, addressed
+// at the footprint's shared corner (tile origin + floor(u) + 1, ...).
 struct AtlasImages {
     Atlas A;
-    __device__ __forceinline__ float operator()(int k, int iu, int iv, float wu0, float wu1, float wv0,
-                                                float wv1) const
+    typedef float2 Slot;
+    __device__ __forceinline__ Slot slot(int k) const
+    {
+        k = min(max(k, 0), A.n - 1);
+        return make_float2((float)((k & ((1 << A.tshift) - 1)) * A.w) + 1.0f, (float)((k >> A.tshift) * A.h) + 1.0f);
+    }
+    __device__ __forceinline__ float operator()(Slot o, int, int, float fu, float fv, float wu0, float wu1,
+                                                float wv0, float wv1) const
     {
         float c00, c10, c01, c11;
-        atlas_quad(A, k, iu, iv, c00, c10, c01, c11);
+        if (A.bf16) {
+            const ushort4 q = tex2Dgather<ushort4>(A.tex, o.x + fu, o.y + fv, 0);
+            c01 = __uint_as_float((unsigned)q.x << 16);
+            c11 = __uint_as_float((unsigned)q.y << 16);
+            c10 = __uint_as_float((unsigned)q.z << 16);
+            c00 = __uint_as_float((unsigned)q.w << 16);
+        } else {
+            const float4 q = tex2Dgather<float4>(A.tex, o.x + fu, o.y + fv, 0);
+            c01 = q.x;
+            c11 = q.y;
+            c10 = q.z;
+            c00 = q.w;
+        }
         return fmaf(wv0, fmaf(wu0, c00, wu1 * c10), wv1 * fmaf(wu0, c01, wu1 * c11));
     }
 };
@@ -57,7 +79,7 @@ __global__ void __launch_bounds__(BP_THREADS)
               int accumulate)
 {
     __shared__ float4 sP[BP_CHUNK][3];
-    __shared__ int sImg[BP_CHUNK];
+    __shared__ typename Images::Slot sImg[BP_CHUNK];
     const int tid = (threadIdx.z * BP_TY + threadIdx.y) * BP_TX + threadIdx.x;
     const int ix = blockIdx.x * BP_TX + threadIdx.x;
     const int iy = blockIdx.y * BP_TY + threadIdx.y;
@@ -81,7 +103,7 @@ __global__ void __launch_bounds__(BP_THREADS)
             sP[t][1] = make_float4(P[4], P[5], P[6], P[7]);
             // an invalid view index gets a zero depth row: it is skipped
             sP[t][2] = ok ? make_float4(P[8], P[9], P[10], P[11]) : make_float4(0.f, 0.f, 0.f, 0.f);
-            sImg[t] = k;
+            sImg[t] = img.slot(k);
         }
         __syncthreads();
         if (!inside) continue;
@@ -102,7 +124,7 @@ __global__ void __launch_bounds__(BP_THREADS)
             const float wu1 = iu + 1 < nu ? au : 0.0f;
             const float wv0 = iv >= 0 ? 1.0f - av : 0.0f;
             const float wv1 = iv + 1 < nv ? av : 0.0f;
-            b += img(sImg[m], iu, iv, wu0, wu1, wv0, wv1);
+            b += img(sImg[m], iu, iv, fu, fv, wu0, wu1, wv0, wv1);
             c += (wu0 + wu1) * (wv0 + wv1);
         }
     }
