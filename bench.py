@@ -125,6 +125,27 @@ def l2_copy_bandwidth(device, mib=16, iters=200):
     return 2.0 * a.numel() * 4 * iters / (s.elapsed_time(e) / 1e3) / 1e9
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
+# launch of the fused forward kernel, from the one-pass ncu capture summarised
+# in profiles/fwd_kernel_perturbed512.md.  Valid only for the kernel sources it
+# was taken on (hash below) and for the FP32 workload; otherwise null.
+FWD_TRAFFIC_BYTES = 2338817536 + 1697584384
+FWD_TRAFFIC_SOURCES = ("project.cu", "atlas.cuh", "ray.cuh")
+FWD_TRAFFIC_HASH = "e8efdb05700c6823"
+
+
+def fwd_traffic(dtype, views):
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in FWD_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2609_30166_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != FWD_TRAFFIC_HASH or dtype != "f32" or views:
+        return None
+    return FWD_TRAFFIC_BYTES
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -290,7 +311,7 @@ def run_ours(args):
         "kernel_ms": {"fwd_correct": statistics.mean(fwd_ms), "back_project": statistics.mean(bp_ms)},
         "residual_after": res,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": fwd_traffic(args.dtype, args.views),
                      "kernel": "fwd_kernel (fused forward + correction)",
                      "l2_gather": {"peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
                                    "peak_method": "torch copy of 16 MiB buffers resident in L2, read+write bytes"},

@@ -1,0 +1,87 @@
+"""Parity at the benchmark's full size (perturbed circular cone beam, 512^3
+volume, 768^2 detector, 720 views), through the same launches bench.py times.
+
+The oracle cannot project the whole workload in FP64, so outputs are checked
+on samples it computes one by one: ray integrals and corrections at sampled
+pixels of every part of the detector, and backprojected sums at sampled voxels
+(the oracle backprojects the GPU's own correction images, which are inputs to
+that step).  FP64 positions of the 512^3 geometry sit ~3200 voxels from the
+source; the FP32 kernels form every sample relative to a point near the
+volume, which keeps the projector within the FP32 tolerance below.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_30166_gb300 import inputs
+from tests.helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def full():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_30166_gb300 import _build, ctrex
+
+    _build.build_library()
+    cfg = inputs.PERTURBED_512
+    P = inputs.projection_matrices(cfg)
+    ctx = ctrex.context_for(cfg, P=P)
+    phantom = inputs.phantom(cfg, device="cuda").to(torch.float32).contiguous()
+    p = ctx.fwd_project(phantom)
+    vol64 = phantom.double().cpu().numpy()
+    pb = oracle.Problem(P, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin, (cfg.nu, cfg.nv), cfg.step_vox)
+    rng = np.random.default_rng(512)
+    n = 240
+    views = rng.integers(0, cfg.n_views, n).astype(np.int32)
+    iu = rng.integers(0, cfg.nu, n)
+    iv = rng.integers(0, cfg.nv, n)
+    return cfg, P, ctx, phantom, p, vol64, pb, views, iu, iv
+
+
+def test_fullsize_forward_sampled_rays(full):
+    cfg, P, ctx, phantom, p, vol64, pb, views, iu, iv = full
+    ref, rs = oracle.forward_rays(pb, vol64, views, iu.astype(float), iv.astype(float))
+    got = p[torch.as_tensor(views, dtype=torch.long), torch.as_tensor(iv), torch.as_tensor(iu)].double().cpu().numpy()
+    assert (ref > 0).sum() > 100  # most sampled rays cross the object
+    err = rel_l2(got, ref)
+    print(f"full-size forward, {len(views)} sampled rays: rel.L2 {err:.3e}")
+    assert err <= TOL32
+
+
+def test_fullsize_correction_and_backprojection(full):
+    cfg, P, ctx, phantom, p, vol64, pb, views, iu, iv = full
+    x = (phantom * 0.9).contiguous()
+    r, sums = ctx.fwd_correct(x, p)
+    # correction at the sampled pixels: R_i (p_i - (A x)_i)
+    x64 = x.double().cpu().numpy()
+    q, rs = oracle.forward_rays(pb, x64, views, iu.astype(float), iv.astype(float))
+    del x64
+    pv = p[torch.as_tensor(views, dtype=torch.long), torch.as_tensor(iv), torch.as_tensor(iu)].double().cpu().numpy()
+    r_ref = np.where(rs > pb.eps_R, (pv - q) / np.where(rs > 0, rs, 1.0), 0.0)
+    r_got = r[torch.as_tensor(views, dtype=torch.long), torch.as_tensor(iv), torch.as_tensor(iu)].double().cpu().numpy()
+    # p - A x cancels (here it is ~10 % of p), so the error is measured against
+    # the scale of the operands, R p: the projector's FP32 tolerance carried over
+    scale = np.where(rs > pb.eps_R, pv / np.where(rs > 0, rs, 1.0), 0.0)
+    err_r = float(np.linalg.norm(r_got - r_ref) / np.linalg.norm(scale))
+    print(f"full-size correction, sampled pixels: |dr| / |R p| = {err_r:.3e} (rel.L2 {rel_l2(r_got, r_ref):.3e})")
+    assert err_r <= TOL32
+    # backprojection of the GPU's correction images at sampled voxels
+    b = ctx.back_project(r, normalize=False, accumulate=False)
+    c = ctx.back_project(torch.ones_like(r), normalize=False, accumulate=False)
+    rng = np.random.default_rng(7)
+    vox = rng.integers(0, cfg.n ** 3, 48)
+    r64 = r.double().cpu().numpy()
+    b_ref, c_ref = oracle.backproject_voxels(pb, r64, vox)
+    del r64
+    bg = b.flatten()[torch.as_tensor(vox)].double().cpu().numpy()
+    cg = c.flatten()[torch.as_tensor(vox)].double().cpu().numpy()
+    err_b, err_c = rel_l2(bg, b_ref), rel_l2(cg, c_ref)
+    print(f"full-size backprojection, sampled voxels: b rel.L2 {err_b:.3e}, c rel.L2 {err_c:.3e}")
+    assert err_b <= TOL32 and err_c <= TOL32
