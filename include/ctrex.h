@@ -239,6 +239,37 @@ int ctrex_sirt_host(ctrex_ctx *ctx, void *vol_host, int vol_dtype, const void *p
 int ctrex_count_samples(ctrex_ctx *ctx, const int *view_idx, int n_idx, long long *out);
 
 /*
+ * 3x3x3 convolution, stride 1, zero padding 1 ("same"), as an implicit GEMM
+ * on the tcgen05 tensor cores: BF16 operands, FP32 accumulation.  Used by the
+ * learned warm start (a 3D U-Net); the paper motivates learned components
+ * next to the physics operators (Sec. 5) but specifies none.
+ *   x       DEVICE bf16 [nb][d][h][w][cin] (channels last).
+ *   wt      DEVICE bf16 [cout][27][cin], tap = kz*9 + ky*3 + kx (k = 0..2
+ *           for offsets -1..+1).
+ *   bias    DEVICE float [cout] or NULL.
+ *   y       DEVICE [nb][d][h][w][cout] of y_dtype (CTREX_F32 or CTREX_BF16),
+ *           overwritten with max(conv + bias, 0) if relu else conv + bias.
+ *   status  DEVICE int, set to 1 if a tensor-core completion wait expired
+ *           (the result is then invalid); never cleared by the library.
+ *   stream  cudaStream_t (NULL = legacy default stream).
+ * The input gradient is this same call on dy with the flipped, transposed
+ * weights wt'[ci][26 - tap][co].  Errors: CTREX_E_ARG, CTREX_E_DTYPE,
+ * CTREX_E_SHAPE, CTREX_E_CUDA.
+ */
+int ctrex_conv3d_fwd(const void *x, const void *wt, const float *bias, void *y, int y_dtype, int nb, int d,
+                     int h, int w, int cin, int cout, int relu, int *status, void *cuda_stream);
+
+/*
+ * Weight gradient of ctrex_conv3d_fwd: dw[co][tap][ci] += sum over voxels of
+ * dy[voxel][co] * x[voxel + offset(tap)][ci] (zero outside).  The voxel sum
+ * is split across CTAs and added with FP32 atomics (not bitwise
+ * reproducible).  x bf16 [nb][d][h][w][cin], dy bf16 [nb][d][h][w][cout],
+ * dw DEVICE float [cout][27][cin] (accumulated: zero it first).
+ */
+int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, int h, int w, int cin,
+                       int cout, int *status, void *cuda_stream);
+
+/*
  * Detector-space correction without any allocation.  The paper has no
  * counterpart: this is an extra entry point for callers that cannot let the
  * library call cudaMalloc (a host whose caching allocator already reserved

@@ -1,0 +1,507 @@
+// conv_tc.cu -- 3x3x3 convolution (stride 1, zero "same" padding) as an
+// implicit GEMM on the 5th-generation tensor cores (tcgen05, sm_103a), for
+// the learned warm start (a 3D U-Net).  BF16 operands, FP32 accumulation in
+// tensor memory (TMEM).  The paper has no such operator; it motivates learned
+// components combined with the physics operators (Sec. 5).
+//
+// One kernel computes C[M][N] = sum_k A[M][k] B[N][k] tile by tile:
+//   * M tile 128 (one UMMA row block, cta_group::1), N tile = BN in {16..128},
+//     K staged 64 elements (one 128-byte row per operand row) at a time;
+//   * operands are gathered from global memory by the CTA's 128 threads
+//     (implicit im2col, so no TMA tiled box fits them) and written straight
+//     into the 128-byte-swizzled K-major shared-memory layout the UMMA
+//     descriptors describe; two stages, so the gather of chunk c+1 overlaps
+//     the MMAs of chunk c;
+//   * one thread issues four tcgen05.mma (K = 16 each) per chunk and commits
+//     them to the stage's mbarrier; the accumulator tile lives in TMEM and is
+//     read back with tcgen05.ld by the four warps (one row per thread) for
+//     the epilogue.
+// Three operand layouts use it:
+//   FWD   A = im2col(x)[m][(tap, ci)], B = w[co][(tap, ci)], C -> y[m][co]
+//         (+ bias, optional ReLU);  m runs over N*D*H*W output voxels (NDHWC).
+//   DGRAD the same with dy as input and the flipped, transposed weights
+//         w'[ci][(tap, co)] (prepared by the caller): dx = conv(dy, w').
+//   WGRAD A = im2col(x)^T[(tap, ci)][m], B = dy^T[co][m]: K runs over voxels,
+//         split across CTAs, partial tiles added to dw[co][(tap, ci)] (FP32).
+// Every wait on an mbarrier is bounded; on expiry the kernel records an error
+// in the status word, releases its TMEM and returns.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "ctrex.h"
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr int STAGES = 2;
+constexpr int THREADS = 128;
+constexpr long long WAIT_LIMIT = 1LL << 26;
+
+enum Op { OP_FWD = 0, OP_WGRAD = 1 };
+
+struct ConvShape {
+    int nb, d, h, w;   // batch and spatial size (NDHWC)
+    int cin, cout;     // channels of the conv input / output (for WGRAD: of x and dy)
+    int relu;          // FWD epilogue
+    long long m_total; // GEMM M (FWD: voxels) / rows of A (WGRAD: 27 * cin)
+    int n_total;       // GEMM N (FWD: cout; WGRAD: cout)
+    long long k_total; // GEMM K (FWD: 27 * cin; WGRAD: voxels)
+    long long k_per_cta;  // WGRAD split-K range per CTA (multiple of BK)
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Bounded wait for the given phase parity; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    const uint32_t a = smem_addr(bar);
+    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, bool accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(id), "r"((uint32_t)accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of 16-byte chunk j of row r in a 128B-swizzled K-major tile.
+__device__ __forceinline__ uint32_t swz(int r, int j) { return (uint32_t)(r * 128 + ((j ^ (r & 7)) << 4)); }
+
+// -------- operand loaders (write one BK-wide chunk of a tile into smem) ----
+
+// A for FWD: row r <-> voxel m0 + r (coordinates decoded once per CTA by the
+// caller into rc = {n, z, y, x}, n < 0 for rows past the end); columns
+// k = (tap, ci), tap = kz*9 + ky*3 + kx.
+__device__ __forceinline__ void load_im2col_rows(const __nv_bfloat16 *__restrict__ x, const ConvShape &S,
+                                                 const int4 rc, long long k0, uint8_t *tile)
+{
+    const int r = threadIdx.x;
+    const bool mrow = rc.x >= 0;
+    const int cin = S.cin;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const long long kb = k0 + 8 * j;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (mrow && (cin & 7) == 0) {
+            const int tap = (int)(kb / cin), ci = (int)(kb - (long long)tap * cin);
+            if (tap < 27) {
+                const int zz = rc.y + tap / 9 - 1, yy = rc.z + (tap / 3) % 3 - 1, xs = rc.w + tap % 3 - 1;
+                if ((unsigned)zz < (unsigned)S.d && (unsigned)yy < (unsigned)S.h && (unsigned)xs < (unsigned)S.w)
+                    v = __ldg(reinterpret_cast<const uint4 *>(
+                        x + ((((long long)rc.x * S.d + zz) * S.h + yy) * S.w + xs) * cin + ci));
+            }
+        } else if (mrow) {
+            __nv_bfloat16 e[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                e[q] = __float2bfloat16_rn(0.0f);
+                const long long k = kb + q;
+                const int tap = (int)(k / cin), ci = (int)(k - (long long)tap * cin);
+                if (tap < 27) {
+                    const int zz = rc.y + tap / 9 - 1, yy = rc.z + (tap / 3) % 3 - 1, xs = rc.w + tap % 3 - 1;
+                    if ((unsigned)zz < (unsigned)S.d && (unsigned)yy < (unsigned)S.h && (unsigned)xs < (unsigned)S.w)
+                        e[q] = x[((((long long)rc.x * S.d + zz) * S.h + yy) * S.w + xs) * cin + ci];
+                }
+            }
+            v = *reinterpret_cast<const uint4 *>(e);
+        }
+        *reinterpret_cast<uint4 *>(tile + swz(r, j)) = v;
+    }
+}
+
+// B for FWD: rows n0 .. n0+BN of a row-major [N][K] matrix (K = ktot).
+template <int BN>
+__device__ __forceinline__ void load_rows_kmajor(const __nv_bfloat16 *__restrict__ w, long long ktot, int nrows,
+                                                 int n0, long long k0, uint8_t *tile)
+{
+    for (int i = threadIdx.x; i < BN * 8; i += THREADS) {
+        const int r = i >> 3, j = i & 7;
+        const long long kb = k0 + 8 * j;
+        const int row = n0 + r;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (row < nrows) {
+            const __nv_bfloat16 *src = w + (long long)row * ktot + kb;
+            if ((ktot & 7) == 0 && kb + 8 <= ktot) {
+                v = __ldg(reinterpret_cast<const uint4 *>(src));
+            } else {
+                __nv_bfloat16 e[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) e[q] = (kb + q < ktot) ? src[q] : __float2bfloat16_rn(0.0f);
+                v = *reinterpret_cast<const uint4 *>(e);
+            }
+        }
+        *reinterpret_cast<uint4 *>(tile + swz(r, j)) = v;
+    }
+}
+
+// A for WGRAD: row r <-> (tap, ci) = q0 + r; columns = voxels m in [k0, k0+64),
+// walked in order (x fastest) from one decoded start voxel.
+__device__ __forceinline__ void load_im2col_cols(const __nv_bfloat16 *__restrict__ x, const ConvShape &S, long long q0,
+                                                 long long k0, uint8_t *tile)
+{
+    const int r = threadIdx.x;
+    const long long q = q0 + r;
+    const int cin = S.cin;
+    const bool qrow = q < 27LL * cin;
+    const int tap = qrow ? (int)(q / cin) : 0, ci = qrow ? (int)(q - (long long)tap * cin) : 0;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    long long u = k0;
+    int xx = (int)(u % S.w);
+    u /= S.w;
+    int y = (int)(u % S.h);
+    u /= S.h;
+    int z = (int)(u % S.d);
+    int n = (int)(u / S.d);
+    long long m = k0;
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) {
+        __nv_bfloat16 e[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            e[t] = __float2bfloat16_rn(0.0f);
+            if (qrow && m < S.k_total) {
+                const int zz = z + dz, yy = y + dy, xs = xx + dx;
+                if ((unsigned)zz < (unsigned)S.d && (unsigned)yy < (unsigned)S.h && (unsigned)xs < (unsigned)S.w)
+                    e[t] = x[((((long long)n * S.d + zz) * S.h + yy) * S.w + xs) * cin + ci];
+            }
+            ++m;
+            if (++xx == S.w) {
+                xx = 0;
+                if (++y == S.h) {
+                    y = 0;
+                    if (++z == S.d) {
+                        z = 0;
+                        ++n;
+                    }
+                }
+            }
+        }
+        *reinterpret_cast<uint4 *>(tile + swz(r, j)) = *reinterpret_cast<const uint4 *>(e);
+    }
+}
+
+// B for WGRAD: row r <-> output channel co = n0 + r; columns = voxels.
+template <int BN>
+__device__ __forceinline__ void load_dy_cols(const __nv_bfloat16 *__restrict__ dy, const ConvShape &S, int n0,
+                                             long long k0, uint8_t *tile)
+{
+    for (int i = threadIdx.x; i < BN * 8; i += THREADS) {
+        const int r = i % BN, j = i / BN;
+        const int co = n0 + r;
+        __nv_bfloat16 e[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const long long m = k0 + 8 * j + t;
+            e[t] = (co < S.cout && m < S.k_total) ? dy[m * S.cout + co] : __float2bfloat16_rn(0.0f);
+        }
+        *reinterpret_cast<uint4 *>(tile + swz(r, j)) = *reinterpret_cast<const uint4 *>(e);
+    }
+}
+
+// ------------------------------- the kernel --------------------------------
+
+template <int OP, int BN>
+__global__ void __launch_bounds__(THREADS) conv_tc_kernel(const __nv_bfloat16 *__restrict__ a_src,
+                                                          const __nv_bfloat16 *__restrict__ b_src,
+                                                          const float *__restrict__ bias, void *__restrict__ out,
+                                                          int out_bf16, ConvShape S, int *__restrict__ status)
+{
+    constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
+    constexpr int TMEM_COLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : 128);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;                         // STAGES x A_BYTES
+    uint8_t *sB = smem + STAGES * A_BYTES;      // STAGES x B_BYTES
+    __shared__ uint64_t bars[STAGES];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int failed_s;
+
+    const int warp = threadIdx.x >> 5;
+    const long long m0 = (long long)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    long long k_begin = 0, k_end = S.k_total;
+    if (OP == OP_WGRAD) {
+        k_begin = (long long)blockIdx.z * S.k_per_cta;
+        k_end = k_begin + S.k_per_cta < S.k_total ? k_begin + S.k_per_cta : S.k_total;
+    }
+    const int nk = (int)((k_end - k_begin + BK - 1) / BK);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed_s = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base_s)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tmem_base_s;
+    constexpr uint32_t ID = idesc(BN);
+
+    int4 rc = make_int4(-1, 0, 0, 0);  // FWD: this thread's output voxel (n, z, y, x)
+    if (OP == OP_FWD) {
+        const long long m = m0 + threadIdx.x;
+        if (m < S.m_total) {
+            long long t = m;
+            rc.w = (int)(t % S.w);
+            t /= S.w;
+            rc.z = (int)(t % S.h);
+            t /= S.h;
+            rc.y = (int)(t % S.d);
+            rc.x = (int)(t / S.d);
+        }
+    }
+    bool ok = true;
+    int committed = -1;
+    for (int c = 0; c < nk; ++c) {
+        const int s = c % STAGES;
+        if (c >= STAGES) {
+            // the MMAs that read this stage two chunks ago must be done
+            if (!mbar_wait(&bars[s], (unsigned)((c / STAGES - 1) & 1))) ok = false;
+        }
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        const long long k0 = k_begin + (long long)c * BK;
+        if (OP == OP_FWD) {
+            load_im2col_rows(a_src, S, rc, k0, sA + s * A_BYTES);
+            load_rows_kmajor<BN>(b_src, S.k_total, S.n_total, n0, k0, sB + s * B_BYTES);
+        } else {
+            load_im2col_cols(a_src, S, m0, k0, sA + s * A_BYTES);
+            load_dy_cols<BN>(b_src, S, n0, k0, sB + s * B_BYTES);
+        }
+        fence_async_smem();
+        tc_before_sync();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_after_sync();
+            const uint32_t a_base = smem_addr(sA + s * A_BYTES), b_base = smem_addr(sB + s * B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                umma_bf16(tmem, sdesc(a_base + 32 * kk), sdesc(b_base + 32 * kk), ID, c > 0 || kk > 0);
+            umma_commit(&bars[s]);
+        }
+        committed = c;
+    }
+    if (ok && nk > 0) {
+        const int last = nk - 1;
+        if (!mbar_wait(&bars[last % STAGES], (unsigned)((last / STAGES) & 1))) ok = false;
+    }
+    ok = __syncthreads_and(ok);
+    tc_after_sync();
+    if (ok && nk > 0) {
+        // epilogue: thread (warp w, lane l) owns accumulator row 32 w + l
+        const long long row = m0 + threadIdx.x;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(lane_addr + (uint32_t)c0, v);
+            if (row >= S.m_total) continue;
+            if (OP == OP_FWD) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int co = n0 + c0 + i;
+                    if (co >= S.n_total) continue;
+                    float y = v[i] + (bias ? bias[co] : 0.0f);
+                    if (S.relu) y = fmaxf(y, 0.0f);
+                    const long long o = row * S.n_total + co;
+                    if (out_bf16)
+                        static_cast<__nv_bfloat16 *>(out)[o] = __float2bfloat16_rn(y);
+                    else
+                        static_cast<float *>(out)[o] = y;
+                }
+            } else {
+                // row = (tap, ci); dw[co][(tap, ci)] += partial
+                const long long q = row;
+                const long long kq = 27LL * S.cin;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int co = n0 + c0 + i;
+                    if (co < S.cout && q < kq) atomicAdd(static_cast<float *>(out) + co * kq + q, v[i]);
+                }
+            }
+        }
+    } else if (nk > 0) {
+        // a wait expired: record it, and give the MMAs already committed a
+        // bounded chance to finish before the tensor memory is released
+        if (threadIdx.x == 0) {
+            atomicExch(status, 1);
+            if (committed >= 0) mbar_wait(&bars[committed % STAGES], (unsigned)((committed / STAGES) & 1));
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+template <int OP, int BN>
+cudaError_t launch_bn(const __nv_bfloat16 *a, const __nv_bfloat16 *b, const float *bias, void *out, int out_bf16,
+                      const ConvShape &S, int *status, cudaStream_t stream)
+{
+    const int smem = STAGES * (BM * 128 + BN * 128) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<OP, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((S.m_total + BM - 1) / BM), (unsigned)((S.n_total + BN - 1) / BN), 1);
+    if (OP == OP_WGRAD) grid.z = (unsigned)((S.k_total + S.k_per_cta - 1) / S.k_per_cta);
+    conv_tc_kernel<OP, BN><<<grid, THREADS, smem, stream>>>(a, b, bias, out, out_bf16, S, status);
+    return cudaGetLastError();
+}
+
+template <int OP>
+cudaError_t launch_op(int bn, const __nv_bfloat16 *a, const __nv_bfloat16 *b, const float *bias, void *out,
+                      int out_bf16, const ConvShape &S, int *status, cudaStream_t stream)
+{
+    switch (bn) {
+    case 16: return launch_bn<OP, 16>(a, b, bias, out, out_bf16, S, status, stream);
+    case 32: return launch_bn<OP, 32>(a, b, bias, out, out_bf16, S, status, stream);
+    case 48: return launch_bn<OP, 48>(a, b, bias, out, out_bf16, S, status, stream);
+    case 64: return launch_bn<OP, 64>(a, b, bias, out, out_bf16, S, status, stream);
+    case 96: return launch_bn<OP, 96>(a, b, bias, out, out_bf16, S, status, stream);
+    default: return launch_bn<OP, 128>(a, b, bias, out, out_bf16, S, status, stream);
+    }
+}
+
+// N tile: the smallest supported width covering n (multiples of 16), else 128.
+int pick_bn(int n)
+{
+    const int opts[] = {16, 32, 48, 64, 96, 128};
+    for (int o : opts)
+        if (n <= o) return o;
+    return 128;
+}
+
+bool shape_ok(int nb, int d, int h, int w, int cin, int cout)
+{
+    return nb >= 1 && d >= 1 && h >= 1 && w >= 1 && cin >= 1 && cout >= 1 && cin <= 4096 && cout <= 4096 &&
+           (long long)nb * d * h * w <= (1LL << 40);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ctrex_conv3d_fwd(const void *x, const void *w, const float *bias, void *y, int y_dtype, int nb, int d, int h,
+                     int wd, int cin, int cout, int relu, int *status, void *stream)
+{
+    if (!x || !w || !y || !status) return CTREX_E_ARG;
+    if (y_dtype != CTREX_F32 && y_dtype != CTREX_BF16) return CTREX_E_DTYPE;
+    if (!shape_ok(nb, d, h, wd, cin, cout)) return CTREX_E_SHAPE;
+    ConvShape S{};
+    S.nb = nb;
+    S.d = d;
+    S.h = h;
+    S.w = wd;
+    S.cin = cin;
+    S.cout = cout;
+    S.relu = relu ? 1 : 0;
+    S.m_total = (long long)nb * d * h * wd;
+    S.n_total = cout;
+    S.k_total = 27LL * cin;
+    S.k_per_cta = S.k_total;
+    const int bn = pick_bn(cout);
+    cudaError_t e = launch_op<OP_FWD>(bn, static_cast<const __nv_bfloat16 *>(x), static_cast<const __nv_bfloat16 *>(w),
+                                      bias, y, y_dtype == CTREX_BF16, S, status, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CTREX_OK : CTREX_E_CUDA;
+}
+
+int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, int h, int wd, int cin, int cout,
+                       int *status, void *stream)
+{
+    if (!x || !dy || !dw || !status) return CTREX_E_ARG;
+    if (!shape_ok(nb, d, h, wd, cin, cout)) return CTREX_E_SHAPE;
+    ConvShape S{};
+    S.nb = nb;
+    S.d = d;
+    S.h = h;
+    S.w = wd;
+    S.cin = cin;
+    S.cout = cout;
+    S.m_total = 27LL * cin;
+    S.n_total = cout;
+    S.k_total = (long long)nb * d * h * wd;
+    // split K so that the grid fills the GPU about twice
+    const long long mt = (S.m_total + BM - 1) / BM;
+    long long splits = (2 * 152 + mt - 1) / mt;
+    long long per = (S.k_total + splits - 1) / splits;
+    per = ((per + BK - 1) / BK) * BK;
+    if (per < BK) per = BK;
+    S.k_per_cta = per;
+    const int bn = pick_bn(cout);
+    cudaError_t e = launch_op<OP_WGRAD>(bn, static_cast<const __nv_bfloat16 *>(x),
+                                        static_cast<const __nv_bfloat16 *>(dy), nullptr, dw, 0, S, status,
+                                        static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? CTREX_OK : CTREX_E_CUDA;
+}
+
+}  // extern "C"

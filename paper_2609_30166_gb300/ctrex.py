@@ -31,6 +31,7 @@ EXPORTS = (
     "ctrex_device_status", "ctrex_set_geometry", "ctrex_set_motion", "ctrex_fwd_project",
     "ctrex_fwd_correct", "ctrex_back_project", "ctrex_adjoint_project", "ctrex_motion_grad",
     "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples", "ctrex_correct_static",
+    "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad",
 )
 
 # Largest n ctrex_correct_static accepts (its static scratch holds 65536 CTA partials of 8192 elements).
@@ -85,6 +86,8 @@ def load_library(path: str = LIB_PATH):
         "ctrex_sirt_host": ([vp, vp, i, vp, i, i, f, vp, f, fp, ip], i),
         "ctrex_count_samples": ([vp, vp, i, ctypes.POINTER(ctypes.c_longlong)], i),
         "ctrex_correct_static": ([vp, vp, vp, vp, i, ctypes.c_longlong, f, vp, vp], i),
+        "ctrex_conv3d_fwd": ([vp, vp, vp, vp, i, i, i, i, i, i, i, i, vp, vp], i),
+        "ctrex_conv3d_wgrad": ([vp, vp, vp, i, i, i, i, i, i, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -339,6 +342,71 @@ def correct_static(p, q, rowsum, r=None, sums=None, eps_R=0.0):
     if rc != OK:
         raise CtrexError(rc, f"ctrex_correct_static failed (n = {n})")
     return r, sums
+
+
+_conv_status = {}
+
+
+def _status(dev):
+    st = _conv_status.get(dev)
+    if st is None:
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        _conv_status[dev] = st
+    return st
+
+
+def conv_status_check(dev=None):
+    """Raise if a tensor-core completion wait expired in an earlier conv call."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if dev is None else dev
+    st = _status(dev)
+    if int(st.item()) != 0:
+        st.zero_()
+        raise CtrexError(-5, "a tcgen05 completion wait expired in a conv kernel")
+
+
+def conv3d(x, wt, bias=None, relu=False, out_dtype=torch.bfloat16):
+    """3x3x3 'same' convolution on the tensor cores.  x bf16 [N, D, H, W, Cin]
+    (channels last), wt bf16 [Cout, 27, Cin]; returns [N, D, H, W, Cout]."""
+    lib = load_library()
+    if x.dtype != torch.bfloat16 or wt.dtype != torch.bfloat16:
+        raise TypeError("conv3d takes bfloat16 x and weights")
+    if x.dim() != 5 or wt.dim() != 3 or wt.shape[1] != 27 or wt.shape[2] != x.shape[4]:
+        raise ValueError(f"conv3d: x {tuple(x.shape)}, wt {tuple(wt.shape)}")
+    x, wt = x.contiguous(), wt.contiguous()
+    nb, d, h, w, cin = x.shape
+    cout = wt.shape[0]
+    y = torch.empty((nb, d, h, w, cout), dtype=out_dtype, device=x.device)
+    if bias is not None:
+        bias = bias.float().contiguous()
+    stream = torch.cuda.current_stream(x.device).cuda_stream
+    rc = lib.ctrex_conv3d_fwd(_ptr(x), _ptr(wt), _ptr(bias), _ptr(y), _dt(y), nb, d, h, w, cin, cout, int(relu),
+                              _ptr(_status(x.device)), ctypes.c_void_p(stream))
+    if rc != OK:
+        raise CtrexError(rc, f"ctrex_conv3d_fwd failed for x {tuple(x.shape)}, wt {tuple(wt.shape)}")
+    return y
+
+
+def conv3d_wgrad(x, dy, dw=None):
+    """dw [Cout, 27, Cin] (float32, accumulated) of conv3d for input x and
+    output gradient dy (both bf16, channels last)."""
+    lib = load_library()
+    x, dy = x.contiguous(), dy.contiguous()
+    nb, d, h, w, cin = x.shape
+    cout = dy.shape[4]
+    if dw is None:
+        dw = torch.zeros((cout, 27, cin), dtype=torch.float32, device=x.device)
+    stream = torch.cuda.current_stream(x.device).cuda_stream
+    rc = lib.ctrex_conv3d_wgrad(_ptr(x), _ptr(dy), _ptr(dw), nb, d, h, w, cin, cout, _ptr(_status(x.device)),
+                                ctypes.c_void_p(stream))
+    if rc != OK:
+        raise CtrexError(rc, "ctrex_conv3d_wgrad failed")
+    return dw
+
+
+def flip_weights(wt):
+    """wt [Cout, 27, Cin] -> the weights of the input-gradient convolution,
+    [Cin, 27, Cout] with the taps reversed (a copy, no arithmetic)."""
+    return wt.flip(1).transpose(0, 2).contiguous()
 
 
 def context_for(cfg, P=None, device=None):

@@ -528,3 +528,51 @@ def test_geometry_rejects_singular_and_zero_depth():
     Pn, src, _ = oracle.setup_views(oracle_problem(cfg, P=-P))
     assert np.allclose(src[0, 0], [-inputs.SOD, 0, 0])
     assert np.allclose(Pn, P)
+
+
+# ---------------------------------------------------------------------------
+# Convolution oracle of the warm-start network: brute-force loops
+# ---------------------------------------------------------------------------
+
+def test_conv_oracle_matches_brute_force():
+    from oracle import conv
+
+    rng = np.random.default_rng(21)
+    nb, d, h, w, cin, cout = 2, 4, 3, 5, 2, 3
+    x = rng.normal(size=(nb, d, h, w, cin))
+    wt = rng.normal(size=(cout, 27, cin))
+    bias = rng.normal(size=cout)
+    y = conv.conv3d(x, wt, bias)
+    ref = np.zeros((nb, d, h, w, cout))
+    for n in range(nb):
+        for z in range(d):
+            for yy in range(h):
+                for xx in range(w):
+                    for co in range(cout):
+                        s = bias[co]
+                        for kz in range(3):
+                            for ky in range(3):
+                                for kx in range(3):
+                                    zz, y2, x2 = z + kz - 1, yy + ky - 1, xx + kx - 1
+                                    if 0 <= zz < d and 0 <= y2 < h and 0 <= x2 < w:
+                                        s += wt[co, kz * 9 + ky * 3 + kx] @ x[n, zz, y2, x2]
+                        ref[n, z, yy, xx, co] = s
+    assert np.allclose(y, ref, atol=1e-12)
+    # gradients: dx equals the convolution of dy with flipped, transposed taps;
+    # dw by brute force
+    dy = rng.normal(size=(nb, d, h, w, cout))
+    dx, dw = conv.conv3d_grads(x, wt, dy)
+    wflip = np.ascontiguousarray(wt[:, ::-1, :].transpose(2, 1, 0))
+    assert np.allclose(dx, conv.conv3d(dy, wflip), atol=1e-12)
+    dw_ref = np.zeros_like(wt)
+    for co in range(cout):
+        for t in range(27):
+            kz, ky, kx = t // 9, (t // 3) % 3, t % 3
+            for n in range(nb):
+                for z in range(d):
+                    for yy in range(h):
+                        for xx in range(w):
+                            zz, y2, x2 = z + kz - 1, yy + ky - 1, xx + kx - 1
+                            if 0 <= zz < d and 0 <= y2 < h and 0 <= x2 < w:
+                                dw_ref[co, t] += dy[n, z, yy, xx, co] * x[n, zz, y2, x2]
+    assert np.allclose(dw, dw_ref, atol=1e-10)
