@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="64^3 workload (quick check)")
+    ap.add_argument("--warm-start-steps", type=int, default=250,
+                    help="train the U-Net warm start this many steps and report time to residual 1e-3 (0: skip)")
     ap.add_argument("--views", type=int, default=0,
                     help="override the number of views (small cases for ncu captures; not a bench line)")
     return ap.parse_args()
@@ -328,6 +330,20 @@ def run_ours(args):
                                                      bp_views=45 if not args.small else 90)
         out["cpu_baseline"] = {"value": ncpu_units / ncpu_s / 1e9, "unit": "GUPS", "cores": omp_threads(),
                                "kind": "oracle", "sample": desc}
+    if rank == 0 and world == 1 and args.warm_start_steps > 0 and not args.views and not args.small:
+        from paper_2609_30166_gb300 import warmstart
+
+        del x, r, p, phantom
+        torch.cuda.empty_cache()
+        ws = warmstart.run(n_train=40, n_test=4, steps=args.warm_start_steps)
+        out["time_to_residual_1e-3"] = {
+            "workload": ws["workload"], "tol": ws["tol"], "held_out_phantoms": ws["test_phantoms"],
+            "plain_sirt_s": ws["plain_s"], "plain_sirt_iters": ws["plain_iters"],
+            "warm_start_s": ws["warm_s"], "warm_start_iters": ws["warm_iters"],
+            "warm_over_plain_time": ws["warm_over_plain_time"],
+            "note": "warm start = 5 SIRT iterations + U-Net (tcgen05 convs) + SIRT; training "
+                    f"({ws['train_steps']} steps on {ws['train_phantoms']} phantoms, {ws['train_s']:.1f} s) not timed",
+        }
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

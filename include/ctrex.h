@@ -264,7 +264,8 @@ int ctrex_conv3d_fwd(const void *x, const void *wt, const float *bias, void *y, 
  * dy[voxel][co] * x[voxel + offset(tap)][ci] (zero outside).  The voxel sum
  * is split across CTAs and added with FP32 atomics (not bitwise
  * reproducible).  x bf16 [nb][d][h][w][cin], dy bf16 [nb][d][h][w][cout],
- * dw DEVICE float [cout][27][cin] (accumulated: zero it first).
+ * dw DEVICE float [cout][27][cin] (accumulated: zero it first).  cin and
+ * cout must be multiples of 8 (CTREX_E_SHAPE otherwise).
  */
 int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, int h, int w, int cin,
                        int cout, int *status, void *cuda_stream);

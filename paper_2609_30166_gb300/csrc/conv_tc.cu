@@ -195,67 +195,81 @@ __device__ __forceinline__ void load_rows_kmajor(const __nv_bfloat16 *__restrict
     }
 }
 
-// A for WGRAD: row r <-> (tap, ci) = q0 + r; columns = voxels m in [k0, k0+64),
-// walked in order (x fastest) from one decoded start voxel.
-__device__ __forceinline__ void load_im2col_cols(const __nv_bfloat16 *__restrict__ x, const ConvShape &S, long long q0,
-                                                 long long k0, uint8_t *tile)
+// Transposes an 8x8 block of BF16 held as 8 rows of 16 bytes (in[v] = eight
+// channels of voxel v) into out[c] = channel c of the eight voxels.
+__device__ __forceinline__ void transpose8x8(const uint4 in[8], uint4 out[8])
 {
-    const int r = threadIdx.x;
-    const long long q = q0 + r;
-    const int cin = S.cin;
-    const bool qrow = q < 27LL * cin;
-    const int tap = qrow ? (int)(q / cin) : 0, ci = qrow ? (int)(q - (long long)tap * cin) : 0;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    long long u = k0;
-    int xx = (int)(u % S.w);
-    u /= S.w;
-    int y = (int)(u % S.h);
-    u /= S.h;
-    int z = (int)(u % S.d);
-    int n = (int)(u / S.d);
-    long long m = k0;
-#pragma unroll 1
-    for (int j = 0; j < 8; ++j) {
-        __nv_bfloat16 e[8];
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(in);  // w[4 v + c / 2]
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            e[t] = __float2bfloat16_rn(0.0f);
-            if (qrow && m < S.k_total) {
-                const int zz = z + dz, yy = y + dy, xs = xx + dx;
-                if ((unsigned)zz < (unsigned)S.d && (unsigned)yy < (unsigned)S.h && (unsigned)xs < (unsigned)S.w)
-                    e[t] = x[((((long long)n * S.d + zz) * S.h + yy) * S.w + xs) * cin + ci];
-            }
-            ++m;
-            if (++xx == S.w) {
-                xx = 0;
-                if (++y == S.h) {
-                    y = 0;
-                    if (++z == S.d) {
-                        z = 0;
-                        ++n;
-                    }
-                }
-            }
-        }
-        *reinterpret_cast<uint4 *>(tile + swz(r, j)) = *reinterpret_cast<const uint4 *>(e);
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t sel = (c & 1) ? 0x7632u : 0x5410u;
+        uint32_t o[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) o[p] = __byte_perm(w[4 * (2 * p) + c / 2], w[4 * (2 * p + 1) + c / 2], sel);
+        out[c] = make_uint4(o[0], o[1], o[2], o[3]);
     }
 }
 
-// B for WGRAD: row r <-> output channel co = n0 + r; columns = voxels.
-template <int BN>
-__device__ __forceinline__ void load_dy_cols(const __nv_bfloat16 *__restrict__ dy, const ConvShape &S, int n0,
-                                             long long k0, uint8_t *tile)
+// Decodes voxel m (x fastest) of the NDHWC grid.
+__device__ __forceinline__ void decode_voxel(const ConvShape &S, long long m, int &n, int &z, int &y, int &x)
 {
-    for (int i = threadIdx.x; i < BN * 8; i += THREADS) {
-        const int r = i % BN, j = i / BN;
-        const int co = n0 + r;
-        __nv_bfloat16 e[8];
+    long long u = m;
+    x = (int)(u % S.w);
+    u /= S.w;
+    y = (int)(u % S.h);
+    u /= S.h;
+    z = (int)(u % S.d);
+    n = (int)(u / S.d);
+}
+
+// WGRAD operands (K = voxels, both stored channels-last): each 8 x 8 block of
+// (8 rows = channels) x (8 voxels) is read as eight 16-byte channel vectors,
+// one per voxel, and transposed in registers into the K-major tile.
+//   A: rows (tap, ci) = q0 + r, value x[voxel + offset(tap)][ci];
+//   B: rows co = n0 + r,        value dy[voxel][co].
+// Channel counts must be multiples of 8 (the caller checks).
+template <bool IS_A, int ROWS>
+__device__ __forceinline__ void load_kvoxel_blocks(const __nv_bfloat16 *__restrict__ src, const ConvShape &S,
+                                                   long long row0, long long k0, uint8_t *tile)
+{
+    constexpr int NBLK = (ROWS / 8) * 8;  // (row groups) x (8 voxel groups of the 64-voxel chunk)
+    const int ch = IS_A ? S.cin : S.cout;
+    for (int b = threadIdx.x; b < NBLK; b += THREADS) {
+        const int rg = b >> 3, vg = b & 7;
+        const long long q = row0 + 8 * rg;  // first row of the group
+        int tap = 0, c0 = 0;
+        bool rows_ok;
+        if (IS_A) {
+            rows_ok = q < 27LL * ch;
+            tap = rows_ok ? (int)(q / ch) : 0;
+            c0 = rows_ok ? (int)(q - (long long)tap * ch) : 0;
+        } else {
+            rows_ok = q < ch;
+            c0 = (int)q;
+        }
+        const int dz = tap / 9 - 1, dyy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        uint4 in[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
-            const long long m = k0 + 8 * j + t;
-            e[t] = (co < S.cout && m < S.k_total) ? dy[m * S.cout + co] : __float2bfloat16_rn(0.0f);
+            in[t] = make_uint4(0u, 0u, 0u, 0u);
+            const long long m = k0 + 8 * vg + t;
+            if (rows_ok && m < S.k_total) {
+                int n, z, y, x;
+                decode_voxel(S, m, n, z, y, x);
+                if (IS_A) {
+                    z += dz;
+                    y += dyy;
+                    x += dx;
+                }
+                if ((unsigned)z < (unsigned)S.d && (unsigned)y < (unsigned)S.h && (unsigned)x < (unsigned)S.w)
+                    in[t] = __ldg(reinterpret_cast<const uint4 *>(
+                        src + ((((long long)n * S.d + z) * S.h + y) * S.w + x) * ch + c0));
+            }
         }
-        *reinterpret_cast<uint4 *>(tile + swz(r, j)) = *reinterpret_cast<const uint4 *>(e);
+        uint4 out[8];
+        transpose8x8(in, out);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(tile + swz(8 * rg + c, vg)) = out[c];
     }
 }
 
@@ -334,8 +348,8 @@ __global__ void __launch_bounds__(THREADS) conv_tc_kernel(const __nv_bfloat16 *_
             load_im2col_rows(a_src, S, rc, k0, sA + s * A_BYTES);
             load_rows_kmajor<BN>(b_src, S.k_total, S.n_total, n0, k0, sB + s * B_BYTES);
         } else {
-            load_im2col_cols(a_src, S, m0, k0, sA + s * A_BYTES);
-            load_dy_cols<BN>(b_src, S, n0, k0, sB + s * B_BYTES);
+            load_kvoxel_blocks<true, BM>(a_src, S, m0, k0, sA + s * A_BYTES);
+            load_kvoxel_blocks<false, BN>(b_src, S, n0, k0, sB + s * B_BYTES);
         }
         fence_async_smem();
         tc_before_sync();
@@ -479,7 +493,7 @@ int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, 
                        int *status, void *stream)
 {
     if (!x || !dy || !dw || !status) return CTREX_E_ARG;
-    if (!shape_ok(nb, d, h, wd, cin, cout)) return CTREX_E_SHAPE;
+    if (!shape_ok(nb, d, h, wd, cin, cout) || (cin & 7) || (cout & 7)) return CTREX_E_SHAPE;
     ConvShape S{};
     S.nb = nb;
     S.d = d;

@@ -1,0 +1,26 @@
+"""What the learned warm start gains over plain SIRT: on held-out phantoms
+the trained U-Net's output is far closer to the truth than its 5-iteration
+SIRT input, and SIRT started from it reaches relative data residual 1e-3 in
+fewer iterations and less wall time than SIRT from zero (time includes the
+input iterations and the network)."""
+
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def test_warm_start_beats_plain_sirt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_30166_gb300 import _build, warmstart
+
+    _build.build_library()
+    res = warmstart.run(n_train=40, n_test=2, steps=250)
+    print({k: v for k, v in res.items() if k != "per_phantom"})
+    assert res["loss_last"] < 0.5 * res["loss_first"]
+    assert res["net_err"] < 0.6 * res["sirt_in_err"]
+    for r in res["per_phantom"]:
+        assert r["plain_rho"] <= 1e-3 and r["warm_rho"] <= 1e-3
+        assert r["warm_iters"] < r["plain_iters"]
+    assert res["warm_s"] < res["plain_s"]
