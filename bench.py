@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="64^3 workload (quick check)")
-    ap.add_argument("--warm-start-steps", type=int, default=250,
+    ap.add_argument("--warm-start-steps", type=int, default=400,
                     help="train the U-Net warm start this many steps and report time to residual 1e-3 (0: skip)")
     ap.add_argument("--views", type=int, default=0,
                     help="override the number of views (small cases for ncu captures; not a bench line)")
@@ -335,7 +335,7 @@ def run_ours(args):
 
         del x, r, p, phantom
         torch.cuda.empty_cache()
-        ws = warmstart.run(n_train=40, n_test=4, steps=args.warm_start_steps)
+        ws = warmstart.run(n_train=56, n_test=4, steps=args.warm_start_steps)
         out["time_to_residual_1e-3"] = {
             "workload": ws["workload"], "tol": ws["tol"], "held_out_phantoms": ws["test_phantoms"],
             "plain_sirt_s": ws["plain_s"], "plain_sirt_iters": ws["plain_iters"],
