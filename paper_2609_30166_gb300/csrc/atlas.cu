@@ -11,9 +11,11 @@ void atlas_release(AtlasStore &s)
     s = AtlasStore();
 }
 
-cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int device)
+cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int device, bool packed)
 {
-    if (s.array && s.w == w && s.h == h && s.n == n && s.bf16 == (bf16 ? 1 : 0)) return cudaSuccess;
+    packed = packed && bf16;
+    if (s.array && s.w == w && s.h == h && s.n == n && s.bf16 == (bf16 ? 1 : 0) && s.packed == (packed ? 1 : 0))
+        return cudaSuccess;
     atlas_release(s);
     int maxw = 0, maxh = 0;
     cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxSurface2DWidth, device);
@@ -35,8 +37,9 @@ cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int devi
     }
     const long long H = rows * h;
     if (W > maxw || H > maxh || W < 1 || H < 1) return cudaErrorInvalidValue;
-    cudaChannelFormatDesc desc = bf16 ? cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned)
-                                      : cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat);
+    cudaChannelFormatDesc desc = packed ? cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindUnsigned)
+                                 : bf16 ? cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned)
+                                        : cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat);
     cudaError_t e = cudaMallocArray(&s.array, &desc, (size_t)W, (size_t)H, cudaArraySurfaceLoadStore);
     if (e != cudaSuccess) {
         s.array = nullptr;
@@ -62,6 +65,7 @@ cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int devi
     s.n = n;
     s.tshift = tshift;
     s.bf16 = bf16 ? 1 : 0;
+    s.packed = packed ? 1 : 0;
     return cudaSuccess;
 }
 
@@ -74,6 +78,7 @@ Atlas atlas_view(const AtlasStore &s)
     a.n = s.n;
     a.tshift = s.tshift;
     a.bf16 = s.bf16;
+    a.packed = s.packed;
     return a;
 }
 
@@ -91,9 +96,30 @@ __global__ void __launch_bounds__(256) upload_kernel(const T *__restrict__ src, 
     surf2Dwrite(v, surf, X * (int)sizeof(T), Y);
 }
 
+// Packed BF16 slice pairs: texel (x, y) of slice z = (v[z] | v[z + 1] << 16).
+__global__ void __launch_bounds__(256) upload_packed_kernel(const unsigned short *__restrict__ src,
+                                                            cudaSurfaceObject_t surf, int w, int h, int n, int tshift)
+{
+    const int x = blockIdx.x * 64 + (threadIdx.x & 63);
+    const int y = blockIdx.y * 4 + (threadIdx.x >> 6);
+    const int z = blockIdx.z;
+    if (x >= w || y >= h || z >= n) return;
+    const size_t o = ((size_t)z * h + y) * w + x;
+    const unsigned lo = src[o];
+    const unsigned hi = z + 1 < n ? src[o + (size_t)w * h] : 0u;
+    const int X = (z & ((1 << tshift) - 1)) * w + x;
+    const int Y = (z >> tshift) * h + y;
+    surf2Dwrite(lo | (hi << 16), surf, X * 4, Y);
+}
+
 cudaError_t atlas_upload(const AtlasStore &s, const void *src, cudaStream_t stream)
 {
     const dim3 grid((s.w + 63) / 64, (s.h + 3) / 4, s.n);
+    if (s.packed) {
+        upload_packed_kernel<<<grid, 256, 0, stream>>>(static_cast<const unsigned short *>(src), s.surf, s.w, s.h,
+                                                       s.n, s.tshift);
+        return cudaGetLastError();
+    }
     if (s.bf16)
         upload_kernel<unsigned short><<<grid, 256, 0, stream>>>(static_cast<const unsigned short *>(src), s.surf, s.w,
                                                                 s.h, s.n, s.tshift);

@@ -21,6 +21,7 @@ struct Atlas {
     int n = 0;                    // number of slices
     int tshift = 0;               // tiles per atlas row = 1 << tshift
     int bf16 = 0;                 // texels are raw BF16 bit patterns (16-bit unsigned)
+    int packed = 0;               // 32-bit texels: BF16 of slice s (low half) and s + 1 (high half)
 };
 
 // Four texels (x0,y0) (x0+1,y0) (x0,y0+1) (x0+1,y0+1) of slice s (clamped to a
@@ -65,8 +66,32 @@ struct AtlasSampler {
         // keep the gathered footprint inside the tile's neighbourhood
         const int x0 = min(max(ix, -1), A.w - 1), y0 = min(max(iy, -1), A.h - 1);
         float a00, a10, a01, a11, b00, b10, b01, b11;
-        atlas_quad(A, iz, x0, y0, a00, a10, a01, a11);
-        atlas_quad(A, iz + 1, x0, y0, b00, b10, b01, b11);
+        if (A.packed) {
+            // one gather: low halves = slice iz, high halves = slice iz + 1.  Below
+            // the first slice, slice 0 (low halves) plays the role of iz + 1.
+            const int s = min(max(iz, 0), A.n - 1);
+            const float X = (float)(((s & ((1 << A.tshift) - 1)) * A.w) + x0) + 1.0f;
+            const float Y = (float)(((s >> A.tshift) * A.h) + y0) + 1.0f;
+            const uint4 q = tex2Dgather<uint4>(A.tex, X, Y, 0);
+            a01 = __uint_as_float(q.x << 16);
+            a11 = __uint_as_float(q.y << 16);
+            a10 = __uint_as_float(q.z << 16);
+            a00 = __uint_as_float(q.w << 16);
+            if (iz >= 0) {
+                b01 = __uint_as_float(q.x & 0xFFFF0000u);
+                b11 = __uint_as_float(q.y & 0xFFFF0000u);
+                b10 = __uint_as_float(q.z & 0xFFFF0000u);
+                b00 = __uint_as_float(q.w & 0xFFFF0000u);
+            } else {
+                b00 = a00;
+                b10 = a10;
+                b01 = a01;
+                b11 = a11;
+            }
+        } else {
+            atlas_quad(A, iz, x0, y0, a00, a10, a01, a11);
+            atlas_quad(A, iz + 1, x0, y0, b00, b10, b01, b11);
+        }
         const float c0 = fmaf(wy0, fmaf(wx0, a00, wx1 * a10), wy1 * fmaf(wx0, a01, wx1 * a11));
         const float c1 = fmaf(wy0, fmaf(wx0, b00, wx1 * b10), wy1 * fmaf(wx0, b01, wx1 * b11));
         wsum = (wx0 + wx1) * (wy0 + wy1) * (wz0 + wz1);
@@ -87,14 +112,16 @@ struct AtlasStore {
     cudaArray_t array = nullptr;
     cudaTextureObject_t tex = 0;
     cudaSurfaceObject_t surf = 0;
-    int w = 0, h = 0, n = 0, tshift = 0, bf16 = -1;
+    int w = 0, h = 0, n = 0, tshift = 0, bf16 = -1, packed = 0;
 };
-// Creates (or keeps, if the shape matches) an atlas for n slices of w x h.
+// Creates (or keeps, if the shape matches) an atlas for n slices of w x h;
+// packed: 32-bit texels holding BF16 slice pairs (s, s + 1).
 // Returns cudaErrorInvalidValue if it cannot fit the device's 2D texture limits.
-cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int device);
+cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int device, bool packed = false);
 void atlas_release(AtlasStore &s);
 Atlas atlas_view(const AtlasStore &s);
-// Copies slices [n][h][w] (row-major, FP32 or BF16 as the atlas) into the atlas.
+// Copies slices [n][h][w] (row-major, FP32 or BF16 as the atlas) into the
+// atlas; for a packed atlas, texel s holds slices s and s + 1 (zero past n).
 cudaError_t atlas_upload(const AtlasStore &s, const void *src, cudaStream_t stream);
 
 }  // namespace ctrex

@@ -157,7 +157,9 @@ FwdArgs fwd_args(ctrex_ctx *c, const void *vol, int vdt, const int *view_idx, in
 int prepare_atlas(ctrex_ctx *c, FwdArgs &a, const void *vol, int vdt)
 {
     if (c->atlas_unfit) return CTREX_OK;
-    cudaError_t e = atlas_ensure(c->vol_atlas, c->grid.nx, c->grid.ny, c->grid.nz, vdt == CTREX_BF16, c->device);
+    // BF16 volumes: slice pairs packed in 32-bit texels, one gather per sample
+    cudaError_t e = atlas_ensure(c->vol_atlas, c->grid.nx, c->grid.ny, c->grid.nz, vdt == CTREX_BF16, c->device,
+                                 vdt == CTREX_BF16);
     if (e == cudaErrorInvalidValue) {
         cudaGetLastError();
         c->atlas_unfit = true;
