@@ -223,6 +223,32 @@ int ctrex_sirt_iterate(ctrex_ctx *ctx, void *vol, int vol_dtype, const void *p, 
                        float *residual_history, int *iters_done);
 
 /*
+ * Ordered-subset SIRT (Eq. (1) with index sets P_k, Sec. 2.3.2): one cycle
+ * visits the subsets in order; subset S updates
+ *   x += alpha w C_S B_S R_S (p_S - A_S x)
+ * with the fused forward/correction and the backprojector restricted to the
+ * views of S (C_S = column sums over those views).  A single subset of all
+ * views is SIRT; one view per subset is SART-like.
+ *   vol            DEVICE x_0 in, result out.
+ *   p              DEVICE [n_views][nv][nu] measured images (indexed by view).
+ *   subset_views   HOST int32, the subsets' view lists concatenated.
+ *   subset_offsets HOST int32 [n_sets + 1], subset s = views[off[s] .. off[s+1]),
+ *                  off[0] = 0, each subset at most 65535 views.
+ *   w              DEVICE float voxel weights or NULL.
+ *   residual_history HOST float [max_cycles] or NULL: after cycle k, the
+ *                  running residual sqrt(sum_S ||p_S - A_S x_(S)||^2 /
+ *                  sum_S ||p_S||^2), each term at the iterate subset S starts
+ *                  from (one 16-byte-per-subset read per cycle).
+ *   cycles_done    HOST: cycles applied; the loop stops after the first cycle
+ *                  whose residual is <= tol.
+ * Returns CTREX_E_SHAPE for an out-of-range view, CTREX_E_DIVERGED for a
+ * non-finite residual.
+ */
+int ctrex_os_sirt_iterate(ctrex_ctx *ctx, void *vol, int vol_dtype, const void *p, int p_dtype,
+                          const int *subset_views, const int *subset_offsets, int n_sets, int max_cycles,
+                          float alpha, const float *w, float tol, float *residual_history, int *cycles_done);
+
+/*
  * Same as ctrex_sirt_iterate with HOST buffers: copies vol (x_0) and p to
  * device buffers owned by the context, iterates, and copies the volume back
  * into vol.  vol_dtype / p_dtype describe the host arrays.  Synchronous.

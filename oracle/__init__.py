@@ -16,6 +16,7 @@ Each wrapper names the paper passage its C routine follows:
 * ``adjoint``, ``motion_grad``  -- transpose and chain rule of ``forward``
   (Sec. 5 motivates geometry refinement; no formula is printed).
 * ``sirt``                      -- Eq. (1) iterated, all views in one subset.
+* ``os_sirt``                   -- Eq. (1) on ordered subsets of views (Sec. 2.3.2).
 
 Parity status: every routine is pinned by ``tests/test_oracle_pins.py``
 (closed forms, analytic phantoms, adjointness, invariances, brute force and
@@ -106,6 +107,8 @@ def _declare(lib):
     lib.or_motion_grad.argtypes = [pp, _dp, _dp, _ip, ctypes.c_int, _dp, _dp]
     lib.or_sirt.argtypes = [pp, _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_double,
                             ctypes.c_double, ctypes.c_double, _dp, _ip]
+    lib.or_os_sirt.argtypes = [pp, _dp, _dp, _ip, _ip, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _ip]
 
 
 def _f64(a):
@@ -290,6 +293,24 @@ def sirt(pb, p, max_iter, alpha=1.0, w=None, tol=0.0, x0=None, eps_C=EPS_C):
     done = ctypes.c_int(0)
     ret = lib.or_sirt(ctypes.byref(pb._c), _ptr(x), _ptr(p), max_iter, alpha, _ptr(w), tol, pb.eps_R,
                       eps_C, _ptr(hist), ctypes.byref(done))
+    if ret < 0:
+        raise ValueError(f"oracle error {ret}")
+    return x, hist, done.value, ret
+
+
+def os_sirt(pb, p, subsets, max_cycles, alpha=1.0, w=None, tol=0.0, x0=None, eps_C=EPS_C):
+    """(x, residual history per cycle, cycles done, status) of ordered-subset
+    SIRT over the list of view lists ``subsets``."""
+    lib = _load()
+    p = _f64(p)
+    x = np.zeros(pb.vol_shape) if x0 is None else _f64(x0).copy()
+    w = None if w is None else _f64(w)
+    views = np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.int32) for s in subsets]), dtype=np.int32)
+    offsets = np.ascontiguousarray(np.cumsum([0] + [len(s) for s in subsets]), dtype=np.int32)
+    hist = np.full(max_cycles, np.nan)
+    done = ctypes.c_int(0)
+    ret = lib.or_os_sirt(ctypes.byref(pb._c), _ptr(x), _ptr(p), _ptr(views, _ip), _ptr(offsets, _ip), len(subsets),
+                         max_cycles, alpha, _ptr(w), tol, pb.eps_R, eps_C, _ptr(hist), ctypes.byref(done))
     if ret < 0:
         raise ValueError(f"oracle error {ret}")
     return x, hist, done.value, ret

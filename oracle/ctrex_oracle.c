@@ -932,3 +932,63 @@ int or_sirt(const or_problem *pb, double *x, const double *p, int max_iter, doub
     free(r);
     return ret;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Ordered-subset SIRT: Eq. (1) evaluated on the views of one subset at a   */
+/* time (Sec. 2.3.2, index sets P_k).                                       */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * One cycle visits the subsets in order; subset S updates
+ *   x += alpha w C_S B_S R_S (p_S - A_S x),
+ * C_S the column sums of the backprojector over the views of S only.
+ * Reading (the paper leaves the stopping rule to Rex): the residual of a cycle
+ * is the running residual sqrt(sum_S ||p_S - A_S x_(S)||^2 / sum_S ||p_S||^2),
+ * each term taken at the iterate x_(S) that subset S starts from (for subsets
+ * that partition the views the denominator is ||p||^2); after cycle c it is
+ * hist[c], and the loop stops once it is <= tol.  With a single subset holding
+ * every view this is SIRT with the test after the update.
+ * views: concatenated subset view lists; offsets[0..n_sub_sets].
+ */
+int or_os_sirt(const or_problem *pb, double *x, const double *p, const int *views, const int *offsets,
+               int n_sets, int max_cycles, double alpha, const double *w, double tol, double eps_R,
+               double eps_C, double *hist, int *cycles_done)
+{
+    long npix = (long)pb->nu * pb->nv;
+    int maxlen = 0;
+    for (int s = 0; s < n_sets; ++s)
+        if (offsets[s + 1] - offsets[s] > maxlen) maxlen = offsets[s + 1] - offsets[s];
+    double *q = (double *)malloc(sizeof(double) * (size_t)(maxlen > 0 ? maxlen : 1) * npix);
+    double *rs = (double *)malloc(sizeof(double) * (size_t)(maxlen > 0 ? maxlen : 1) * npix);
+    double *r = (double *)malloc(sizeof(double) * (size_t)(maxlen > 0 ? maxlen : 1) * npix);
+    double *ps = (double *)malloc(sizeof(double) * (size_t)(maxlen > 0 ? maxlen : 1) * npix);
+    int ret = 0;
+    *cycles_done = 0;
+    for (int c = 0; c < max_cycles && !ret; ++c) {
+        double acc = 0.0, p2 = 0.0;
+        for (int s = 0; s < n_sets; ++s) {
+            const int *vs = views + offsets[s];
+            int n = offsets[s + 1] - offsets[s];
+            if (n <= 0) continue;
+            int e = or_forward(pb, x, vs, n, q, rs);
+            if (e) { ret = e; break; }
+            for (int k = 0; k < n; ++k) memcpy(ps + (size_t)k * npix, p + (size_t)vs[k] * npix, sizeof(double) * npix);
+            double sums[2];
+            or_correct((long)n * npix, ps, q, rs, eps_R, r, sums);
+            acc += sums[0];
+            p2 += sums[1];
+            or_backproject(pb, r, vs, n, w, alpha, eps_C, x, NULL, NULL);
+        }
+        if (ret) break;
+        double rho = p2 > 0.0 ? sqrt(acc / p2) : sqrt(acc);
+        if (hist) hist[c] = rho;
+        *cycles_done = c + 1;
+        if (!isfinite(rho)) { ret = 1; break; }
+        if (rho <= tol) break;
+    }
+    free(q);
+    free(rs);
+    free(r);
+    free(ps);
+    return ret;
+}

@@ -51,6 +51,11 @@ struct ctrex_ctx {
     Atlas img_atlas_view;
     bool img_atlas_unfit = false;
     bool atlas_unfit = false;  // geometry exceeds the 2D texture limits: row-major sampling
+    // ordered-subset SIRT: concatenated subset view lists, per-subset norms
+    int *d_subset_views = nullptr;
+    size_t subset_views_bytes = 0;
+    double *d_subset_sums = nullptr;
+    size_t subset_sums_bytes = 0;
     // host-buffer entry point scratch
     void *d_hvol = nullptr, *d_hp = nullptr;
     float *d_hw = nullptr;
@@ -261,6 +266,8 @@ int ctrex_destroy(ctrex_ctx *c)
         dfree(c->d_hvol);
         dfree(c->d_hp);
         dfree(c->d_hw);
+        dfree(c->d_subset_views);
+        dfree(c->d_subset_sums);
         atlas_release(c->vol_atlas);
         atlas_release(c->img_atlas);
     }
@@ -621,6 +628,78 @@ int ctrex_sirt_iterate(ctrex_ctx *c, void *vol, int vdt, const void *p, int pdt,
         int be = ctrex_back_project(c, c->d_r, pdt, vol, vdt, w, alpha, 1, 1, nullptr, V);
         if (be) return be;
         if (iters_done) *iters_done = k + 1;
+    }
+    return ctrex_device_status(c);
+}
+
+int ctrex_os_sirt_iterate(ctrex_ctx *c, void *vol, int vdt, const void *p, int pdt, const int *subset_views,
+                          const int *subset_offsets, int n_sets, int max_cycles, float alpha, const float *w,
+                          float tol, float *hist, int *cycles_done)
+{
+    if (!c) return CTREX_E_ARG;
+    if (cycles_done) *cycles_done = 0;
+    if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_geometry has not been called");
+    if (!vol || !p || !subset_views || !subset_offsets) return fail(c, CTREX_E_ARG, "os_sirt: NULL argument");
+    if (!dtype_ok(vdt) || !dtype_ok(pdt)) return fail(c, CTREX_E_DTYPE, "os_sirt: bad dtype");
+    if (n_sets < 1 || max_cycles < 0) return fail(c, CTREX_E_ARG, "os_sirt: need n_sets >= 1, max_cycles >= 0");
+    const int V = c->grid.n_views;
+    if (subset_offsets[0] != 0) return fail(c, CTREX_E_ARG, "os_sirt: subset_offsets[0] must be 0");
+    int maxlen = 0;
+    for (int s = 0; s < n_sets; ++s) {
+        const int n = subset_offsets[s + 1] - subset_offsets[s];
+        if (n < 0 || n > 65535) return fail(c, CTREX_E_SHAPE, "os_sirt: subset %d has size %d", s, n);
+        if (n > maxlen) maxlen = n;
+    }
+    const int total = subset_offsets[n_sets];
+    for (int i = 0; i < total; ++i)
+        if (subset_views[i] < 0 || subset_views[i] >= V)
+            return fail(c, CTREX_E_SHAPE, "os_sirt: view %d out of range", subset_views[i]);
+    DeviceGuard g(c->device);
+    int e = ensure(c, (void **)&c->d_subset_views, &c->subset_views_bytes, sizeof(int) * (size_t)(total > 0 ? total : 1),
+                   "subset view lists");
+    if (e) return e;
+    e = ensure(c, (void **)&c->d_subset_sums, &c->subset_sums_bytes, sizeof(double) * 2 * (size_t)n_sets,
+               "subset residual norms");
+    if (e) return e;
+    const size_t rb = (size_t)(maxlen > 0 ? maxlen : 1) * c->grid.nu * c->grid.nv * dtype_size(pdt);
+    e = ensure(c, &c->d_r, &c->r_bytes, rb, "correction images");
+    if (e) return e;
+    e = ensure_partials(c, maxlen > 0 ? maxlen : 1);
+    if (e) return e;
+    if (total > 0)
+        CT_CUDA(c, cudaMemcpyAsync(c->d_subset_views, subset_views, sizeof(int) * (size_t)total, cudaMemcpyHostToDevice,
+                                   c->stream));
+    CT_CUDA(c, cudaMemsetAsync(c->d_subset_sums, 0, sizeof(double) * 2 * (size_t)n_sets, c->stream));
+    std::vector<double> sums(2 * (size_t)n_sets);
+    for (int k = 0; k < max_cycles; ++k) {
+        for (int s = 0; s < n_sets; ++s) {
+            const int n = subset_offsets[s + 1] - subset_offsets[s];
+            if (n == 0) continue;
+            const int *vs = c->d_subset_views + subset_offsets[s];
+            FwdArgs a = fwd_args(c, vol, vdt, vs, n);
+            a.p_by_view = 1;
+            e = prepare_atlas(c, a, vol, vdt);
+            if (e) return e;
+            cudaError_t ce = launch_forward_correct(a, p, pdt, c->d_r, pdt, c->d_partials, c->partials_cap,
+                                                    c->d_subset_sums + 2 * (size_t)s);
+            if (ce != cudaSuccess) return cuda_fail(c, ce, "os_sirt: fwd_correct");
+            int be = ctrex_back_project(c, c->d_r, pdt, vol, vdt, w, alpha, 1, 1, vs, n);
+            if (be) return be;
+        }
+        CT_CUDA(c, cudaMemcpyAsync(sums.data(), c->d_subset_sums, sizeof(double) * 2 * (size_t)n_sets,
+                                   cudaMemcpyDeviceToHost, c->stream));
+        CT_CUDA(c, cudaStreamSynchronize(c->stream));
+        double acc = 0.0, p2 = 0.0;
+        for (int s = 0; s < n_sets; ++s) {
+            if (subset_offsets[s + 1] == subset_offsets[s]) continue;
+            acc += sums[2 * (size_t)s];
+            p2 += sums[2 * (size_t)s + 1];
+        }
+        const double rho = p2 > 0.0 ? sqrt(acc / p2) : sqrt(acc);
+        if (hist) hist[k] = (float)rho;
+        if (cycles_done) *cycles_done = k + 1;
+        if (!isfinite(rho)) return fail(c, CTREX_E_DIVERGED, "os_sirt: residual not finite in cycle %d", k);
+        if (rho <= (double)tol) break;
     }
     return ctrex_device_status(c);
 }

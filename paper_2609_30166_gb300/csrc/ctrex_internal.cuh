@@ -83,6 +83,7 @@ struct FwdArgs {
     int n_idx;
     cudaStream_t stream;
     unsigned *devcheck;         // device status word
+    int p_by_view = 0;          // correction: measured images indexed by view, not by list position
 };
 
 cudaError_t launch_forward(const FwdArgs &a, void *proj, int proj_dtype, float *rowsum);

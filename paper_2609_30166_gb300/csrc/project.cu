@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
     fwd_kernel(Grid G, const ViewGPU *__restrict__ views, const MotionGPU *__restrict__ motion,
                const float *__restrict__ coef_g, const Sampler vol,
                const int *__restrict__ view_idx, TP *__restrict__ out, float *__restrict__ rowsum_out,
-               const TP *__restrict__ p, float *__restrict__ partials, unsigned *devcheck)
+               const TP *__restrict__ p, float *__restrict__ partials, unsigned *devcheck, int p_by_view)
 {
     __shared__ float s_coef[MOTION ? 8 * 8 * 8 * 3 : 1];
     __shared__ float s_red[2][FWD_TX * FWD_TY / 32];
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
         float e2 = 0.0f, p2 = 0.0f;
         if (in_pix && !ok) Storage<TP>::store(out + pix, 0.0f);
         if (inside) {
-            const float pm = Storage<TP>::load(p + pix);
+            const float pm = Storage<TP>::load(p + (p_by_view ? ((size_t)view * G.nv + iv) * G.nu + iu : pix));
             const float e = pm - val;
             const float Rw = rs > G.eps_R ? 1.0f / rs : 0.0f;
             Storage<TP>::store(out + pix, Rw * e);
@@ -224,10 +224,10 @@ static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, flo
     const dim3 grid = fwd_grid(G, a.n_idx), block(FWD_TX, FWD_TY);
     if (a.motion)
         fwd_kernel<Sampler, TP, MODE, true><<<grid, block, 0, a.stream>>>(
-            G, a.views, a.motion, a.coef_idx, smp, a.view_idx, out, rowsum, p, partials, a.devcheck);
+            G, a.views, a.motion, a.coef_idx, smp, a.view_idx, out, rowsum, p, partials, a.devcheck, a.p_by_view);
     else
         fwd_kernel<Sampler, TP, MODE, false><<<grid, block, 0, a.stream>>>(
-            G, a.views, nullptr, nullptr, smp, a.view_idx, out, rowsum, p, partials, a.devcheck);
+            G, a.views, nullptr, nullptr, smp, a.view_idx, out, rowsum, p, partials, a.devcheck, a.p_by_view);
     return cudaGetLastError();
 }
 

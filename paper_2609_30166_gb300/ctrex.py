@@ -31,7 +31,7 @@ EXPORTS = (
     "ctrex_device_status", "ctrex_set_geometry", "ctrex_set_motion", "ctrex_fwd_project",
     "ctrex_fwd_correct", "ctrex_back_project", "ctrex_adjoint_project", "ctrex_motion_grad",
     "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples", "ctrex_correct_static",
-    "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad",
+    "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad", "ctrex_os_sirt_iterate",
 )
 
 # Largest n ctrex_correct_static accepts (its static scratch holds 65536 CTA partials of 8192 elements).
@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "ctrex_correct_static": ([vp, vp, vp, vp, i, ctypes.c_longlong, f, vp, vp], i),
         "ctrex_conv3d_fwd": ([vp, vp, vp, vp, i, i, i, i, i, i, i, i, vp, vp], i),
         "ctrex_conv3d_wgrad": ([vp, vp, vp, i, i, i, i, i, i, vp, vp], i),
+        "ctrex_os_sirt_iterate": ([vp, vp, i, vp, i, ip, ip, i, i, f, vp, f, fp, ip], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -285,6 +286,25 @@ class Context:
                                                 hist.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                                 ctypes.byref(done)))
         return vol, hist[:max_iter], done.value
+
+    def os_sirt_iterate(self, vol, p, subsets, max_cycles, alpha=1.0, w=None, tol=0.0):
+        """Ordered-subset SIRT over ``subsets`` (a list of view lists)."""
+        self._sync_stream()
+        vol = self._dev(vol, "vol", self.vol_shape)
+        p = self._dev(p, "p", (self.n_views,) + self.det_shape)
+        if w is not None:
+            w = self._dev(w, "w", self.vol_shape, dtypes=(torch.float32,))
+        views = np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.int32) for s in subsets]),
+                                     dtype=np.int32)
+        offsets = np.ascontiguousarray(np.cumsum([0] + [len(s) for s in subsets]), dtype=np.int32)
+        hist = np.full(max(max_cycles, 1), np.nan, dtype=np.float32)
+        done = ctypes.c_int(0)
+        ip = ctypes.POINTER(ctypes.c_int)
+        self._check(self.lib.ctrex_os_sirt_iterate(
+            self._h, _ptr(vol), _dt(vol), _ptr(p), _dt(p), views.ctypes.data_as(ip), offsets.ctypes.data_as(ip),
+            len(subsets), int(max_cycles), float(alpha), _ptr(w), float(tol),
+            hist.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(done)))
+        return vol, hist[:max_cycles], done.value
 
     def sirt_host(self, vol_host, p_host, max_iter, alpha=1.0, w_host=None, tol=0.0):
         """SIRT on HOST tensors (CPU, ideally pinned): the library copies in,

@@ -346,3 +346,30 @@ def identity_theta(n_views: int) -> np.ndarray:
     th = np.zeros((n_views, 15))
     th[:, 6:15] = np.eye(3).reshape(9)
     return th
+
+
+# ---------------------------------------------------------------------------
+# Ordered-subset schedules (the index sets P_k of Sec. 2.3.2)
+# ---------------------------------------------------------------------------
+
+def _bit_reversal_order(n):
+    bits = max(1, (n - 1).bit_length())
+    order = sorted(range(n), key=lambda i: int(format(i, f"0{bits}b")[::-1], 2))
+    return order
+
+
+def subsets_cyclic(n_views, n_subsets, spread=True):
+    """Interleaved subsets {s, s + n, s + 2n, ...}; with ``spread`` they are
+    visited in bit-reversed order so consecutive subsets are far apart in
+    angle (a geometry-dependent ordering).  Every view appears exactly once."""
+    sets = [list(range(s, n_views, n_subsets)) for s in range(n_subsets)]
+    if spread:
+        sets = [sets[i] for i in _bit_reversal_order(n_subsets)]
+    return [s for s in sets if s]
+
+
+def subsets_random(n_views, n_subsets, seed):
+    """A seeded random permutation of the views cut into n_subsets
+    near-equal contiguous pieces."""
+    perm = np.random.Generator(np.random.PCG64(seed)).permutation(n_views)
+    return [list(map(int, c)) for c in np.array_split(perm, n_subsets) if len(c)]

@@ -576,3 +576,54 @@ def test_conv_oracle_matches_brute_force():
                             if 0 <= zz < d and 0 <= y2 < h and 0 <= x2 < w:
                                 dw_ref[co, t] += dy[n, z, yy, xx, co] * x[n, zz, y2, x2]
     assert np.allclose(dw, dw_ref, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Ordered-subset SIRT (Sec. 2.3.2)
+# ---------------------------------------------------------------------------
+
+def test_os_sirt_single_subset_is_sirt():
+    cfg = small(n=16, nu=20, nv=20, n_views=6, trajectory="perturbed", seed=31)
+    pb = oracle_problem(cfg)
+    p, _ = oracle.forward(pb, inputs.phantom(cfg.scaled(n_ellipsoids=4)).numpy())
+    xs, hs, ds, _ = oracle.sirt(pb, p, 4)
+    xo, ho, do, _ = oracle.os_sirt(pb, p, [list(range(cfg.n_views))], 4)
+    assert ds == do == 4
+    assert np.array_equal(xs, xo) and np.array_equal(hs, ho)
+
+
+def test_os_sirt_cycle_is_dense_composition(dense8):
+    cfg, pb, A, B = dense8
+    rng = np.random.default_rng(32)
+    p = A @ rng.uniform(0, 1, size=A.shape[1])
+    w = rng.uniform(0.3, 1.0, size=A.shape[1])
+    alpha = 0.8
+    npix = cfg.nu * cfg.nv
+    subsets = [[2, 0], [3], [1]]
+    x = rng.uniform(0, 1, size=A.shape[1])
+    x_ref = x.copy()
+    acc = p2 = 0.0
+    for S in subsets:
+        rows = np.concatenate([np.arange(v * npix, (v + 1) * npix) for v in S])
+        As, Bs = A[rows], B[:, rows]
+        rs = As.sum(axis=1)
+        R = np.where(rs > pb.eps_R, 1.0 / np.where(rs > 0, rs, 1), 0.0)
+        cs = Bs.sum(axis=1)
+        C = np.where(cs > oracle.EPS_C, 1.0 / np.where(cs > 0, cs, 1), 0.0)
+        e = p[rows] - As @ x_ref
+        acc += e @ e
+        p2 += p[rows] @ p[rows]
+        x_ref = x_ref + alpha * w * C * (Bs @ (R * e))
+    xo, ho, do, _ = oracle.os_sirt(pb, p.reshape(cfg.n_views, cfg.nv, cfg.nu), subsets, 1, alpha=alpha,
+                                   w=w.reshape(cfg.vol_shape), x0=x.reshape(cfg.vol_shape))
+    assert do == 1
+    assert np.allclose(xo.ravel(), x_ref, rtol=0, atol=1e-12)
+    assert ho[0] == pytest.approx(np.sqrt(acc / p2), rel=1e-12)
+
+
+def test_subset_schedules_partition_views():
+    for sets in (inputs.subsets_cyclic(90, 10), inputs.subsets_cyclic(7, 3, spread=False),
+                 inputs.subsets_random(90, 7, seed=3)):
+        flat = sorted(v for s in sets for v in s)
+        assert flat == list(range(max(flat) + 1))
+    assert inputs.subsets_cyclic(8, 4)[:2] == [[0, 4], [2, 6]]  # bit-reversed visiting order
