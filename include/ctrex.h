@@ -142,6 +142,21 @@ int ctrex_set_motion(ctrex_ctx *ctx, const float *theta, const float *coef, cons
                      double margin_mm);
 
 /*
+ * Extended field of view (Sec. 3.6, Sec. 4.3.2): per-view detector window of
+ * the BACKPROJECTOR.  View v's backprojection sees only detector columns
+ * u_lo..u_hi and rows v_lo..v_hi; taps outside count as off the detector for
+ * both the sum b and its normalisation c.  The forward projector keeps the
+ * whole detector.  Moving the inner edge of an offset-centre-of-rotation scan
+ * per view (and per iteration) to a random column between the physical edge
+ * and the projected centre of rotation is the paper's remedy for the central
+ * field-of-view ring.
+ *   window  HOST int32 [n_views][4] = (u_lo, u_hi, v_lo, v_hi), clipped to the
+ *           detector; copied (the call synchronises the stream).  NULL resets
+ *           to the whole detector.  set_geometry also resets it.
+ */
+int ctrex_set_bp_window(ctrex_ctx *ctx, const int *window);
+
+/*
  * A x (Sec. 4.1 projection operator; Sec. 3.4 mean over sub-angles; motion
  * if set).  Ray from the source through the pixel centre, clipped to the
  * box, fixed-step truncated-midpoint quadrature with trilinear interpolation

@@ -38,7 +38,11 @@
  *   R5 R_i = 1 / (row sum of A) and w_j multiplies after normalisation;
  *   R6 motion: x' = A (R(omega) x + t), y = x' + s_v u(x'), u a uniform cubic
  *      B-spline on an 8^3 control grid spanning the nominal box, clip box
- *      dilated by a fixed margin.
+ *      dilated by a fixed margin;
+ *   R11 extended field of view (Sec. 3.6, Sec. 4.3.2): the backprojector of
+ *      view v sees only detector columns u_lo..u_hi and rows v_lo..v_hi (its
+ *      effective edge); taps outside count as off the detector for both the
+ *      sum and its normalisation; the forward keeps the whole detector.
  *
  * Conventions: volume vol[iz][iy][ix] (x fastest), voxel (0,0,0) centred at
  * origin (mm), index coordinate g = (x - origin) / vox.  Projection images
@@ -66,6 +70,7 @@ typedef struct {
     const double *coef;   /* [8][8][8][3] (z,y,x,component) or NULL       */
     const double *s_view; /* [n_views] or NULL (then s_v = 0)              */
     double margin;        /* mm, clip-box dilation when motion is on       */
+    const int *bp_window; /* [n_views][4] (u_lo, u_hi, v_lo, v_hi) or NULL */
 } or_problem;
 
 /* Per (view, sub-angle) quantities derived from P (Sec. 2.2.1). */
@@ -619,10 +624,18 @@ static void bp_voxel(const or_problem *pb, const or_view *ov, const double *r, c
             double fu0 = floor(u), fv0 = floor(v);
             int iu0 = (int)fu0, iv0 = (int)fv0;
             double fu = u - fu0, fv = v - fv0;
+            int ulo = 0, uhi = pb->nu - 1, vlo = 0, vhi = pb->nv - 1;
+            if (pb->bp_window) {
+                const int *wd = pb->bp_window + 4 * (size_t)view;
+                ulo = wd[0] > ulo ? wd[0] : ulo;
+                uhi = wd[1] < uhi ? wd[1] : uhi;
+                vlo = wd[2] > vlo ? wd[2] : vlo;
+                vhi = wd[3] < vhi ? wd[3] : vhi;
+            }
             for (int dv = 0; dv < 2; ++dv)
                 for (int du = 0; du < 2; ++du) {
                     int iu = iu0 + du, iv = iv0 + dv;
-                    if (iu < 0 || iu >= pb->nu || iv < 0 || iv >= pb->nv) continue;
+                    if (iu < ulo || iu > uhi || iv < vlo || iv > vhi) continue;
                     double wgt = (du ? fu : 1.0 - fu) * (dv ? fv : 1.0 - fv);
                     b += wgt * img[(size_t)iv * pb->nu + iu] / pb->n_sub;
                     c += wgt / pb->n_sub;

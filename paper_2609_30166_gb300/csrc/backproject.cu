@@ -75,11 +75,12 @@ struct AtlasImages {
 template <typename Images, typename TV>
 __global__ void __launch_bounds__(BP_THREADS)
     bp_kernel(Grid G, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx, int n_idx,
-              const Images img, TV *__restrict__ vol, const float *__restrict__ w, float alpha, int normalize,
-              int accumulate)
+              const Images img, const int4 *__restrict__ window, TV *__restrict__ vol, const float *__restrict__ w,
+              float alpha, int normalize, int accumulate)
 {
     __shared__ float4 sP[BP_CHUNK][3];
     __shared__ typename Images::Slot sImg[BP_CHUNK];
+    __shared__ int4 sWin[BP_CHUNK];  // per-view detector window (u_lo, u_hi, v_lo, v_hi)
     const int tid = (threadIdx.z * BP_TY + threadIdx.y) * BP_TX + threadIdx.x;
     const int ix = blockIdx.x * BP_TX + threadIdx.x;
     const int iy = blockIdx.y * BP_TY + threadIdx.y;
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(BP_THREADS)
             // an invalid view index gets a zero depth row: it is skipped
             sP[t][2] = ok ? make_float4(P[8], P[9], P[10], P[11]) : make_float4(0.f, 0.f, 0.f, 0.f);
             sImg[t] = img.slot(k);
+            sWin[t] = window ? window[view] : make_int4(0, G.nu - 1, 0, G.nv - 1);
         }
         __syncthreads();
         if (!inside) continue;
@@ -116,14 +118,19 @@ __global__ void __launch_bounds__(BP_THREADS)
             const float h2 = fmaf(p1.x, fx, fmaf(p1.y, fy, fmaf(p1.z, fz, p1.w)));
             const float inv = __frcp_rn(h3);
             const float u = h1 * inv, v = h2 * inv;
-            if (!(u > -1.0f && u < (float)nu && v > -1.0f && v < (float)nv)) continue;
+            // taps outside the view's detector window (the whole detector by
+            // default) count as off the detector
+            const int4 win = sWin[m];
+            if (!(u > (float)(win.x - 1) && u < (float)(win.y + 1) && v > (float)(win.z - 1) &&
+                  v < (float)(win.w + 1)))
+                continue;
             const float fu = floorf(u), fv = floorf(v);
             const int iu = (int)fu, iv = (int)fv;
             const float au = u - fu, av = v - fv;
-            const float wu0 = iu >= 0 ? 1.0f - au : 0.0f;
-            const float wu1 = iu + 1 < nu ? au : 0.0f;
-            const float wv0 = iv >= 0 ? 1.0f - av : 0.0f;
-            const float wv1 = iv + 1 < nv ? av : 0.0f;
+            const float wu0 = iu >= win.x ? 1.0f - au : 0.0f;
+            const float wu1 = iu + 1 <= win.y ? au : 0.0f;
+            const float wv0 = iv >= win.z ? 1.0f - av : 0.0f;
+            const float wv1 = iv + 1 <= win.w ? av : 0.0f;
             b += img(sImg[m], iu, iv, fu, fv, wu0, wu1, wv0, wv1);
             c += (wu0 + wu1) * (wv0 + wv1);
         }
@@ -146,7 +153,7 @@ static cudaError_t bp_launch(const BpArgs &a, const Images &img)
     const Grid &G = *a.grid;
     const dim3 block(BP_TX, BP_TY, BP_TZ);
     const dim3 grid((G.nx + BP_TX - 1) / BP_TX, (G.ny + BP_TY - 1) / BP_TY, (G.nz + BP_TZ - 1) / BP_TZ);
-    bp_kernel<Images, TV><<<grid, block, 0, a.stream>>>(G, a.views, a.view_idx, a.n_idx, img,
+    bp_kernel<Images, TV><<<grid, block, 0, a.stream>>>(G, a.views, a.view_idx, a.n_idx, img, a.window,
                                                        static_cast<TV *>(a.vol), a.w, a.alpha, a.normalize,
                                                        a.accumulate);
     return cudaGetLastError();

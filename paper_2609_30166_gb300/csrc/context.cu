@@ -51,6 +51,9 @@ struct ctrex_ctx {
     Atlas img_atlas_view;
     bool img_atlas_unfit = false;
     bool atlas_unfit = false;  // geometry exceeds the 2D texture limits: row-major sampling
+    // backprojector detector windows (extended field of view), int4 per view
+    int4 *d_window = nullptr;
+    bool has_window = false;
     // ordered-subset SIRT: concatenated subset view lists, per-subset norms
     int *d_subset_views = nullptr;
     size_t subset_views_bytes = 0;
@@ -267,6 +270,7 @@ int ctrex_destroy(ctrex_ctx *c)
         dfree(c->d_hp);
         dfree(c->d_hw);
         dfree(c->d_subset_views);
+        dfree(c->d_window);
         dfree(c->d_subset_sums);
         atlas_release(c->vol_atlas);
         atlas_release(c->img_atlas);
@@ -366,6 +370,8 @@ int ctrex_set_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, co
         }
     }
     dfree(c->d_views);
+    dfree(c->d_window);
+    c->has_window = false;
     // motion buffers are sized by n_views: drop them with the old geometry
     dfree(c->d_motion);
     dfree(c->d_dRdw);
@@ -458,6 +464,29 @@ int ctrex_set_motion(ctrex_ctx *c, const float *theta, const float *coef, const 
     return CTREX_OK;
 }
 
+int ctrex_set_bp_window(ctrex_ctx *c, const int *window)
+{
+    if (!c) return CTREX_E_ARG;
+    if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_bp_window before set_geometry");
+    if (!window) {
+        c->has_window = false;
+        return CTREX_OK;
+    }
+    const int V = c->grid.n_views;
+    std::vector<int4> hw((size_t)V);
+    for (int v = 0; v < V; ++v) {
+        const int *q = window + 4 * (size_t)v;
+        hw[(size_t)v] = make_int4(q[0] > 0 ? q[0] : 0, q[1] < c->grid.nu - 1 ? q[1] : c->grid.nu - 1,
+                                  q[2] > 0 ? q[2] : 0, q[3] < c->grid.nv - 1 ? q[3] : c->grid.nv - 1);
+    }
+    DeviceGuard g(c->device);
+    if (!c->d_window) CT_CUDA(c, cudaMalloc((void **)&c->d_window, sizeof(int4) * (size_t)V));
+    CT_CUDA(c, cudaMemcpyAsync(c->d_window, hw.data(), sizeof(int4) * (size_t)V, cudaMemcpyHostToDevice, c->stream));
+    CT_CUDA(c, cudaStreamSynchronize(c->stream));  // hw is a local buffer
+    c->has_window = true;
+    return CTREX_OK;
+}
+
 int ctrex_fwd_project(ctrex_ctx *c, const void *vol, int vdt, void *proj, int pdt, float *rowsum,
                       const int *view_idx, int n_idx)
 {
@@ -535,6 +564,7 @@ int ctrex_back_project(ctrex_ctx *c, const void *r, int rdt, void *vol, int vdt,
     a.normalize = normalize ? 1 : 0;
     a.accumulate = accumulate ? 1 : 0;
     a.stream = c->stream;
+    a.window = c->has_window ? c->d_window : nullptr;
     if (n_idx > 0 && !c->img_atlas_unfit) {
         cudaError_t ae = atlas_ensure(c->img_atlas, c->grid.nu, c->grid.nv, n_idx, rdt == CTREX_BF16, c->device);
         if (ae == cudaErrorInvalidValue) {

@@ -96,6 +96,7 @@ cudaError_t launch_count_samples(const FwdArgs &a, unsigned long long *out);
 struct BpArgs {
     const Grid *grid;
     const Atlas *atlas = nullptr;  // correction images uploaded into a texture atlas, or nullptr
+    const int4 *window = nullptr;  // per-view detector window of the backprojector, or nullptr
     const ViewGPU *views;
     const int *view_idx;
     int n_idx;

@@ -31,7 +31,7 @@ EXPORTS = (
     "ctrex_device_status", "ctrex_set_geometry", "ctrex_set_motion", "ctrex_fwd_project",
     "ctrex_fwd_correct", "ctrex_back_project", "ctrex_adjoint_project", "ctrex_motion_grad",
     "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples", "ctrex_correct_static",
-    "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad", "ctrex_os_sirt_iterate",
+    "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad", "ctrex_os_sirt_iterate", "ctrex_set_bp_window",
 )
 
 # Largest n ctrex_correct_static accepts (its static scratch holds 65536 CTA partials of 8192 elements).
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
         "ctrex_conv3d_fwd": ([vp, vp, vp, vp, i, i, i, i, i, i, i, i, vp, vp], i),
         "ctrex_conv3d_wgrad": ([vp, vp, vp, i, i, i, i, i, i, vp, vp], i),
         "ctrex_os_sirt_iterate": ([vp, vp, i, vp, i, ip, ip, i, i, f, vp, f, fp, ip], i),
+        "ctrex_set_bp_window": ([vp, ip], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -199,6 +200,18 @@ class Context:
             args.append(t)
         self._motion_keep = args  # the set-up kernel reads them on the stream
         self._check(self.lib.ctrex_set_motion(self._h, *[_ptr(a) for a in args], float(margin)))
+
+    def set_bp_window(self, window=None):
+        """Per-view backprojection detector windows [n_views, 4] = (u_lo, u_hi,
+        v_lo, v_hi) (extended field of view), or None for the whole detector."""
+        if window is None:
+            self._check(self.lib.ctrex_set_bp_window(self._h, None))
+            return
+        win = np.ascontiguousarray(window, dtype=np.int32)
+        if win.shape != (self.n_views, 4):
+            raise ValueError(f"window must be [{self.n_views}, 4]")
+        self._sync_stream()
+        self._check(self.lib.ctrex_set_bp_window(self._h, win.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
 
     def fwd_project(self, vol, proj=None, rowsum=None, view_idx=None, out_dtype=None):
         self._sync_stream()

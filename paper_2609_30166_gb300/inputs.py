@@ -37,7 +37,8 @@ class Config:
     nv: int
     n_views: int
     n_sub: int = 1
-    trajectory: str = "circular"      # circular | perturbed | helical
+    trajectory: str = "circular"      # circular | perturbed | helical | offset
+    det_offset: float = 0.0           # offset: lateral detector shift (pixels), centre of rotation off-centre
     seed: int = 1
     helical_turns: float = 0.0
     z_span: float = 0.0               # helical: source z runs -z_span .. +z_span (mm)
@@ -128,6 +129,8 @@ def detector_frames(cfg: Config):
     """Per (view, sub) source, detector centre, u axis, v axis: arrays [V, S, 3].
 
     circular:  angle 2*pi*v/V, z = 0.
+    offset:    circular with the detector shifted by ``det_offset`` pixels along
+               u (offset centre of rotation, extended field of view).
     perturbed: circular, then per view (draw order: du, dv in pixels U[-2, 2];
                tilt U[-0.5, 0.5] deg about the detector normal; source jitter
                3 x U[-0.2, 0.2] mm) the detector is offset by du*u + dv*v,
@@ -161,6 +164,8 @@ def detector_frames(cfg: Config):
             a = v * da + (s + 0.5 - 0.5 * S) * da / S
             z = (-cfg.z_span + p * a) if cfg.trajectory == "helical" else 0.0
             src, ctr, u, w = _circular_pose(a, z, cfg)
+            if cfg.trajectory == "offset":
+                ctr = ctr + cfg.det_offset * u
             if rng is not None:
                 n = np.cross(u, w)
                 n /= np.linalg.norm(n)
@@ -373,3 +378,19 @@ def subsets_random(n_views, n_subsets, seed):
     near-equal contiguous pieces."""
     perm = np.random.Generator(np.random.PCG64(seed)).permutation(n_views)
     return [list(map(int, c)) for c in np.array_split(perm, n_subsets) if len(c)]
+
+
+def efov_windows(cfg, u_cor, seed):
+    """Per-view backprojection windows [V, 4] = (u_lo, u_hi, v_lo, v_hi) for an
+    offset-centre-of-rotation scan whose rotation axis projects at column
+    ``u_cor``: the inner detector edge is moved, per view, to a column drawn
+    uniformly from [0, u_cor] (between the physical edge and the projected
+    centre of rotation); PCG64(seed), one draw per view."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo = rng.integers(0, int(u_cor) + 1, size=cfg.n_views)
+    win = np.zeros((cfg.n_views, 4), dtype=np.int32)
+    win[:, 0] = lo
+    win[:, 1] = cfg.nu - 1
+    win[:, 2] = 0
+    win[:, 3] = cfg.nv - 1
+    return win

@@ -627,3 +627,32 @@ def test_subset_schedules_partition_views():
         flat = sorted(v for s in sets for v in s)
         assert flat == list(range(max(flat) + 1))
     assert inputs.subsets_cyclic(8, 4)[:2] == [[0, 4], [2, 6]]  # bit-reversed visiting order
+
+
+# ---------------------------------------------------------------------------
+# Extended field of view: per-view backprojection windows (Sec. 3.6, 4.3.2)
+# ---------------------------------------------------------------------------
+
+def test_bp_window_equals_cropped_detector():
+    cfg = small(n=16, nu=30, nv=24, n_views=5, trajectory="perturbed", seed=41)
+    pb = oracle_problem(cfg)
+    rng = np.random.default_rng(41)
+    r = rng.normal(size=(cfg.n_views, cfg.nv, cfg.nu))
+    full = np.tile(np.array([0, cfg.nu - 1, 0, cfg.nv - 1], np.int32), (cfg.n_views, 1))
+    _, b0, c0 = oracle.backproject(pb, r)
+    _, b1, c1 = oracle.backproject(pb.with_window(full), r)
+    assert np.array_equal(b0, b1) and np.array_equal(c0, c1)
+    # a window [u0, u1] x [v0, v1] is the backprojector of a detector cropped to
+    # it: shift the pixel origin by (u0, v0) and crop the images
+    win = np.array([[3, 25, 2, 20], [0, 29, 5, 23], [7, 20, 0, 23], [1, 28, 1, 22], [10, 29, 4, 15]], np.int32)
+    _, bw, cw = oracle.backproject(pb.with_window(win), r)
+    bc, cc = np.zeros(cfg.vol_shape), np.zeros(cfg.vol_shape)
+    for v in range(cfg.n_views):
+        u0, u1, v0, v1 = win[v]
+        T = np.array([[1.0, 0.0, -u0], [0.0, 1.0, -v0], [0.0, 0.0, 1.0]])
+        Pc = (T @ pb.P[v, 0])[None, None]
+        pv = oracle.Problem(Pc, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin, (u1 - u0 + 1, v1 - v0 + 1))
+        _, bv, cv = oracle.backproject(pv, r[v:v + 1, v0:v1 + 1, u0:u1 + 1])
+        bc += bv
+        cc += cv
+    assert np.allclose(bw, bc, atol=1e-12) and np.allclose(cw, cc, atol=1e-12)
