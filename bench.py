@@ -298,6 +298,12 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / fwd_avg / 1e9
     l2_peak = l2_copy_bandwidth(device)
+    from paper_2609_30166_gb300 import ctrex as _ct
+
+    gather_peak = _ct.probe_gather_rate(device)
+    gathers_per_sample = 1 if tdt == torch.bfloat16 else 2
+    fwd_gathers = gathers_per_sample * n_samples / fwd_avg
+    bp_gathers = n_updates / (statistics.mean(bp_ms) / 1e3)
     out = {
         "metric": METRIC, "value": value, "unit": "GUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -317,6 +323,10 @@ def run_ours(args):
                      "kernel": "fwd_kernel (fused forward + correction)",
                      "l2_gather": {"peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
                                    "peak_method": "torch copy of 16 MiB buffers resident in L2, read+write bytes"},
+                     "tex_gather": {"achieved": fwd_gathers, "peak": gather_peak, "unit": "gathers/s",
+                                    "frac": fwd_gathers / gather_peak, "per_sample": gathers_per_sample,
+                                    "bp_achieved": bp_gathers, "bp_frac": bp_gathers / gather_peak,
+                                    "peak_method": "ctrex_probe_gather_rate: tex2Dgather on an L1-resident texture"},
                      "note": f"algorithmic gather bytes = 8 taps x {elt} B per sample; peak = HBM copy "
                              f"bandwidth ({peak_kind}); the gather is served mostly from L1/L2"},
         "gpu_launches": 3 * args.steps,

@@ -312,6 +312,15 @@ int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, 
                        int cout, int *status, void *cuda_stream);
 
 /*
+ * Measured ceiling of the texture path: tex2Dgather calls per second on the
+ * current device, on a 64 KiB texture that stays in L1 (each call returns a
+ * 2x2 footprint, four 32-bit values, per thread).  Allocates and frees a
+ * small array; synchronises the stream.  The projectors issue 2 gathers per
+ * FP32 sample, 1 per BF16 sample and 1 per backprojected voxel-view.
+ */
+int ctrex_probe_gather_rate(void *cuda_stream, double *gathers_per_s);
+
+/*
  * Detector-space correction without any allocation.  The paper has no
  * counterpart: this is an extra entry point for callers that cannot let the
  * library call cudaMalloc (a host whose caching allocator already reserved

@@ -52,6 +52,75 @@ __device__ __forceinline__ void atlas_quad(const Atlas &A, int s, int x0, int y0
 // (gx, gy, gz); same weights as the row-major sampler, two gathers.
 struct AtlasSampler {
     Atlas A;
+    const float2 *tile = nullptr;  // shared-memory table: slice -> (atlas x, y of its tile) + 1
+
+    static constexpr int TILE_TABLE = 2048;
+    // Fills the per-CTA tile-origin table (all threads call; barrier inside).
+    __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads)
+    {
+        const int n = min(A.n, TILE_TABLE);
+        for (int s = tid; s < n; s += nthreads)
+            table[s] = make_float2((float)((s & ((1 << A.tshift) - 1)) * A.w) + 1.0f,
+                                   (float)((s >> A.tshift) * A.h) + 1.0f);
+        __syncthreads();
+        tile = table;
+    }
+    __device__ __forceinline__ float2 origin(int s) const
+    {
+        if (s < TILE_TABLE) return tile[s];
+        return make_float2((float)((s & ((1 << A.tshift) - 1)) * A.w) + 1.0f, (float)((s >> A.tshift) * A.h) + 1.0f);
+    }
+
+    // Interior sample: all eight taps inside the grid (0 <= g < n - 1 on each
+    // axis), so no zero-padding weights; the row-sum weight is 1.
+    __device__ __forceinline__ float interior(float gx, float gy, float gz) const
+    {
+        const float fx = floorf(gx), fy = floorf(gy), fz = floorf(gz);
+        const int iz = (int)fz;
+        const float ax = gx - fx, ay = gy - fy, az = gz - fz;
+        const float2 o0 = origin(iz);
+        float a00, a10, a01, a11, b00, b10, b01, b11;
+        if (A.packed) {
+            const uint4 q = tex2Dgather<uint4>(A.tex, o0.x + fx, o0.y + fy, 0);
+            a01 = __uint_as_float(q.x << 16);
+            a11 = __uint_as_float(q.y << 16);
+            a10 = __uint_as_float(q.z << 16);
+            a00 = __uint_as_float(q.w << 16);
+            b01 = __uint_as_float(q.x & 0xFFFF0000u);
+            b11 = __uint_as_float(q.y & 0xFFFF0000u);
+            b10 = __uint_as_float(q.z & 0xFFFF0000u);
+            b00 = __uint_as_float(q.w & 0xFFFF0000u);
+        } else {
+            const float2 o1 = origin(iz + 1);
+            if (A.bf16) {
+                const ushort4 q = tex2Dgather<ushort4>(A.tex, o0.x + fx, o0.y + fy, 0);
+                const ushort4 r = tex2Dgather<ushort4>(A.tex, o1.x + fx, o1.y + fy, 0);
+                a01 = __uint_as_float((unsigned)q.x << 16);
+                a11 = __uint_as_float((unsigned)q.y << 16);
+                a10 = __uint_as_float((unsigned)q.z << 16);
+                a00 = __uint_as_float((unsigned)q.w << 16);
+                b01 = __uint_as_float((unsigned)r.x << 16);
+                b11 = __uint_as_float((unsigned)r.y << 16);
+                b10 = __uint_as_float((unsigned)r.z << 16);
+                b00 = __uint_as_float((unsigned)r.w << 16);
+            } else {
+                const float4 q = tex2Dgather<float4>(A.tex, o0.x + fx, o0.y + fy, 0);
+                const float4 r = tex2Dgather<float4>(A.tex, o1.x + fx, o1.y + fy, 0);
+                a01 = q.x;
+                a11 = q.y;
+                a10 = q.z;
+                a00 = q.w;
+                b01 = r.x;
+                b11 = r.y;
+                b10 = r.z;
+                b00 = r.w;
+            }
+        }
+        const float c0 = fmaf(ay, fmaf(ax, a11 - a01, a01) - fmaf(ax, a10 - a00, a00), fmaf(ax, a10 - a00, a00));
+        const float c1 = fmaf(ay, fmaf(ax, b11 - b01, b01) - fmaf(ax, b10 - b00, b00), fmaf(ax, b10 - b00, b00));
+        return fmaf(az, c1 - c0, c0);
+    }
+
     __device__ __forceinline__ float operator()(float gx, float gy, float gz, float &wsum) const
     {
         const float fx = floorf(gx), fy = floorf(gy), fz = floorf(gz);
@@ -104,6 +173,9 @@ template <typename TV>
 struct LinearSampler {
     const TV *vol;
     int nx, ny, nz;
+    static constexpr int TILE_TABLE = 1;
+    __device__ __forceinline__ void bind(float2 *, int, int) {}
+    __device__ __forceinline__ float interior(float gx, float gy, float gz) const;
     __device__ __forceinline__ float operator()(float gx, float gy, float gz, float &wsum) const;
 };
 

@@ -15,6 +15,7 @@
 namespace ctrex {
 
 constexpr int BP_TX = 32, BP_TY = 4, BP_TZ = 2;
+constexpr int BP_VZ = 2;  // voxels per thread along z (consecutive slices)
 constexpr int BP_THREADS = BP_TX * BP_TY * BP_TZ;
 constexpr int BP_CHUNK = 128;
 
@@ -72,23 +73,60 @@ struct AtlasImages {
     }
 };
 
-template <typename Images, typename TV>
-__global__ void __launch_bounds__(BP_THREADS)
+// 1/x: the hardware approximation refined by one Newton-Raphson step
+// r1 = r0 (2 - x r0), which roughly doubles its correct bits.
+__device__ __forceinline__ float recip(float x)
+{
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(x));
+    return r0 * fmaf(-x, r0, 2.0f);
+}
+
+// One voxel-view term: bilinear sample of the view's correction image at the
+// projection (h1/h3, h2/h3) of the voxel centre, accumulated into b, and the
+// in-range weight into c.  Taps outside the window [lo.x, hi.x] x [lo.y,
+// hi.y] (the detector, or a per-view backprojection window) count as off the
+// detector.  Projections whose four taps are all inside (the common case)
+// take the short path: plain weights and c += 1.
+template <typename Images>
+__device__ __forceinline__ void bp_term(const Images &img, const typename Images::Slot &slot, float h1, float h2,
+                                        float h3, float2 lo, float2 hi, float &b, float &c)
+{
+    if (!(h3 > 0.0f)) return;
+    const float inv = recip(h3);
+    const float u = h1 * inv, v = h2 * inv;
+    const float fu = floorf(u), fv = floorf(v);
+    const float au = u - fu, av = v - fv;
+    if (u >= lo.x && u <= hi.x && v >= lo.y && v <= hi.y) {
+        b += img(slot, (int)fu, (int)fv, fu, fv, 1.0f - au, au, 1.0f - av, av);
+        c += 1.0f;
+    } else if (u > lo.x - 1.0f && u < hi.x + 1.0f && v > lo.y - 1.0f && v < hi.y + 1.0f) {
+        const float wu0 = fu >= lo.x ? 1.0f - au : 0.0f;
+        const float wu1 = fu + 1.0f <= hi.x ? au : 0.0f;
+        const float wv0 = fv >= lo.y ? 1.0f - av : 0.0f;
+        const float wv1 = fv + 1.0f <= hi.y ? av : 0.0f;
+        b += img(slot, (int)fu, (int)fv, fu, fv, wu0, wu1, wv0, wv1);
+        c += (wu0 + wu1) * (wv0 + wv1);
+    }
+}
+
+template <typename Images, typename TV, bool WINDOW>
+__global__ void __launch_bounds__(BP_THREADS, 4)
     bp_kernel(Grid G, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx, int n_idx,
               const Images img, const int4 *__restrict__ window, TV *__restrict__ vol, const float *__restrict__ w,
               float alpha, int normalize, int accumulate)
 {
     __shared__ float4 sP[BP_CHUNK][3];
     __shared__ typename Images::Slot sImg[BP_CHUNK];
-    __shared__ int4 sWin[BP_CHUNK];  // per-view detector window (u_lo, u_hi, v_lo, v_hi)
+    __shared__ float4 sWin[WINDOW ? BP_CHUNK : 1];  // per-view window (u_lo, u_hi, v_lo, v_hi)
     const int tid = (threadIdx.z * BP_TY + threadIdx.y) * BP_TX + threadIdx.x;
     const int ix = blockIdx.x * BP_TX + threadIdx.x;
     const int iy = blockIdx.y * BP_TY + threadIdx.y;
-    const int iz = blockIdx.z * BP_TZ + threadIdx.z;
+    const int iz = (blockIdx.z * BP_TZ + threadIdx.z) * BP_VZ;  // this thread: slices iz, iz + 1
     const bool inside = ix < G.nx && iy < G.ny && iz < G.nz;
     const float fx = (float)ix, fy = (float)iy, fz = (float)iz;
-    const int nu = G.nu, nv = G.nv;
-    float b = 0.0f, c = 0.0f;
+    float2 lo = make_float2(0.0f, 0.0f), hi = make_float2((float)(G.nu - 1), (float)(G.nv - 1));
+    float b0 = 0.0f, c0 = 0.0f, b1 = 0.0f, c1 = 0.0f;
     const int total = n_idx * G.n_sub;
     for (int base = 0; base < total; base += BP_CHUNK) {
         const int cnt = min(BP_CHUNK, total - base);
@@ -105,46 +143,43 @@ __global__ void __launch_bounds__(BP_THREADS)
             // an invalid view index gets a zero depth row: it is skipped
             sP[t][2] = ok ? make_float4(P[8], P[9], P[10], P[11]) : make_float4(0.f, 0.f, 0.f, 0.f);
             sImg[t] = img.slot(k);
-            sWin[t] = window ? window[view] : make_int4(0, G.nu - 1, 0, G.nv - 1);
+            if (WINDOW) {
+                const int4 wd = window[view];
+                sWin[t] = make_float4((float)wd.x, (float)wd.y, (float)wd.z, (float)wd.w);
+            }
         }
         __syncthreads();
         if (!inside) continue;
         for (int m = 0; m < cnt; ++m) {
-            const float4 p2 = sP[m][2];
+            const float4 p0 = sP[m][0], p1 = sP[m][1], p2 = sP[m][2];
+            const typename Images::Slot slot = sImg[m];
+            if (WINDOW) {
+                const float4 wd = sWin[m];
+                lo = make_float2(wd.x, wd.z);
+                hi = make_float2(wd.y, wd.w);
+            }
+            // voxel (ix, iy, iz) and its z neighbour: h(z + 1) = h(z) + P[:, 2]
             const float h3 = fmaf(p2.x, fx, fmaf(p2.y, fy, fmaf(p2.z, fz, p2.w)));
-            if (!(h3 > 0.0f)) continue;
-            const float4 p0 = sP[m][0], p1 = sP[m][1];
             const float h1 = fmaf(p0.x, fx, fmaf(p0.y, fy, fmaf(p0.z, fz, p0.w)));
             const float h2 = fmaf(p1.x, fx, fmaf(p1.y, fy, fmaf(p1.z, fz, p1.w)));
-            const float inv = __frcp_rn(h3);
-            const float u = h1 * inv, v = h2 * inv;
-            // taps outside the view's detector window (the whole detector by
-            // default) count as off the detector
-            const int4 win = sWin[m];
-            if (!(u > (float)(win.x - 1) && u < (float)(win.y + 1) && v > (float)(win.z - 1) &&
-                  v < (float)(win.w + 1)))
-                continue;
-            const float fu = floorf(u), fv = floorf(v);
-            const int iu = (int)fu, iv = (int)fv;
-            const float au = u - fu, av = v - fv;
-            const float wu0 = iu >= win.x ? 1.0f - au : 0.0f;
-            const float wu1 = iu + 1 <= win.y ? au : 0.0f;
-            const float wv0 = iv >= win.z ? 1.0f - av : 0.0f;
-            const float wv1 = iv + 1 <= win.w ? av : 0.0f;
-            b += img(sImg[m], iu, iv, fu, fv, wu0, wu1, wv0, wv1);
-            c += (wu0 + wu1) * (wv0 + wv1);
+            bp_term(img, slot, h1, h2, h3, lo, hi, b0, c0);
+            bp_term(img, slot, h1 + p0.z, h2 + p1.z, h3 + p2.z, lo, hi, b1, c1);
         }
     }
     if (!inside) return;
-    b *= G.inv_sub;
-    c *= G.inv_sub;
-    const size_t j = ((size_t)iz * G.ny + iy) * G.nx + ix;
-    float scale = alpha;
-    if (normalize) scale *= (c > 1e-6f ? 1.0f / c : 0.0f);
-    if (w) scale *= __ldg(w + j);
-    const float upd = scale * b;
-    const float out = accumulate ? Storage<TV>::load(vol + j) + upd : upd;
-    Storage<TV>::store(vol + j, out);
+#pragma unroll
+    for (int q = 0; q < BP_VZ; ++q) {
+        if (iz + q >= G.nz) break;
+        const float b = (q == 0 ? b0 : b1) * G.inv_sub;
+        const float c = (q == 0 ? c0 : c1) * G.inv_sub;
+        const size_t j = ((size_t)(iz + q) * G.ny + iy) * G.nx + ix;
+        float scale = alpha;
+        if (normalize) scale *= (c > 1e-6f ? 1.0f / c : 0.0f);
+        if (w) scale *= __ldg(w + j);
+        const float upd = scale * b;
+        const float out = accumulate ? Storage<TV>::load(vol + j) + upd : upd;
+        Storage<TV>::store(vol + j, out);
+    }
 }
 
 template <typename Images, typename TV>
@@ -152,10 +187,16 @@ static cudaError_t bp_launch(const BpArgs &a, const Images &img)
 {
     const Grid &G = *a.grid;
     const dim3 block(BP_TX, BP_TY, BP_TZ);
-    const dim3 grid((G.nx + BP_TX - 1) / BP_TX, (G.ny + BP_TY - 1) / BP_TY, (G.nz + BP_TZ - 1) / BP_TZ);
-    bp_kernel<Images, TV><<<grid, block, 0, a.stream>>>(G, a.views, a.view_idx, a.n_idx, img, a.window,
-                                                       static_cast<TV *>(a.vol), a.w, a.alpha, a.normalize,
-                                                       a.accumulate);
+    const dim3 grid((G.nx + BP_TX - 1) / BP_TX, (G.ny + BP_TY - 1) / BP_TY,
+                    (G.nz + BP_TZ * BP_VZ - 1) / (BP_TZ * BP_VZ));
+    if (a.window)
+        bp_kernel<Images, TV, true><<<grid, block, 0, a.stream>>>(G, a.views, a.view_idx, a.n_idx, img, a.window,
+                                                                 static_cast<TV *>(a.vol), a.w, a.alpha, a.normalize,
+                                                                 a.accumulate);
+    else
+        bp_kernel<Images, TV, false><<<grid, block, 0, a.stream>>>(G, a.views, a.view_idx, a.n_idx, img, nullptr,
+                                                                  static_cast<TV *>(a.vol), a.w, a.alpha,
+                                                                  a.normalize, a.accumulate);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,72 @@
+// probe.cu -- measured ceilings used to judge the projectors: the texture
+// unit's gather throughput on an L1-resident texture (the projectors are
+// bound by the texture return path, not by HBM).
+#include "atlas.cuh"
+
+namespace {
+
+constexpr int PROBE_W = 128;  // 128 x 128 FP32 texels = 64 KiB, L1 resident
+
+__global__ void __launch_bounds__(128) gather_probe_kernel(cudaTextureObject_t tex, int iters, float *sink)
+{
+    float acc = 0.0f;
+    unsigned x = (blockIdx.x * 37u + threadIdx.x) & (PROBE_W - 1);
+    unsigned y = (blockIdx.x * 11u + threadIdx.x * 3u) & (PROBE_W - 1);
+    for (int i = 0; i < iters; ++i) {
+        const float4 q = tex2Dgather<float4>(tex, (float)x + 1.0f, (float)y + 1.0f, 0);
+        acc += q.x + q.y + q.z + q.w;
+        x = (x + 5u) & (PROBE_W - 1);
+        y = (y + 3u) & (PROBE_W - 1);
+    }
+    if (acc == 123456.0f) sink[0] = acc;  // keeps the loop alive
+}
+
+}  // namespace
+
+extern "C" int ctrex_probe_gather_rate(void *cuda_stream, double *gathers_per_s)
+{
+    if (!gathers_per_s) return CTREX_E_ARG;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return CTREX_E_CUDA;
+    }
+    cudaChannelFormatDesc desc = cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat);
+    cudaArray_t arr = nullptr;
+    cudaTextureObject_t tex = 0;
+    float *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = CTREX_E_CUDA;
+    if (cudaMallocArray(&arr, &desc, PROBE_W, PROBE_W) == cudaSuccess && cudaMalloc((void **)&sink, 4) == cudaSuccess &&
+        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        cudaResourceDesc rd = {};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = arr;
+        cudaTextureDesc td = {};
+        td.addressMode[0] = td.addressMode[1] = cudaAddressModeBorder;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        if (cudaCreateTextureObject(&tex, &rd, &td, nullptr) == cudaSuccess) {
+            const int blocks = sms * 16, iters = 2048;
+            gather_probe_kernel<<<blocks, 128, 0, stream>>>(tex, 64, sink);  // warm-up
+            cudaEventRecord(e0, stream);
+            gather_probe_kernel<<<blocks, 128, 0, stream>>>(tex, iters, sink);
+            cudaEventRecord(e1, stream);
+            float ms = 0.0f;
+            if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+                ms > 0.0f) {
+                *gathers_per_s = (double)blocks * 128.0 * iters / (ms * 1e-3);
+                rc = CTREX_OK;
+            }
+        }
+    }
+    cudaGetLastError();
+    if (tex) cudaDestroyTextureObject(tex);
+    if (arr) cudaFreeArray(arr);
+    if (sink) cudaFree(sink);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
+}

@@ -26,6 +26,40 @@ __device__ __forceinline__ float LinearSampler<TV>::operator()(float gx, float g
     return trilinear(vol, nx, ny, nz, gx, gy, gz, wsum);
 }
 
+template <typename TV>
+__device__ __forceinline__ float LinearSampler<TV>::interior(float gx, float gy, float gz) const
+{
+    float ws;
+    return trilinear(vol, nx, ny, nz, gx, gy, gz, ws);
+}
+
+// Samples k of the interior range [ka, kb) have every trilinear tap inside the
+// grid: g0 + k sg in [eps, n - 1 - eps] on each axis, with a margin eps far
+// above the rounding of the sample positions, so the short path is exact.
+__device__ __forceinline__ void interior_range(const Grid &G, const Ray &R, int &ka, int &kb)
+{
+    const float eps = 1e-2f;
+    const int n[3] = {G.nx, G.ny, G.nz};
+    float lo = 0.0f, hi = (float)(R.K - 1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float l = eps, h = (float)(n[a] - 1) - eps;
+        if (R.sg[a] != 0.0f) {
+            const float inv = 1.0f / R.sg[a];
+            const float t0 = (l - R.g0[a]) * inv, t1 = (h - R.g0[a]) * inv;
+            lo = fmaxf(lo, fminf(t0, t1));
+            hi = fminf(hi, fmaxf(t0, t1));
+        } else if (!(R.g0[a] >= l && R.g0[a] <= h)) {
+            hi = -1.0f;
+        }
+    }
+    ka = (int)ceilf(lo);
+    kb = (int)floorf(hi) + 1;
+    // keep one sample of rounding slack on each side in the exact path
+    ka = min(max(ka + 1, 0), R.K - 1);
+    kb = max(min(kb - 1, R.K - 1), ka);
+}
+
 // Integral of one pixel (mean over its sub-angle rays): value and row sum.
 template <typename Sampler, bool MOTION>
 __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__restrict__ views,
@@ -40,7 +74,9 @@ __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__r
         if (!setup_ray(G, V, u, v, R)) continue;
         float a = 0.0f, ars = 0.0f;
         const int Km1 = R.K - 1;
-        for (int k = 0; k < Km1; ++k) {
+        int ka = Km1, kb = Km1;
+        if (!MOTION) interior_range(G, R, ka, kb);
+        auto general = [&](int k) {
             float g[3];
             g[0] = fmaf((float)k, R.sg[0], R.g0[0]);
             g[1] = fmaf((float)k, R.sg[1], R.g0[1]);
@@ -55,6 +91,15 @@ __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__r
             float ws;
             a += vol(g[0], g[1], g[2], ws);
             ars += ws;
+        };
+        const int kstop = MOTION ? Km1 : ka;
+        for (int k = 0; k < kstop; ++k) general(k);
+        if (!MOTION) {
+            for (int k = ka; k < kb; ++k)
+                a += vol.interior(fmaf((float)k, R.sg[0], R.g0[0]), fmaf((float)k, R.sg[1], R.g0[1]),
+                                  fmaf((float)k, R.sg[2], R.g0[2]));
+            ars += (float)(kb - ka);
+            for (int k = kb; k < Km1; ++k) general(k);
         }
         a *= G.step_mm;
         ars *= G.step_mm;
@@ -81,12 +126,15 @@ __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__r
 template <typename Sampler, typename TP, int MODE, bool MOTION>
 __global__ void __launch_bounds__(FWD_TX *FWD_TY)
     fwd_kernel(Grid G, const ViewGPU *__restrict__ views, const MotionGPU *__restrict__ motion,
-               const float *__restrict__ coef_g, const Sampler vol,
+               const float *__restrict__ coef_g, const Sampler vol_in,
                const int *__restrict__ view_idx, TP *__restrict__ out, float *__restrict__ rowsum_out,
                const TP *__restrict__ p, float *__restrict__ partials, unsigned *devcheck, int p_by_view)
 {
     __shared__ float s_coef[MOTION ? 8 * 8 * 8 * 3 : 1];
     __shared__ float s_red[2][FWD_TX * FWD_TY / 32];
+    __shared__ float2 s_tile[Sampler::TILE_TABLE];
+    Sampler vol = vol_in;
+    vol.bind(s_tile, threadIdx.y * FWD_TX + threadIdx.x, FWD_TX * FWD_TY);
     const int k = blockIdx.y;
     int view = view_idx ? view_idx[k] : k;
     bool ok = true;

@@ -32,6 +32,7 @@ EXPORTS = (
     "ctrex_fwd_correct", "ctrex_back_project", "ctrex_adjoint_project", "ctrex_motion_grad",
     "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples", "ctrex_correct_static",
     "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad", "ctrex_os_sirt_iterate", "ctrex_set_bp_window",
+    "ctrex_probe_gather_rate",
 )
 
 # Largest n ctrex_correct_static accepts (its static scratch holds 65536 CTA partials of 8192 elements).
@@ -90,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         "ctrex_conv3d_wgrad": ([vp, vp, vp, i, i, i, i, i, i, vp, vp], i),
         "ctrex_os_sirt_iterate": ([vp, vp, i, vp, i, ip, ip, i, i, f, vp, f, fp, ip], i),
         "ctrex_set_bp_window": ([vp, ip], i),
+        "ctrex_probe_gather_rate": ([vp, ctypes.POINTER(d)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -440,6 +442,19 @@ def flip_weights(wt):
     """wt [Cout, 27, Cin] -> the weights of the input-gradient convolution,
     [Cin, 27, Cout] with the taps reversed (a copy, no arithmetic)."""
     return wt.flip(1).transpose(0, 2).contiguous()
+
+
+def probe_gather_rate(device=None):
+    """Measured tex2Dgather calls per second (L1-resident texture)."""
+    lib = load_library()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    out = ctypes.c_double(0.0)
+    with torch.cuda.device(dev):
+        rc = lib.ctrex_probe_gather_rate(ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream),
+                                         ctypes.byref(out))
+    if rc != OK:
+        raise CtrexError(rc, "gather-rate probe failed")
+    return out.value
 
 
 def context_for(cfg, P=None, device=None):
