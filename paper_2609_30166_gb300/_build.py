@@ -43,7 +43,20 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build_library(extra_flags=(), verbose=False) -> str:
+def build_library(extra_flags=(), verbose=False, lib=None, build_dir=None) -> str:
+    """Build libctrex.so (or ``lib``, with objects in ``build_dir``) with the
+    given extra nvcc flags."""
+    global LIB, BUILD
+    lib_path, build_path = LIB, BUILD
+    if lib is not None:
+        LIB, BUILD = lib, build_dir or os.path.join(os.path.dirname(lib), "_objs")
+    try:
+        return _build(extra_flags, verbose)
+    finally:
+        LIB, BUILD = lib_path, build_path
+
+
+def _build(extra_flags, verbose) -> str:
     os.makedirs(BUILD, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")))

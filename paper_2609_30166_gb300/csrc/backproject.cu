@@ -18,6 +18,9 @@ constexpr int BP_TX = 32, BP_TY = 4, BP_TZ = 2;
 constexpr int BP_VZ = 2;  // voxels per thread along z (consecutive slices)
 constexpr int BP_THREADS = BP_TX * BP_TY * BP_TZ;
 constexpr int BP_CHUNK = 128;
+#ifndef CTREX_BP_MIN_BLOCKS
+#define CTREX_BP_MIN_BLOCKS 8  // CTAs per SM the register budget is sized for (full occupancy)
+#endif
 
 // Bilinear sample of one correction image at (u, v) = (iu + au, iv + av),
 // zero outside the detector (taps outside get zero weight).  A Slot holds what
@@ -111,7 +114,7 @@ __device__ __forceinline__ void bp_term(const Images &img, const typename Images
 }
 
 template <typename Images, typename TV, bool WINDOW>
-__global__ void __launch_bounds__(BP_THREADS, 4)
+__global__ void __launch_bounds__(BP_THREADS, CTREX_BP_MIN_BLOCKS)
     bp_kernel(Grid G, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx, int n_idx,
               const Images img, const int4 *__restrict__ window, TV *__restrict__ vol, const float *__restrict__ w,
               float alpha, int normalize, int accumulate)

@@ -15,7 +15,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libctrex.so")
+# CTREX_LIB may point at another build of the same sources (e.g. a variant
+# compiled with different tuning flags); the default is the in-tree build.
+LIB_PATH = os.environ.get("CTREX_LIB") or os.path.join(_HERE, "libctrex.so")
 
 F32, BF16 = 0, 1
 OK = 0
