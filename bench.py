@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="64^3 workload (quick check)")
     ap.add_argument("--warm-start-steps", type=int, default=400,
                     help="train the U-Net warm start this many steps and report time to residual 1e-3 (0: skip)")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the per-row measurements (sub-angle, motion, adjoint, gradient, conv)")
     ap.add_argument("--views", type=int, default=0,
                     help="override the number of views (small cases for ncu captures; not a bench line)")
     return ap.parse_args()
@@ -214,6 +216,96 @@ def build_workload(cfg, device, dtype):
     return ctx, P, phantom, p, tdt
 
 
+def _time(fn, reps=3, warm=1):
+    """Mean CUDA-event time (s) of fn() on the current stream."""
+    import torch
+
+    for _ in range(warm):
+        fn()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / 1e3 / reps
+
+
+# FP32 operations per motion-warped sample: 64-control-point cubic B-spline
+# (per point one weight product and three FMAs, plus per-axis weights), the
+# pose (9 FMA + 3), trilinear interpolation; counted from ray.cuh.
+MOTION_OPS_PER_SAMPLE = 64 * 4 + 16 + 3 * 10 + 12 + 30
+
+
+def measure_rows(device, gather_peak, sm_count, sm_mhz):
+    """Throughput of the survey rows the SIRT step does not exercise, each on
+    its full-size workload, with the ceiling that bounds it."""
+    import torch
+
+    from paper_2609_30166_gb300 import ctrex, inputs
+
+    rows = {}
+    # a3 + a11: helical sub-angle projector, BF16 volume, FP32 accumulation
+    cfg = inputs.HELICAL_256
+    ctx = ctrex.context_for(cfg, device=device)
+    vol16 = inputs.phantom(cfg, device=str(device)).to(torch.bfloat16).contiguous()
+    out = torch.empty((cfg.n_views, cfg.nv, cfg.nu), dtype=torch.float32, device=device)
+    ns = ctx.count_samples()
+    t = _time(lambda: ctx.fwd_project(vol16, proj=out))
+    rows["a3_helical_subangle_bf16"] = {"workload": cfg.name, "samples": ns, "ms": t * 1e3,
+                                        "gsamples_per_s": ns / t / 1e9,
+                                        "tex_gather_frac": ns / t / gather_peak}
+    del ctx, vol16, out
+    # a4, a8, a9: motion-aware projector, matched adjoint, motion gradient
+    cfg = inputs.MOTION_256
+    ctx = ctrex.context_for(cfg, device=device)
+    th, co, sv = inputs.motion_params(cfg)
+    f = lambda a: torch.as_tensor(a, dtype=torch.float32, device=device).contiguous()  # noqa: E731
+    ctx.set_motion(f(th), f(co), f(sv), cfg.margin)
+    vol = inputs.phantom(cfg, device=str(device)).float().contiguous()
+    ns = ctx.count_samples()
+    proj = ctx.fwd_project(vol)
+    g = torch.randn(proj.shape, device=device, generator=torch.Generator(device=device).manual_seed(1))
+    adj = torch.zeros_like(vol)
+    alu_peak = sm_count * 128 * sm_mhz * 1e6  # FP32 lanes x clock (an FMA counted once)
+    t_f = _time(lambda: ctx.fwd_project(vol, proj=proj))
+    t_a = _time(lambda: ctx.adjoint_project(g, vol=adj))
+    t_g = _time(lambda: ctx.motion_grad(vol, g), reps=2)
+    rows["a4_motion_projector"] = {"workload": cfg.name, "samples": ns, "ms": t_f * 1e3,
+                                   "gsamples_per_s": ns / t_f / 1e9,
+                                   "alu_frac_est": ns * MOTION_OPS_PER_SAMPLE / t_f / alu_peak,
+                                   "alu_peak_ops_per_s": alu_peak,
+                                   "ops_per_sample_est": MOTION_OPS_PER_SAMPLE}
+    rows["a8_matched_adjoint"] = {"workload": cfg.name, "ms": t_a * 1e3, "gsamples_per_s": ns / t_a / 1e9,
+                                  "atomics_per_s": 8 * ns / t_a}
+    rows["a9_motion_gradient"] = {"workload": cfg.name, "ms": t_g * 1e3, "gsamples_per_s": ns / t_g / 1e9}
+    del ctx, vol, proj, g, adj
+    # a12: tcgen05 implicit-GEMM convolution, the U-Net's levels (batch 2 at 128^3)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16_peak = float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        bf16_peak = 1900.0
+    convs = {}
+    gen = torch.Generator(device=device).manual_seed(2)
+    for (n, cin, cout) in ((128, 16, 16), (64, 32, 32), (32, 64, 64), (16, 128, 128), (32, 192, 64)):
+        x = torch.randn((2, n, n, n, cin), device=device, generator=gen).to(torch.bfloat16)
+        wt = (torch.randn((cout, 27, cin), device=device, generator=gen) * 0.05).to(torch.bfloat16)
+        dy = torch.randn((2, n, n, n, cout), device=device, generator=gen).to(torch.bfloat16)
+        flops = 2.0 * x.numel() / cin * 27 * cin * cout
+        t_fw = _time(lambda: ctrex.conv3d(x, wt, relu=True))
+        t_wg = _time(lambda: ctrex.conv3d_wgrad(x, dy))
+        convs[f"{n}^3 x2, {cin}->{cout}"] = {"fwd_ms": t_fw * 1e3, "fwd_tflops": flops / t_fw / 1e12,
+                                             "wgrad_ms": t_wg * 1e3, "wgrad_tflops": flops / t_wg / 1e12}
+    ctrex.conv_status_check(device)
+    best = max(v["fwd_tflops"] for v in convs.values())
+    rows["a12_conv3d_tcgen05"] = {"layers": convs, "best_fwd_tflops": best, "bf16_peak_tflops": bf16_peak,
+                                  "best_fwd_frac": best / bf16_peak}
+    torch.cuda.empty_cache()
+    return rows
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -333,6 +425,12 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_rows and not args.views and not args.small:
+        sm_count = torch.cuda.get_device_properties(device).multi_processor_count
+        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        del x, r
+        torch.cuda.empty_cache()
+        out["rows"] = measure_rows(device, gather_peak, sm_count, sm_mhz)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         vol_np = phantom.double().cpu().numpy()
         ncpu_units, ncpu_s, desc = oracle_sample_run(cfg, P, vol_np, n_fwd_views=1 if not args.small else 8,
@@ -343,7 +441,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and args.warm_start_steps > 0 and not args.views and not args.small:
         from paper_2609_30166_gb300 import warmstart
 
-        del x, r, p, phantom
+        del p, phantom
         torch.cuda.empty_cache()
         ws = warmstart.run(n_train=56, n_test=4, steps=args.warm_start_steps)
         out["time_to_residual_1e-3"] = {

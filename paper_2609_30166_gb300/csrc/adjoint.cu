@@ -225,44 +225,53 @@ __device__ __forceinline__ void grad_sample(const Grid &G, const MotionGPU &m, c
         gM[3 * r + 2] = fmaf(ggp[r], g[2], gM[3 * r + 2]);
     }
     if (s_gcoef == nullptr || m.s == 0.0f) return;
-    // dL/dcoef[cell][c] += s * dL/dy[c] * beta product.  All lanes of the warp
-    // take part (inactive lanes contribute zero); if the warp sits in one
-    // spline cell the 192 contributions are warp-reduced before one shared
-    // atomic each, else every lane adds its own.
+    // dL/dcoef[cell + (i, j, k)][c] += s * dL/dy[c] * wx[i] wy[j] wz[k] for the
+    // 4 x 4 x 4 support of each lane's spline cell.  Lanes are served one cell
+    // at a time (a warp's rays usually share one cell, rarely two); for the
+    // lanes of that cell the 192 contributions are summed across the warp by
+    // a reduce-scatter in six passes of 32 entries (31 shuffles each), after
+    // which lane l owns entry 32 p + l and adds it to shared memory: no two
+    // lanes of a warp touch the same address.
     const unsigned full = 0xffffffffu;
-    const unsigned act_mask = __ballot_sync(full, active && scale != 0.0f);
-    if (act_mask == 0u) return;  // warp-uniform
-    const int leader = __ffs(act_mask) - 1;
-    const int cell = (i0[2] * 8 + i0[1]) * 8 + i0[0];
-    const int lead_cell = __shfl_sync(full, cell, leader);
-    const bool mine = (act_mask >> (threadIdx.x & 31)) & 1u;
-    const bool uniform = __all_sync(full, !mine || cell == lead_cell);
-    const float vs[3] = {m.s * gy[0], m.s * gy[1], m.s * gy[2]};
     const int lane = threadIdx.x & 31;
+    const int cell = (i0[2] * 8 + i0[1]) * 8 + i0[0];
+    unsigned pending = __ballot_sync(full, active && scale != 0.0f);
+    const float vs[3] = {m.s * gy[0], m.s * gy[1], m.s * gy[2]};
+    while (pending) {  // warp-uniform
+        const int leader = __ffs(pending) - 1;
+        const int lcell = __shfl_sync(full, cell, leader);
+        const bool mine = ((pending >> lane) & 1u) && cell == lcell;
+        const float on = mine ? 1.0f : 0.0f;
+        const int li0[3] = {__shfl_sync(full, i0[0], leader), __shfl_sync(full, i0[1], leader),
+                            __shfl_sync(full, i0[2], leader)};
+        // entry e = c * 64 + (k * 16 + j * 4 + i): pass p (32 entries) holds one
+        // component c = p / 2 and the two z planes k = 2 (p % 2) + {0, 1}
 #pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
-        const int cz = min(i0[2] - 1 + k, 7);
-#pragma unroll 1
-        for (int j = 0; j < 4; ++j) {
-            const int cy = min(i0[1] - 1 + j, 7);
+        for (int pass = 0; pass < 6; ++pass) {
+            const float vc = on * (pass < 2 ? vs[0] : (pass < 4 ? vs[1] : vs[2]));
+            const float wz0 = (pass & 1) ? wz[2] : wz[0], wz1 = (pass & 1) ? wz[3] : wz[1];
+            float v[32];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int cx = min(i0[0] - 1 + i, 7);
-                const float wt = wx[i] * wy[j] * wz[k];
-                float* dst = s_gcoef + 3 * ((cz * 8 + cy) * 8 + cx);
+            for (int q = 0; q < 32; ++q) v[q] = vc * (q < 16 ? wz0 : wz1) * wy[(q >> 2) & 3] * wx[q & 3];
+            // recursive halving: after the offset-o stage a lane keeps the half
+            // of its entries whose bit matches its own lane bit o
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float val = wt * vs[c];
-                    if (uniform) {
+            for (int o = 16, half = 16; o > 0; o >>= 1, half >>= 1) {
+                const bool upper = (lane & o) != 0;
 #pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) val += __shfl_xor_sync(full, val, off);
-                        if (lane == leader && val != 0.0f) atomicAdd(dst + c, val);
-                    } else if (val != 0.0f) {
-                        atomicAdd(dst + c, val);
-                    }
+                for (int q = 0; q < half; ++q) {
+                    const float send = upper ? v[q] : v[q + half];
+                    const float keep = upper ? v[q + half] : v[q];
+                    v[q] = keep + __shfl_xor_sync(full, send, o);
                 }
             }
+            // lane owns entry 32 pass + lane: c = pass / 2, (i, j, k) from the lane
+            const int c = pass >> 1;
+            const int cx = min(li0[0] - 1 + (lane & 3), 7), cy = min(li0[1] - 1 + ((lane >> 2) & 3), 7),
+                      cz = min(li0[2] - 1 + 2 * (pass & 1) + (lane >> 4), 7);
+            if (v[0] != 0.0f) atomicAdd(s_gcoef + 3 * ((cz * 8 + cy) * 8 + cx) + c, v[0]);
         }
+        pending &= ~__ballot_sync(full, mine);
     }
 }
 
