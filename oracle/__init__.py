@@ -88,7 +88,7 @@ class _CProblem(ctypes.Structure):
         ("n_views", ctypes.c_int), ("n_sub", ctypes.c_int),
         ("step_vox", ctypes.c_double),
         ("P", _dp), ("theta", _dp), ("coef", _dp), ("s_view", _dp),
-        ("margin", ctypes.c_double), ("bp_window", _ip),
+        ("margin", ctypes.c_double), ("bp_window", _ip), ("bp_subvoxel", ctypes.c_int),
     ]
 
 
@@ -130,7 +130,7 @@ class Problem:
     """
 
     def __init__(self, P, vol_shape, vox, origin, det, step_vox=0.5, theta=None, coef=None,
-                 s_view=None, margin=0.0, bp_window=None):
+                 s_view=None, margin=0.0, bp_window=None, bp_subvoxel=1):
         P = _f64(P)
         if P.ndim == 3:
             P = P[:, None]
@@ -146,10 +146,12 @@ class Problem:
         self.s_view = None if s_view is None else _f64(s_view)
         self.margin = float(margin)
         self.bp_window = None if bp_window is None else np.ascontiguousarray(bp_window, dtype=np.int32)
+        self.bp_subvoxel = int(bp_subvoxel)
         self._c = _CProblem(self.nx, self.ny, self.nz, (ctypes.c_double * 3)(*self.vox),
                             (ctypes.c_double * 3)(*self.origin), self.nu, self.nv, self.n_views,
                             self.n_sub, self.step_vox, _ptr(self.P), _ptr(self.theta),
-                            _ptr(self.coef), _ptr(self.s_view), self.margin, _ptr(self.bp_window, _ip))
+                            _ptr(self.coef), _ptr(self.s_view), self.margin, _ptr(self.bp_window, _ip),
+                            self.bp_subvoxel)
 
     @property
     def vol_shape(self):
@@ -165,17 +167,22 @@ class Problem:
 
     def with_motion(self, theta=None, coef=None, s_view=None, margin=0.0):
         return Problem(self.P, self.vol_shape, self.vox, self.origin, (self.nu, self.nv),
-                       self.step_vox, theta, coef, s_view, margin, self.bp_window)
+                       self.step_vox, theta, coef, s_view, margin, self.bp_window, self.bp_subvoxel)
 
     def with_P(self, P):
         return Problem(P, self.vol_shape, self.vox, self.origin, (self.nu, self.nv), self.step_vox,
-                       self.theta, self.coef, self.s_view, self.margin, self.bp_window)
+                       self.theta, self.coef, self.s_view, self.margin, self.bp_window, self.bp_subvoxel)
+
+    def with_subvoxel(self, s):
+        """The same problem whose backprojector averages s^3 sub-voxel points."""
+        return Problem(self.P, self.vol_shape, self.vox, self.origin, (self.nu, self.nv), self.step_vox,
+                       self.theta, self.coef, self.s_view, self.margin, self.bp_window, s)
 
     def with_window(self, bp_window):
         """The same problem whose backprojector sees per-view detector windows
         [n_views, 4] = (u_lo, u_hi, v_lo, v_hi) (extended field of view)."""
         return Problem(self.P, self.vol_shape, self.vox, self.origin, (self.nu, self.nv), self.step_vox,
-                       self.theta, self.coef, self.s_view, self.margin, bp_window)
+                       self.theta, self.coef, self.s_view, self.margin, bp_window, self.bp_subvoxel)
 
 
 def _views(pb, views):

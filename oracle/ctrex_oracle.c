@@ -42,7 +42,10 @@
  *   R11 extended field of view (Sec. 3.6, Sec. 4.3.2): the backprojector of
  *      view v sees only detector columns u_lo..u_hi and rows v_lo..v_hi (its
  *      effective edge); taps outside count as off the detector for both the
- *      sum and its normalisation; the forward keeps the whole detector.
+ *      sum and its normalisation; the forward keeps the whole detector;
+ *   R12 sub-voxel backprojection (Sec. 4.3.2, motion blur): with s > 1 the
+ *      backprojected value and column sum of a voxel are the means over the
+ *      s^3 points at offsets ((a + 1/2)/s - 1/2) voxel on each axis.
  *
  * Conventions: volume vol[iz][iy][ix] (x fastest), voxel (0,0,0) centred at
  * origin (mm), index coordinate g = (x - origin) / vox.  Projection images
@@ -71,6 +74,7 @@ typedef struct {
     const double *s_view; /* [n_views] or NULL (then s_v = 0)              */
     double margin;        /* mm, clip-box dilation when motion is on       */
     const int *bp_window; /* [n_views][4] (u_lo, u_hi, v_lo, v_hi) or NULL */
+    int bp_subvoxel;      /* > 1: backproject onto s^3 sub-voxel points     */
 } or_problem;
 
 /* Per (view, sub-angle) quantities derived from P (Sec. 2.2.1). */
@@ -603,11 +607,9 @@ int or_correct(long n, const double *p, const double *q, const double *rowsum, d
  * projected voxel centre, c = the same with r replaced by ones.  r is
  * [n_sel][nv][nu] in the order of views[].
  */
-static void bp_voxel(const or_problem *pb, const or_view *ov, const double *r, const int *views,
-                     int n_sel, int ix, int iy, int iz, double *b_out, double *c_out)
+static void bp_point(const or_problem *pb, const or_view *ov, const double *r, const int *views, int n_sel,
+                     const double X[3], double *b_out, double *c_out)
 {
-    double X[3] = {pb->origin[0] + ix * pb->vox[0], pb->origin[1] + iy * pb->vox[1],
-                   pb->origin[2] + iz * pb->vox[2]};
     double b = 0.0, c = 0.0;
     size_t npix = (size_t)pb->nu * pb->nv;
     for (int k = 0; k < n_sel; ++k) {
@@ -644,6 +646,28 @@ static void bp_voxel(const or_problem *pb, const or_view *ov, const double *r, c
     }
     *b_out = b;
     *c_out = c;
+}
+
+static void bp_voxel(const or_problem *pb, const or_view *ov, const double *r, const int *views,
+                     int n_sel, int ix, int iy, int iz, double *b_out, double *c_out)
+{
+    const int sv = pb->bp_subvoxel > 1 ? pb->bp_subvoxel : 1;
+    const int i[3] = {ix, iy, iz};
+    double b = 0.0, c = 0.0;
+    for (int az = 0; az < sv; ++az)
+        for (int ay = 0; ay < sv; ++ay)
+            for (int ax = 0; ax < sv; ++ax) {
+                const int a[3] = {ax, ay, az};
+                double X[3];
+                for (int d = 0; d < 3; ++d)
+                    X[d] = pb->origin[d] + (i[d] + (a[d] + 0.5) / sv - 0.5) * pb->vox[d];
+                double bb, cc;
+                bp_point(pb, ov, r, views, n_sel, X, &bb, &cc);
+                b += bb;
+                c += cc;
+            }
+    *b_out = b / ((double)sv * sv * sv);
+    *c_out = c / ((double)sv * sv * sv);
 }
 
 /*

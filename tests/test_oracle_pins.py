@@ -656,3 +656,26 @@ def test_bp_window_equals_cropped_detector():
         bc += bv
         cc += cv
     assert np.allclose(bw, bc, atol=1e-12) and np.allclose(cw, cc, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Sub-voxel backprojection (Sec. 4.3.2)
+# ---------------------------------------------------------------------------
+
+def test_subvoxel_bp_is_block_mean_of_fine_grid():
+    cfg = small(n=8, nu=26, nv=22, n_views=4, trajectory="perturbed", seed=51)
+    pb = oracle_problem(cfg)
+    rng = np.random.default_rng(51)
+    r = rng.normal(size=(cfg.n_views, cfg.nv, cfg.nu))
+    _, b1, c1 = oracle.backproject(pb.with_subvoxel(1), r)
+    _, b0, c0 = oracle.backproject(pb, r)
+    assert np.array_equal(b0, b1) and np.array_equal(c0, c1)
+    s = 2
+    _, bs, cs = oracle.backproject(pb.with_subvoxel(s), r)
+    fine_vox = cfg.vox / s
+    fine_origin = tuple(o - 0.5 * cfg.vox + 0.5 * fine_vox for o in cfg.origin)
+    n2 = cfg.n * s
+    pf = oracle.Problem(pb.P, (n2, n2, n2), (fine_vox,) * 3, fine_origin, (cfg.nu, cfg.nv))
+    _, bf, cf = oracle.backproject(pf, r)
+    blk = lambda a: a.reshape(cfg.n, s, cfg.n, s, cfg.n, s).mean(axis=(1, 3, 5))  # noqa: E731
+    assert np.allclose(bs, blk(bf), atol=1e-12) and np.allclose(cs, blk(cf), atol=1e-12)
