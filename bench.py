@@ -428,9 +428,19 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_rows and not args.views and not args.small:
         sm_count = torch.cuda.get_device_properties(device).multi_processor_count
         sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        # sub-voxel backprojection (2^3 points per voxel) of the last step's
+        # correction images, on the same workload
+        ctx.set_bp_subvoxel(2)
+        t_sv = _time(lambda: ctx.back_project(r, vol=x, alpha=1.0, normalize=True, accumulate=True), reps=2)
+        ctx.set_bp_subvoxel(1)
+        sv_points = 8 * n_updates
         del x, r
         torch.cuda.empty_cache()
         out["rows"] = measure_rows(device, gather_peak, sm_count, sm_mhz)
+        out["rows"]["a14_subvoxel_bp"] = {"workload": cfg.name, "s": 2, "ms": t_sv * 1e3,
+                                          "point_updates": sv_points, "gpoint_updates_per_s": sv_points / t_sv / 1e9,
+                                          "tex_gather_frac": sv_points / t_sv / gather_peak,
+                                          "centre_bp_ms": statistics.mean(bp_ms)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         vol_np = phantom.double().cpu().numpy()
         ncpu_units, ncpu_s, desc = oracle_sample_run(cfg, P, vol_np, n_fwd_views=1 if not args.small else 8,

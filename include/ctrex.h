@@ -157,6 +157,22 @@ int ctrex_set_motion(ctrex_ctx *ctx, const float *theta, const float *coef, cons
 int ctrex_set_bp_window(ctrex_ctx *ctx, const int *window);
 
 /*
+ * Sub-voxel backprojection (Sec. 4.3.2, motion-blur compensation: the
+ * backprojector accumulates onto a finer voxel grid).  With s > 1 every
+ * backprojection (ctrex_back_project and the SIRT / OS-SIRT loops) takes,
+ * for voxel j, the means over the s^3 points at index offsets
+ * ((a + 1/2)/s - 1/2), a = 0..s-1, on each axis, of the bilinear correction
+ * sample and of its in-range weight; C_j is 1 / (that mean weight summed
+ * over the views).  The finer grid is not stored.  Equivalent to a
+ * backprojection of b and c onto the s-times finer grid followed by the
+ * s x s x s block mean.  The forward projector is unchanged.
+ *   s        1 (off, the default) .. CTREX_MAX_SUBVOXEL, else CTREX_E_ARG.
+ * The setting belongs to the context and survives set_geometry.
+ */
+#define CTREX_MAX_SUBVOXEL 8
+int ctrex_set_bp_subvoxel(ctrex_ctx *ctx, int s);
+
+/*
  * A x (Sec. 4.1 projection operator; Sec. 3.4 mean over sub-angles; motion
  * if set).  Ray from the source through the pixel centre, clipped to the
  * box, fixed-step truncated-midpoint quadrature with trilinear interpolation

@@ -21,6 +21,9 @@ constexpr int BP_CHUNK = 128;
 #ifndef CTREX_BP_MIN_BLOCKS
 #define CTREX_BP_MIN_BLOCKS 8  // CTAs per SM the register budget is sized for (full occupancy)
 #endif
+#ifndef CTREX_BP_SUBV_MIN_BLOCKS
+#define CTREX_BP_SUBV_MIN_BLOCKS 5  // the same for the sub-voxel variant (48 registers)
+#endif
 
 // Bilinear sample of one correction image at (u, v) = (iu + au, iv + av),
 // zero outside the detector (taps outside get zero weight).  A Slot holds what
@@ -113,11 +116,16 @@ __device__ __forceinline__ void bp_term(const Images &img, const typename Images
     }
 }
 
-template <typename Images, typename TV, bool WINDOW>
-__global__ void __launch_bounds__(BP_THREADS, CTREX_BP_MIN_BLOCKS)
+// SUBV: sub-voxel backprojection (Sec. 4.3.2, motion blur).  Each voxel's b
+// and c are the means over sv^3 points at index offsets ((a + 1/2)/sv - 1/2)
+// per axis; the points are visited inside the view loop, so the finer grid
+// lives only in registers.  Its longer loop body gets a larger register
+// budget (fewer resident CTAs per SM).
+template <typename Images, typename TV, bool WINDOW, bool SUBV>
+__global__ void __launch_bounds__(BP_THREADS, SUBV ? CTREX_BP_SUBV_MIN_BLOCKS : CTREX_BP_MIN_BLOCKS)
     bp_kernel(Grid G, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx, int n_idx,
               const Images img, const int4 *__restrict__ window, TV *__restrict__ vol, const float *__restrict__ w,
-              float alpha, int normalize, int accumulate)
+              float alpha, int normalize, int accumulate, int sv)
 {
     __shared__ float4 sP[BP_CHUNK][3];
     __shared__ typename Images::Slot sImg[BP_CHUNK];
@@ -161,6 +169,24 @@ __global__ void __launch_bounds__(BP_THREADS, CTREX_BP_MIN_BLOCKS)
                 lo = make_float2(wd.x, wd.z);
                 hi = make_float2(wd.y, wd.w);
             }
+            if (SUBV) {
+                const float d = 1.0f / (float)sv, o = 0.5f * d - 0.5f;
+                for (int az = 0; az < sv; ++az) {
+                    const float gz = fz + fmaf((float)az, d, o);
+                    for (int ay = 0; ay < sv; ++ay) {
+                        const float gy = fy + fmaf((float)ay, d, o);
+                        for (int ax = 0; ax < sv; ++ax) {
+                            const float gx = fx + fmaf((float)ax, d, o);
+                            const float h3 = fmaf(p2.x, gx, fmaf(p2.y, gy, fmaf(p2.z, gz, p2.w)));
+                            const float h1 = fmaf(p0.x, gx, fmaf(p0.y, gy, fmaf(p0.z, gz, p0.w)));
+                            const float h2 = fmaf(p1.x, gx, fmaf(p1.y, gy, fmaf(p1.z, gz, p1.w)));
+                            bp_term(img, slot, h1, h2, h3, lo, hi, b0, c0);
+                            bp_term(img, slot, h1 + p0.z, h2 + p1.z, h3 + p2.z, lo, hi, b1, c1);
+                        }
+                    }
+                }
+                continue;
+            }
             // voxel (ix, iy, iz) and its z neighbour: h(z + 1) = h(z) + P[:, 2]
             const float h3 = fmaf(p2.x, fx, fmaf(p2.y, fy, fmaf(p2.z, fz, p2.w)));
             const float h1 = fmaf(p0.x, fx, fmaf(p0.y, fy, fmaf(p0.z, fz, p0.w)));
@@ -170,11 +196,12 @@ __global__ void __launch_bounds__(BP_THREADS, CTREX_BP_MIN_BLOCKS)
         }
     }
     if (!inside) return;
+    const float mean = SUBV ? G.inv_sub / (float)(sv * sv * sv) : G.inv_sub;
 #pragma unroll
     for (int q = 0; q < BP_VZ; ++q) {
         if (iz + q >= G.nz) break;
-        const float b = (q == 0 ? b0 : b1) * G.inv_sub;
-        const float c = (q == 0 ? c0 : c1) * G.inv_sub;
+        const float b = (q == 0 ? b0 : b1) * mean;
+        const float c = (q == 0 ? c0 : c1) * mean;
         const size_t j = ((size_t)(iz + q) * G.ny + iy) * G.nx + ix;
         float scale = alpha;
         if (normalize) scale *= (c > 1e-6f ? 1.0f / c : 0.0f);
@@ -185,6 +212,19 @@ __global__ void __launch_bounds__(BP_THREADS, CTREX_BP_MIN_BLOCKS)
     }
 }
 
+template <typename Images, typename TV, bool SUBV>
+static void bp_launch_window(const BpArgs &a, const Images &img, dim3 grid, dim3 block)
+{
+    if (a.window)
+        bp_kernel<Images, TV, true, SUBV><<<grid, block, 0, a.stream>>>(*a.grid, a.views, a.view_idx, a.n_idx, img,
+                                                                       a.window, static_cast<TV *>(a.vol), a.w,
+                                                                       a.alpha, a.normalize, a.accumulate, a.subvox);
+    else
+        bp_kernel<Images, TV, false, SUBV><<<grid, block, 0, a.stream>>>(*a.grid, a.views, a.view_idx, a.n_idx, img,
+                                                                        nullptr, static_cast<TV *>(a.vol), a.w,
+                                                                        a.alpha, a.normalize, a.accumulate, a.subvox);
+}
+
 template <typename Images, typename TV>
 static cudaError_t bp_launch(const BpArgs &a, const Images &img)
 {
@@ -192,14 +232,10 @@ static cudaError_t bp_launch(const BpArgs &a, const Images &img)
     const dim3 block(BP_TX, BP_TY, BP_TZ);
     const dim3 grid((G.nx + BP_TX - 1) / BP_TX, (G.ny + BP_TY - 1) / BP_TY,
                     (G.nz + BP_TZ * BP_VZ - 1) / (BP_TZ * BP_VZ));
-    if (a.window)
-        bp_kernel<Images, TV, true><<<grid, block, 0, a.stream>>>(G, a.views, a.view_idx, a.n_idx, img, a.window,
-                                                                 static_cast<TV *>(a.vol), a.w, a.alpha, a.normalize,
-                                                                 a.accumulate);
+    if (a.subvox > 1)
+        bp_launch_window<Images, TV, true>(a, img, grid, block);
     else
-        bp_kernel<Images, TV, false><<<grid, block, 0, a.stream>>>(G, a.views, a.view_idx, a.n_idx, img, nullptr,
-                                                                  static_cast<TV *>(a.vol), a.w, a.alpha,
-                                                                  a.normalize, a.accumulate);
+        bp_launch_window<Images, TV, false>(a, img, grid, block);
     return cudaGetLastError();
 }
 

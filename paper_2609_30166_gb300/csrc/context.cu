@@ -54,6 +54,8 @@ struct ctrex_ctx {
     // backprojector detector windows (extended field of view), int4 per view
     int4 *d_window = nullptr;
     bool has_window = false;
+    // sub-voxel backprojection points per axis (motion blur), 1 = off
+    int bp_subvoxel = 1;
     // ordered-subset SIRT: concatenated subset view lists, per-subset norms
     int *d_subset_views = nullptr;
     size_t subset_views_bytes = 0;
@@ -487,6 +489,14 @@ int ctrex_set_bp_window(ctrex_ctx *c, const int *window)
     return CTREX_OK;
 }
 
+int ctrex_set_bp_subvoxel(ctrex_ctx *c, int s)
+{
+    if (!c) return CTREX_E_ARG;
+    if (s < 1 || s > CTREX_MAX_SUBVOXEL) return fail(c, CTREX_E_ARG, "set_bp_subvoxel: s must be in [1, 8]");
+    c->bp_subvoxel = s;
+    return CTREX_OK;
+}
+
 int ctrex_fwd_project(ctrex_ctx *c, const void *vol, int vdt, void *proj, int pdt, float *rowsum,
                       const int *view_idx, int n_idx)
 {
@@ -565,6 +575,7 @@ int ctrex_back_project(ctrex_ctx *c, const void *r, int rdt, void *vol, int vdt,
     a.accumulate = accumulate ? 1 : 0;
     a.stream = c->stream;
     a.window = c->has_window ? c->d_window : nullptr;
+    a.subvox = c->bp_subvoxel;
     if (n_idx > 0 && !c->img_atlas_unfit) {
         cudaError_t ae = atlas_ensure(c->img_atlas, c->grid.nu, c->grid.nv, n_idx, rdt == CTREX_BF16, c->device);
         if (ae == cudaErrorInvalidValue) {

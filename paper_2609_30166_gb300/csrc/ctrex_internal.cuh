@@ -108,6 +108,7 @@ struct BpArgs {
     float alpha;
     int normalize;
     int accumulate;
+    int subvox = 1;  // sub-voxel points per axis (1 = voxel centre only)
     cudaStream_t stream;
 };
 cudaError_t launch_backproject(const BpArgs &a);

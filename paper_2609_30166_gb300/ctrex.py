@@ -34,7 +34,7 @@ EXPORTS = (
     "ctrex_fwd_correct", "ctrex_back_project", "ctrex_adjoint_project", "ctrex_motion_grad",
     "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples", "ctrex_correct_static",
     "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad", "ctrex_os_sirt_iterate", "ctrex_set_bp_window",
-    "ctrex_probe_gather_rate",
+    "ctrex_probe_gather_rate", "ctrex_set_bp_subvoxel",
 )
 
 # Largest n ctrex_correct_static accepts (its static scratch holds 65536 CTA partials of 8192 elements).
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         "ctrex_conv3d_wgrad": ([vp, vp, vp, i, i, i, i, i, i, vp, vp], i),
         "ctrex_os_sirt_iterate": ([vp, vp, i, vp, i, ip, ip, i, i, f, vp, f, fp, ip], i),
         "ctrex_set_bp_window": ([vp, ip], i),
+        "ctrex_set_bp_subvoxel": ([vp, i], i),
         "ctrex_probe_gather_rate": ([vp, ctypes.POINTER(d)], i),
     }
     for name, (args, res) in sig.items():
@@ -216,6 +217,10 @@ class Context:
             raise ValueError(f"window must be [{self.n_views}, 4]")
         self._sync_stream()
         self._check(self.lib.ctrex_set_bp_window(self._h, win.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+
+    def set_bp_subvoxel(self, s=1):
+        """Sub-voxel backprojection: s^3 points per voxel (1 = off)."""
+        self._check(self.lib.ctrex_set_bp_subvoxel(self._h, int(s)))
 
     def fwd_project(self, vol, proj=None, rowsum=None, view_idx=None, out_dtype=None):
         self._sync_stream()

@@ -85,6 +85,19 @@ def test_fullsize_correction_and_backprojection(full):
     err_b, err_c = rel_l2(bg, b_ref), rel_l2(cg, c_ref)
     print(f"full-size backprojection, sampled voxels: b rel.L2 {err_b:.3e}, c rel.L2 {err_c:.3e}")
     assert err_b <= TOL32 and err_c <= TOL32
+    # sub-voxel backprojection (2^3 points per voxel), as the bench times it
+    ctx.set_bp_subvoxel(2)
+    try:
+        b = ctx.back_project(r, normalize=False, accumulate=False)
+    finally:
+        ctx.set_bp_subvoxel(1)
+    vox = vox[:16]
+    r64 = r.double().cpu().numpy()
+    b_ref, _ = oracle.backproject_voxels(pb.with_subvoxel(2), r64, vox)
+    del r64
+    err_s = rel_l2(b.flatten()[torch.as_tensor(vox)].double().cpu().numpy(), b_ref)
+    print(f"full-size sub-voxel backprojection, sampled voxels: b rel.L2 {err_s:.3e}")
+    assert err_s <= TOL32
 
 
 def _sampled(cfg, n, seed):
