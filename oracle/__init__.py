@@ -89,6 +89,8 @@ class _CProblem(ctypes.Structure):
         ("step_vox", ctypes.c_double),
         ("P", _dp), ("theta", _dp), ("coef", _dp), ("s_view", _dp),
         ("margin", ctypes.c_double), ("bp_window", _ip), ("bp_subvoxel", ctypes.c_int),
+        ("cyl", ctypes.c_int), ("cyl_dr", ctypes.c_double), ("cyl_dz", ctypes.c_double),
+        ("cyl_pose", _dp),
     ]
 
 
@@ -126,11 +128,13 @@ class Problem:
 
     P: [n_views, n_sub, 3, 4]; vol_shape (nz, ny, nx); vox, origin in (x, y, z)
     order, mm; det (nu, nv); theta [n_views, 15]; coef [8, 8, 8, 3]; s_view
-    [n_views].
+    [n_views].  cyl = (dr, dz, pose[3, 4]) switches to the aligned cylindrical
+    domain (reading R13): vol_shape is then (N_z, N_phi, N_r) and vox, origin
+    are unused.
     """
 
     def __init__(self, P, vol_shape, vox, origin, det, step_vox=0.5, theta=None, coef=None,
-                 s_view=None, margin=0.0, bp_window=None, bp_subvoxel=1):
+                 s_view=None, margin=0.0, bp_window=None, bp_subvoxel=1, cyl=None):
         P = _f64(P)
         if P.ndim == 3:
             P = P[:, None]
@@ -147,11 +151,16 @@ class Problem:
         self.margin = float(margin)
         self.bp_window = None if bp_window is None else np.ascontiguousarray(bp_window, dtype=np.int32)
         self.bp_subvoxel = int(bp_subvoxel)
+        self.cyl = None
+        if cyl is not None:
+            dr, dz, pose = cyl
+            self.cyl = (float(dr), float(dz), _f64(pose).reshape(3, 4).copy())
+        cdr, cdz, cpose = self.cyl if self.cyl else (0.0, 0.0, None)
         self._c = _CProblem(self.nx, self.ny, self.nz, (ctypes.c_double * 3)(*self.vox),
                             (ctypes.c_double * 3)(*self.origin), self.nu, self.nv, self.n_views,
                             self.n_sub, self.step_vox, _ptr(self.P), _ptr(self.theta),
                             _ptr(self.coef), _ptr(self.s_view), self.margin, _ptr(self.bp_window, _ip),
-                            self.bp_subvoxel)
+                            self.bp_subvoxel, 1 if self.cyl else 0, cdr, cdz, _ptr(cpose))
 
     @property
     def vol_shape(self):
@@ -159,30 +168,46 @@ class Problem:
 
     @property
     def min_vox(self):
+        if self.cyl:
+            return min(self.cyl[0], self.cyl[1])
         return min(self.vox)
 
     @property
     def eps_R(self):
         return 1e-6 * self.min_vox
 
+    def _replace(self, **kw):
+        args = dict(P=self.P, vol_shape=self.vol_shape, vox=self.vox, origin=self.origin,
+                    det=(self.nu, self.nv), step_vox=self.step_vox, theta=self.theta, coef=self.coef,
+                    s_view=self.s_view, margin=self.margin, bp_window=self.bp_window,
+                    bp_subvoxel=self.bp_subvoxel, cyl=self.cyl)
+        args.update(kw)
+        return Problem(**args)
+
     def with_motion(self, theta=None, coef=None, s_view=None, margin=0.0):
-        return Problem(self.P, self.vol_shape, self.vox, self.origin, (self.nu, self.nv),
-                       self.step_vox, theta, coef, s_view, margin, self.bp_window, self.bp_subvoxel)
+        return self._replace(theta=theta, coef=coef, s_view=s_view, margin=margin)
 
     def with_P(self, P):
-        return Problem(P, self.vol_shape, self.vox, self.origin, (self.nu, self.nv), self.step_vox,
-                       self.theta, self.coef, self.s_view, self.margin, self.bp_window, self.bp_subvoxel)
+        return self._replace(P=P)
 
     def with_subvoxel(self, s):
         """The same problem whose backprojector averages s^3 sub-voxel points."""
-        return Problem(self.P, self.vol_shape, self.vox, self.origin, (self.nu, self.nv), self.step_vox,
-                       self.theta, self.coef, self.s_view, self.margin, self.bp_window, s)
+        return self._replace(bp_subvoxel=s)
 
     def with_window(self, bp_window):
         """The same problem whose backprojector sees per-view detector windows
         [n_views, 4] = (u_lo, u_hi, v_lo, v_hi) (extended field of view)."""
-        return Problem(self.P, self.vol_shape, self.vox, self.origin, (self.nu, self.nv), self.step_vox,
-                       self.theta, self.coef, self.s_view, self.margin, bp_window, self.bp_subvoxel)
+        return self._replace(bp_window=bp_window)
+
+
+def cylinder_problem(P, n_r, n_phi, n_z, dr, dz, det, pose=None, step_vox=0.5):
+    """A problem on the aligned cylindrical domain: N_r rings of pitch dr,
+    N_phi sectors, N_z slices of pitch dz (mm); pose [3, 4] maps world mm to
+    the cylinder frame (identity if None)."""
+    if pose is None:
+        pose = np.hstack([np.eye(3), np.zeros((3, 1))])
+    return Problem(P, (n_z, n_phi, n_r), (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), det, step_vox,
+                   cyl=(dr, dz, pose))
 
 
 def _views(pb, views):

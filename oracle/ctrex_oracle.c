@@ -45,7 +45,19 @@
  *      sum and its normalisation; the forward keeps the whole detector;
  *   R12 sub-voxel backprojection (Sec. 4.3.2, motion blur): with s > 1 the
  *      backprojected value and column sum of a voxel are the means over the
- *      s^3 points at offsets ((a + 1/2)/s - 1/2) voxel on each axis.
+ *      s^3 points at offsets ((a + 1/2)/s - 1/2) voxel on each axis;
+ *   R13 aligned cylindrical domain (Sec. 3.5; projector and backprojector
+ *      adaptations in Sec. 4.2 / 4.3): a rigid pose maps world x to the
+ *      frame q = Rc x + tc, whose z axis is the cylinder axis.  Voxel (i, j,
+ *      k) sits at r = (i + 1/2) dr, phi = (j + 1/2) 2 pi / N_phi, z = (k -
+ *      (N_z - 1)/2) dz.  A sample at q has index coordinates g_r = r/dr -
+ *      1/2 (clamped to >= 0: inside the first ring centre the value of ring
+ *      0 is used), g_phi = phi / (2 pi / N_phi) - 1/2 taken modulo N_phi
+ *      (periodic), g_z = q_z/dz + (N_z - 1)/2; trilinear interpolation in
+ *      these, zero outside in r (beyond ring N_r - 1) and z.  Rays are
+ *      clipped to the bounding cylinder r <= N_r dr, |q_z| <= N_z dz / 2;
+ *      the step is step_vox * min(dr, dz); the rest of the projector and the
+ *      backprojector (at the voxel centres mapped back to world) is as above.
  *
  * Conventions: volume vol[iz][iy][ix] (x fastest), voxel (0,0,0) centred at
  * origin (mm), index coordinate g = (x - origin) / vox.  Projection images
@@ -75,6 +87,12 @@ typedef struct {
     double margin;        /* mm, clip-box dilation when motion is on       */
     const int *bp_window; /* [n_views][4] (u_lo, u_hi, v_lo, v_hi) or NULL */
     int bp_subvoxel;      /* > 1: backproject onto s^3 sub-voxel points     */
+    /* aligned cylindrical domain (Sec. 3.5, reading R13): when cyl != 0 the
+     * grid is (nx, ny, nz) = (N_r, N_phi, N_z) with ring pitch cyl_dr, slice
+     * pitch cyl_dz (mm) and sector 2 pi / N_phi; vox and origin are unused */
+    int cyl;
+    double cyl_dr, cyl_dz;
+    const double *cyl_pose; /* [12] row-major 3x4: q = Rc x + tc (world mm -> frame mm) */
 } or_problem;
 
 /* Per (view, sub-angle) quantities derived from P (Sec. 2.2.1). */
@@ -106,8 +124,28 @@ static void inv3(const double *m, double det, double *r)
     r[8] = (m[0] * m[4] - m[1] * m[3]) / det;
 }
 
+/* Cylinder frame -> world: x = Rc^T (q - tc). */
+static void cyl_to_world(const or_problem *pb, const double q[3], double x[3])
+{
+    const double *T = pb->cyl_pose;
+    double d[3] = {q[0] - T[3], q[1] - T[7], q[2] - T[11]};
+    for (int a = 0; a < 3; ++a) x[a] = T[a] * d[0] + T[4 + a] * d[1] + T[8 + a] * d[2];
+}
+
+/* World -> cylinder frame: q = Rc x + tc. */
+static void world_to_cyl(const or_problem *pb, const double x[3], double q[3])
+{
+    const double *T = pb->cyl_pose;
+    for (int r = 0; r < 3; ++r) q[r] = T[4 * r] * x[0] + T[4 * r + 1] * x[1] + T[4 * r + 2] * x[2] + T[4 * r + 3];
+}
+
 static void volume_centre(const or_problem *pb, double c[3])
 {
+    if (pb->cyl) {
+        const double q0[3] = {0.0, 0.0, 0.0};
+        cyl_to_world(pb, q0, c);
+        return;
+    }
     const int n[3] = {pb->nx, pb->ny, pb->nz};
     for (int a = 0; a < 3; ++a) c[a] = pb->origin[a] + 0.5 * (n[a] - 1) * pb->vox[a];
 }
@@ -227,6 +265,50 @@ static double trilinear(const or_problem *pb, const double *vol, const double g[
         grad[2] = gz;
     }
     return val;
+}
+
+/*
+ * Reading R13: interpolation on the cylindrical grid at index coordinate g =
+ * (g_r, g_phi, g_z): g_r clamped to >= 0, phi periodic, zero outside in r and
+ * z.  wsum as for trilinear().
+ */
+static double cyl_interp(const or_problem *pb, const double *vol, const double g[3], double *wsum)
+{
+    const int nr = pb->nx, np = pb->ny, nz = pb->nz;
+    double gr = g[0] < 0.0 ? 0.0 : g[0];
+    *wsum = 0.0;
+    if (!(gr < (double)nr && g[2] >= -1.0 && g[2] < (double)nz)) return 0.0;
+    double fr = floor(gr), fp = floor(g[1]), fz = floor(g[2]);
+    int i0 = (int)fr, j0 = (int)fp, k0 = (int)fz;
+    double ar = gr - fr, ap = g[1] - fp, az = g[2] - fz;
+    double val = 0.0, ws = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dp = 0; dp < 2; ++dp)
+            for (int dr = 0; dr < 2; ++dr) {
+                int i = i0 + dr, k = k0 + dz;
+                int j = ((j0 + dp) % np + np) % np;
+                if (i >= nr || k < 0 || k >= nz) continue;
+                double wgt = (dr ? ar : 1.0 - ar) * (dp ? ap : 1.0 - ap) * (dz ? az : 1.0 - az);
+                val += wgt * (vol ? vol[((size_t)k * np + j) * nr + i] : 1.0);
+                ws += wgt;
+            }
+    *wsum = ws;
+    return val;
+}
+
+/* Reading R13: frame point q -> cylindrical index coordinates. */
+static void cyl_index(const or_problem *pb, const double q[3], double g[3])
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    const double dphi = two_pi / pb->ny;
+    double r = sqrt(q[0] * q[0] + q[1] * q[1]);
+    double phi = atan2(q[1], q[0]);
+    if (phi < 0.0) phi += two_pi;
+    g[0] = r / pb->cyl_dr - 0.5;
+    g[1] = phi / dphi - 0.5;
+    if (g[1] < 0.0) g[1] += pb->ny;
+    if (g[1] >= pb->ny) g[1] -= pb->ny;
+    g[2] = q[2] / pb->cyl_dz + 0.5 * (pb->nz - 1);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -402,10 +484,50 @@ static void warp_point(const or_problem *pb, int view, const double x[3], double
 /* Forward projector (Sec. 4.1 "Projection operator", readings R1-R3).     */
 /* ---------------------------------------------------------------------- */
 
+/* Reading R13: clip the half line to the bounding cylinder of the domain. */
+static int clip_ray_cyl(const or_problem *pb, const double s[3], const double d[3], double *t_in,
+                        double *t_out)
+{
+    double qs[3], qe[3], e[3], qd[3];
+    world_to_cyl(pb, s, qs);
+    for (int a = 0; a < 3; ++a) e[a] = s[a] + d[a];
+    world_to_cyl(pb, e, qe);
+    for (int a = 0; a < 3; ++a) qd[a] = qe[a] - qs[a];
+    double R = pb->nx * pb->cyl_dr, Z = 0.5 * pb->nz * pb->cyl_dz;
+    double t0 = 0.0, t1 = INFINITY;
+    /* mantle: |qs_xy + t qd_xy|^2 <= R^2 */
+    double a = qd[0] * qd[0] + qd[1] * qd[1];
+    double b = 2.0 * (qs[0] * qd[0] + qs[1] * qd[1]);
+    double c = qs[0] * qs[0] + qs[1] * qs[1] - R * R;
+    if (a == 0.0) {
+        if (c > 0.0) return 0;
+    } else {
+        double disc = b * b - 4.0 * a * c;
+        if (!(disc > 0.0)) return 0;
+        double sq = sqrt(disc);
+        double ta = (-b - sq) / (2.0 * a), tb = (-b + sq) / (2.0 * a);
+        if (ta > t0) t0 = ta;
+        if (tb < t1) t1 = tb;
+    }
+    /* end caps */
+    if (qd[2] == 0.0) {
+        if (qs[2] < -Z || qs[2] > Z) return 0;
+    } else {
+        double ta = (-Z - qs[2]) / qd[2], tb = (Z - qs[2]) / qd[2];
+        if (ta > tb) { double tmp = ta; ta = tb; tb = tmp; }
+        if (ta > t0) t0 = ta;
+        if (tb < t1) t1 = tb;
+    }
+    *t_in = t0;
+    *t_out = t1;
+    return t1 > t0;
+}
+
 /* Clip the half line s + t d, t >= 0, to the (possibly dilated) box. */
 static int clip_ray(const or_problem *pb, const double s[3], const double d[3], double *t_in,
                     double *t_out)
 {
+    if (pb->cyl) return clip_ray_cyl(pb, s, d, t_in, t_out);
     const int n[3] = {pb->nx, pb->ny, pb->nz};
     double m = (pb->theta || pb->coef) ? pb->margin : 0.0;
     double t0 = 0.0, t1 = INFINITY;
@@ -428,6 +550,7 @@ static int clip_ray(const or_problem *pb, const double s[3], const double d[3], 
 
 static double step_mm(const or_problem *pb)
 {
+    if (pb->cyl) return pb->step_vox * (pb->cyl_dr < pb->cyl_dz ? pb->cyl_dr : pb->cyl_dz);
     double v = pb->vox[0];
     if (pb->vox[1] < v) v = pb->vox[1];
     if (pb->vox[2] < v) v = pb->vox[2];
@@ -486,8 +609,15 @@ static void fwd_sample(void *vctx, const double x[3], double w)
     fwd_acc *c = (fwd_acc *)vctx;
     double y[3], g[3], ws;
     warp_point(c->pb, c->view, x, y);
-    to_index(c->pb, y, g);
-    c->val += w * trilinear(c->pb, c->vol, g, &ws, NULL);
+    if (c->pb->cyl) {
+        double q[3];
+        world_to_cyl(c->pb, y, q);
+        cyl_index(c->pb, q, g);
+        c->val += w * cyl_interp(c->pb, c->vol, g, &ws);
+    } else {
+        to_index(c->pb, y, g);
+        c->val += w * trilinear(c->pb, c->vol, g, &ws, NULL);
+    }
     c->rs += w * ws;
 }
 
@@ -659,8 +789,20 @@ static void bp_voxel(const or_problem *pb, const or_view *ov, const double *r, c
             for (int ax = 0; ax < sv; ++ax) {
                 const int a[3] = {ax, ay, az};
                 double X[3];
-                for (int d = 0; d < 3; ++d)
-                    X[d] = pb->origin[d] + (i[d] + (a[d] + 0.5) / sv - 0.5) * pb->vox[d];
+                if (pb->cyl) {
+                    /* reading R13: sub-point of the cylindrical voxel, mapped to world */
+                    double gi[3], q[3];
+                    for (int d = 0; d < 3; ++d) gi[d] = i[d] + (a[d] + 0.5) / sv - 0.5;
+                    double r = (gi[0] + 0.5) * pb->cyl_dr;
+                    double phi = (gi[1] + 0.5) * (6.283185307179586476925286766559 / pb->ny);
+                    q[0] = r * cos(phi);
+                    q[1] = r * sin(phi);
+                    q[2] = (gi[2] - 0.5 * (pb->nz - 1)) * pb->cyl_dz;
+                    cyl_to_world(pb, q, X);
+                } else {
+                    for (int d = 0; d < 3; ++d)
+                        X[d] = pb->origin[d] + (i[d] + (a[d] + 0.5) / sv - 0.5) * pb->vox[d];
+                }
                 double bb, cc;
                 bp_point(pb, ov, r, views, n_sel, X, &bb, &cc);
                 b += bb;
@@ -757,6 +899,7 @@ static void adj_sample(void *vctx, const double x[3], double w)
 /* vol_out (overwritten) = A^T y for y [n_sel][nv][nu]. */
 int or_adjoint(const or_problem *pb, const double *y, const int *views, int n_sel, double *vol_out)
 {
+    if (pb->cyl) return OR_E_ARG; /* the transpose is written for the Cartesian grid only */
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;
@@ -884,6 +1027,7 @@ static void grad_sample(void *vctx, const double x[3], double w)
 int or_motion_grad(const or_problem *pb, const double *vol, const double *g, const int *views,
                    int n_sel, double *grad_theta, double *grad_coef)
 {
+    if (pb->cyl) return OR_E_ARG; /* Cartesian grid only */
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;

@@ -679,3 +679,182 @@ def test_subvoxel_bp_is_block_mean_of_fine_grid():
     _, bf, cf = oracle.backproject(pf, r)
     blk = lambda a: a.reshape(cfg.n, s, cfg.n, s, cfg.n, s).mean(axis=(1, 3, 5))  # noqa: E731
     assert np.allclose(bs, blk(bf), atol=1e-12) and np.allclose(cs, blk(cf), atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Aligned cylindrical domain (Sec. 3.5, reading R13)
+# ---------------------------------------------------------------------------
+
+def _axial_P(x0, y0, D=300.0, f=40.0, uc=10.0, vc=10.0):
+    """A projection whose source sits at (x0, y0, -D): the ray through pixel
+    (uc, vc) runs along +z through (x0, y0)."""
+    return np.array([[f, 0.0, uc, -f * x0 + uc * D],
+                     [0.0, f, vc, -f * y0 + vc * D],
+                     [0.0, 0.0, 1.0, D]])
+
+
+def _rot_x(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[1.0, 0.0, 0.0], [0.0, c, -s], [0.0, s, c]])
+
+
+def _pose(R, t):
+    return np.hstack([R, np.asarray(t, float)[:, None]])
+
+
+def test_cylinder_axial_rays_closed_form():
+    # rays parallel to the cylinder axis: r and phi are constant, so the ray
+    # reduces to the 1D truncated-midpoint rule of P1 along z on the values
+    # the (r, phi) position selects
+    n_r, n_p, n_z, dr, dz = 6, 12, 10, 1.5, 1.0
+    rng = np.random.default_rng(13)
+    vol = rng.uniform(0.0, 1.0, size=(n_z, n_p, n_r))
+    dphi = 2 * math.pi / n_p
+
+    def axial(r0, phi0):
+        x0, y0 = r0 * math.cos(phi0), r0 * math.sin(phi0)
+        pb = oracle.cylinder_problem(_axial_P(x0, y0)[None], n_r, n_p, n_z, dr, dz, (21, 21))
+        val, rs = oracle.forward_rays(pb, vol, np.zeros(1, np.int32), np.array([10.0]), np.array([10.0]))
+        return val[0], rs[0]
+
+    def closed(col):
+        return dz * (col.sum() - (col[0] + col[-1]) / 8.0)
+
+    for i, j in ((2, 3), (5, 0), (0, 11)):
+        val, rs = axial((i + 0.5) * dr, (j + 0.5) * dphi)
+        assert val == pytest.approx(closed(vol[:, j, i]), rel=1e-12)
+        assert rs == pytest.approx(dz * (n_z - 0.25), rel=1e-12)
+    # inside the first ring centre the ring-0 value is used (clamp)
+    val, _ = axial(0.2 * dr, 7.5 * dphi)
+    assert val == pytest.approx(closed(vol[:, 7, 0]), rel=1e-12)
+    # phi = 0 lies halfway between the last and the first sector (periodic)
+    val, _ = axial(3.5 * dr, 0.0)
+    assert val == pytest.approx(closed(0.5 * (vol[:, n_p - 1, 3] + vol[:, 0, 3])), rel=1e-12)
+    # outside the bounding cylinder: nothing
+    val, rs = axial(n_r * dr + 0.01, 1.0)
+    assert val == 0.0 and rs == 0.0
+
+
+def test_cylinder_rotation_about_axis_is_a_sector_roll():
+    cfg = small(n=8, nu=24, nv=20, n_views=5, trajectory="perturbed", seed=21)
+    P = inputs.projection_matrices(cfg)
+    n_r, n_p, n_z, dr, dz = 5, 16, 7, 2.6, 3.8
+    vol = np.random.default_rng(21).uniform(size=(n_z, n_p, n_r))
+    m = 3
+    tilt = _rot_x(0.2)
+    pb0 = oracle.cylinder_problem(P, n_r, n_p, n_z, dr, dz, (cfg.nu, cfg.nv), pose=_pose(tilt, [0.4, -0.3, 0.2]))
+    # frame rotated by m sectors about its own axis: a world point's sector index grows by m
+    Rm = inputs.rot_z(m * 2 * math.pi / n_p)
+    pbm = oracle.cylinder_problem(P, n_r, n_p, n_z, dr, dz, (cfg.nu, cfg.nv),
+                                  pose=_pose(Rm @ tilt, Rm @ np.array([0.4, -0.3, 0.2])))
+    a, ra = oracle.forward(pbm, vol)
+    b, rb = oracle.forward(pb0, np.roll(vol, -m, axis=1))
+    assert np.abs(a).max() > 1.0
+    # equal up to the rounding of the rotated sample positions
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max() and np.abs(ra - rb).max() <= 1e-10 * np.abs(ra).max()
+
+
+def test_cylinder_rigid_change_of_world_frame():
+    # moving the scanner and the cylinder together by a rigid motion G changes nothing
+    cfg = small(n=8, nu=24, nv=20, n_views=4, trajectory="perturbed", seed=22)
+    P = inputs.projection_matrices(cfg)[:, 0]
+    n_r, n_p, n_z, dr, dz = 5, 12, 6, 2.6, 4.0
+    vol = np.random.default_rng(22).uniform(size=(n_z, n_p, n_r))
+    pose = _pose(_rot_x(-0.15), [0.5, 0.2, -0.4])
+    G = _pose(inputs.rot_z(0.7) @ _rot_x(0.3), [3.0, -2.0, 1.5])
+    Gi = np.hstack([G[:, :3].T, -(G[:, :3].T @ G[:, 3])[:, None]])
+
+    def compose(A, B):  # (A o B)(x) = A (B x) for 3x4 affine maps
+        return np.hstack([A[:, :3] @ B[:, :3], (A[:, :3] @ B[:, 3] + A[:, 3])[:, None]])
+
+    P2 = np.stack([Pv @ np.vstack([Gi, [0, 0, 0, 1]]) for Pv in P])  # P2 (G x) = P x
+    pb1 = oracle.cylinder_problem(P, n_r, n_p, n_z, dr, dz, (cfg.nu, cfg.nv), pose=pose)
+    pb2 = oracle.cylinder_problem(P2, n_r, n_p, n_z, dr, dz, (cfg.nu, cfg.nv), pose=compose(pose, Gi))
+    a, _ = oracle.forward(pb1, vol)
+    b, _ = oracle.forward(pb2, vol)
+    assert np.abs(a).max() > 1.0 and np.allclose(a, b, rtol=1e-10, atol=1e-10)
+
+
+def _cyl_centres_world(n_r, n_p, n_z, dr, dz, pose):
+    """World positions of the cylinder voxel centres [n_z, n_p, n_r, 3]."""
+    r = (np.arange(n_r) + 0.5) * dr
+    phi = (np.arange(n_p) + 0.5) * 2 * math.pi / n_p
+    z = (np.arange(n_z) - 0.5 * (n_z - 1)) * dz
+    Z, PH, Rr = np.meshgrid(z, phi, r, indexing="ij")
+    q = np.stack([Rr * np.cos(PH), Rr * np.sin(PH), Z], axis=-1)
+    Rc, tc = pose[:, :3], pose[:, 3]
+    return (q - tc) @ Rc  # Rc^T (q - tc), row-vector form
+
+
+def test_cylinder_gaussian_line_integrals_converge():
+    # a Cartesian Gaussian sampled at the cylinder voxel centres: the line
+    # integrals converge to the analytic ones at second order
+    cfg = small(n=8, nu=20, nv=20, n_views=3, trajectory="perturbed", seed=23)
+    P = inputs.projection_matrices(cfg)[:, 0]
+    pose = _pose(_rot_x(0.12) @ inputs.rot_z(0.3), [0.6, -0.4, 0.3])
+    c = np.array([6.0, 3.0, -2.0])  # world centre of the blob
+    sig = 2.5
+    R, H = 16.0, 24.0
+    # 48 rays through the blob's projection, shifted by up to a pixel
+    rng = np.random.default_rng(23)
+    views = (np.arange(48) % 3).astype(np.int32)
+    offs = rng.uniform(-1.0, 1.0, size=(48, 2))
+    h = np.einsum("vij,j->vi", P[views], np.append(c, 1.0))
+    us = h[:, 0] / h[:, 2] + offs[:, 0]
+    vs = h[:, 1] / h[:, 2] + offs[:, 1]
+    # analytic integral of exp(-|x - c|^2 / sig^2) along each ray (the blob sits
+    # well inside the cylinder): sig sqrt(pi) exp(-d^2 / sig^2), d = distance to c
+    ref = []
+    for v, u, w in zip(views, us, vs):
+        M, p4 = P[v][:, :3], P[v][:, 3]
+        s = -np.linalg.solve(M, p4)
+        d = np.linalg.solve(M, np.array([u, w, 1.0]))
+        d /= np.linalg.norm(d)
+        e = c - s
+        dist2 = e @ e - (e @ d) ** 2
+        ref.append(sig * math.sqrt(math.pi) * math.exp(-dist2 / sig ** 2))
+    ref = np.array(ref)
+    errs = []
+    for k in (1, 2, 4):
+        n_r, n_p, n_z = 12 * k, 48 * k, 18 * k
+        dr, dz = R / n_r, H / n_z
+        X = _cyl_centres_world(n_r, n_p, n_z, dr, dz, pose)
+        vol = np.exp(-((X - c) ** 2).sum(-1) / sig ** 2)
+        pb = oracle.cylinder_problem(P, n_r, n_p, n_z, dr, dz, (cfg.nu, cfg.nv), pose=pose)
+        val, _ = oracle.forward_rays(pb, vol, views, us, vs)
+        errs.append(rel_l2(val, ref))
+    # second order: each halving of (dr, dphi, dz) divides the error by ~4; a
+    # misplaced grid (half-cell shift, wrong pose) would leave an O(h) or O(1) error
+    assert errs[2] < 5e-3
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
+
+
+def test_cylinder_bp_is_cartesian_bp_at_voxel_centres():
+    cfg = small(n=8, nu=24, nv=22, n_views=6, trajectory="perturbed", seed=24)
+    P = inputs.projection_matrices(cfg)
+    n_r, n_p, n_z, dr, dz = 5, 14, 6, 2.8, 4.5
+    pose = _pose(_rot_x(0.1), [0.3, 0.5, -0.2])
+    pb = oracle.cylinder_problem(P, n_r, n_p, n_z, dr, dz, (cfg.nu, cfg.nv), pose=pose)
+    r = np.random.default_rng(24).normal(size=(cfg.n_views, cfg.nv, cfg.nu))
+    _, b, c = oracle.backproject(pb, r)
+    X = _cyl_centres_world(n_r, n_p, n_z, dr, dz, pose)
+    rng = np.random.default_rng(25)
+    for flat in rng.integers(0, b.size, 12):
+        k, j, i = np.unravel_index(flat, b.shape)
+        one = oracle.Problem(P, (1, 1, 1), (1.0, 1.0, 1.0), tuple(X[k, j, i]), (cfg.nu, cfg.nv))
+        _, b1, c1 = oracle.backproject(one, r)
+        assert b[k, j, i] == pytest.approx(b1[0, 0, 0], rel=1e-12, abs=1e-12)
+        assert c[k, j, i] == pytest.approx(c1[0, 0, 0], rel=1e-12, abs=1e-12)
+    # sub-voxel points of the cylinder are the centres of the 2x finer cylinder grid
+    _, b2, c2 = oracle.backproject(pb.with_subvoxel(2), r)
+    fine = oracle.cylinder_problem(P, 2 * n_r, 2 * n_p, 2 * n_z, dr / 2, dz / 2, (cfg.nu, cfg.nv), pose=pose)
+    _, bf, cf = oracle.backproject(fine, r)
+    blk = lambda a: a.reshape(n_z, 2, n_p, 2, n_r, 2).mean(axis=(1, 3, 5))  # noqa: E731
+    assert np.allclose(b2, blk(bf), atol=1e-12) and np.allclose(c2, blk(cf), atol=1e-12)
+
+
+def test_cylinder_refuses_adjoint():
+    cfg = small(n=8, nu=12, nv=12, n_views=2)
+    pb = oracle.cylinder_problem(inputs.projection_matrices(cfg), 4, 8, 4, 2.0, 2.0, (12, 12))
+    with pytest.raises(ValueError):
+        oracle.adjoint(pb, np.zeros((2, 12, 12)))
