@@ -281,6 +281,24 @@ def measure_rows(device, gather_peak, sm_count, sm_mhz):
                                   "atomics_per_s": 8 * ns / t_a}
     rows["a9_motion_gradient"] = {"workload": cfg.name, "ms": t_g * 1e3, "gsamples_per_s": ns / t_g / 1e9}
     del ctx, vol, proj, g, adj
+    # cylindrical domain (Sec. 3.5): one SIRT step on the vial workload
+    cc = inputs.CYL_VIAL
+    ctx = ctrex.context_for_cylinder(cc, device=device)
+    vol = inputs.cyl_phantom(cc, device=str(device)).float().contiguous()
+    p = ctx.fwd_project(vol)
+    ns = ctx.count_samples()
+    nu_ = cc.n_r * cc.n_phi * cc.n_z * cc.base.n_views * cc.base.n_sub
+    x = torch.zeros_like(vol)
+    r = torch.empty_like(p)
+    sums = torch.zeros(2, dtype=torch.float64, device=device)
+    t_fc = _time(lambda: ctx.fwd_correct(x, p, r=r, sums=sums), reps=2)
+    t_bp = _time(lambda: ctx.back_project(r, vol=x, alpha=1.0), reps=2)
+    rows["a15_cylinder_sirt_step"] = {"workload": cc.name, "samples": ns, "updates": nu_,
+                                      "fwd_correct_ms": t_fc * 1e3, "back_project_ms": t_bp * 1e3,
+                                      "gups": (ns + nu_) / (t_fc + t_bp) / 1e9,
+                                      "fwd_tex_gather_frac": 2 * ns / t_fc / gather_peak,
+                                      "bp_tex_gather_frac": nu_ / t_bp / gather_peak}
+    del ctx, vol, p, x, r
     # a12: tcgen05 implicit-GEMM convolution, the U-Net's levels (batch 2 at 128^3)
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:

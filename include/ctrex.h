@@ -77,6 +77,20 @@ typedef struct {
     int nu, nv;
 } ctrex_det_grid;
 
+/*
+ * Aligned cylindrical volume domain (Sec. 3.5; projector / backprojector
+ * adaptations in Sec. 4.2 / 4.3): n_r rings of pitch dr (mm), n_phi
+ * sectors of 2 pi / n_phi, n_z slices of pitch dz (mm).  pose is a rigid
+ * 3x4 row-major map q = Rc x + tc from world mm to the cylinder frame, whose
+ * z axis is the cylinder axis.  Voxel (i, j, k) sits at frame point r =
+ * (i + 1/2) dr, phi = (j + 1/2) 2 pi / n_phi, z = (k - (n_z - 1)/2) dz.
+ */
+typedef struct {
+    int n_r, n_phi, n_z;
+    double dr, dz;
+    double pose[12];
+} ctrex_cyl_grid;
+
 /* Library version string (static storage). */
 const char *ctrex_version(void);
 
@@ -119,6 +133,33 @@ int ctrex_device_status(ctrex_ctx *ctx);
  */
 int ctrex_set_geometry(ctrex_ctx *ctx, const double *P, int n_views, int n_sub,
                        const ctrex_vol_grid *vol, const ctrex_det_grid *det, double step_vox);
+
+/*
+ * The same projection set-up on the aligned cylindrical domain (Sec. 3.5).
+ * Every operator then works on volumes of [n_z][n_phi][n_r] (r fastest):
+ *   - the projector clips each ray to the bounding cylinder r <= n_r dr,
+ *     |z| <= n_z dz / 2 (instead of the box) and maps each sample to
+ *     (r, phi, z) before the lookup: trilinear interpolation in the index
+ *     coordinates r/dr - 1/2 (clamped to >= 0: inside the first ring centre
+ *     the ring-0 value is used), phi / (2 pi / n_phi) - 1/2 (periodic) and
+ *     z/dz + (n_z - 1)/2, zero outside in r and z; fixed step step_vox *
+ *     min(dr, dz) as for the box;
+ *   - the backprojector maps each voxel point to the frame, then to the
+ *     detector; its accumulation, C, w, alpha, windows and sub-voxel points
+ *     are unchanged;
+ *   - R uses the threshold 1e-6 * min(dr, dz).
+ *   P        HOST double [n_views][n_sub][3][4] (world mm -> pixels); the
+ *            pose is folded into them, so they are copied.
+ *   cyl      HOST grid and pose (pose rotation orthonormal within 1e-9,
+ *            det +1, else CTREX_E_ARG); n_phi >= 3.
+ * Volumes are sampled through a texture atlas; one that exceeds the
+ * device's 2D texture limits fails at the first projection with
+ * CTREX_E_SHAPE.  set_motion (with parameters), adjoint_project and
+ * motion_grad return CTREX_E_STATE on this domain.  Clears any motion, BP
+ * window and earlier geometry; ctrex_set_geometry switches back.
+ */
+int ctrex_set_geometry_cylinder(ctrex_ctx *ctx, const double *P, int n_views, int n_sub,
+                                const ctrex_cyl_grid *cyl, const ctrex_det_grid *det, double step_vox);
 
 /*
  * Sec. 2.2.2 affine volume pose (rigid then affine) and Sec. 3.1.1 / 4.2.1

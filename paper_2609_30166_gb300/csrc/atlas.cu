@@ -11,10 +11,12 @@ void atlas_release(AtlasStore &s)
     s = AtlasStore();
 }
 
-cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int device, bool packed)
+cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int device, bool packed, bool wrap)
 {
     packed = packed && bf16;
-    if (s.array && s.w == w && s.h == h && s.n == n && s.bf16 == (bf16 ? 1 : 0) && s.packed == (packed ? 1 : 0))
+    if (wrap) h += 1;
+    if (s.array && s.w == w && s.h == h && s.n == n && s.bf16 == (bf16 ? 1 : 0) && s.packed == (packed ? 1 : 0) &&
+        s.wrap == (wrap ? 1 : 0))
         return cudaSuccess;
     atlas_release(s);
     int maxw = 0, maxh = 0;
@@ -66,6 +68,7 @@ cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int devi
     s.tshift = tshift;
     s.bf16 = bf16 ? 1 : 0;
     s.packed = packed ? 1 : 0;
+    s.wrap = wrap ? 1 : 0;
     return cudaSuccess;
 }
 
@@ -82,15 +85,16 @@ Atlas atlas_view(const AtlasStore &s)
     return a;
 }
 
+// Tile rows y < hd come from source row y; a wrap row (y == hd) repeats row 0.
 template <typename T>
 __global__ void __launch_bounds__(256) upload_kernel(const T *__restrict__ src, cudaSurfaceObject_t surf, int w,
-                                                     int h, int n, int tshift)
+                                                     int h, int n, int tshift, int hd)
 {
     const int x = blockIdx.x * 64 + (threadIdx.x & 63);
     const int y = blockIdx.y * 4 + (threadIdx.x >> 6);
     const int z = blockIdx.z;
     if (x >= w || y >= h || z >= n) return;
-    const T v = src[((size_t)z * h + y) * w + x];
+    const T v = src[((size_t)z * hd + (y < hd ? y : 0)) * w + x];
     const int X = (z & ((1 << tshift) - 1)) * w + x;
     const int Y = (z >> tshift) * h + y;
     surf2Dwrite(v, surf, X * (int)sizeof(T), Y);
@@ -120,12 +124,13 @@ cudaError_t atlas_upload(const AtlasStore &s, const void *src, cudaStream_t stre
                                                        s.n, s.tshift);
         return cudaGetLastError();
     }
+    const int hd = s.h - s.wrap;  // rows of source data per slice
     if (s.bf16)
         upload_kernel<unsigned short><<<grid, 256, 0, stream>>>(static_cast<const unsigned short *>(src), s.surf, s.w,
-                                                                s.h, s.n, s.tshift);
+                                                                s.h, s.n, s.tshift, hd);
     else
         upload_kernel<float><<<grid, 256, 0, stream>>>(static_cast<const float *>(src), s.surf, s.w, s.h, s.n,
-                                                       s.tshift);
+                                                       s.tshift, hd);
     return cudaGetLastError();
 }
 

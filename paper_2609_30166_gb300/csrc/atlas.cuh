@@ -24,15 +24,11 @@ struct Atlas {
     int packed = 0;               // 32-bit texels: BF16 of slice s (low half) and s + 1 (high half)
 };
 
-// Four texels (x0,y0) (x0+1,y0) (x0,y0+1) (x0+1,y0+1) of slice s (clamped to a
-// valid slice; out-of-slice texels are the neighbouring tile's, so callers
-// give them zero weight).
-__device__ __forceinline__ void atlas_quad(const Atlas &A, int s, int x0, int y0, float &c00, float &c10,
-                                           float &c01, float &c11)
+// Four texels of one footprint addressed by their shared corner (X, Y) in
+// atlas coordinates (tile origin + (x0, y0) + 1); see atlas_quad.
+__device__ __forceinline__ void atlas_quad_at(const Atlas &A, float X, float Y, float &c00, float &c10, float &c01,
+                                              float &c11)
 {
-    s = min(max(s, 0), A.n - 1);
-    const float X = (float)(((s & ((1 << A.tshift) - 1)) * A.w) + x0) + 1.0f;
-    const float Y = (float)(((s >> A.tshift) * A.h) + y0) + 1.0f;
     if (A.bf16) {
         const ushort4 q = tex2Dgather<ushort4>(A.tex, X, Y, 0);
         c01 = __uint_as_float((unsigned)q.x << 16);
@@ -48,6 +44,18 @@ __device__ __forceinline__ void atlas_quad(const Atlas &A, int s, int x0, int y0
     }
 }
 
+// Four texels (x0,y0) (x0+1,y0) (x0,y0+1) (x0+1,y0+1) of slice s (clamped to a
+// valid slice; out-of-slice texels are the neighbouring tile's, so callers
+// give them zero weight).
+__device__ __forceinline__ void atlas_quad(const Atlas &A, int s, int x0, int y0, float &c00, float &c10,
+                                           float &c01, float &c11)
+{
+    s = min(max(s, 0), A.n - 1);
+    const float X = (float)(((s & ((1 << A.tshift) - 1)) * A.w) + x0) + 1.0f;
+    const float Y = (float)(((s >> A.tshift) * A.h) + y0) + 1.0f;
+    atlas_quad_at(A, X, Y, c00, c10, c01, c11);
+}
+
 // Zero-padded trilinear interpolation of a volume atlas at index coordinate
 // (gx, gy, gz); same weights as the row-major sampler, two gathers.
 struct AtlasSampler {
@@ -55,6 +63,7 @@ struct AtlasSampler {
     const float2 *tile = nullptr;  // shared-memory table: slice -> (atlas x, y of its tile) + 1
 
     static constexpr int TILE_TABLE = 2048;
+    static constexpr bool CYLINDER = false;
     // Fills the per-CTA tile-origin table (all threads call; barrier inside).
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads)
     {
@@ -174,6 +183,7 @@ struct LinearSampler {
     const TV *vol;
     int nx, ny, nz;
     static constexpr int TILE_TABLE = 1;
+    static constexpr bool CYLINDER = false;
     __device__ __forceinline__ void bind(float2 *, int, int) {}
     __device__ __forceinline__ float interior(float gx, float gy, float gz) const;
     __device__ __forceinline__ float operator()(float gx, float gy, float gz, float &wsum) const;
@@ -185,11 +195,14 @@ struct AtlasStore {
     cudaTextureObject_t tex = 0;
     cudaSurfaceObject_t surf = 0;
     int w = 0, h = 0, n = 0, tshift = 0, bf16 = -1, packed = 0;
+    int wrap = 0;  // tiles carry one extra row repeating row 0 (periodic axis); h counts it
 };
 // Creates (or keeps, if the shape matches) an atlas for n slices of w x h;
-// packed: 32-bit texels holding BF16 slice pairs (s, s + 1).
+// packed: 32-bit texels holding BF16 slice pairs (s, s + 1); wrap: every
+// tile gets an extra row h that repeats row 0 (the atlas's h is then h + 1).
 // Returns cudaErrorInvalidValue if it cannot fit the device's 2D texture limits.
-cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int device, bool packed = false);
+cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int device, bool packed = false,
+                         bool wrap = false);
 void atlas_release(AtlasStore &s);
 Atlas atlas_view(const AtlasStore &s);
 // Copies slices [n][h][w] (row-major, FP32 or BF16 as the atlas) into the

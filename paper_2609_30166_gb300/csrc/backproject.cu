@@ -11,6 +11,7 @@
 // whose detector footprint over all views is a band of rows.
 #include "atlas.cuh"
 #include "ctrex_internal.cuh"
+#include "cylinder.cuh"
 
 namespace ctrex {
 
@@ -121,11 +122,15 @@ __device__ __forceinline__ void bp_term(const Images &img, const typename Images
 // per axis; the points are visited inside the view loop, so the finer grid
 // lives only in registers.  Its longer loop body gets a larger register
 // budget (fewer resident CTAs per SM).
-template <typename Images, typename TV, bool WINDOW, bool SUBV>
+// CYL: the aligned cylindrical domain (Sec. 3.5): voxel (ix, iy, iz) is ring
+// ix, sector iy, slice iz; its point is mapped to the cylinder frame (the
+// frame the view matrices are expressed in) before projection, and the z
+// neighbour lies dz further along the axis.
+template <typename Images, typename TV, bool WINDOW, bool SUBV, bool CYL>
 __global__ void __launch_bounds__(BP_THREADS, SUBV ? CTREX_BP_SUBV_MIN_BLOCKS : CTREX_BP_MIN_BLOCKS)
     bp_kernel(Grid G, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx, int n_idx,
               const Images img, const int4 *__restrict__ window, TV *__restrict__ vol, const float *__restrict__ w,
-              float alpha, int normalize, int accumulate, int sv)
+              float alpha, int normalize, int accumulate, int sv, const CylGPU cyl)
 {
     __shared__ float4 sP[BP_CHUNK][3];
     __shared__ typename Images::Slot sImg[BP_CHUNK];
@@ -135,7 +140,14 @@ __global__ void __launch_bounds__(BP_THREADS, SUBV ? CTREX_BP_SUBV_MIN_BLOCKS : 
     const int iy = blockIdx.y * BP_TY + threadIdx.y;
     const int iz = (blockIdx.z * BP_TZ + threadIdx.z) * BP_VZ;  // this thread: slices iz, iz + 1
     const bool inside = ix < G.nx && iy < G.ny && iz < G.nz;
-    const float fx = (float)ix, fy = (float)iy, fz = (float)iz;
+    float fx = (float)ix, fy = (float)iy, fz = (float)iz;
+    if (CYL && !SUBV) {
+        float x, y, z;
+        cyl_point(cyl, fx, fy, fz, x, y, z);
+        fx = x;
+        fy = y;
+        fz = z;
+    }
     float2 lo = make_float2(0.0f, 0.0f), hi = make_float2((float)(G.nu - 1), (float)(G.nv - 1));
     float b0 = 0.0f, c0 = 0.0f, b1 = 0.0f, c1 = 0.0f;
     const int total = n_idx * G.n_sub;
@@ -175,24 +187,42 @@ __global__ void __launch_bounds__(BP_THREADS, SUBV ? CTREX_BP_SUBV_MIN_BLOCKS : 
                     const float gz = fz + fmaf((float)az, d, o);
                     for (int ay = 0; ay < sv; ++ay) {
                         const float gy = fy + fmaf((float)ay, d, o);
+                        float sn = 0.0f, cs = 0.0f;
+                        if (CYL) sincosf((gy + 0.5f) * cyl.dphi, &sn, &cs);
                         for (int ax = 0; ax < sv; ++ax) {
                             const float gx = fx + fmaf((float)ax, d, o);
-                            const float h3 = fmaf(p2.x, gx, fmaf(p2.y, gy, fmaf(p2.z, gz, p2.w)));
-                            const float h1 = fmaf(p0.x, gx, fmaf(p0.y, gy, fmaf(p0.z, gz, p0.w)));
-                            const float h2 = fmaf(p1.x, gx, fmaf(p1.y, gy, fmaf(p1.z, gz, p1.w)));
+                            float X = gx, Y = gy, Z = gz;
+                            if (CYL) {
+                                const float r = (gx + 0.5f) * cyl.dr;
+                                X = r * cs;
+                                Y = r * sn;
+                                Z = (gz - cyl.zc) * cyl.dz;
+                            }
+                            const float h3 = fmaf(p2.x, X, fmaf(p2.y, Y, fmaf(p2.z, Z, p2.w)));
+                            const float h1 = fmaf(p0.x, X, fmaf(p0.y, Y, fmaf(p0.z, Z, p0.w)));
+                            const float h2 = fmaf(p1.x, X, fmaf(p1.y, Y, fmaf(p1.z, Z, p1.w)));
                             bp_term(img, slot, h1, h2, h3, lo, hi, b0, c0);
-                            bp_term(img, slot, h1 + p0.z, h2 + p1.z, h3 + p2.z, lo, hi, b1, c1);
+                            if (CYL)
+                                bp_term(img, slot, fmaf(p0.z, cyl.dz, h1), fmaf(p1.z, cyl.dz, h2),
+                                        fmaf(p2.z, cyl.dz, h3), lo, hi, b1, c1);
+                            else
+                                bp_term(img, slot, h1 + p0.z, h2 + p1.z, h3 + p2.z, lo, hi, b1, c1);
                         }
                     }
                 }
                 continue;
             }
             // voxel (ix, iy, iz) and its z neighbour: h(z + 1) = h(z) + P[:, 2]
+            // (+ dz P[:, 2] on the cylinder, whose matrices act on frame mm)
             const float h3 = fmaf(p2.x, fx, fmaf(p2.y, fy, fmaf(p2.z, fz, p2.w)));
             const float h1 = fmaf(p0.x, fx, fmaf(p0.y, fy, fmaf(p0.z, fz, p0.w)));
             const float h2 = fmaf(p1.x, fx, fmaf(p1.y, fy, fmaf(p1.z, fz, p1.w)));
             bp_term(img, slot, h1, h2, h3, lo, hi, b0, c0);
-            bp_term(img, slot, h1 + p0.z, h2 + p1.z, h3 + p2.z, lo, hi, b1, c1);
+            if (CYL)
+                bp_term(img, slot, fmaf(p0.z, cyl.dz, h1), fmaf(p1.z, cyl.dz, h2), fmaf(p2.z, cyl.dz, h3), lo, hi,
+                        b1, c1);
+            else
+                bp_term(img, slot, h1 + p0.z, h2 + p1.z, h3 + p2.z, lo, hi, b1, c1);
         }
     }
     if (!inside) return;
@@ -212,17 +242,27 @@ __global__ void __launch_bounds__(BP_THREADS, SUBV ? CTREX_BP_SUBV_MIN_BLOCKS : 
     }
 }
 
-template <typename Images, typename TV, bool SUBV>
+template <typename Images, typename TV, bool SUBV, bool CYL>
 static void bp_launch_window(const BpArgs &a, const Images &img, dim3 grid, dim3 block)
 {
+    const CylGPU cyl = a.cyl ? *a.cyl : CylGPU{};
     if (a.window)
-        bp_kernel<Images, TV, true, SUBV><<<grid, block, 0, a.stream>>>(*a.grid, a.views, a.view_idx, a.n_idx, img,
-                                                                       a.window, static_cast<TV *>(a.vol), a.w,
-                                                                       a.alpha, a.normalize, a.accumulate, a.subvox);
+        bp_kernel<Images, TV, true, SUBV, CYL><<<grid, block, 0, a.stream>>>(
+            *a.grid, a.views, a.view_idx, a.n_idx, img, a.window, static_cast<TV *>(a.vol), a.w, a.alpha,
+            a.normalize, a.accumulate, a.subvox, cyl);
     else
-        bp_kernel<Images, TV, false, SUBV><<<grid, block, 0, a.stream>>>(*a.grid, a.views, a.view_idx, a.n_idx, img,
-                                                                        nullptr, static_cast<TV *>(a.vol), a.w,
-                                                                        a.alpha, a.normalize, a.accumulate, a.subvox);
+        bp_kernel<Images, TV, false, SUBV, CYL><<<grid, block, 0, a.stream>>>(
+            *a.grid, a.views, a.view_idx, a.n_idx, img, nullptr, static_cast<TV *>(a.vol), a.w, a.alpha,
+            a.normalize, a.accumulate, a.subvox, cyl);
+}
+
+template <typename Images, typename TV, bool CYL>
+static void bp_launch_subv(const BpArgs &a, const Images &img, dim3 grid, dim3 block)
+{
+    if (a.subvox > 1)
+        bp_launch_window<Images, TV, true, CYL>(a, img, grid, block);
+    else
+        bp_launch_window<Images, TV, false, CYL>(a, img, grid, block);
 }
 
 template <typename Images, typename TV>
@@ -232,10 +272,10 @@ static cudaError_t bp_launch(const BpArgs &a, const Images &img)
     const dim3 block(BP_TX, BP_TY, BP_TZ);
     const dim3 grid((G.nx + BP_TX - 1) / BP_TX, (G.ny + BP_TY - 1) / BP_TY,
                     (G.nz + BP_TZ * BP_VZ - 1) / (BP_TZ * BP_VZ));
-    if (a.subvox > 1)
-        bp_launch_window<Images, TV, true>(a, img, grid, block);
+    if (a.cyl)
+        bp_launch_subv<Images, TV, true>(a, img, grid, block);
     else
-        bp_launch_window<Images, TV, false>(a, img, grid, block);
+        bp_launch_subv<Images, TV, false>(a, img, grid, block);
     return cudaGetLastError();
 }
 

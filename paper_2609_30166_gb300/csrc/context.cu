@@ -56,6 +56,9 @@ struct ctrex_ctx {
     bool has_window = false;
     // sub-voxel backprojection points per axis (motion blur), 1 = off
     int bp_subvoxel = 1;
+    // aligned cylindrical domain (set by ctrex_set_geometry_cylinder)
+    bool cyl = false;
+    CylGPU cylg{};
     // ordered-subset SIRT: concatenated subset view lists, per-subset norms
     int *d_subset_views = nullptr;
     size_t subset_views_bytes = 0;
@@ -159,6 +162,7 @@ FwdArgs fwd_args(ctrex_ctx *c, const void *vol, int vdt, const int *view_idx, in
     a.n_idx = n_idx;
     a.stream = c->stream;
     a.devcheck = c->d_devcheck;
+    a.cyl = c->cyl ? &c->cylg : nullptr;
     return a;
 }
 
@@ -166,6 +170,22 @@ FwdArgs fwd_args(ctrex_ctx *c, const void *vol, int vdt, const int *view_idx, in
 // the volume does not fit the 2D texture limits the row-major path is used.
 int prepare_atlas(ctrex_ctx *c, FwdArgs &a, const void *vol, int vdt)
 {
+    if (c->cyl) {
+        // cylindrical domain: z-slice tiles of N_r x (N_phi + 1), the last row
+        // repeating sector 0; no row-major fallback
+        cudaError_t e = atlas_ensure(c->vol_atlas, c->grid.nx, c->grid.ny, c->grid.nz, vdt == CTREX_BF16, c->device,
+                                     false, true);
+        if (e == cudaErrorInvalidValue) {
+            cudaGetLastError();
+            return fail(c, CTREX_E_SHAPE, "cylindrical volume exceeds the 2D texture limits of the device");
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "volume atlas allocation");
+        e = atlas_upload(c->vol_atlas, vol, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "volume atlas upload");
+        c->vol_atlas_view = atlas_view(c->vol_atlas);
+        a.atlas = &c->vol_atlas_view;
+        return CTREX_OK;
+    }
     if (c->atlas_unfit) return CTREX_OK;
     // BF16 volumes: slice pairs packed in 32-bit texels, one gather per sample
     cudaError_t e = atlas_ensure(c->vol_atlas, c->grid.nx, c->grid.ny, c->grid.nz, vdt == CTREX_BF16, c->device,
@@ -302,29 +322,17 @@ int ctrex_device_status(ctrex_ctx *c)
     return CTREX_OK;
 }
 
-int ctrex_set_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, const ctrex_vol_grid *vol,
-                       const ctrex_det_grid *det, double step_vox)
+// Shared by the Cartesian and the cylindrical set-up.  P maps the frame the
+// grid is indexed in (mm) to pixels; voxel i of axis a sits at origin[a] +
+// i vox[a] in that frame; ctr is the volume centre (sign normalisation of P);
+// min_pitch the smallest physical pitch (step and row-sum threshold).
+static int build_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, const int n[3], const double vox[3],
+                          const double origin[3], const double ctr[3], double min_pitch, const ctrex_det_grid *det,
+                          double step_vox)
 {
-    if (!c) return CTREX_E_ARG;
-    if (!P || !vol || !det) return fail(c, CTREX_E_ARG, "set_geometry: NULL argument");
-    if (n_views < 1 || n_sub < 1 || (long long)n_views * n_sub > (1 << 24))
-        return fail(c, CTREX_E_SHAPE, "set_geometry: bad n_views %d / n_sub %d", n_views, n_sub);
-    if (vol->nx < 1 || vol->ny < 1 || vol->nz < 1 || (long long)vol->nx * vol->ny * vol->nz >= (1LL << 31))
-        return fail(c, CTREX_E_SHAPE, "set_geometry: volume %d x %d x %d unsupported", vol->nx, vol->ny, vol->nz);
-    if (det->nu < 1 || det->nv < 1 || det->nv > 4 * 65535 || (long long)det->nu * det->nv >= (1LL << 31))
-        return fail(c, CTREX_E_SHAPE, "set_geometry: detector %d x %d unsupported", det->nu, det->nv);
-    for (int a = 0; a < 3; ++a)
-        if (!(vol->vox[a] > 0.0) || !isfinite(vol->origin[a]))
-            return fail(c, CTREX_E_ARG, "set_geometry: voxel pitch must be > 0 and origin finite");
-    // bounded step keeps every ray's sample count (and kernel run time) bounded
-    if (!(step_vox >= 1e-2 && step_vox <= 100.0))
-        return fail(c, CTREX_E_ARG, "set_geometry: step_vox must lie in [0.01, 100]");
     DeviceGuard g(c->device);
     const int nvs = n_views * n_sub;
     std::vector<ViewGPU> hv((size_t)nvs);
-    const int n[3] = {vol->nx, vol->ny, vol->nz};
-    double ctr[3];
-    for (int a = 0; a < 3; ++a) ctr[a] = vol->origin[a] + 0.5 * (n[a] - 1) * vol->vox[a];
     const double uc = 0.5 * (det->nu - 1), vc = 0.5 * (det->nv - 1);
     for (int q = 0; q < nvs; ++q) {
         const double *Pi = P + 12 * (size_t)q;
@@ -356,17 +364,17 @@ int ctrex_set_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, co
         for (int a = 0; a < 3; ++a) {
             const double mc = Mi[3 * a] * uc + Mi[3 * a + 1] * vc + Mi[3 * a + 2];
             const double dref = lam * mc;  // X(uc,vc) - source, mm
-            V.dref[a] = (float)(dref / vol->vox[a]);
-            V.ref[a] = (float)((src[a] + dref - vol->origin[a]) / vol->vox[a]);
-            V.qu[a] = (float)(lam * Mi[3 * a] / vol->vox[a]);
-            V.qv[a] = (float)(lam * Mi[3 * a + 1] / vol->vox[a]);
+            V.dref[a] = (float)(dref / vox[a]);
+            V.ref[a] = (float)((src[a] + dref - origin[a]) / vox[a]);
+            V.qu[a] = (float)(lam * Mi[3 * a] / vox[a]);
+            V.qv[a] = (float)(lam * Mi[3 * a + 1] / vox[a]);
         }
         // h = Pn [origin + vox * i; 1]
         for (int r = 0; r < 3; ++r) {
             double acc = Pn[4 * r + 3];
             for (int a = 0; a < 3; ++a) {
-                V.P[4 * r + a] = (float)(Pn[4 * r + a] * vol->vox[a]);
-                acc += Pn[4 * r + a] * vol->origin[a];
+                V.P[4 * r + a] = (float)(Pn[4 * r + a] * vox[a]);
+                acc += Pn[4 * r + a] * origin[a];
             }
             V.P[4 * r + 3] = (float)acc;
         }
@@ -387,20 +395,19 @@ int ctrex_set_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, co
     CT_CUDA(c, cudaMalloc((void **)&c->d_views, sizeof(ViewGPU) * (size_t)nvs));
     CT_CUDA(c, cudaMemcpy(c->d_views, hv.data(), sizeof(ViewGPU) * (size_t)nvs, cudaMemcpyHostToDevice));
     Grid &G = c->grid;
-    G.nx = vol->nx;
-    G.ny = vol->ny;
-    G.nz = vol->nz;
+    G.nx = n[0];
+    G.ny = n[1];
+    G.nz = n[2];
     G.nu = det->nu;
     G.nv = det->nv;
     G.n_views = n_views;
     G.n_sub = n_sub;
-    double minv = vol->vox[0];
+    const double minv = min_pitch;
     for (int a = 0; a < 3; ++a) {
-        c->vox[a] = vol->vox[a];
-        c->origin[a] = vol->origin[a];
-        G.vox[a] = (float)vol->vox[a];
+        c->vox[a] = vox[a];
+        c->origin[a] = origin[a];
+        G.vox[a] = (float)vox[a];
         G.spl_scale[a] = (float)(5.0 / n[a]);
-        if (vol->vox[a] < minv) minv = vol->vox[a];
     }
     c->step_vox = step_vox;
     G.step_mm = (float)(step_vox * minv);
@@ -409,6 +416,7 @@ int ctrex_set_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, co
     G.eps_R = (float)(1e-6 * minv);
     G.inv_sub = (float)(1.0 / n_sub);
     c->has_motion = false;
+    c->cyl = false;
     c->has_geom = true;
     c->atlas_unfit = false;
     c->img_atlas_unfit = false;
@@ -416,10 +424,119 @@ int ctrex_set_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, co
     return CTREX_OK;
 }
 
+
+int ctrex_set_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, const ctrex_vol_grid *vol,
+                       const ctrex_det_grid *det, double step_vox)
+{
+    if (!c) return CTREX_E_ARG;
+    if (!P || !vol || !det) return fail(c, CTREX_E_ARG, "set_geometry: NULL argument");
+    if (n_views < 1 || n_sub < 1 || (long long)n_views * n_sub > (1 << 24))
+        return fail(c, CTREX_E_SHAPE, "set_geometry: bad n_views %d / n_sub %d", n_views, n_sub);
+    if (vol->nx < 1 || vol->ny < 1 || vol->nz < 1 || (long long)vol->nx * vol->ny * vol->nz >= (1LL << 31))
+        return fail(c, CTREX_E_SHAPE, "set_geometry: volume %d x %d x %d unsupported", vol->nx, vol->ny, vol->nz);
+    if (det->nu < 1 || det->nv < 1 || det->nv > 4 * 65535 || (long long)det->nu * det->nv >= (1LL << 31))
+        return fail(c, CTREX_E_SHAPE, "set_geometry: detector %d x %d unsupported", det->nu, det->nv);
+    for (int a = 0; a < 3; ++a)
+        if (!(vol->vox[a] > 0.0) || !isfinite(vol->origin[a]))
+            return fail(c, CTREX_E_ARG, "set_geometry: voxel pitch must be > 0 and origin finite");
+    // bounded step keeps every ray's sample count (and kernel run time) bounded
+    if (!(step_vox >= 1e-2 && step_vox <= 100.0))
+        return fail(c, CTREX_E_ARG, "set_geometry: step_vox must lie in [0.01, 100]");
+    const int n[3] = {vol->nx, vol->ny, vol->nz};
+    double ctr[3], minv = vol->vox[0];
+    for (int a = 0; a < 3; ++a) {
+        ctr[a] = vol->origin[a] + 0.5 * (n[a] - 1) * vol->vox[a];
+        minv = fmin(minv, vol->vox[a]);
+    }
+    return build_geometry(c, P, n_views, n_sub, n, vol->vox, vol->origin, ctr, minv, det, step_vox);
+}
+
+int ctrex_set_geometry_cylinder(ctrex_ctx *c, const double *P, int n_views, int n_sub, const ctrex_cyl_grid *cyl,
+                                const ctrex_det_grid *det, double step_vox)
+{
+    if (!c) return CTREX_E_ARG;
+    if (!P || !cyl || !det) return fail(c, CTREX_E_ARG, "set_geometry_cylinder: NULL argument");
+    if (n_views < 1 || n_sub < 1 || (long long)n_views * n_sub > (1 << 24))
+        return fail(c, CTREX_E_SHAPE, "set_geometry_cylinder: bad n_views %d / n_sub %d", n_views, n_sub);
+    if (cyl->n_r < 1 || cyl->n_phi < 3 || cyl->n_z < 1 ||
+        (long long)cyl->n_r * (cyl->n_phi + 1) * cyl->n_z >= (1LL << 31))
+        return fail(c, CTREX_E_SHAPE, "set_geometry_cylinder: grid %d x %d x %d unsupported", cyl->n_r, cyl->n_phi,
+                    cyl->n_z);
+    if (det->nu < 1 || det->nv < 1 || det->nv > 4 * 65535 || (long long)det->nu * det->nv >= (1LL << 31))
+        return fail(c, CTREX_E_SHAPE, "set_geometry_cylinder: detector %d x %d unsupported", det->nu, det->nv);
+    if (!(cyl->dr > 0.0 && isfinite(cyl->dr) && cyl->dz > 0.0 && isfinite(cyl->dz)))
+        return fail(c, CTREX_E_ARG, "set_geometry_cylinder: dr and dz must be finite and > 0");
+    if (!(step_vox >= 1e-2 && step_vox <= 100.0))
+        return fail(c, CTREX_E_ARG, "set_geometry_cylinder: step_vox must lie in [0.01, 100]");
+    // the pose must be a rigid motion: Rc orthonormal with det +1
+    const double *T = cyl->pose;
+    for (int k = 0; k < 12; ++k)
+        if (!isfinite(T[k])) return fail(c, CTREX_E_ARG, "set_geometry_cylinder: non-finite pose");
+    double Rc[9];
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) Rc[3 * r + k] = T[4 * r + k];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const double d = Rc[i] * Rc[j] + Rc[3 + i] * Rc[3 + j] + Rc[6 + i] * Rc[6 + j];
+            if (fabs(d - (i == j ? 1.0 : 0.0)) > 1e-9)
+                return fail(c, CTREX_E_ARG, "set_geometry_cylinder: pose rotation is not orthonormal");
+        }
+    if (!(det3(Rc) > 0.0)) return fail(c, CTREX_E_ARG, "set_geometry_cylinder: pose rotation is a reflection");
+    // P_q = P [Rc^T | -Rc^T tc]: the matrices act on cylinder-frame mm
+    const size_t nvs = (size_t)n_views * n_sub;
+    std::vector<double> Pq(12 * nvs);
+    const double tc[3] = {T[3], T[7], T[11]};
+    double inv[12];
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) inv[4 * r + k] = Rc[3 * k + r];
+        inv[4 * r + 3] = -(Rc[r] * tc[0] + Rc[3 + r] * tc[1] + Rc[6 + r] * tc[2]);
+    }
+    for (size_t q = 0; q < nvs; ++q) {
+        const double *Pi = P + 12 * q;
+        double *Po = Pq.data() + 12 * q;
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 4; ++k) {
+                double acc = k == 3 ? Pi[4 * r + 3] : 0.0;
+                for (int m = 0; m < 3; ++m) acc += Pi[4 * r + m] * inv[4 * m + k];
+                Po[4 * r + k] = acc;
+            }
+    }
+    const int n[3] = {cyl->n_r, cyl->n_phi, cyl->n_z};
+    const double one[3] = {1.0, 1.0, 1.0}, zero[3] = {0.0, 0.0, 0.0};
+    const int e = build_geometry(c, Pq.data(), n_views, n_sub, n, one, zero, zero, fmin(cyl->dr, cyl->dz), det,
+                                 step_vox);
+    if (e) return e;
+    CylGPU &C = c->cylg;
+    const double two_pi = 6.283185307179586476925286766559;
+    C.n_r = cyl->n_r;
+    C.n_phi = cyl->n_phi;
+    C.n_z = cyl->n_z;
+    C.dr = (float)cyl->dr;
+    C.dphi = (float)(two_pi / cyl->n_phi);
+    C.dz = (float)cyl->dz;
+    C.inv_dr = (float)(1.0 / cyl->dr);
+    C.inv_dphi = (float)(cyl->n_phi / two_pi);
+    C.inv_dz = (float)(1.0 / cyl->dz);
+    C.zc = (float)(0.5 * (cyl->n_z - 1));
+    C.R = (float)(cyl->n_r * cyl->dr);
+    C.Z = (float)(0.5 * cyl->n_z * cyl->dz);
+    // bounding box of the cylinder (frame mm), for anything that reads the clip box
+    for (int a = 0; a < 2; ++a) {
+        c->grid.lo[a] = -C.R;
+        c->grid.hi[a] = C.R;
+    }
+    c->grid.lo[2] = -C.Z;
+    c->grid.hi[2] = C.Z;
+    c->cyl = true;
+    return CTREX_OK;
+}
+
 int ctrex_set_motion(ctrex_ctx *c, const float *theta, const float *coef, const float *s_view, double margin_mm)
 {
     if (!c) return CTREX_E_ARG;
     if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_motion before set_geometry");
+    if (c->cyl && (theta || coef || s_view))
+        return fail(c, CTREX_E_STATE, "set_motion: the motion model is defined on the Cartesian grid only");
     double box = 0.0;
     const int nn[3] = {c->grid.nx, c->grid.ny, c->grid.nz};
     for (int a = 0; a < 3; ++a) box = fmax(box, nn[a] * c->vox[a]);
@@ -576,6 +693,7 @@ int ctrex_back_project(ctrex_ctx *c, const void *r, int rdt, void *vol, int vdt,
     a.stream = c->stream;
     a.window = c->has_window ? c->d_window : nullptr;
     a.subvox = c->bp_subvoxel;
+    a.cyl = c->cyl ? &c->cylg : nullptr;
     if (n_idx > 0 && !c->img_atlas_unfit) {
         cudaError_t ae = atlas_ensure(c->img_atlas, c->grid.nu, c->grid.nv, n_idx, rdt == CTREX_BF16, c->device);
         if (ae == cudaErrorInvalidValue) {
@@ -600,6 +718,7 @@ int ctrex_adjoint_project(ctrex_ctx *c, const float *proj, float *vol, const int
     if (!c) return CTREX_E_ARG;
     int e = check_views(c, view_idx, n_idx);
     if (e) return e;
+    if (c->cyl) return fail(c, CTREX_E_STATE, "adjoint_project: Cartesian grid only");
     if (n_idx == 0) return CTREX_OK;
     if (!proj || !vol) return fail(c, CTREX_E_ARG, "adjoint_project: NULL buffer");
     DeviceGuard g(c->device);

@@ -51,6 +51,18 @@ struct Grid {
     float spl_scale[3];  // B-spline coordinate: xi = (g + 1/2) * spl_scale + 1
 };
 
+// Aligned cylindrical domain (Sec. 3.5): N_r rings x N_phi sectors x N_z
+// slices.  Ray and voxel positions are in the cylinder frame (mm; its z axis
+// is the cylinder axis); index coordinates g_r = r / dr - 1/2 (clamped to
+// >= 0), g_phi = phi / dphi - 1/2 (periodic), g_z = z / dz + zc.
+struct CylGPU {
+    int n_r, n_phi, n_z;
+    float dr, dphi, dz;              // mm, rad, mm
+    float inv_dr, inv_dphi, inv_dz;  // reciprocals
+    float zc;                        // (N_z - 1) / 2
+    float R, Z;                      // bounding cylinder: radius, half height (mm)
+};
+
 template <typename T> struct Storage;
 template <> struct Storage<float> {
     static __device__ __forceinline__ float load(const float *p) { return __ldg(p); }
@@ -84,6 +96,7 @@ struct FwdArgs {
     cudaStream_t stream;
     unsigned *devcheck;         // device status word
     int p_by_view = 0;          // correction: measured images indexed by view, not by list position
+    const CylGPU *cyl = nullptr;  // cylindrical domain, or nullptr (Cartesian grid)
 };
 
 cudaError_t launch_forward(const FwdArgs &a, void *proj, int proj_dtype, float *rowsum);
@@ -109,6 +122,7 @@ struct BpArgs {
     int normalize;
     int accumulate;
     int subvox = 1;  // sub-voxel points per axis (1 = voxel centre only)
+    const CylGPU *cyl = nullptr;  // cylindrical domain, or nullptr (Cartesian grid)
     cudaStream_t stream;
 };
 cudaError_t launch_backproject(const BpArgs &a);

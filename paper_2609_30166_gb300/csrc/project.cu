@@ -11,6 +11,7 @@
 // many views, whose rays all cross the same z-slab of the volume, so that
 // slab stays in L2 while it is being sampled.
 #include "atlas.cuh"
+#include "cylinder.cuh"
 #include "ray.cuh"
 
 namespace ctrex {
@@ -61,6 +62,8 @@ __device__ __forceinline__ void interior_range(const Grid &G, const Ray &R, int 
 }
 
 // Integral of one pixel (mean over its sub-angle rays): value and row sum.
+// On the cylindrical domain the ray is clipped to the bounding cylinder and
+// every sample is mapped to (r, phi, z) by the sampler; the rest is shared.
 template <typename Sampler, bool MOTION>
 __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__restrict__ views,
                                                const MotionGPU &mo, const float *coef,
@@ -71,11 +74,15 @@ __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__r
     for (int s = 0; s < G.n_sub; ++s) {
         const ViewGPU V = views[view * G.n_sub + s];
         Ray R;
-        if (!setup_ray(G, V, u, v, R)) continue;
+        if constexpr (Sampler::CYLINDER) {
+            if (!setup_ray_cyl(G, vol.C, V, u, v, R)) continue;
+        } else {
+            if (!setup_ray(G, V, u, v, R)) continue;
+        }
         float a = 0.0f, ars = 0.0f;
         const int Km1 = R.K - 1;
         int ka = Km1, kb = Km1;
-        if (!MOTION) interior_range(G, R, ka, kb);
+        if (!MOTION && !Sampler::CYLINDER) interior_range(G, R, ka, kb);
         auto general = [&](int k) {
             float g[3];
             g[0] = fmaf((float)k, R.sg[0], R.g0[0]);
@@ -232,8 +239,9 @@ __global__ void __launch_bounds__(1024) finish_sums_kernel(const float *__restri
 }
 
 // Exact sample count (same set-up arithmetic as the projector).
+template <bool CYL>
 __global__ void __launch_bounds__(FWD_TX *FWD_TY)
-    count_kernel(Grid G, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx,
+    count_kernel(Grid G, CylGPU C, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx,
                  unsigned long long *out)
 {
     const int k = blockIdx.y;
@@ -245,7 +253,10 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
     if (iu < G.nu && iv < G.nv) {
         for (int s = 0; s < G.n_sub; ++s) {
             Ray R;
-            if (setup_ray(G, views[view * G.n_sub + s], (float)iu, (float)iv, R)) n += (unsigned long long)R.K;
+            const ViewGPU &V = views[view * G.n_sub + s];
+            const bool hit = CYL ? setup_ray_cyl(G, C, V, (float)iu, (float)iv, R)
+                                 : setup_ray(G, V, (float)iu, (float)iv, R);
+            if (hit) n += (unsigned long long)R.K;
         }
     }
 #pragma unroll
@@ -270,12 +281,18 @@ static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, flo
 {
     const Grid &G = *a.grid;
     const dim3 grid = fwd_grid(G, a.n_idx), block(FWD_TX, FWD_TY);
-    if (a.motion)
-        fwd_kernel<Sampler, TP, MODE, true><<<grid, block, 0, a.stream>>>(
-            G, a.views, a.motion, a.coef_idx, smp, a.view_idx, out, rowsum, p, partials, a.devcheck, a.p_by_view);
-    else
-        fwd_kernel<Sampler, TP, MODE, false><<<grid, block, 0, a.stream>>>(
-            G, a.views, nullptr, nullptr, smp, a.view_idx, out, rowsum, p, partials, a.devcheck, a.p_by_view);
+    if constexpr (!Sampler::CYLINDER) {
+        if (a.motion) {
+            fwd_kernel<Sampler, TP, MODE, true><<<grid, block, 0, a.stream>>>(
+                G, a.views, a.motion, a.coef_idx, smp, a.view_idx, out, rowsum, p, partials, a.devcheck,
+                a.p_by_view);
+            return cudaGetLastError();
+        }
+    } else if (a.motion) {
+        return cudaErrorNotSupported;  // the motion warp is defined on the Cartesian grid only
+    }
+    fwd_kernel<Sampler, TP, MODE, false><<<grid, block, 0, a.stream>>>(
+        G, a.views, nullptr, nullptr, smp, a.view_idx, out, rowsum, p, partials, a.devcheck, a.p_by_view);
     return cudaGetLastError();
 }
 
@@ -284,6 +301,11 @@ static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, flo
 template <typename TP, int MODE>
 static cudaError_t fwd_dispatch_sampler(const FwdArgs &a, TP *out, float *rowsum, const TP *p, float *partials)
 {
+    if (a.cyl) {  // the cylindrical domain is sampled from its atlas only
+        if (!a.atlas) return cudaErrorInvalidValue;
+        return fwd_launch<CylSampler, TP, MODE>(a, CylSampler{AtlasSampler{*a.atlas}, *a.cyl}, out, rowsum, p,
+                                               partials);
+    }
     if (a.atlas) return fwd_launch<AtlasSampler, TP, MODE>(a, AtlasSampler{*a.atlas}, out, rowsum, p, partials);
     const Grid &G = *a.grid;
     if (a.vol_dtype == CTREX_F32)
@@ -330,8 +352,11 @@ cudaError_t launch_count_samples(const FwdArgs &a, unsigned long long *out)
 {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), a.stream);
     if (e != cudaSuccess || a.n_idx == 0) return e;
-    count_kernel<<<fwd_grid(*a.grid, a.n_idx), dim3(FWD_TX, FWD_TY), 0, a.stream>>>(*a.grid, a.views,
-                                                                                 a.view_idx, out);
+    const dim3 grid = fwd_grid(*a.grid, a.n_idx), block(FWD_TX, FWD_TY);
+    if (a.cyl)
+        count_kernel<true><<<grid, block, 0, a.stream>>>(*a.grid, *a.cyl, a.views, a.view_idx, out);
+    else
+        count_kernel<false><<<grid, block, 0, a.stream>>>(*a.grid, CylGPU{}, a.views, a.view_idx, out);
     return cudaGetLastError();
 }
 

@@ -18,35 +18,31 @@ struct Ray {
     int K;
 };
 
-// Sets up the ray of view parameters V through detector point (u, v).
-// Returns false if the half line from the source misses the clip box.
-__device__ __forceinline__ bool setup_ray(const Grid &G, const ViewGPU &V, float u, float v, Ray &R)
+// The line of view parameters V through detector point (u, v): X, a point
+// near the volume, and dg, index units per mm along the ray; the source sits
+// at t = -len (t in mm from X).
+__device__ __forceinline__ void ray_line(const Grid &G, const ViewGPU &V, float u, float v, float X[3], float dg[3],
+                                         float &len)
 {
     const float du = u - G.uc, dv = v - G.vc;
-    float X[3], D[3];
+    float D[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         X[a] = fmaf(dv, V.qv[a], fmaf(du, V.qu[a], V.ref[a]));
         D[a] = fmaf(dv, V.qv[a], fmaf(du, V.qu[a], V.dref[a]));
     }
     const float m0 = D[0] * G.vox[0], m1 = D[1] * G.vox[1], m2 = D[2] * G.vox[2];
-    const float len = sqrtf(fmaf(m0, m0, fmaf(m1, m1, m2 * m2)));
+    len = sqrtf(fmaf(m0, m0, fmaf(m1, m1, m2 * m2)));
     const float il = 1.0f / len;
-    float dg[3] = {D[0] * il, D[1] * il, D[2] * il};  // voxels per mm along the ray
-    // t: mm along the ray measured from X; the source sits at t = -len.
-    float t0 = -len, t1 = INFINITY;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (dg[a] != 0.0f) {
-            const float inv = 1.0f / dg[a];
-            const float ta = (G.lo[a] - X[a]) * inv, tb = (G.hi[a] - X[a]) * inv;
-            t0 = fmaxf(t0, fminf(ta, tb));
-            t1 = fminf(t1, fmaxf(ta, tb));
-        } else if (X[a] < G.lo[a] || X[a] > G.hi[a]) {
-            return false;
-        }
-    }
-    if (!(t1 > t0)) return false;
+    dg[0] = D[0] * il;
+    dg[1] = D[1] * il;
+    dg[2] = D[2] * il;
+}
+
+// Samples of the clipped segment [t0, t1] (truncated-midpoint rule).
+__device__ __forceinline__ void finish_ray(const Grid &G, const float X[3], const float dg[3], float t0, float t1,
+                                           Ray &R)
+{
     const float step = G.step_mm;
     const float L = t1 - t0;
     int K = (int)ceilf(L / step);
@@ -62,6 +58,28 @@ __device__ __forceinline__ bool setup_ray(const Grid &G, const ViewGPU &V, float
     }
     R.w_last = t1 - a_last;
     R.K = K;
+}
+
+// Sets up the ray of view parameters V through detector point (u, v).
+// Returns false if the half line from the source misses the clip box.
+__device__ __forceinline__ bool setup_ray(const Grid &G, const ViewGPU &V, float u, float v, Ray &R)
+{
+    float X[3], dg[3], len;
+    ray_line(G, V, u, v, X, dg, len);
+    float t0 = -len, t1 = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (dg[a] != 0.0f) {
+            const float inv = 1.0f / dg[a];
+            const float ta = (G.lo[a] - X[a]) * inv, tb = (G.hi[a] - X[a]) * inv;
+            t0 = fmaxf(t0, fminf(ta, tb));
+            t1 = fminf(t1, fmaxf(ta, tb));
+        } else if (X[a] < G.lo[a] || X[a] > G.hi[a]) {
+            return false;
+        }
+    }
+    if (!(t1 > t0)) return false;
+    finish_ray(G, X, dg, t0, t1, R);
     return true;
 }
 

@@ -34,7 +34,7 @@ EXPORTS = (
     "ctrex_fwd_correct", "ctrex_back_project", "ctrex_adjoint_project", "ctrex_motion_grad",
     "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples", "ctrex_correct_static",
     "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad", "ctrex_os_sirt_iterate", "ctrex_set_bp_window",
-    "ctrex_probe_gather_rate", "ctrex_set_bp_subvoxel",
+    "ctrex_probe_gather_rate", "ctrex_set_bp_subvoxel", "ctrex_set_geometry_cylinder",
 )
 
 # Largest n ctrex_correct_static accepts (its static scratch holds 65536 CTA partials of 8192 elements).
@@ -54,6 +54,11 @@ class VolGrid(ctypes.Structure):
 
 class DetGrid(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_int), ("nv", ctypes.c_int)]
+
+
+class CylGrid(ctypes.Structure):
+    _fields_ = [("n_r", ctypes.c_int), ("n_phi", ctypes.c_int), ("n_z", ctypes.c_int),
+                ("dr", ctypes.c_double), ("dz", ctypes.c_double), ("pose", ctypes.c_double * 12)]
 
 
 _lib = None
@@ -94,6 +99,8 @@ def load_library(path: str = LIB_PATH):
         "ctrex_os_sirt_iterate": ([vp, vp, i, vp, i, ip, ip, i, i, f, vp, f, fp, ip], i),
         "ctrex_set_bp_window": ([vp, ip], i),
         "ctrex_set_bp_subvoxel": ([vp, i], i),
+        "ctrex_set_geometry_cylinder": ([vp, ctypes.POINTER(d), i, i, ctypes.POINTER(CylGrid),
+                                         ctypes.POINTER(DetGrid), d], i),
         "ctrex_probe_gather_rate": ([vp, ctypes.POINTER(d)], i),
     }
     for name, (args, res) in sig.items():
@@ -192,6 +199,26 @@ class Context:
         self._check(self.lib.ctrex_set_geometry(self._h, P.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                 V, S, ctypes.byref(vg), ctypes.byref(dg), float(step_vox)))
         self.vol_shape = (nz, ny, nx)
+        self.det_shape = (int(det[1]), int(det[0]))
+        self.n_views, self.n_sub = V, S
+
+    def set_geometry_cylinder(self, P, n_r, n_phi, n_z, dr, dz, det, pose=None, step_vox=0.5):
+        """The aligned cylindrical domain: n_r rings of dr mm, n_phi sectors,
+        n_z slices of dz mm; pose [3, 4] maps world mm to the cylinder frame
+        (identity if None).  Volumes are then [n_z, n_phi, n_r]."""
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        if P.ndim == 3:
+            P = P[:, None]
+        V, S = P.shape[:2]
+        if pose is None:
+            pose = np.hstack([np.eye(3), np.zeros((3, 1))])
+        pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(12)
+        cg = CylGrid(int(n_r), int(n_phi), int(n_z), float(dr), float(dz), (ctypes.c_double * 12)(*pose))
+        dg = DetGrid(int(det[0]), int(det[1]))
+        self._check(self.lib.ctrex_set_geometry_cylinder(
+            self._h, P.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), V, S, ctypes.byref(cg), ctypes.byref(dg),
+            float(step_vox)))
+        self.vol_shape = (int(n_z), int(n_phi), int(n_r))
         self.det_shape = (int(det[1]), int(det[0]))
         self.n_views, self.n_sub = V, S
 
@@ -462,6 +489,19 @@ def probe_gather_rate(device=None):
     if rc != OK:
         raise CtrexError(rc, "gather-rate probe failed")
     return out.value
+
+
+def context_for_cylinder(ccfg, P=None, device=None):
+    """A Context on the cylindrical domain of an ``inputs.CylConfig``."""
+    from . import inputs
+
+    if P is None:
+        P = inputs.projection_matrices(ccfg.base)
+    ctx = Context(device)
+    b = ccfg.base
+    ctx.set_geometry_cylinder(P, ccfg.n_r, ccfg.n_phi, ccfg.n_z, ccfg.dr, ccfg.dz, (b.nu, b.nv),
+                              pose=inputs.cylinder_pose(ccfg), step_vox=ccfg.step_vox)
+    return ctx
 
 
 def context_for(cfg, P=None, device=None):

@@ -322,6 +322,138 @@ def phantom(cfg: Config, seed: Optional[int] = None, device: str = "cpu", sub: i
 
 
 # ---------------------------------------------------------------------------
+# Aligned cylindrical domain (Sec. 3.5): a vial on the scanner's trajectory
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass(frozen=True)
+class CylConfig:
+    """A cylindrical reconstruction domain of N_r rings x N_phi sectors x N_z
+    slices inside a bounding cylinder of the given radius and height, scanned
+    on the trajectory (views, detector) of ``base``.  The cylinder axis is
+    tilted by ``tilt_deg`` (about x, then y) against the rotation axis and
+    its centre sits at ``shift`` (mm): the misalignment the domain's rigid
+    pose absorbs."""
+
+    name: str
+    base: Config
+    n_r: int
+    n_phi: int
+    n_z: int
+    radius: float = 15.0
+    height: float = 30.0
+    tilt_deg: tuple = (0.8, -0.6)
+    shift: tuple = (0.4, -0.3, 0.2)
+    seed: int = 7
+    n_inclusions: int = 12
+
+    @property
+    def dr(self) -> float:
+        return self.radius / self.n_r
+
+    @property
+    def dz(self) -> float:
+        return self.height / self.n_z
+
+    @property
+    def vol_shape(self) -> tuple:
+        return (self.n_z, self.n_phi, self.n_r)
+
+    @property
+    def step_vox(self) -> float:
+        return self.base.step_vox
+
+    def scaled(self, **kw) -> "CylConfig":
+        return dataclasses.replace(self, **kw)
+
+
+CYL_SMALL = CylConfig("cylinder-24x64x32-64^2-60v",
+                      CIRCULAR_64.scaled(name="perturbed-64^2-60v", nu=64, nv=64, n_views=60,
+                                         trajectory="perturbed", seed=8),
+                      n_r=24, n_phi=64, n_z=32)
+CYL_VIAL = CylConfig("cylinder-256x1024x512-768^2-720v", PERTURBED_512, n_r=256, n_phi=1024, n_z=512)
+
+
+def cylinder_pose(ccfg: CylConfig) -> np.ndarray:
+    """3x4 rigid map q = Rc x + tc from world mm to the cylinder frame (axis =
+    frame z): Rc = (Ry(b) Rx(a))^T for the tilt (a, b), and the frame origin
+    at ``shift``."""
+    a, b = (math.radians(t) for t in ccfg.tilt_deg)
+    ca, sa, cb, sb = math.cos(a), math.sin(a), math.cos(b), math.sin(b)
+    rx = np.array([[1.0, 0.0, 0.0], [0.0, ca, -sa], [0.0, sa, ca]])
+    ry = np.array([[cb, 0.0, sb], [0.0, 1.0, 0.0], [-sb, 0.0, cb]])
+    Rc = (ry @ rx).T
+    tc = -Rc @ np.asarray(ccfg.shift, float)
+    return np.hstack([Rc, tc[:, None]])
+
+
+def cyl_phantom(ccfg: CylConfig, seed: Optional[int] = None, device: str = "cpu", sub: int = 2):
+    """A vial phantom on the cylindrical grid [N_z, N_phi, N_r] (float64
+    torch tensor), defined in the cylinder frame (radius R, height H):
+
+    - glass wall 0.86 R <= r <= 0.94 R, -0.46 H <= z <= 0.40 H, and bottom
+      r <= 0.94 R, -0.46 H <= z < -0.42 H: density 1;
+    - frozen solution r < 0.86 R, -0.42 H <= z <= 0.15 H: density
+      0.35 (1 + 0.15 sin(2 pi r / (R/6) + psi)) (concentric layers);
+    - n_inclusions ellipsoids inside the solution (pores and crystals).
+
+    Draw order from PCG64(seed or ccfg.seed): psi U[0, 2 pi]; per inclusion
+    radius 0.75 R sqrt(U), angle U[0, 2 pi], z U[-0.38 H, 0.10 H], full axes
+    3 x U[0.6, 3] mm, rotation (4 normals), density U[-0.25, 0.25].  Each
+    voxel is the mean over sub^3 points spread evenly over its (r, phi, z)
+    cell."""
+    import torch
+
+    rng = np.random.Generator(np.random.PCG64(ccfg.seed if seed is None else seed))
+    R, H = ccfg.radius, ccfg.height
+    psi = float(rng.uniform(0.0, 2.0 * math.pi))
+    incl = []
+    for _ in range(ccfg.n_inclusions):
+        rc = 0.75 * R * math.sqrt(rng.uniform())
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        zc = rng.uniform(-0.38 * H, 0.10 * H)
+        semi = 0.5 * rng.uniform(0.6, 3.0, size=3)
+        rot = random_rotation(rng)
+        dens = float(rng.uniform(-0.25, 0.25))
+        incl.append((np.array([rc * math.cos(ph), rc * math.sin(ph), zc]), semi, rot, dens))
+    f64 = dict(dtype=torch.float64, device=device)
+    off = (torch.arange(sub, **f64) + 0.5) / sub - 0.5
+    r = ((torch.arange(ccfg.n_r, **f64)[:, None] + 0.5 + off[None, :]) * ccfg.dr).reshape(-1)
+    phi = ((torch.arange(ccfg.n_phi, **f64)[:, None] + 0.5 + off[None, :]) * (2 * math.pi / ccfg.n_phi)).reshape(-1)
+    zall = ((torch.arange(ccfg.n_z, **f64)[:, None] - 0.5 * (ccfg.n_z - 1) + off[None, :]) * ccfg.dz)
+    cphi, sphi = torch.cos(phi), torch.sin(phi)
+    vol = torch.zeros(ccfg.vol_shape, **f64)
+    chunk = 8
+    for k0 in range(0, ccfg.n_z, chunk):
+        k1 = min(ccfg.n_z, k0 + chunk)
+        z = zall[k0:k1].reshape(-1)[:, None, None]        # [kz*sub, 1, 1]
+        rr = r[None, None, :]                               # [1, 1, nr*sub]
+        val = torch.zeros((z.shape[0], 1, rr.shape[2]), **f64)
+        wall = (rr >= 0.86 * R) & (rr <= 0.94 * R) & (z >= -0.46 * H) & (z <= 0.40 * H)
+        bottom = (rr <= 0.94 * R) & (z >= -0.46 * H) & (z < -0.42 * H)
+        sol = (rr < 0.86 * R) & (z >= -0.42 * H) & (z <= 0.15 * H)
+        layers = 0.35 * (1.0 + 0.15 * torch.sin(2 * math.pi * rr / (R / 6.0) + psi))
+        val = val + (wall | bottom).to(torch.float64) + sol.to(torch.float64) * layers
+        val = val.expand(-1, phi.shape[0], -1).clone()     # [kz*sub, nphi*sub, nr*sub]
+        zlo, zhi = float(z.min()), float(z.max())
+        for c, semi, rot, dens in incl:
+            rmax = float(semi.max())
+            if c[2] + rmax < zlo or c[2] - rmax > zhi:
+                continue
+            Q = torch.tensor((rot / semi[None, :]).T, **f64)
+            X = rr * cphi[None, :, None] - float(c[0])
+            Y = rr * sphi[None, :, None] - float(c[1])
+            Z = z - float(c[2])
+            q2 = 0.0
+            for row in range(3):
+                qr = Q[row, 0] * X + Q[row, 1] * Y + Q[row, 2] * Z
+                q2 = q2 + qr * qr
+            val += dens * (q2 <= 1.0).to(torch.float64)
+        nz = k1 - k0
+        vol[k0:k1] = val.view(nz, sub, ccfg.n_phi, sub, ccfg.n_r, sub).mean(dim=(1, 3, 5))
+    return vol
+
+
+# ---------------------------------------------------------------------------
 # Motion parameters
 # ---------------------------------------------------------------------------
 
