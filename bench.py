@@ -45,6 +45,8 @@ def parse():
                     help="skip the per-row measurements (sub-angle, motion, adjoint, gradient, conv)")
     ap.add_argument("--views", type=int, default=0,
                     help="override the number of views (small cases for ncu captures; not a bench line)")
+    ap.add_argument("--domain", default="cartesian", choices=["cartesian", "cylinder"],
+                    help="cylinder: the SIRT step on the aligned cylindrical vial domain (Sec. 3.5); not a bench line")
     return ap.parse_args()
 
 
@@ -133,9 +135,9 @@ def l2_copy_bandwidth(device, mib=16, iters=200):
 # launch of the fused forward kernel, from the one-pass ncu capture summarised
 # in profiles/fwd_kernel_perturbed512.md.  Valid only for the kernel sources it
 # was taken on (hash below) and for the FP32 workload; otherwise null.
-FWD_TRAFFIC_BYTES = 2335221760 + 1695271424
-FWD_TRAFFIC_SOURCES = ("project.cu", "atlas.cuh", "ray.cuh")
-FWD_TRAFFIC_HASH = "f5fc642daed36e22"
+FWD_TRAFFIC_BYTES = 2332405504 + 1694862080
+FWD_TRAFFIC_SOURCES = ("project.cu", "atlas.cuh", "ray.cuh", "cylinder.cuh")
+FWD_TRAFFIC_HASH = "f289f91e37e0fe10"
 
 
 def fwd_traffic(dtype, views):
@@ -205,9 +207,14 @@ def build_workload(cfg, device, dtype):
 
     from paper_2609_30166_gb300 import ctrex, inputs
 
-    P = inputs.projection_matrices(cfg)
-    ctx = ctrex.context_for(cfg, P=P, device=device)
-    phantom = inputs.phantom(cfg, device=str(device)).to(torch.float32).contiguous()
+    if isinstance(cfg, inputs.CylConfig):
+        P = inputs.projection_matrices(cfg.base)
+        ctx = ctrex.context_for_cylinder(cfg, P=P, device=device)
+        phantom = inputs.cyl_phantom(cfg, device=str(device)).to(torch.float32).contiguous()
+    else:
+        P = inputs.projection_matrices(cfg)
+        ctx = ctrex.context_for(cfg, P=P, device=device)
+        phantom = inputs.phantom(cfg, device=str(device)).to(torch.float32).contiguous()
     p32 = ctx.fwd_project(phantom)  # inverse-crime measured data
     torch.cuda.synchronize(device)
     tdt = torch.float32 if dtype == "f32" else torch.bfloat16
@@ -335,12 +342,21 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
-    cfg = inputs.CIRCULAR_64 if args.small else inputs.PERTURBED_512
-    if args.views:
-        cfg = cfg.scaled(n_views=args.views, name=f"{cfg.name}-views{args.views}")
+    cyl = args.domain == "cylinder"
+    if cyl:
+        cfg = inputs.CYL_SMALL if args.small else inputs.CYL_VIAL
+        if args.views:
+            cfg = cfg.scaled(base=cfg.base.scaled(n_views=args.views), name=f"{cfg.name}-views{args.views}")
+        geo = cfg.base
+    else:
+        cfg = inputs.CIRCULAR_64 if args.small else inputs.PERTURBED_512
+        if args.views:
+            cfg = cfg.scaled(n_views=args.views, name=f"{cfg.name}-views{args.views}")
+        geo = cfg
     ctx, P, phantom, p, tdt = build_workload(cfg, device, args.dtype)
     n_samples = ctx.count_samples()
-    n_updates = cfg.n ** 3 * cfg.n_views * cfg.n_sub
+    nz_, ny_, nx_ = cfg.vol_shape
+    n_updates = nz_ * ny_ * nx_ * geo.n_views * geo.n_sub
     units = n_samples + n_updates
 
     x = torch.zeros(cfg.vol_shape, dtype=tdt, device=device)
@@ -419,8 +435,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.dtype == "f32" else "bf16",
         "data": "synthetic (seeded ellipsoid + Gaussian-blob phantom, projections simulated by the projector)",
-        "config": {"workload": cfg.name, "volume": list(cfg.vol_shape), "detector": [cfg.nv, cfg.nu],
-                   "views": cfg.n_views, "sub_angles": cfg.n_sub, "step_vox": cfg.step_vox,
+        "config": {"workload": cfg.name, "volume": list(cfg.vol_shape), "detector": [geo.nv, geo.nu],
+                   "views": geo.n_views, "sub_angles": geo.n_sub, "step_vox": geo.step_vox,
                    "storage": args.dtype, "accumulation": "f32",
                    "l2": "inputs larger than L2 (volume, projections and correction images > 129 MB); no flush",
                    "parallelism": f"replicas x{world}", "samples_per_step": n_samples,
@@ -429,7 +445,7 @@ def run_ours(args):
         "kernel_ms": {"fwd_correct": statistics.mean(fwd_ms), "back_project": statistics.mean(bp_ms)},
         "residual_after": res,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": fwd_traffic(args.dtype, args.views),
+                     "frac": achieved / peak, "traffic": None if cyl else fwd_traffic(args.dtype, args.views),
                      "kernel": "fwd_kernel (fused forward + correction)",
                      "l2_gather": {"peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
                                    "peak_method": "torch copy of 16 MiB buffers resident in L2, read+write bytes"},
@@ -443,7 +459,7 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_rows and not args.views and not args.small:
+    if rank == 0 and world == 1 and not args.no_rows and not args.views and not args.small and not cyl:
         sm_count = torch.cuda.get_device_properties(device).multi_processor_count
         sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
         # sub-voxel backprojection (2^3 points per voxel) of the last step's
@@ -459,14 +475,14 @@ def run_ours(args):
                                           "point_updates": sv_points, "gpoint_updates_per_s": sv_points / t_sv / 1e9,
                                           "tex_gather_frac": sv_points / t_sv / gather_peak,
                                           "centre_bp_ms": statistics.mean(bp_ms)}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not cyl:
         vol_np = phantom.double().cpu().numpy()
         ncpu_units, ncpu_s, desc = oracle_sample_run(cfg, P, vol_np, n_fwd_views=1 if not args.small else 8,
                                                      bp_edge=32 if not args.small else 16,
                                                      bp_views=45 if not args.small else 90)
         out["cpu_baseline"] = {"value": ncpu_units / ncpu_s / 1e9, "unit": "GUPS", "cores": omp_threads(),
                                "kind": "oracle", "sample": desc}
-    if rank == 0 and world == 1 and args.warm_start_steps > 0 and not args.views and not args.small:
+    if rank == 0 and world == 1 and args.warm_start_steps > 0 and not args.views and not args.small and not cyl:
         from paper_2609_30166_gb300 import warmstart
 
         del p, phantom
