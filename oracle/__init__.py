@@ -90,7 +90,7 @@ class _CProblem(ctypes.Structure):
         ("P", _dp), ("theta", _dp), ("coef", _dp), ("s_view", _dp),
         ("margin", ctypes.c_double), ("bp_window", _ip), ("bp_subvoxel", ctypes.c_int),
         ("cyl", ctypes.c_int), ("cyl_dr", ctypes.c_double), ("cyl_dz", ctypes.c_double),
-        ("cyl_pose", _dp),
+        ("cyl_pose", _dp), ("joseph", ctypes.c_int),
     ]
 
 
@@ -134,7 +134,7 @@ class Problem:
     """
 
     def __init__(self, P, vol_shape, vox, origin, det, step_vox=0.5, theta=None, coef=None,
-                 s_view=None, margin=0.0, bp_window=None, bp_subvoxel=1, cyl=None):
+                 s_view=None, margin=0.0, bp_window=None, bp_subvoxel=1, cyl=None, joseph=False):
         P = _f64(P)
         if P.ndim == 3:
             P = P[:, None]
@@ -151,6 +151,7 @@ class Problem:
         self.margin = float(margin)
         self.bp_window = None if bp_window is None else np.ascontiguousarray(bp_window, dtype=np.int32)
         self.bp_subvoxel = int(bp_subvoxel)
+        self.joseph = bool(joseph)
         self.cyl = None
         if cyl is not None:
             dr, dz, pose = cyl
@@ -160,7 +161,8 @@ class Problem:
                             (ctypes.c_double * 3)(*self.origin), self.nu, self.nv, self.n_views,
                             self.n_sub, self.step_vox, _ptr(self.P), _ptr(self.theta),
                             _ptr(self.coef), _ptr(self.s_view), self.margin, _ptr(self.bp_window, _ip),
-                            self.bp_subvoxel, 1 if self.cyl else 0, cdr, cdz, _ptr(cpose))
+                            self.bp_subvoxel, 1 if self.cyl else 0, cdr, cdz, _ptr(cpose),
+                            1 if self.joseph else 0)
 
     @property
     def vol_shape(self):
@@ -180,7 +182,7 @@ class Problem:
         args = dict(P=self.P, vol_shape=self.vol_shape, vox=self.vox, origin=self.origin,
                     det=(self.nu, self.nv), step_vox=self.step_vox, theta=self.theta, coef=self.coef,
                     s_view=self.s_view, margin=self.margin, bp_window=self.bp_window,
-                    bp_subvoxel=self.bp_subvoxel, cyl=self.cyl)
+                    bp_subvoxel=self.bp_subvoxel, cyl=self.cyl, joseph=self.joseph)
         args.update(kw)
         return Problem(**args)
 
@@ -193,6 +195,10 @@ class Problem:
     def with_subvoxel(self, s):
         """The same problem whose backprojector averages s^3 sub-voxel points."""
         return self._replace(bp_subvoxel=s)
+
+    def with_joseph(self, on=True):
+        """The same problem with the classical Joseph projector (reading R14)."""
+        return self._replace(joseph=on)
 
     def with_window(self, bp_window):
         """The same problem whose backprojector sees per-view detector windows
@@ -259,7 +265,10 @@ def forward_rays(pb, vol, view, u, v):
 def count_samples(pb, views=None):
     lib = _load()
     v, n = _views(pb, views)
-    return int(lib.or_count_samples(ctypes.byref(pb._c), _ptr(v, _ip), n))
+    c = int(lib.or_count_samples(ctypes.byref(pb._c), _ptr(v, _ip), n))
+    if c < 0:
+        raise ValueError(f"oracle error {c}")
+    return c
 
 
 def correct(p, q, rowsum, eps_R):

@@ -93,6 +93,7 @@ typedef struct {
     int cyl;
     double cyl_dr, cyl_dz;
     const double *cyl_pose; /* [12] row-major 3x4: q = Rc x + tc (world mm -> frame mm) */
+    int joseph;             /* 1: classical Joseph projector (reading R14) instead of R2 */
 } or_problem;
 
 /* Per (view, sub-angle) quantities derived from P (Sec. 2.2.1). */
@@ -621,12 +622,70 @@ static void fwd_sample(void *vctx, const double x[3], double w)
     c->rs += w * ws;
 }
 
+/*
+ * Reading R14: the Joseph line integral of one ray and its row sum.  Slice
+ * k of principal axis m is the plane g_m = k; the crossing point's other two
+ * index coordinates are interpolated bilinearly (taps outside the grid
+ * contribute nothing); every crossing in front of the source counts with
+ * the path length vox_m / |d_m| between neighbouring planes.
+ */
+static void joseph_ray(const or_problem *pb, const or_view *ov, const double *vol, double u, double v,
+                       double *val, double *rs, long *ncross)
+{
+    long cnt = 0;
+    const int n[3] = {pb->nx, pb->ny, pb->nz};
+    double d[3], g0[3], dgt[3];
+    ray_direction(ov, u, v, d);
+    for (int a = 0; a < 3; ++a) {
+        g0[a] = (ov->src[a] - pb->origin[a]) / pb->vox[a]; /* source, index coordinates */
+        dgt[a] = d[a] / pb->vox[a];                         /* index units per mm */
+    }
+    int m = 0;
+    for (int a = 1; a < 3; ++a)
+        if (fabs(dgt[a]) > fabs(dgt[m])) m = a;
+    const int a1 = m == 0 ? 1 : 0, a2 = m == 2 ? 1 : 2; /* the two in-slice axes, in order */
+    const double dl = 1.0 / fabs(dgt[m]);               /* mm between neighbouring planes */
+    double sum = 0.0, wsum = 0.0;
+    for (int k = 0; k < n[m]; ++k) {
+        double t = (k - g0[m]) / dgt[m];
+        if (!(t >= 0.0)) continue; /* behind the source */
+        double p = g0[a1] + t * dgt[a1], q = g0[a2] + t * dgt[a2];
+        double fp = floor(p), fq = floor(q);
+        int ip = (int)fp, iq = (int)fq;
+        double ap = p - fp, aq = q - fq;
+        if (!(p > -1.0 && p < n[a1] && q > -1.0 && q < n[a2])) continue;
+        ++cnt;
+        for (int dq = 0; dq < 2; ++dq)
+            for (int dp = 0; dp < 2; ++dp) {
+                int i1 = ip + dp, i2 = iq + dq;
+                if (i1 < 0 || i1 >= n[a1] || i2 < 0 || i2 >= n[a2]) continue;
+                int idx[3];
+                idx[m] = k;
+                idx[a1] = i1;
+                idx[a2] = i2;
+                double wgt = (dp ? ap : 1.0 - ap) * (dq ? aq : 1.0 - aq);
+                sum += wgt * (vol ? vol[((size_t)idx[2] * n[1] + idx[1]) * n[0] + idx[0]] : 1.0);
+                wsum += wgt;
+            }
+    }
+    *val = dl * sum;
+    *rs = dl * wsum;
+    if (ncross) *ncross = cnt;
+}
+
 /* Sec. 3.4: a pixel is the mean over its S angular sub-projections. */
 static void pixel_value(const or_problem *pb, const or_view *ov, const double *vol, int view,
                         double u, double v, double *val, double *rs)
 {
     double sv = 0.0, sr = 0.0;
     for (int s = 0; s < pb->n_sub; ++s) {
+        if (pb->joseph) {
+            double a, b;
+            joseph_ray(pb, &ov[(size_t)view * pb->n_sub + s], vol, u, v, &a, &b, NULL);
+            sv += a;
+            sr += b;
+            continue;
+        }
         fwd_acc c = {pb, vol, view, 0.0, 0.0};
         march(pb, &ov[(size_t)view * pb->n_sub + s], u, v, fwd_sample, &c);
         sv += c.val;
@@ -640,9 +699,16 @@ static void pixel_value(const or_problem *pb, const or_view *ov, const double *v
  * A x and the row sums A 1 for the views listed in views[0..n_sel) (all views
  * if views == NULL, n_sel == n_views).  proj, rowsum: [n_sel][nv][nu].
  */
+/* The Joseph projector is defined on the Cartesian grid without motion. */
+static int joseph_unsupported(const or_problem *pb)
+{
+    return pb->joseph && (pb->cyl || pb->theta || pb->coef);
+}
+
 int or_forward(const or_problem *pb, const double *vol, const int *views, int n_sel, double *proj,
                double *rowsum)
 {
+    if (joseph_unsupported(pb)) return OR_E_ARG;
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;
@@ -665,6 +731,7 @@ int or_forward(const or_problem *pb, const double *vol, const int *views, int n_
 int or_forward_rays(const or_problem *pb, const double *vol, const int *view, const double *u,
                     const double *v, long n, double *val, double *rowsum)
 {
+    if (joseph_unsupported(pb)) return OR_E_ARG;
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;
@@ -679,9 +746,11 @@ int or_forward_rays(const or_problem *pb, const double *vol, const int *view, co
     return 0;
 }
 
-/* Number of samples (segments) of every ray of the listed views, summed. */
+/* Number of samples (segments; for Joseph, slice crossings with at least
+ * one tap inside the grid) of every ray of the listed views, summed. */
 long or_count_samples(const or_problem *pb, const int *views, int n_sel)
 {
+    if (joseph_unsupported(pb)) return OR_E_ARG;
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;
@@ -695,6 +764,13 @@ long or_count_samples(const or_problem *pb, const int *views, int n_sel)
             for (int iu = 0; iu < pb->nu; ++iu) {
                 double d[3], t0, t1;
                 const or_view *o = &ov[(size_t)view * pb->n_sub + s];
+                if (pb->joseph) {
+                    double a, b;
+                    long c;
+                    joseph_ray(pb, o, NULL, iu, iv, &a, &b, &c);
+                    total += c;
+                    continue;
+                }
                 ray_direction(o, iu, iv, d);
                 if (clip_ray(pb, o->src, d, &t0, &t1)) total += (long)ceil((t1 - t0) / D);
             }
@@ -899,7 +975,8 @@ static void adj_sample(void *vctx, const double x[3], double w)
 /* vol_out (overwritten) = A^T y for y [n_sel][nv][nu]. */
 int or_adjoint(const or_problem *pb, const double *y, const int *views, int n_sel, double *vol_out)
 {
-    if (pb->cyl) return OR_E_ARG; /* the transpose is written for the Cartesian grid only */
+    /* the transpose of the trilinear projector on the Cartesian grid only */
+    if (pb->cyl || pb->joseph) return OR_E_ARG;
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;
@@ -1027,7 +1104,7 @@ static void grad_sample(void *vctx, const double x[3], double w)
 int or_motion_grad(const or_problem *pb, const double *vol, const double *g, const int *views,
                    int n_sel, double *grad_theta, double *grad_coef)
 {
-    if (pb->cyl) return OR_E_ARG; /* Cartesian grid only */
+    if (pb->cyl || pb->joseph) return OR_E_ARG; /* trilinear projector, Cartesian grid only */
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;

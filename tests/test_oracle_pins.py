@@ -858,3 +858,182 @@ def test_cylinder_refuses_adjoint():
     pb = oracle.cylinder_problem(inputs.projection_matrices(cfg), 4, 8, 4, 2.0, 2.0, (12, 12))
     with pytest.raises(ValueError):
         oracle.adjoint(pb, np.zeros((2, 12, 12)))
+
+
+# ---------------------------------------------------------------------------
+# Classical Joseph projector (reading R14)
+# ---------------------------------------------------------------------------
+
+def _x_axial_P(y0, z0, D=300.0, f=40.0, uc=10.0, vc=10.0):
+    """Source at (-D, y0, z0): the ray through pixel (uc, vc) runs along +x."""
+    return np.array([[0.0, f, 0.0, -f * y0],
+                     [0.0, 0.0, f, -f * z0],
+                     [0.0, 0.0, 0.0, 0.0]]) + np.array([[uc, 0, 0, uc * D], [vc, 0, 0, vc * D], [1.0, 0, 0, D]])
+
+
+def _joseph_grid(n=(9, 7, 6), vox=(1.2, 0.9, 1.5)):
+    origin = tuple(-0.5 * (k - 1) * v for k, v in zip(n, vox))
+    return (n[2], n[1], n[0]), vox, origin
+
+
+def test_joseph_axial_rays_closed_form():
+    shape, vox, origin = _joseph_grid()
+    vol = np.random.default_rng(41).uniform(size=shape)
+    nz, ny, nx = shape
+    for j, k, fy in ((3, 2, 0.0), (1, 4, 0.3), (5, 0, 0.75)):
+        y0 = origin[1] + (j + fy) * vox[1]
+        z0 = origin[2] + k * vox[2]
+        pb = oracle.Problem(_x_axial_P(y0, z0)[None], shape, vox, origin, (21, 21)).with_joseph()
+        val, rs = oracle.forward_rays(pb, vol, np.zeros(1, np.int32), np.array([10.0]), np.array([10.0]))
+        row = (1.0 - fy) * vol[k, j, :] + (fy * vol[k, j + 1, :] if fy > 0 else 0.0)
+        # one sample per slice, at every voxel centre of the row: no end corrections
+        assert val[0] == pytest.approx(vox[0] * row.sum(), rel=1e-12)
+        assert rs[0] == pytest.approx(vox[0] * nx, rel=1e-12)
+    # the trilinear projector on the same ray has the end corrections of P1
+    pb = oracle.Problem(_x_axial_P(origin[1] + 3 * vox[1], origin[2] + 2 * vox[2])[None], shape, vox, origin,
+                        (21, 21), step_vox=0.5)
+    row = vol[2, 3, :]
+    val, _ = oracle.forward_rays(pb, vol, np.zeros(1, np.int32), np.array([10.0]), np.array([10.0]))
+    assert val[0] != pytest.approx(vox[0] * row.sum(), rel=1e-6)
+
+
+def _chord(src, d, lo, hi):
+    t0, t1 = -np.inf, np.inf
+    for a in range(3):
+        ta, tb = (lo[a] - src[a]) / d[a], (hi[a] - src[a]) / d[a]
+        t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+    return t0, t1
+
+
+def _joseph_linear_check(P, shape, vox, rng, n_rays=400, det=(40, 40), urange=(15, 25)):
+    """Joseph on a linear volume against chord length x f(chord midpoint),
+    for rays that cross both faces of their principal axis inside the grid;
+    returns how many rays were checked."""
+    n = (shape[2], shape[1], shape[0])
+    origin = tuple(-0.5 * (k - 1) * v for k, v in zip(n, vox))
+    c0, c = 0.4, np.array([0.05, -0.03, 0.02])
+    Z, Y, X = np.meshgrid(*[origin[a] + np.arange(n[a]) * vox[a] for a in (2, 1, 0)], indexing="ij")
+    vol = c0 + c[0] * X + c[1] * Y + c[2] * Z
+    pb = oracle.Problem(P, shape, vox, origin, det).with_joseph()
+    lo = np.array([origin[a] - 0.5 * vox[a] for a in range(3)])
+    hi = np.array([origin[a] + (n[a] - 0.5) * vox[a] for a in range(3)])
+    checked = 0
+    for _ in range(n_rays):
+        v = int(rng.integers(0, len(P)))
+        u, w = rng.uniform(*urange, size=2)
+        M, p4 = P[v][:, :3], P[v][:, 3]
+        s = -np.linalg.solve(M, p4)
+        d = np.linalg.solve(M, np.array([u, w, 1.0]))
+        d /= np.linalg.norm(d)
+        if d @ (-s) < 0:
+            d = -d
+        m = int(np.argmax(np.abs(d) / np.array(vox)))  # fastest index coordinate
+        t0 = (lo[m] - s[m]) / d[m]
+        t1 = (hi[m] - s[m]) / d[m]
+        t0, t1 = min(t0, t1), max(t0, t1)
+        ok = True
+        for t in (t0, t1):
+            p = s + t * d
+            for a in range(3):
+                if a != m and not (origin[a] + 1e-9 <= p[a] <= origin[a] + (n[a] - 1) * vox[a] - 1e-9):
+                    ok = False
+        if not ok:
+            continue
+        mid = s + 0.5 * (t0 + t1) * d
+        val, rs = oracle.forward_rays(pb, vol, np.array([v], np.int32), np.array([u]), np.array([w]))
+        L = t1 - t0
+        assert val[0] == pytest.approx(L * (c0 + c @ mid), rel=1e-11)
+        assert rs[0] == pytest.approx(L, rel=1e-11)
+        checked += 1
+    return checked
+
+
+def test_joseph_linear_volume_and_row_sums_exact():
+    # a linear function sampled at the voxel centres is reproduced exactly by
+    # bilinear interpolation inside the grid, and the slice sum is the
+    # midpoint rule over the chord between the two principal faces, exact for
+    # a linear integrand: value = chord length x f(chord midpoint)
+    cfg = small(n=8, nu=40, nv=40, n_views=6, trajectory="perturbed", seed=42)
+    P = inputs.projection_matrices(cfg)[:, 0]
+    rng = np.random.default_rng(42)
+    assert _joseph_linear_check(P, (14, 13, 15), (1.0, 1.1, 0.9), rng) > 20
+    # strongly anisotropic voxels, rays 60 degrees from x in the x-y plane:
+    # |d_y| > |d_x| but the x index changes faster (0.5/0.8 > 0.87/2), so x
+    # is the principal axis
+    Ps = []
+    for a in (58.0, 60.0, 62.0):
+        e = np.array([math.cos(math.radians(a)), math.sin(math.radians(a)), 0.0])
+        src = -200.0 * e
+        uax = np.array([-e[1], e[0], 0.0]) * 0.5
+        Ps.append(inputs.cone_matrix(src, 200.0 * e, uax, np.array([0.0, 0.0, 0.5]), 40, 40))
+    assert _joseph_linear_check(np.array(Ps), (8, 12, 10), (0.8, 2.0, 1.0), rng, urange=(17, 23)) > 20
+
+
+def test_joseph_axis_swap_equivariance():
+    # swapping the x and y axes of the volume together with the geometry
+    # leaves the projections unchanged (no axis is favoured)
+    cfg = small(n=8, nu=20, nv=18, n_views=8, trajectory="perturbed", seed=43)
+    P = inputs.projection_matrices(cfg)
+    shape, vox, origin = (6, 7, 9), (1.3, 0.8, 1.1), (-4.0, -2.5, -3.0)
+    vol = np.random.default_rng(43).uniform(size=shape)
+    pb = oracle.Problem(P, shape, vox, origin, (cfg.nu, cfg.nv)).with_joseph()
+    S = np.array([[0, 1, 0, 0], [1, 0, 0, 0], [0, 0, 1, 0], [0, 0, 0, 1]], float)  # (x, y) swap
+    P2 = P @ S
+    pb2 = oracle.Problem(P2, (shape[0], shape[2], shape[1]), (vox[1], vox[0], vox[2]),
+                         (origin[1], origin[0], origin[2]), (cfg.nu, cfg.nv)).with_joseph()
+    a, ra = oracle.forward(pb, vol)
+    b, rb = oracle.forward(pb2, vol.transpose(0, 2, 1))
+    assert np.abs(a).max() > 1.0
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max() and np.abs(ra - rb).max() <= 1e-10 * np.abs(ra).max()
+
+
+def test_joseph_gaussian_line_integrals_converge():
+    # a Gaussian sampled at the voxel centres: second-order convergence to the
+    # analytic line integrals, over rays whose principal axes are x, y and z
+    c, sig = np.array([1.5, -1.0, 0.8]), 2.2
+    cfg = small(n=8, nu=20, nv=20, n_views=4, trajectory="perturbed", seed=44)
+    P = list(inputs.projection_matrices(cfg)[:, 0])
+    # a view from above (rays mostly along z)
+    P.append(np.array([[40.0, 0.0, 10.0, 10.0 * 300.0], [0.0, 40.0, 10.0, 10.0 * 300.0], [0.0, 0.0, 1.0, 300.0]]))
+    P = np.array(P)
+    rng = np.random.default_rng(44)
+    views = np.repeat(np.arange(5), 10).astype(np.int32)
+    h = np.einsum("vij,j->vi", P[views], np.append(c, 1.0))
+    us = h[:, 0] / h[:, 2] + rng.uniform(-1, 1, len(views))
+    vs = h[:, 1] / h[:, 2] + rng.uniform(-1, 1, len(views))
+    ref, axes = [], set()
+    for v, u, w in zip(views, us, vs):
+        M, p4 = P[v][:, :3], P[v][:, 3]
+        s = -np.linalg.solve(M, p4)
+        d = np.linalg.solve(M, np.array([u, w, 1.0]))
+        d /= np.linalg.norm(d)
+        axes.add(int(np.argmax(np.abs(d))))
+        e = c - s
+        ref.append(sig * math.sqrt(math.pi) * math.exp(-(e @ e - (e @ d) ** 2) / sig ** 2))
+    ref = np.array(ref)
+    assert axes == {0, 1, 2}
+    errs = []
+    for k in (2, 4, 8):
+        n = 12 * k
+        vx = 24.0 / n
+        org = -0.5 * (n - 1) * vx
+        g = org + np.arange(n) * vx
+        Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+        vol = np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) / sig ** 2)
+        pb = oracle.Problem(P, (n, n, n), (vx,) * 3, (org,) * 3, (cfg.nu, cfg.nv)).with_joseph()
+        val, _ = oracle.forward_rays(pb, vol, views, us, vs)
+        errs.append(rel_l2(val, ref))
+    # h / sigma = 0.45, 0.23, 0.11: a half-voxel misplacement would halve the
+    # error per level at best
+    assert errs[2] < 5e-3
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0
+
+
+def test_joseph_refusals():
+    cfg = small(n=8, nu=12, nv=12, n_views=2)
+    pb = oracle_problem(cfg).with_joseph()
+    with pytest.raises(ValueError):
+        oracle.adjoint(pb, np.zeros((2, 12, 12)))
+    th = inputs.identity_theta(2)
+    with pytest.raises(ValueError):
+        oracle.forward(pb.with_motion(theta=th), np.zeros(cfg.vol_shape))
