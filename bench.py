@@ -468,6 +468,17 @@ def run_ours(args):
         t_sv = _time(lambda: ctx.back_project(r, vol=x, alpha=1.0, normalize=True, accumulate=True), reps=2)
         ctx.set_bp_subvoxel(1)
         sv_points = 8 * n_updates
+        # classical Joseph forward projector (one gather per slice crossing):
+        # the same SIRT step with it, on the same workload
+        ctx.set_projector("joseph")
+        ns_j = ctx.count_samples()
+        t_jf = _time(lambda: ctx.fwd_correct(x, p, r=r, sums=sums), reps=2)
+        t_jb = _time(lambda: ctx.back_project(r, vol=x, alpha=1.0, normalize=True, accumulate=True), reps=2)
+        ctx.set_projector("trilinear")
+        joseph_row = {"workload": cfg.name, "samples": ns_j, "fwd_correct_ms": t_jf * 1e3,
+                      "back_project_ms": t_jb * 1e3, "gups": (ns_j + n_updates) / (t_jf + t_jb) / 1e9,
+                      "fwd_tex_gather_frac": ns_j / t_jf / gather_peak,
+                      "trilinear_fwd_correct_ms": statistics.mean(fwd_ms)}
         del x, r
         torch.cuda.empty_cache()
         out["rows"] = measure_rows(device, gather_peak, sm_count, sm_mhz)
@@ -475,6 +486,7 @@ def run_ours(args):
                                           "point_updates": sv_points, "gpoint_updates_per_s": sv_points / t_sv / 1e9,
                                           "tex_gather_frac": sv_points / t_sv / gather_peak,
                                           "centre_bp_ms": statistics.mean(bp_ms)}
+        out["rows"]["a16_joseph_sirt_step"] = joseph_row
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not cyl:
         vol_np = phantom.double().cpu().numpy()
         ncpu_units, ncpu_s, desc = oracle_sample_run(cfg, P, vol_np, n_fwd_views=1 if not args.small else 8,

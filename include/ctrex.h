@@ -214,6 +214,31 @@ int ctrex_set_bp_window(ctrex_ctx *ctx, const int *window);
 int ctrex_set_bp_subvoxel(ctrex_ctx *ctx, int s);
 
 /*
+ * Forward projector of every forward call (fwd_project, fwd_correct, the
+ * SIRT loops and count_samples; the backprojector is unchanged):
+ *   CTREX_PROJ_TRILINEAR  (default) fixed-step trilinear quadrature, Sec. 4.1.
+ *   CTREX_PROJ_JOSEPH     classical Joseph (Sec. 4.1 cites Joseph's method):
+ *       the principal axis m of a ray is the one whose index coordinate
+ *       changes fastest along it (the lowest on ties); every slice k = 0..N_m-1
+ *       crossed in front of the source is interpolated bilinearly at the
+ *       crossing (zero outside the grid) and weighted with vox_m / |d_m| (d
+ *       the unit direction), the path length between neighbouring planes.
+ *       Row sums are the same sum of in-range weights.  count_samples then
+ *       counts slice crossings with a tap inside the grid.  The context keeps
+ *       the volume as x-, y- and z-slice stacks in one texture atlas (three
+ *       copies; CTREX_E_SHAPE at the first projection if it exceeds the
+ *       device's 2D texture limits).
+ * Joseph is defined on the Cartesian grid without motion: CTREX_E_STATE if
+ * the cylindrical domain or motion is set, and set_motion, adjoint_project
+ * and motion_grad return CTREX_E_STATE while it is selected.
+ * set_geometry_cylinder resets the projector to trilinear.  Unknown kind:
+ * CTREX_E_ARG.
+ */
+#define CTREX_PROJ_TRILINEAR 0
+#define CTREX_PROJ_JOSEPH 1
+int ctrex_set_projector(ctrex_ctx *ctx, int kind);
+
+/*
  * A x (Sec. 4.1 projection operator; Sec. 3.4 mean over sub-angles; motion
  * if set).  Ray from the source through the pixel centre, clipped to the
  * box, fixed-step truncated-midpoint quadrature with trilinear interpolation

@@ -3,6 +3,29 @@
 
 namespace ctrex {
 
+// Zero every texel of a new array (its content is undefined): taps outside a
+// slice read neighbouring tiles, unused tiles or padding with weight zero,
+// and zero times a stale NaN would not be zero.
+__global__ void __launch_bounds__(256) clear_kernel(cudaSurfaceObject_t surf, int W, int H, int bytes)
+{
+    const int x = blockIdx.x * 64 + (threadIdx.x & 63);
+    const int y = blockIdx.y * 4 + (threadIdx.x >> 6);
+    if (x >= W || y >= H) return;
+    if (bytes == 4)
+        surf2Dwrite(0u, surf, x * 4, y);
+    else
+        surf2Dwrite((unsigned short)0, surf, x * 2, y);
+}
+
+cudaError_t atlas_clear(cudaSurfaceObject_t surf, int W, int H, int bytes)
+{
+    const dim3 grid((W + 63) / 64, (H + 3) / 4);
+    clear_kernel<<<grid, 256>>>(surf, W, H, bytes);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e;
+}
+
 void atlas_release(AtlasStore &s)
 {
     if (s.tex) cudaDestroyTextureObject(s.tex);
@@ -58,6 +81,7 @@ cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int devi
     td.normalizedCoords = 0;
     e = cudaCreateTextureObject(&s.tex, &rd, &td, nullptr);
     if (e == cudaSuccess) e = cudaCreateSurfaceObject(&s.surf, &rd);
+    if (e == cudaSuccess) e = atlas_clear(s.surf, (int)W, (int)H, packed || !bf16 ? 4 : 2);
     if (e != cudaSuccess) {
         atlas_release(s);
         return e;
@@ -131,6 +155,70 @@ cudaError_t atlas_upload(const AtlasStore &s, const void *src, cudaStream_t stre
     else
         upload_kernel<float><<<grid, 256, 0, stream>>>(static_cast<const float *>(src), s.surf, s.w, s.h, s.n,
                                                        s.tshift, hd);
+    return cudaGetLastError();
+}
+
+// Three-stack atlas of the Joseph projector: tile t at ((t & mask) W, (t >>
+// tshift) H).  x-slice k is tile k with texel (y, z); y-slice k is tile nx + k
+// with texel (x, z); z-slice k is tile nx + ny + k with texel (x, y).
+template <typename T>
+__device__ __forceinline__ void jos_write(cudaSurfaceObject_t surf, int W, int H, int tshift, int t, int u, int v,
+                                          T val)
+{
+    const int X = (t & ((1 << tshift) - 1)) * W + u;
+    const int Y = (t >> tshift) * H + v;
+    surf2Dwrite(val, surf, X * (int)sizeof(T), Y);
+}
+
+// y- and z-slice stacks: reads and writes both run along x.
+template <typename T>
+__global__ void __launch_bounds__(256) jos_upload_yz(const T *__restrict__ src, cudaSurfaceObject_t surf, int nx,
+                                                     int ny, int nz, int W, int H, int tshift)
+{
+    const int x = blockIdx.x * 64 + (threadIdx.x & 63);
+    const int y = blockIdx.y * 4 + (threadIdx.x >> 6);
+    const int z = blockIdx.z;
+    if (x >= nx || y >= ny || z >= nz) return;
+    const T v = src[((size_t)z * ny + y) * nx + x];
+    jos_write(surf, W, H, tshift, nx + ny + z, x, y, v);
+    jos_write(surf, W, H, tshift, nx + y, x, z, v);
+}
+
+// x-slice stack: a 32 x 32 (x, y) block of one z-slice is transposed in
+// shared memory, so the writes run along y.
+template <typename T>
+__global__ void __launch_bounds__(256) jos_upload_x(const T *__restrict__ src, cudaSurfaceObject_t surf, int nx,
+                                                    int ny, int nz, int W, int H, int tshift)
+{
+    __shared__ T tile[32][33];
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, z = blockIdx.z;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int y = y0 + ty + 8 * r, x = x0 + tx;
+        if (x < nx && y < ny) tile[ty + 8 * r][tx] = src[((size_t)z * ny + y) * nx + x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int x = x0 + ty + 8 * r, y = y0 + tx;
+        if (x < nx && y < ny) jos_write(surf, W, H, tshift, x, y, z, tile[tx][ty + 8 * r]);
+    }
+}
+
+cudaError_t atlas_upload_joseph(const AtlasStore &s, const void *src, int nx, int ny, int nz, cudaStream_t stream)
+{
+    if (s.n != nx + ny + nz || s.w < max(nx, ny) || s.h < max(ny, nz) || s.packed) return cudaErrorInvalidValue;
+    const dim3 g1((nx + 63) / 64, (ny + 3) / 4, nz), g2((nx + 31) / 32, (ny + 31) / 32, nz);
+    if (s.bf16) {
+        const unsigned short *p = static_cast<const unsigned short *>(src);
+        jos_upload_yz<unsigned short><<<g1, 256, 0, stream>>>(p, s.surf, nx, ny, nz, s.w, s.h, s.tshift);
+        jos_upload_x<unsigned short><<<g2, 256, 0, stream>>>(p, s.surf, nx, ny, nz, s.w, s.h, s.tshift);
+    } else {
+        const float *p = static_cast<const float *>(src);
+        jos_upload_yz<float><<<g1, 256, 0, stream>>>(p, s.surf, nx, ny, nz, s.w, s.h, s.tshift);
+        jos_upload_x<float><<<g2, 256, 0, stream>>>(p, s.surf, nx, ny, nz, s.w, s.h, s.tshift);
+    }
     return cudaGetLastError();
 }
 

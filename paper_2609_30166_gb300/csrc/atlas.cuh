@@ -64,6 +64,7 @@ struct AtlasSampler {
 
     static constexpr int TILE_TABLE = 2048;
     static constexpr bool CYLINDER = false;
+    static constexpr bool JOSEPH = false;
     // Fills the per-CTA tile-origin table (all threads call; barrier inside).
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads)
     {
@@ -184,6 +185,7 @@ struct LinearSampler {
     int nx, ny, nz;
     static constexpr int TILE_TABLE = 1;
     static constexpr bool CYLINDER = false;
+    static constexpr bool JOSEPH = false;
     __device__ __forceinline__ void bind(float2 *, int, int) {}
     __device__ __forceinline__ float interior(float gx, float gy, float gz) const;
     __device__ __forceinline__ float operator()(float gx, float gy, float gz, float &wsum) const;
@@ -205,6 +207,11 @@ cudaError_t atlas_ensure(AtlasStore &s, int w, int h, int n, bool bf16, int devi
                          bool wrap = false);
 void atlas_release(AtlasStore &s);
 Atlas atlas_view(const AtlasStore &s);
+// Copies a [nz][ny][nx] volume into a three-stack atlas of nx + ny + nz tiles
+// of at least max(nx, ny) x max(ny, nz) texels (x-, y- then z-slices).
+cudaError_t atlas_upload_joseph(const AtlasStore &s, const void *src, int nx, int ny, int nz, cudaStream_t stream);
+// Zeroes a W x H array of 2- or 4-byte texels (called on every new atlas).
+cudaError_t atlas_clear(cudaSurfaceObject_t surf, int W, int H, int bytes);
 // Copies slices [n][h][w] (row-major, FP32 or BF16 as the atlas) into the
 // atlas; for a packed atlas, texel s holds slices s and s + 1 (zero past n).
 cudaError_t atlas_upload(const AtlasStore &s, const void *src, cudaStream_t stream);

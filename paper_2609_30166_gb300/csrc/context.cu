@@ -59,6 +59,10 @@ struct ctrex_ctx {
     // aligned cylindrical domain (set by ctrex_set_geometry_cylinder)
     bool cyl = false;
     CylGPU cylg{};
+    // forward projector: CTREX_PROJ_TRILINEAR or CTREX_PROJ_JOSEPH (three-stack atlas)
+    int projector = CTREX_PROJ_TRILINEAR;
+    AtlasStore jos_atlas;
+    Atlas jos_atlas_view;
     // ordered-subset SIRT: concatenated subset view lists, per-subset norms
     int *d_subset_views = nullptr;
     size_t subset_views_bytes = 0;
@@ -163,6 +167,7 @@ FwdArgs fwd_args(ctrex_ctx *c, const void *vol, int vdt, const int *view_idx, in
     a.stream = c->stream;
     a.devcheck = c->d_devcheck;
     a.cyl = c->cyl ? &c->cylg : nullptr;
+    a.joseph = c->projector == CTREX_PROJ_JOSEPH ? 1 : 0;
     return a;
 }
 
@@ -170,6 +175,22 @@ FwdArgs fwd_args(ctrex_ctx *c, const void *vol, int vdt, const int *view_idx, in
 // the volume does not fit the 2D texture limits the row-major path is used.
 int prepare_atlas(ctrex_ctx *c, FwdArgs &a, const void *vol, int vdt)
 {
+    if (c->projector == CTREX_PROJ_JOSEPH) {
+        // x-, y- and z-slice stacks in one atlas; no row-major fallback
+        const int nx = c->grid.nx, ny = c->grid.ny, nz = c->grid.nz;
+        cudaError_t e = atlas_ensure(c->jos_atlas, nx > ny ? nx : ny, ny > nz ? ny : nz, nx + ny + nz,
+                                     vdt == CTREX_BF16, c->device, false);
+        if (e == cudaErrorInvalidValue) {
+            cudaGetLastError();
+            return fail(c, CTREX_E_SHAPE, "Joseph projector: volume exceeds the 2D texture limits of the device");
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "Joseph atlas allocation");
+        e = atlas_upload_joseph(c->jos_atlas, vol, nx, ny, nz, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "Joseph atlas upload");
+        c->jos_atlas_view = atlas_view(c->jos_atlas);
+        a.atlas = &c->jos_atlas_view;
+        return CTREX_OK;
+    }
     if (c->cyl) {
         // cylindrical domain: z-slice tiles of N_r x (N_phi + 1), the last row
         // repeating sector 0; no row-major fallback
@@ -296,6 +317,7 @@ int ctrex_destroy(ctrex_ctx *c)
         dfree(c->d_subset_sums);
         atlas_release(c->vol_atlas);
         atlas_release(c->img_atlas);
+        atlas_release(c->jos_atlas);
     }
     delete c;
     return CTREX_OK;
@@ -528,6 +550,7 @@ int ctrex_set_geometry_cylinder(ctrex_ctx *c, const double *P, int n_views, int 
     c->grid.lo[2] = -C.Z;
     c->grid.hi[2] = C.Z;
     c->cyl = true;
+    c->projector = CTREX_PROJ_TRILINEAR;
     return CTREX_OK;
 }
 
@@ -535,8 +558,9 @@ int ctrex_set_motion(ctrex_ctx *c, const float *theta, const float *coef, const 
 {
     if (!c) return CTREX_E_ARG;
     if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_motion before set_geometry");
-    if (c->cyl && (theta || coef || s_view))
-        return fail(c, CTREX_E_STATE, "set_motion: the motion model is defined on the Cartesian grid only");
+    if ((c->cyl || c->projector == CTREX_PROJ_JOSEPH) && (theta || coef || s_view))
+        return fail(c, CTREX_E_STATE, "set_motion: the motion model is defined for the trilinear projector on the "
+                                      "Cartesian grid only");
     double box = 0.0;
     const int nn[3] = {c->grid.nx, c->grid.ny, c->grid.nz};
     for (int a = 0; a < 3; ++a) box = fmax(box, nn[a] * c->vox[a]);
@@ -603,6 +627,19 @@ int ctrex_set_bp_window(ctrex_ctx *c, const int *window)
     CT_CUDA(c, cudaMemcpyAsync(c->d_window, hw.data(), sizeof(int4) * (size_t)V, cudaMemcpyHostToDevice, c->stream));
     CT_CUDA(c, cudaStreamSynchronize(c->stream));  // hw is a local buffer
     c->has_window = true;
+    return CTREX_OK;
+}
+
+int ctrex_set_projector(ctrex_ctx *c, int kind)
+{
+    if (!c) return CTREX_E_ARG;
+    if (kind != CTREX_PROJ_TRILINEAR && kind != CTREX_PROJ_JOSEPH)
+        return fail(c, CTREX_E_ARG, "set_projector: unknown projector %d", kind);
+    if (kind == CTREX_PROJ_JOSEPH && (c->cyl || c->has_motion))
+        return fail(c, CTREX_E_STATE, "set_projector: the Joseph projector is defined on the Cartesian grid "
+                                      "without motion");
+    c->projector = kind;
+    if (kind != CTREX_PROJ_JOSEPH) atlas_release(c->jos_atlas);
     return CTREX_OK;
 }
 
@@ -718,7 +755,9 @@ int ctrex_adjoint_project(ctrex_ctx *c, const float *proj, float *vol, const int
     if (!c) return CTREX_E_ARG;
     int e = check_views(c, view_idx, n_idx);
     if (e) return e;
-    if (c->cyl) return fail(c, CTREX_E_STATE, "adjoint_project: Cartesian grid only");
+    if (c->cyl || c->projector == CTREX_PROJ_JOSEPH)
+        return fail(c, CTREX_E_STATE, "adjoint_project: the transpose of the trilinear projector on the Cartesian "
+                                      "grid only");
     if (n_idx == 0) return CTREX_OK;
     if (!proj || !vol) return fail(c, CTREX_E_ARG, "adjoint_project: NULL buffer");
     DeviceGuard g(c->device);

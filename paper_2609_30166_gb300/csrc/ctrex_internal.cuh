@@ -97,6 +97,7 @@ struct FwdArgs {
     unsigned *devcheck;         // device status word
     int p_by_view = 0;          // correction: measured images indexed by view, not by list position
     const CylGPU *cyl = nullptr;  // cylindrical domain, or nullptr (Cartesian grid)
+    int joseph = 0;               // classical Joseph projector; atlas = the three-stack atlas
 };
 
 cudaError_t launch_forward(const FwdArgs &a, void *proj, int proj_dtype, float *rowsum);

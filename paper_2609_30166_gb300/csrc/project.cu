@@ -12,6 +12,7 @@
 // slab stays in L2 while it is being sampled.
 #include "atlas.cuh"
 #include "cylinder.cuh"
+#include "joseph.cuh"
 #include "ray.cuh"
 
 namespace ctrex {
@@ -73,6 +74,13 @@ __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__r
     float acc = 0.0f, acc_rs = 0.0f;
     for (int s = 0; s < G.n_sub; ++s) {
         const ViewGPU V = views[view * G.n_sub + s];
+        if constexpr (Sampler::JOSEPH) {
+            float a, ars;
+            joseph_integral(G, vol, V, u, v, a, ars);
+            acc += a;
+            acc_rs += ars;
+            continue;
+        }
         Ray R;
         if constexpr (Sampler::CYLINDER) {
             if (!setup_ray_cyl(G, vol.C, V, u, v, R)) continue;
@@ -238,8 +246,10 @@ __global__ void __launch_bounds__(1024) finish_sums_kernel(const float *__restri
     }
 }
 
-// Exact sample count (same set-up arithmetic as the projector).
-template <bool CYL>
+// Exact sample count (same set-up arithmetic as the projector): ray
+// segments, or for the Joseph projector slice crossings with a tap inside.
+enum CountKind { COUNT_BOX = 0, COUNT_CYL = 1, COUNT_JOSEPH = 2 };
+template <int KIND>
 __global__ void __launch_bounds__(FWD_TX *FWD_TY)
     count_kernel(Grid G, CylGPU C, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx,
                  unsigned long long *out)
@@ -254,8 +264,13 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
         for (int s = 0; s < G.n_sub; ++s) {
             Ray R;
             const ViewGPU &V = views[view * G.n_sub + s];
-            const bool hit = CYL ? setup_ray_cyl(G, C, V, (float)iu, (float)iv, R)
-                                 : setup_ray(G, V, (float)iu, (float)iv, R);
+            if (KIND == COUNT_JOSEPH) {
+                JRay J;
+                if (joseph_setup(G, V, (float)iu, (float)iv, J)) n += (unsigned long long)(J.khi - J.klo + 1);
+                continue;
+            }
+            const bool hit = KIND == COUNT_CYL ? setup_ray_cyl(G, C, V, (float)iu, (float)iv, R)
+                                               : setup_ray(G, V, (float)iu, (float)iv, R);
             if (hit) n += (unsigned long long)R.K;
         }
     }
@@ -281,7 +296,7 @@ static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, flo
 {
     const Grid &G = *a.grid;
     const dim3 grid = fwd_grid(G, a.n_idx), block(FWD_TX, FWD_TY);
-    if constexpr (!Sampler::CYLINDER) {
+    if constexpr (!Sampler::CYLINDER && !Sampler::JOSEPH) {
         if (a.motion) {
             fwd_kernel<Sampler, TP, MODE, true><<<grid, block, 0, a.stream>>>(
                 G, a.views, a.motion, a.coef_idx, smp, a.view_idx, out, rowsum, p, partials, a.devcheck,
@@ -289,7 +304,7 @@ static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, flo
             return cudaGetLastError();
         }
     } else if (a.motion) {
-        return cudaErrorNotSupported;  // the motion warp is defined on the Cartesian grid only
+        return cudaErrorNotSupported;  // the motion warp is defined for the trilinear Cartesian projector only
     }
     fwd_kernel<Sampler, TP, MODE, false><<<grid, block, 0, a.stream>>>(
         G, a.views, nullptr, nullptr, smp, a.view_idx, out, rowsum, p, partials, a.devcheck, a.p_by_view);
@@ -301,6 +316,12 @@ static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, flo
 template <typename TP, int MODE>
 static cudaError_t fwd_dispatch_sampler(const FwdArgs &a, TP *out, float *rowsum, const TP *p, float *partials)
 {
+    if (a.joseph) {  // the Joseph projector reads its three-stack atlas only
+        if (!a.atlas || a.cyl) return cudaErrorInvalidValue;
+        const Grid &G = *a.grid;
+        JosephSampler js{AtlasSampler{*a.atlas}, {G.nx, G.ny, G.nz}, {0, G.nx, G.nx + G.ny}};
+        return fwd_launch<JosephSampler, TP, MODE>(a, js, out, rowsum, p, partials);
+    }
     if (a.cyl) {  // the cylindrical domain is sampled from its atlas only
         if (!a.atlas) return cudaErrorInvalidValue;
         return fwd_launch<CylSampler, TP, MODE>(a, CylSampler{AtlasSampler{*a.atlas}, *a.cyl}, out, rowsum, p,
@@ -354,9 +375,11 @@ cudaError_t launch_count_samples(const FwdArgs &a, unsigned long long *out)
     if (e != cudaSuccess || a.n_idx == 0) return e;
     const dim3 grid = fwd_grid(*a.grid, a.n_idx), block(FWD_TX, FWD_TY);
     if (a.cyl)
-        count_kernel<true><<<grid, block, 0, a.stream>>>(*a.grid, *a.cyl, a.views, a.view_idx, out);
+        count_kernel<COUNT_CYL><<<grid, block, 0, a.stream>>>(*a.grid, *a.cyl, a.views, a.view_idx, out);
+    else if (a.joseph)
+        count_kernel<COUNT_JOSEPH><<<grid, block, 0, a.stream>>>(*a.grid, CylGPU{}, a.views, a.view_idx, out);
     else
-        count_kernel<false><<<grid, block, 0, a.stream>>>(*a.grid, CylGPU{}, a.views, a.view_idx, out);
+        count_kernel<COUNT_BOX><<<grid, block, 0, a.stream>>>(*a.grid, CylGPU{}, a.views, a.view_idx, out);
     return cudaGetLastError();
 }
 

@@ -34,8 +34,10 @@ EXPORTS = (
     "ctrex_fwd_correct", "ctrex_back_project", "ctrex_adjoint_project", "ctrex_motion_grad",
     "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples", "ctrex_correct_static",
     "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad", "ctrex_os_sirt_iterate", "ctrex_set_bp_window",
-    "ctrex_probe_gather_rate", "ctrex_set_bp_subvoxel", "ctrex_set_geometry_cylinder",
+    "ctrex_probe_gather_rate", "ctrex_set_bp_subvoxel", "ctrex_set_geometry_cylinder", "ctrex_set_projector",
 )
+
+PROJ_TRILINEAR, PROJ_JOSEPH = 0, 1
 
 # Largest n ctrex_correct_static accepts (its static scratch holds 65536 CTA partials of 8192 elements).
 CORRECT_STATIC_MAX_N = 1 << 29
@@ -99,6 +101,7 @@ def load_library(path: str = LIB_PATH):
         "ctrex_os_sirt_iterate": ([vp, vp, i, vp, i, ip, ip, i, i, f, vp, f, fp, ip], i),
         "ctrex_set_bp_window": ([vp, ip], i),
         "ctrex_set_bp_subvoxel": ([vp, i], i),
+        "ctrex_set_projector": ([vp, i], i),
         "ctrex_set_geometry_cylinder": ([vp, ctypes.POINTER(d), i, i, ctypes.POINTER(CylGrid),
                                          ctypes.POINTER(DetGrid), d], i),
         "ctrex_probe_gather_rate": ([vp, ctypes.POINTER(d)], i),
@@ -244,6 +247,11 @@ class Context:
             raise ValueError(f"window must be [{self.n_views}, 4]")
         self._sync_stream()
         self._check(self.lib.ctrex_set_bp_window(self._h, win.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+
+    def set_projector(self, kind="trilinear"):
+        """Forward projector: "trilinear" (default) or "joseph"."""
+        k = {"trilinear": PROJ_TRILINEAR, "joseph": PROJ_JOSEPH}[kind]
+        self._check(self.lib.ctrex_set_projector(self._h, k))
 
     def set_bp_subvoxel(self, s=1):
         """Sub-voxel backprojection: s^3 points per voxel (1 = off)."""
