@@ -91,6 +91,8 @@ class _CProblem(ctypes.Structure):
         ("margin", ctypes.c_double), ("bp_window", _ip), ("bp_subvoxel", ctypes.c_int),
         ("cyl", ctypes.c_int), ("cyl_dr", ctypes.c_double), ("cyl_dz", ctypes.c_double),
         ("cyl_pose", _dp), ("joseph", ctypes.c_int),
+        ("roi", ctypes.c_int), ("roi_n", ctypes.c_int * 3), ("roi_vox", ctypes.c_double * 3),
+        ("roi_origin", ctypes.c_double * 3),
     ]
 
 
@@ -134,7 +136,7 @@ class Problem:
     """
 
     def __init__(self, P, vol_shape, vox, origin, det, step_vox=0.5, theta=None, coef=None,
-                 s_view=None, margin=0.0, bp_window=None, bp_subvoxel=1, cyl=None, joseph=False):
+                 s_view=None, margin=0.0, bp_window=None, bp_subvoxel=1, cyl=None, joseph=False, roi=None):
         P = _f64(P)
         if P.ndim == 3:
             P = P[:, None]
@@ -152,6 +154,11 @@ class Problem:
         self.bp_window = None if bp_window is None else np.ascontiguousarray(bp_window, dtype=np.int32)
         self.bp_subvoxel = int(bp_subvoxel)
         self.joseph = bool(joseph)
+        self.roi = None
+        if roi is not None:  # (roi_shape (nz, ny, nx), vox (x, y, z), origin (x, y, z))
+            rshape, rvox, rorg = roi
+            self.roi = (tuple(int(v) for v in rshape), tuple(float(v) for v in rvox),
+                        tuple(float(v) for v in rorg))
         self.cyl = None
         if cyl is not None:
             dr, dz, pose = cyl
@@ -162,10 +169,22 @@ class Problem:
                             self.n_sub, self.step_vox, _ptr(self.P), _ptr(self.theta),
                             _ptr(self.coef), _ptr(self.s_view), self.margin, _ptr(self.bp_window, _ip),
                             self.bp_subvoxel, 1 if self.cyl else 0, cdr, cdz, _ptr(cpose),
-                            1 if self.joseph else 0)
+                            1 if self.joseph else 0, 1 if self.roi else 0,
+                            (ctypes.c_int * 3)(*(self.roi[0][::-1] if self.roi else (0, 0, 0))),
+                            (ctypes.c_double * 3)(*(self.roi[1] if self.roi else (0.0, 0.0, 0.0))),
+                            (ctypes.c_double * 3)(*(self.roi[2] if self.roi else (0.0, 0.0, 0.0))))
+
+    @property
+    def grid_shape(self):
+        return (self.nz, self.ny, self.nx)
 
     @property
     def vol_shape(self):
+        """Shape of a volume argument: the grid, or with an ROI the flat
+        concatenation of the context grid's and the ROI grid's voxels."""
+        if self.roi:
+            rz, ry, rx = self.roi[0]
+            return (self.nz * self.ny * self.nx + rz * ry * rx,)
         return (self.nz, self.ny, self.nx)
 
     @property
@@ -179,10 +198,10 @@ class Problem:
         return 1e-6 * self.min_vox
 
     def _replace(self, **kw):
-        args = dict(P=self.P, vol_shape=self.vol_shape, vox=self.vox, origin=self.origin,
+        args = dict(P=self.P, vol_shape=self.grid_shape, vox=self.vox, origin=self.origin,
                     det=(self.nu, self.nv), step_vox=self.step_vox, theta=self.theta, coef=self.coef,
                     s_view=self.s_view, margin=self.margin, bp_window=self.bp_window,
-                    bp_subvoxel=self.bp_subvoxel, cyl=self.cyl, joseph=self.joseph)
+                    bp_subvoxel=self.bp_subvoxel, cyl=self.cyl, joseph=self.joseph, roi=self.roi)
         args.update(kw)
         return Problem(**args)
 
@@ -195,6 +214,11 @@ class Problem:
     def with_subvoxel(self, s):
         """The same problem whose backprojector averages s^3 sub-voxel points."""
         return self._replace(bp_subvoxel=s)
+
+    def with_roi(self, roi_shape, roi_vox, roi_origin):
+        """The same problem with a finer ROI grid (reading R15): roi_shape
+        (nz, ny, nx), roi_vox and roi_origin (x, y, z) mm."""
+        return self._replace(roi=(roi_shape, roi_vox, roi_origin))
 
     def with_joseph(self, on=True):
         """The same problem with the classical Joseph projector (reading R14)."""

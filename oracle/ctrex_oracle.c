@@ -94,6 +94,12 @@ typedef struct {
     double cyl_dr, cyl_dz;
     const double *cyl_pose; /* [12] row-major 3x4: q = Rc x + tc (world mm -> frame mm) */
     int joseph;             /* 1: classical Joseph projector (reading R14) instead of R2 */
+    /* multi-resolution ROI (Sec. 3.7 method B, reading R15): a finer grid
+     * inside the context grid's box; volumes are then the context grid's
+     * voxels followed by the ROI grid's */
+    int roi;
+    int roi_n[3];
+    double roi_vox[3], roi_origin[3];
 } or_problem;
 
 /* Per (view, sub-angle) quantities derived from P (Sec. 2.2.1). */
@@ -149,6 +155,26 @@ static void volume_centre(const or_problem *pb, double c[3])
     }
     const int n[3] = {pb->nx, pb->ny, pb->nz};
     for (int a = 0; a < 3; ++a) c[a] = pb->origin[a] + 0.5 * (n[a] - 1) * pb->vox[a];
+}
+
+/* Reading R15: the ROI grid as a problem of its own (same views). */
+static or_problem roi_part(const or_problem *pb)
+{
+    or_problem f = *pb;
+    f.nx = pb->roi_n[0];
+    f.ny = pb->roi_n[1];
+    f.nz = pb->roi_n[2];
+    for (int a = 0; a < 3; ++a) {
+        f.vox[a] = pb->roi_vox[a];
+        f.origin[a] = pb->roi_origin[a];
+    }
+    f.roi = 0;
+    return f;
+}
+
+static long grid_voxels(const or_problem *pb)
+{
+    return (long)pb->nx * pb->ny * pb->nz;
 }
 
 /*
@@ -673,12 +699,76 @@ static void joseph_ray(const or_problem *pb, const or_view *ov, const double *vo
     if (ncross) *ncross = cnt;
 }
 
+/* Reading R2 on one piece [a, b] of a ray: samples of grid g (volume vg). */
+static void piece(const or_problem *g, const double *vg, const double s0[3], const double d[3], double a,
+                  double b, double *val, double *rs)
+{
+    double D = step_mm(g);
+    long K = (long)ceil((b - a) / D);
+    for (long k = 0; k < K; ++k) {
+        double ak = a + k * D;
+        double bk = ak + D < b ? ak + D : b;
+        double w = bk - ak;
+        if (!(w > 0.0)) continue;
+        double t = 0.5 * (ak + bk), x[3], gi[3], ws;
+        for (int r = 0; r < 3; ++r) x[r] = s0[r] + t * d[r];
+        to_index(g, x, gi);
+        *val += w * trilinear(g, vg, gi, &ws, NULL);
+        *rs += w * ws;
+    }
+}
+
+/* Reading R15: context pieces before and after the ROI box, the ROI piece
+ * between, each on its own grid. */
+static void roi_ray(const or_problem *pb, const or_view *ov, const double *vol, double u, double v,
+                    double *val, double *rs)
+{
+    double d[3], t0, t1, r0, r1;
+    *val = *rs = 0.0;
+    ray_direction(ov, u, v, d);
+    if (!clip_ray(pb, ov->src, d, &t0, &t1)) return;
+    or_problem f = roi_part(pb);
+    const double *vf = vol ? vol + grid_voxels(pb) : NULL;
+    if (clip_ray(&f, ov->src, d, &r0, &r1) && r1 > t0 && r0 < t1) {
+        if (r0 < t0) r0 = t0;
+        if (r1 > t1) r1 = t1;
+        piece(pb, vol, ov->src, d, t0, r0, val, rs);
+        piece(&f, vf, ov->src, d, r0, r1, val, rs);
+        piece(pb, vol, ov->src, d, r1, t1, val, rs);
+    } else {
+        piece(pb, vol, ov->src, d, t0, t1, val, rs);
+    }
+}
+
+/* Reading R15: samples of the three pieces. */
+static long roi_count(const or_problem *pb, const or_view *ov, double u, double v)
+{
+    double d[3], t0, t1, r0, r1;
+    ray_direction(ov, u, v, d);
+    if (!clip_ray(pb, ov->src, d, &t0, &t1)) return 0;
+    or_problem f = roi_part(pb);
+    double Dc = step_mm(pb), Df = step_mm(&f);
+    if (clip_ray(&f, ov->src, d, &r0, &r1) && r1 > t0 && r0 < t1) {
+        if (r0 < t0) r0 = t0;
+        if (r1 > t1) r1 = t1;
+        return (long)ceil((r0 - t0) / Dc) + (long)ceil((r1 - r0) / Df) + (long)ceil((t1 - r1) / Dc);
+    }
+    return (long)ceil((t1 - t0) / Dc);
+}
+
 /* Sec. 3.4: a pixel is the mean over its S angular sub-projections. */
 static void pixel_value(const or_problem *pb, const or_view *ov, const double *vol, int view,
                         double u, double v, double *val, double *rs)
 {
     double sv = 0.0, sr = 0.0;
     for (int s = 0; s < pb->n_sub; ++s) {
+        if (pb->roi) {
+            double a, b;
+            roi_ray(pb, &ov[(size_t)view * pb->n_sub + s], vol, u, v, &a, &b);
+            sv += a;
+            sr += b;
+            continue;
+        }
         if (pb->joseph) {
             double a, b;
             joseph_ray(pb, &ov[(size_t)view * pb->n_sub + s], vol, u, v, &a, &b, NULL);
@@ -702,6 +792,7 @@ static void pixel_value(const or_problem *pb, const or_view *ov, const double *v
 /* The Joseph projector is defined on the Cartesian grid without motion. */
 static int joseph_unsupported(const or_problem *pb)
 {
+    if (pb->roi && (pb->joseph || pb->cyl || pb->theta || pb->coef)) return 1; /* R15: trilinear, no motion */
     return pb->joseph && (pb->cyl || pb->theta || pb->coef);
 }
 
@@ -769,6 +860,10 @@ long or_count_samples(const or_problem *pb, const int *views, int n_sel)
                     long c;
                     joseph_ray(pb, o, NULL, iu, iv, &a, &b, &c);
                     total += c;
+                    continue;
+                }
+                if (pb->roi) {
+                    total += roi_count(pb, o, iu, iv);
                     continue;
                 }
                 ray_direction(o, iu, iv, d);
@@ -900,12 +995,16 @@ int or_backproject(const or_problem *pb, const double *r, const int *views, int 
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;
-    long nvox = (long)pb->nx * pb->ny * pb->nz;
+    long nc = grid_voxels(pb);
+    or_problem f = pb->roi ? roi_part(pb) : *pb;
+    long nvox = nc + (pb->roi ? grid_voxels(&f) : 0);
 #pragma omp parallel for schedule(dynamic, 64)
     for (long j = 0; j < nvox; ++j) {
-        int ix = (int)(j % pb->nx), iy = (int)((j / pb->nx) % pb->ny), iz = (int)(j / ((long)pb->nx * pb->ny));
+        const or_problem *g = j < nc ? pb : &f; /* reading R15: the ROI voxels follow */
+        long jj = j < nc ? j : j - nc;
+        int ix = (int)(jj % g->nx), iy = (int)((jj / g->nx) % g->ny), iz = (int)(jj / ((long)g->nx * g->ny));
         double b, c;
-        bp_voxel(pb, ov, r, views, n_sel, ix, iy, iz, &b, &c);
+        bp_voxel(g, ov, r, views, n_sel, ix, iy, iz, &b, &c);
         if (b_out) b_out[j] = b;
         if (c_out) c_out[j] = c;
         if (x) {
@@ -924,11 +1023,15 @@ int or_backproject_voxels(const or_problem *pb, const double *r, const int *view
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;
+    long nc = grid_voxels(pb);
+    or_problem f = pb->roi ? roi_part(pb) : *pb;
 #pragma omp parallel for schedule(dynamic, 1)
     for (long q = 0; q < n_vox; ++q) {
         long j = vox[q];
-        int ix = (int)(j % pb->nx), iy = (int)((j / pb->nx) % pb->ny), iz = (int)(j / ((long)pb->nx * pb->ny));
-        bp_voxel(pb, ov, r, views, n_sel, ix, iy, iz, &b_out[q], &c_out[q]);
+        const or_problem *g = (pb->roi && j >= nc) ? &f : pb;
+        if (g == &f) j -= nc;
+        int ix = (int)(j % g->nx), iy = (int)((j / g->nx) % g->ny), iz = (int)(j / ((long)g->nx * g->ny));
+        bp_voxel(g, ov, r, views, n_sel, ix, iy, iz, &b_out[q], &c_out[q]);
     }
     free(ov);
     return 0;
@@ -976,7 +1079,7 @@ static void adj_sample(void *vctx, const double x[3], double w)
 int or_adjoint(const or_problem *pb, const double *y, const int *views, int n_sel, double *vol_out)
 {
     /* the transpose of the trilinear projector on the Cartesian grid only */
-    if (pb->cyl || pb->joseph) return OR_E_ARG;
+    if (pb->cyl || pb->joseph || pb->roi) return OR_E_ARG;
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;
@@ -1104,7 +1207,7 @@ static void grad_sample(void *vctx, const double x[3], double w)
 int or_motion_grad(const or_problem *pb, const double *vol, const double *g, const int *views,
                    int n_sel, double *grad_theta, double *grad_coef)
 {
-    if (pb->cyl || pb->joseph) return OR_E_ARG; /* trilinear projector, Cartesian grid only */
+    if (pb->cyl || pb->joseph || pb->roi) return OR_E_ARG; /* trilinear projector, one Cartesian grid */
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;

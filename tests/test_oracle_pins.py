@@ -1037,3 +1037,97 @@ def test_joseph_refusals():
     th = inputs.identity_theta(2)
     with pytest.raises(ValueError):
         oracle.forward(pb.with_motion(theta=th), np.zeros(cfg.vol_shape))
+
+
+# ---------------------------------------------------------------------------
+# Multi-resolution ROI (reading R15)
+# ---------------------------------------------------------------------------
+
+def _roi_setup(nc=(12, 10, 8), vc=1.0, lo=(4, 3, 2), nroi=(4, 4, 3), ratio=2):
+    """Context grid nc (x, y, z) of pitch vc centred at 0; an ROI covering the
+    context voxels [lo, lo + nroi) at pitch vc / ratio (faces aligned)."""
+    shape = (nc[2], nc[1], nc[0])
+    origin = tuple(-0.5 * (n - 1) * vc for n in nc)
+    vf = vc / ratio
+    rn = tuple(k * ratio for k in nroi)
+    rorigin = tuple(origin[a] + (lo[a] - 0.5) * vc + 0.5 * vf for a in range(3))
+    return shape, (vc,) * 3, origin, (rn[2], rn[1], rn[0]), (vf,) * 3, rorigin
+
+
+def test_roi_parts_equal_single_grid_projections():
+    cfg = small(n=8, nu=30, nv=26, n_views=6, trajectory="perturbed", seed=71)
+    P = inputs.projection_matrices(cfg)
+    shape, vox, origin, rshape, rvox, rorg = _roi_setup(nc=(26, 24, 20), lo=(9, 8, 7), nroi=(8, 8, 6))
+    base = oracle.Problem(P, shape, vox, origin, (cfg.nu, cfg.nv))
+    pb = base.with_roi(rshape, rvox, rorg)
+    fine = oracle.Problem(P, rshape, rvox, rorg, (cfg.nu, cfg.nv))
+    rng = np.random.default_rng(71)
+    xc = rng.uniform(size=shape)
+    xf = rng.uniform(size=rshape)
+    nc = xc.size
+    # ROI values only: the ROI piece of every ray is the fine grid's own clip
+    a, ra = oracle.forward(pb, np.concatenate([np.zeros(nc), xf.ravel()]))
+    b, _ = oracle.forward(fine, xf)
+    assert np.abs(b).max() > 1.0 and np.allclose(a, b, rtol=1e-12, atol=1e-12)
+    # context values only, on rays that miss the ROI box: the context projection
+    c, _ = oracle.forward(pb, np.concatenate([xc.ravel(), np.zeros(xf.size)]))
+    d, _ = oracle.forward(base, xc)
+    _, rs_f = oracle.forward(fine, np.ones(rshape))
+    miss = rs_f == 0.0
+    assert miss.sum() > 100 and (~miss).sum() > 100
+    assert np.allclose(c[miss], d[miss], rtol=1e-12, atol=1e-12)
+    # and the two resolutions add
+    e, _ = oracle.forward(pb, np.concatenate([xc.ravel(), xf.ravel()]))
+    assert np.allclose(e, a + c, rtol=1e-12, atol=1e-12)
+
+
+def test_roi_axial_ray_closed_form():
+    # a ray along x through the centre of context row (j, k): context pieces
+    # before and after the ROI, each the P1 rule with the context voxel just
+    # inside the ROI entering through the last tap, and the ROI piece the P1
+    # rule on the mean of the four ROI rows around the ray
+    shape, vox, origin, rshape, rvox, rorg = _roi_setup()
+    nz, ny, nx = shape
+    rng = np.random.default_rng(72)
+    xc = rng.uniform(size=shape)
+    xf = rng.uniform(size=rshape)
+    j, k = 4, 3  # inside the ROI's y range [3, 7) and z range [2, 5)
+    y0 = origin[1] + j * vox[1]
+    z0 = origin[2] + k * vox[2]
+    pb = oracle.Problem(_x_axial_P(y0, z0)[None], shape, vox, origin, (21, 21)).with_roi(rshape, rvox, rorg)
+    val, rs = oracle.forward_rays(pb, np.concatenate([xc.ravel(), xf.ravel()]), np.zeros(1, np.int32),
+                                  np.array([10.0]), np.array([10.0]))
+    lo, hi = 4, 8  # ROI covers context columns [4, 8)
+    f = xc[k, j, :]
+    entry, exit_ = f[:lo], f[hi:]
+    vc = vox[0]
+    ctx_in = vc * (entry.sum() - entry[0] / 8 - entry[-1] / 8 + f[lo] / 8)
+    ctx_out = vc * (exit_.sum() - exit_[0] / 8 - exit_[-1] / 8 + f[hi - 1] / 8)
+    # the ray sits halfway between ROI rows 2 (j - 3) * 2 + {0, 1} and slices 2 (k - 2) + {0, 1}
+    jy, kz = 2 * (j - 3), 2 * (k - 2)
+    g = 0.25 * (xf[kz, jy, :] + xf[kz, jy + 1, :] + xf[kz + 1, jy, :] + xf[kz + 1, jy + 1, :])
+    roi_piece = rvox[0] * (g.sum() - g[0] / 8 - g[-1] / 8)
+    assert val[0] == pytest.approx(ctx_in + roi_piece + ctx_out, rel=1e-11)
+    ones = oracle.forward_rays(pb, np.ones(pb.vol_shape), np.zeros(1, np.int32), np.array([10.0]),
+                               np.array([10.0]))[0][0]
+    n_in, n_out, n_roi = lo, nx - hi, rshape[2]
+    assert ones == pytest.approx(vc * (n_in - 1 / 8) + vc * (n_out - 1 / 8) + rvox[0] * (n_roi - 1 / 4), rel=1e-11)
+
+
+def test_roi_backprojection_is_per_grid():
+    cfg = small(n=8, nu=30, nv=26, n_views=5, trajectory="perturbed", seed=73)
+    P = inputs.projection_matrices(cfg)
+    shape, vox, origin, rshape, rvox, rorg = _roi_setup(nc=(26, 24, 20), lo=(9, 8, 7), nroi=(8, 8, 6))
+    base = oracle.Problem(P, shape, vox, origin, (cfg.nu, cfg.nv))
+    pb = base.with_roi(rshape, rvox, rorg)
+    fine = oracle.Problem(P, rshape, rvox, rorg, (cfg.nu, cfg.nv))
+    r = np.random.default_rng(73).normal(size=(cfg.n_views, cfg.nv, cfg.nu))
+    _, b, c = oracle.backproject(pb, r)
+    _, bc, cc = oracle.backproject(base, r)
+    _, bf, cf = oracle.backproject(fine, r)
+    nc = bc.size
+    assert np.array_equal(b[:nc], bc.ravel()) and np.array_equal(c[:nc], cc.ravel())
+    assert np.array_equal(b[nc:], bf.ravel()) and np.array_equal(c[nc:], cf.ravel())
+    vox_idx = np.array([0, 17, nc - 1, nc, nc + 100, b.size - 1])
+    bv, cv = oracle.backproject_voxels(pb, r, vox_idx)
+    assert np.array_equal(bv, b[vox_idx]) and np.array_equal(cv, c[vox_idx])
