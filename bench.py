@@ -306,6 +306,27 @@ def measure_rows(device, gather_peak, sm_count, sm_mhz):
                                       "fwd_tex_gather_frac": 2 * ns / t_fc / gather_peak,
                                       "bp_tex_gather_frac": nu_ / t_bp / gather_peak}
     del ctx, vol, p, x, r
+    # multi-resolution ROI (Sec. 3.7): one SIRT step on a 256^3 context grid
+    # with a 4x finer 256^3 ROI, projected together
+    rc = inputs.ROI_FOCUS
+    ctx = ctrex.context_for(rc.base, device=device)
+    ctx.set_roi(rc.roi_shape, (rc.roi_vox,) * 3, rc.roi_origin)
+    xc, xf = inputs.roi_phantom(rc, device=str(device))
+    vol = torch.cat([xc.flatten(), xf.flatten()]).float().contiguous()
+    del xc, xf
+    p = ctx.fwd_project(vol)
+    ns = ctx.count_samples()
+    nu_ = vol.numel() * rc.base.n_views * rc.base.n_sub
+    x = torch.zeros_like(vol)
+    r = torch.empty_like(p)
+    t_fc = _time(lambda: ctx.fwd_correct(x, p, r=r, sums=sums), reps=2)
+    t_bp = _time(lambda: ctx.back_project(r, vol=x, alpha=1.0), reps=2)
+    rows["a17_roi_sirt_step"] = {"workload": rc.name, "samples": ns, "updates": nu_,
+                                 "fwd_correct_ms": t_fc * 1e3, "back_project_ms": t_bp * 1e3,
+                                 "gups": (ns + nu_) / (t_fc + t_bp) / 1e9,
+                                 "fwd_tex_gather_frac": 2 * ns / t_fc / gather_peak,
+                                 "bp_tex_gather_frac": nu_ / t_bp / gather_peak}
+    del ctx, vol, p, x, r
     # a12: tcgen05 implicit-GEMM convolution, the U-Net's levels (batch 2 at 128^3)
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:

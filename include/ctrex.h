@@ -234,6 +234,33 @@ int ctrex_set_bp_subvoxel(ctrex_ctx *ctx, int s);
  * set_geometry_cylinder resets the projector to trilinear.  Unknown kind:
  * CTREX_E_ARG.
  */
+/*
+ * Multi-resolution ROI (Sec. 3.7; its simultaneous form, where the
+ * projector's sampling switches between a high-resolution ROI volume and the
+ * low-resolution context volume by ray position).  roi is a second, finer
+ * Cartesian grid (same conventions as ctrex_vol_grid) whose box lies inside
+ * the grid of set_geometry (the context grid); else CTREX_E_ARG.  Once set,
+ * every volume buffer (vol, w) of the projection, backprojection and SIRT
+ * calls holds the context grid's voxels followed by the ROI grid's
+ * (nx ny nz + roi nx ny nz elements):
+ *   - the forward clips each ray to the context box and splits it at the ROI
+ *     box; the context pieces and the ROI piece each follow the fixed-step
+ *     truncated-midpoint rule with their own grid's step (step_vox times its
+ *     smallest pitch) and sample their own grid (zero-padded trilinear);
+ *     row sums add over the pieces;
+ *   - the backprojector updates both grids, each with its own column sums C
+ *     (the context grid everywhere, also under the ROI);
+ *   - count_samples counts the samples of all pieces.
+ * The ROI path is the trilinear projector on a Cartesian grid without
+ * motion: CTREX_E_STATE on the cylindrical domain, with motion or with the
+ * Joseph projector (and set_motion, set_projector(JOSEPH) and
+ * adjoint_project return CTREX_E_STATE while an ROI is set).  Both grids are
+ * sampled through texture atlases (CTREX_E_SHAPE at the first projection if
+ * one exceeds the device's 2D texture limits).  NULL removes the ROI;
+ * set_geometry and set_geometry_cylinder remove it too.
+ */
+int ctrex_set_roi(ctrex_ctx *ctx, const ctrex_vol_grid *roi);
+
 #define CTREX_PROJ_TRILINEAR 0
 #define CTREX_PROJ_JOSEPH 1
 int ctrex_set_projector(ctrex_ctx *ctx, int kind);

@@ -63,6 +63,16 @@ struct ctrex_ctx {
     int projector = CTREX_PROJ_TRILINEAR;
     AtlasStore jos_atlas;
     Atlas jos_atlas_view;
+    // multi-resolution ROI (set by ctrex_set_roi): a finer grid whose voxels
+    // follow the context grid's in every volume buffer
+    std::vector<double> hostP;  // world matrices of the current geometry
+    double ctr[3] = {0, 0, 0};  // the centre P was sign-normalised with
+    bool roi = false;
+    Grid roi_grid{};
+    ViewGPU *d_views_roi = nullptr;
+    RoiGPU roig{};
+    AtlasStore roi_atlas;
+    Atlas roi_atlas_view;
     // ordered-subset SIRT: concatenated subset view lists, per-subset norms
     int *d_subset_views = nullptr;
     size_t subset_views_bytes = 0;
@@ -168,7 +178,16 @@ FwdArgs fwd_args(ctrex_ctx *c, const void *vol, int vdt, const int *view_idx, in
     a.devcheck = c->d_devcheck;
     a.cyl = c->cyl ? &c->cylg : nullptr;
     a.joseph = c->projector == CTREX_PROJ_JOSEPH ? 1 : 0;
+    a.roi = c->roi ? &c->roig : nullptr;
     return a;
+}
+
+size_t grid_voxels(const Grid &G) { return (size_t)G.nx * G.ny * G.nz; }
+
+// Elements of a volume buffer: the grid, then the ROI grid if one is set.
+size_t volume_elems(const ctrex_ctx *c)
+{
+    return grid_voxels(c->grid) + (c->roi ? grid_voxels(c->roi_grid) : 0);
 }
 
 // Uploads vol into the context's texture atlas and points a.atlas at it; if
@@ -189,6 +208,27 @@ int prepare_atlas(ctrex_ctx *c, FwdArgs &a, const void *vol, int vdt)
         if (e != cudaSuccess) return cuda_fail(c, e, "Joseph atlas upload");
         c->jos_atlas_view = atlas_view(c->jos_atlas);
         a.atlas = &c->jos_atlas_view;
+        return CTREX_OK;
+    }
+    if (c->roi) {
+        // context and ROI grids in atlases of their own; no row-major fallback
+        const size_t off = grid_voxels(c->grid) * dtype_size(vdt);
+        const Grid *gs[2] = {&c->grid, &c->roi_grid};
+        AtlasStore *st[2] = {&c->vol_atlas, &c->roi_atlas};
+        Atlas *vw[2] = {&c->vol_atlas_view, &c->roi_atlas_view};
+        for (int i = 0; i < 2; ++i) {
+            cudaError_t e = atlas_ensure(*st[i], gs[i]->nx, gs[i]->ny, gs[i]->nz, vdt == CTREX_BF16, c->device, false);
+            if (e == cudaErrorInvalidValue) {
+                cudaGetLastError();
+                return fail(c, CTREX_E_SHAPE, "ROI projection: a grid exceeds the 2D texture limits of the device");
+            }
+            if (e != cudaSuccess) return cuda_fail(c, e, "ROI atlas allocation");
+            e = atlas_upload(*st[i], static_cast<const char *>(vol) + (i ? off : 0), c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "ROI atlas upload");
+            *vw[i] = atlas_view(*st[i]);
+        }
+        a.atlas = &c->vol_atlas_view;
+        a.roi_atlas = &c->roi_atlas_view;
         return CTREX_OK;
     }
     if (c->cyl) {
@@ -318,6 +358,8 @@ int ctrex_destroy(ctrex_ctx *c)
         atlas_release(c->vol_atlas);
         atlas_release(c->img_atlas);
         atlas_release(c->jos_atlas);
+        atlas_release(c->roi_atlas);
+        dfree(c->d_views_roi);
     }
     delete c;
     return CTREX_OK;
@@ -348,14 +390,12 @@ int ctrex_device_status(ctrex_ctx *c)
 // grid is indexed in (mm) to pixels; voxel i of axis a sits at origin[a] +
 // i vox[a] in that frame; ctr is the volume centre (sign normalisation of P);
 // min_pitch the smallest physical pitch (step and row-sum threshold).
-static int build_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, const int n[3], const double vox[3],
-                          const double origin[3], const double ctr[3], double min_pitch, const ctrex_det_grid *det,
-                          double step_vox)
+// Per-(view, sub) FP32 parameters of P on a grid (vox, origin); ctr fixes
+// the sign normalisation.
+static int compute_views(ctrex_ctx *c, const double *P, int nvs, int n_sub, const double vox[3],
+                         const double origin[3], const double ctr[3], double uc, double vc, std::vector<ViewGPU> &hv)
 {
-    DeviceGuard g(c->device);
-    const int nvs = n_views * n_sub;
-    std::vector<ViewGPU> hv((size_t)nvs);
-    const double uc = 0.5 * (det->nu - 1), vc = 0.5 * (det->nv - 1);
+    hv.assign((size_t)nvs, ViewGPU{});
     for (int q = 0; q < nvs; ++q) {
         const double *Pi = P + 12 * (size_t)q;
         double M[9], fro = 0.0;
@@ -401,7 +441,26 @@ static int build_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub,
             V.P[4 * r + 3] = (float)acc;
         }
     }
+    return CTREX_OK;
+}
+
+static int build_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub, const int n[3], const double vox[3],
+                          const double origin[3], const double ctr[3], double min_pitch, const ctrex_det_grid *det,
+                          double step_vox)
+{
+    DeviceGuard g(c->device);
+    const int nvs = n_views * n_sub;
+    std::vector<ViewGPU> hv;
+    const double uc = 0.5 * (det->nu - 1), vc = 0.5 * (det->nv - 1);
+    int e = compute_views(c, P, nvs, n_sub, vox, origin, ctr, uc, vc, hv);
+    if (e) return e;
+    // the world matrices and the centre, for a later ROI grid
+    c->hostP.assign(P, P + 12 * (size_t)nvs);
+    for (int a = 0; a < 3; ++a) c->ctr[a] = ctr[a];
     dfree(c->d_views);
+    dfree(c->d_views_roi);
+    c->roi = false;
+    atlas_release(c->roi_atlas);
     dfree(c->d_window);
     c->has_window = false;
     // motion buffers are sized by n_views: drop them with the old geometry
@@ -558,7 +617,7 @@ int ctrex_set_motion(ctrex_ctx *c, const float *theta, const float *coef, const 
 {
     if (!c) return CTREX_E_ARG;
     if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_motion before set_geometry");
-    if ((c->cyl || c->projector == CTREX_PROJ_JOSEPH) && (theta || coef || s_view))
+    if ((c->cyl || c->roi || c->projector == CTREX_PROJ_JOSEPH) && (theta || coef || s_view))
         return fail(c, CTREX_E_STATE, "set_motion: the motion model is defined for the trilinear projector on the "
                                       "Cartesian grid only");
     double box = 0.0;
@@ -630,12 +689,75 @@ int ctrex_set_bp_window(ctrex_ctx *c, const int *window)
     return CTREX_OK;
 }
 
+int ctrex_set_roi(ctrex_ctx *c, const ctrex_vol_grid *roi)
+{
+    if (!c) return CTREX_E_ARG;
+    if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_roi before set_geometry");
+    DeviceGuard g(c->device);
+    if (!roi) {
+        c->roi = false;
+        dfree(c->d_views_roi);
+        atlas_release(c->roi_atlas);
+        return CTREX_OK;
+    }
+    if (c->cyl || c->has_motion || c->projector != CTREX_PROJ_TRILINEAR)
+        return fail(c, CTREX_E_STATE, "set_roi: the ROI projector is the trilinear one on a Cartesian grid without "
+                                      "motion");
+    if (roi->nx < 1 || roi->ny < 1 || roi->nz < 1 ||
+        (long long)roi->nx * roi->ny * roi->nz + (long long)grid_voxels(c->grid) >= (1LL << 31))
+        return fail(c, CTREX_E_SHAPE, "set_roi: grid %d x %d x %d unsupported", roi->nx, roi->ny, roi->nz);
+    const int n[3] = {roi->nx, roi->ny, roi->nz}, nc[3] = {c->grid.nx, c->grid.ny, c->grid.nz};
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!(roi->vox[a] > 0.0) || !isfinite(roi->vox[a]) || !isfinite(roi->origin[a]))
+            return fail(c, CTREX_E_ARG, "set_roi: voxel pitch must be > 0 and origin finite");
+        // the ROI box must lie inside the context grid's box
+        lo[a] = roi->origin[a] - 0.5 * roi->vox[a];
+        hi[a] = roi->origin[a] + (n[a] - 0.5) * roi->vox[a];
+        const double clo = c->origin[a] - 0.5 * c->vox[a], chi = c->origin[a] + (nc[a] - 0.5) * c->vox[a];
+        const double tol = 1e-9 * (chi - clo);
+        if (lo[a] < clo - tol || hi[a] > chi + tol)
+            return fail(c, CTREX_E_ARG, "set_roi: the ROI box leaves the context grid's box on axis %d", a);
+    }
+    const int nvs = c->grid.n_views * c->grid.n_sub;
+    std::vector<ViewGPU> hv;
+    int e = compute_views(c, c->hostP.data(), nvs, c->grid.n_sub, roi->vox, roi->origin, c->ctr, c->grid.uc,
+                          c->grid.vc, hv);
+    if (e) return e;
+    dfree(c->d_views_roi);
+    CT_CUDA(c, cudaMalloc((void **)&c->d_views_roi, sizeof(ViewGPU) * (size_t)nvs));
+    CT_CUDA(c, cudaMemcpy(c->d_views_roi, hv.data(), sizeof(ViewGPU) * (size_t)nvs, cudaMemcpyHostToDevice));
+    Grid &F = c->roi_grid;
+    F = c->grid;
+    F.nx = n[0];
+    F.ny = n[1];
+    F.nz = n[2];
+    double minf = roi->vox[0];
+    for (int a = 0; a < 3; ++a) {
+        F.vox[a] = (float)roi->vox[a];
+        minf = fmin(minf, roi->vox[a]);
+        F.lo[a] = -0.5f;
+        F.hi[a] = (float)(n[a] - 0.5);
+    }
+    F.step_mm = (float)(c->step_vox * minf);
+    RoiGPU &R = c->roig;
+    for (int a = 0; a < 3; ++a) {
+        R.sc[a] = (float)(c->vox[a] / roi->vox[a]);
+        R.oc[a] = (float)((c->origin[a] - roi->origin[a]) / roi->vox[a]);
+        R.lo[a] = (float)((lo[a] - c->origin[a]) / c->vox[a]);
+        R.hi[a] = (float)((hi[a] - c->origin[a]) / c->vox[a]);
+    }
+    R.step_mm = F.step_mm;
+    c->roi = true;
+    return CTREX_OK;
+}
+
 int ctrex_set_projector(ctrex_ctx *c, int kind)
 {
     if (!c) return CTREX_E_ARG;
     if (kind != CTREX_PROJ_TRILINEAR && kind != CTREX_PROJ_JOSEPH)
         return fail(c, CTREX_E_ARG, "set_projector: unknown projector %d", kind);
-    if (kind == CTREX_PROJ_JOSEPH && (c->cyl || c->has_motion))
+    if (kind == CTREX_PROJ_JOSEPH && (c->cyl || c->has_motion || c->roi))
         return fail(c, CTREX_E_STATE, "set_projector: the Joseph projector is defined on the Cartesian grid "
                                       "without motion");
     c->projector = kind;
@@ -747,6 +869,15 @@ int ctrex_back_project(ctrex_ctx *c, const void *r, int rdt, void *vol, int vdt,
     }
     cudaError_t ce = launch_backproject(a);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "back_project launch");
+    if (c->roi) {  // the ROI grid's voxels follow the context grid's
+        const size_t nc = grid_voxels(c->grid);
+        a.grid = &c->roi_grid;
+        a.views = c->d_views_roi;
+        a.vol = static_cast<char *>(vol) + nc * dtype_size(vdt);
+        a.w = w ? w + nc : nullptr;
+        ce = launch_backproject(a);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "back_project launch (ROI grid)");
+    }
     return CTREX_OK;
 }
 
@@ -755,8 +886,8 @@ int ctrex_adjoint_project(ctrex_ctx *c, const float *proj, float *vol, const int
     if (!c) return CTREX_E_ARG;
     int e = check_views(c, view_idx, n_idx);
     if (e) return e;
-    if (c->cyl || c->projector == CTREX_PROJ_JOSEPH)
-        return fail(c, CTREX_E_STATE, "adjoint_project: the transpose of the trilinear projector on the Cartesian "
+    if (c->cyl || c->roi || c->projector == CTREX_PROJ_JOSEPH)
+        return fail(c, CTREX_E_STATE, "adjoint_project: the transpose of the trilinear projector on one Cartesian "
                                       "grid only");
     if (n_idx == 0) return CTREX_OK;
     if (!proj || !vol) return fail(c, CTREX_E_ARG, "adjoint_project: NULL buffer");
@@ -912,7 +1043,7 @@ int ctrex_sirt_host(ctrex_ctx *c, void *vol_h, int vdt, const void *p_h, int pdt
     if (!dtype_ok(vdt) || !dtype_ok(pdt)) return fail(c, CTREX_E_DTYPE, "sirt_host: bad dtype");
     DeviceGuard g(c->device);
     const Grid &G = c->grid;
-    const size_t nvox = (size_t)G.nx * G.ny * G.nz;
+    const size_t nvox = volume_elems(c);
     const size_t vb = nvox * dtype_size(vdt);
     const size_t pb = (size_t)G.n_views * G.nu * G.nv * dtype_size(pdt);
     int e = ensure(c, &c->d_hvol, &c->hvol_bytes, vb, "host-SIRT volume");

@@ -63,6 +63,15 @@ struct CylGPU {
     float R, Z;                      // bounding cylinder: radius, half height (mm)
 };
 
+// Multi-resolution ROI (Sec. 3.7): a finer grid inside the context grid's
+// box.  ROI index coordinates from context ones: g_roi = g_ctx * sc + oc;
+// the ROI box in context index coordinates is [lo, hi].
+struct RoiGPU {
+    float sc[3], oc[3];
+    float lo[3], hi[3];
+    float step_mm;  // the ROI grid's step
+};
+
 template <typename T> struct Storage;
 template <> struct Storage<float> {
     static __device__ __forceinline__ float load(const float *p) { return __ldg(p); }
@@ -98,6 +107,8 @@ struct FwdArgs {
     int p_by_view = 0;          // correction: measured images indexed by view, not by list position
     const CylGPU *cyl = nullptr;  // cylindrical domain, or nullptr (Cartesian grid)
     int joseph = 0;               // classical Joseph projector; atlas = the three-stack atlas
+    const RoiGPU *roi = nullptr;  // multi-resolution ROI: atlas = context grid, roi_atlas = ROI grid
+    const Atlas *roi_atlas = nullptr;
 };
 
 cudaError_t launch_forward(const FwdArgs &a, void *proj, int proj_dtype, float *rowsum);

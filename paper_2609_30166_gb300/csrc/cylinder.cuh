@@ -70,6 +70,7 @@ struct CylSampler {
     static constexpr int TILE_TABLE = AtlasSampler::TILE_TABLE;
     static constexpr bool CYLINDER = true;
     static constexpr bool JOSEPH = false;
+    static constexpr bool ROI = false;
 
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads) { base.bind(table, tid, nthreads); }
 

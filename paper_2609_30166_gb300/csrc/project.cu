@@ -14,6 +14,7 @@
 #include "cylinder.cuh"
 #include "joseph.cuh"
 #include "ray.cuh"
+#include "roi.cuh"
 
 namespace ctrex {
 
@@ -74,6 +75,13 @@ __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__r
     float acc = 0.0f, acc_rs = 0.0f;
     for (int s = 0; s < G.n_sub; ++s) {
         const ViewGPU V = views[view * G.n_sub + s];
+        if constexpr (Sampler::ROI) {
+            float a, ars;
+            roi_integral<false>(G, vol, V, u, v, a, ars);
+            acc += a;
+            acc_rs += ars;
+            continue;
+        }
         if constexpr (Sampler::JOSEPH) {
             float a, ars;
             joseph_integral(G, vol, V, u, v, a, ars);
@@ -248,10 +256,10 @@ __global__ void __launch_bounds__(1024) finish_sums_kernel(const float *__restri
 
 // Exact sample count (same set-up arithmetic as the projector): ray
 // segments, or for the Joseph projector slice crossings with a tap inside.
-enum CountKind { COUNT_BOX = 0, COUNT_CYL = 1, COUNT_JOSEPH = 2 };
+enum CountKind { COUNT_BOX = 0, COUNT_CYL = 1, COUNT_JOSEPH = 2, COUNT_ROI = 3 };
 template <int KIND>
 __global__ void __launch_bounds__(FWD_TX *FWD_TY)
-    count_kernel(Grid G, CylGPU C, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx,
+    count_kernel(Grid G, CylGPU C, RoiGPU Q, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx,
                  unsigned long long *out)
 {
     const int k = blockIdx.y;
@@ -264,6 +272,13 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
         for (int s = 0; s < G.n_sub; ++s) {
             Ray R;
             const ViewGPU &V = views[view * G.n_sub + s];
+            if (KIND == COUNT_ROI) {
+                RoiSampler rs{};
+                rs.R = Q;
+                float a, b;
+                n += (unsigned long long)roi_integral<true>(G, rs, V, (float)iu, (float)iv, a, b);
+                continue;
+            }
             if (KIND == COUNT_JOSEPH) {
                 JRay J;
                 if (joseph_setup(G, V, (float)iu, (float)iv, J)) n += (unsigned long long)(J.khi - J.klo + 1);
@@ -296,7 +311,7 @@ static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, flo
 {
     const Grid &G = *a.grid;
     const dim3 grid = fwd_grid(G, a.n_idx), block(FWD_TX, FWD_TY);
-    if constexpr (!Sampler::CYLINDER && !Sampler::JOSEPH) {
+    if constexpr (!Sampler::CYLINDER && !Sampler::JOSEPH && !Sampler::ROI) {
         if (a.motion) {
             fwd_kernel<Sampler, TP, MODE, true><<<grid, block, 0, a.stream>>>(
                 G, a.views, a.motion, a.coef_idx, smp, a.view_idx, out, rowsum, p, partials, a.devcheck,
@@ -316,6 +331,11 @@ static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, flo
 template <typename TP, int MODE>
 static cudaError_t fwd_dispatch_sampler(const FwdArgs &a, TP *out, float *rowsum, const TP *p, float *partials)
 {
+    if (a.roi) {  // context and ROI grids, each from its own atlas
+        if (!a.atlas || !a.roi_atlas || a.cyl || a.joseph) return cudaErrorInvalidValue;
+        RoiSampler rs{AtlasSampler{*a.atlas}, AtlasSampler{*a.roi_atlas}, *a.roi};
+        return fwd_launch<RoiSampler, TP, MODE>(a, rs, out, rowsum, p, partials);
+    }
     if (a.joseph) {  // the Joseph projector reads its three-stack atlas only
         if (!a.atlas || a.cyl) return cudaErrorInvalidValue;
         const Grid &G = *a.grid;
@@ -375,11 +395,15 @@ cudaError_t launch_count_samples(const FwdArgs &a, unsigned long long *out)
     if (e != cudaSuccess || a.n_idx == 0) return e;
     const dim3 grid = fwd_grid(*a.grid, a.n_idx), block(FWD_TX, FWD_TY);
     if (a.cyl)
-        count_kernel<COUNT_CYL><<<grid, block, 0, a.stream>>>(*a.grid, *a.cyl, a.views, a.view_idx, out);
+        count_kernel<COUNT_CYL><<<grid, block, 0, a.stream>>>(*a.grid, *a.cyl, RoiGPU{}, a.views, a.view_idx, out);
     else if (a.joseph)
-        count_kernel<COUNT_JOSEPH><<<grid, block, 0, a.stream>>>(*a.grid, CylGPU{}, a.views, a.view_idx, out);
+        count_kernel<COUNT_JOSEPH><<<grid, block, 0, a.stream>>>(*a.grid, CylGPU{}, RoiGPU{}, a.views, a.view_idx,
+                                                                 out);
+    else if (a.roi)
+        count_kernel<COUNT_ROI><<<grid, block, 0, a.stream>>>(*a.grid, CylGPU{}, *a.roi, a.views, a.view_idx, out);
     else
-        count_kernel<COUNT_BOX><<<grid, block, 0, a.stream>>>(*a.grid, CylGPU{}, a.views, a.view_idx, out);
+        count_kernel<COUNT_BOX><<<grid, block, 0, a.stream>>>(*a.grid, CylGPU{}, RoiGPU{}, a.views, a.view_idx,
+                                                              out);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,7 @@ EXPORTS = (
     "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples", "ctrex_correct_static",
     "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad", "ctrex_os_sirt_iterate", "ctrex_set_bp_window",
     "ctrex_probe_gather_rate", "ctrex_set_bp_subvoxel", "ctrex_set_geometry_cylinder", "ctrex_set_projector",
+    "ctrex_set_roi",
 )
 
 PROJ_TRILINEAR, PROJ_JOSEPH = 0, 1
@@ -102,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         "ctrex_set_bp_window": ([vp, ip], i),
         "ctrex_set_bp_subvoxel": ([vp, i], i),
         "ctrex_set_projector": ([vp, i], i),
+        "ctrex_set_roi": ([vp, ctypes.POINTER(VolGrid)], i),
         "ctrex_set_geometry_cylinder": ([vp, ctypes.POINTER(d), i, i, ctypes.POINTER(CylGrid),
                                          ctypes.POINTER(DetGrid), d], i),
         "ctrex_probe_gather_rate": ([vp, ctypes.POINTER(d)], i),
@@ -202,8 +204,31 @@ class Context:
         self._check(self.lib.ctrex_set_geometry(self._h, P.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                 V, S, ctypes.byref(vg), ctypes.byref(dg), float(step_vox)))
         self.vol_shape = (nz, ny, nx)
+        self.grid_shape = self.vol_shape
+        self.roi_shape = None
         self.det_shape = (int(det[1]), int(det[0]))
         self.n_views, self.n_sub = V, S
+
+    def set_roi(self, roi_shape=None, vox=None, origin=None):
+        """A finer ROI grid (roi_shape (nz, ny, nx), vox and origin (x, y, z)
+        mm) inside the grid: volumes then become flat [context voxels, ROI
+        voxels].  None removes it."""
+        if roi_shape is None:
+            self._check(self.lib.ctrex_set_roi(self._h, None))
+            self.vol_shape, self.roi_shape = self.grid_shape, None
+            return
+        nz, ny, nx = (int(s) for s in roi_shape)
+        vg = VolGrid(nx, ny, nz, (ctypes.c_double * 3)(*vox), (ctypes.c_double * 3)(*origin))
+        self._check(self.lib.ctrex_set_roi(self._h, ctypes.byref(vg)))
+        self.roi_shape = (nz, ny, nx)
+        gz, gy, gx = self.grid_shape
+        self.vol_shape = (gz * gy * gx + nz * ny * nx,)
+
+    def split_volume(self, vol):
+        """(context grid view, ROI grid view) of a flat multi-resolution volume."""
+        gz, gy, gx = self.grid_shape
+        n = gz * gy * gx
+        return vol[:n].view(self.grid_shape), vol[n:].view(self.roi_shape)
 
     def set_geometry_cylinder(self, P, n_r, n_phi, n_z, dr, dz, det, pose=None, step_vox=0.5):
         """The aligned cylindrical domain: n_r rings of dr mm, n_phi sectors,
@@ -222,6 +247,8 @@ class Context:
             self._h, P.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), V, S, ctypes.byref(cg), ctypes.byref(dg),
             float(step_vox)))
         self.vol_shape = (int(n_z), int(n_phi), int(n_r))
+        self.grid_shape = self.vol_shape
+        self.roi_shape = None
         self.det_shape = (int(det[1]), int(det[0]))
         self.n_views, self.n_sub = V, S
 

@@ -454,6 +454,56 @@ def cyl_phantom(ccfg: CylConfig, seed: Optional[int] = None, device: str = "cpu"
 
 
 # ---------------------------------------------------------------------------
+# Multi-resolution ROI (Sec. 3.7): a coarse context grid and a fine ROI cube
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass(frozen=True)
+class RoiConfig:
+    """A context grid (``base``: its n, box and trajectory) and a cubic ROI
+    grid of roi_n voxels over a roi_box mm cube centred at roi_centre."""
+
+    name: str
+    base: Config
+    roi_n: int
+    roi_box: float
+    roi_centre: tuple = (0.0, 0.0, 0.0)
+
+    @property
+    def roi_vox(self) -> float:
+        return self.roi_box / self.roi_n
+
+    @property
+    def roi_origin(self) -> tuple:
+        return tuple(c - 0.5 * self.roi_box + 0.5 * self.roi_vox for c in self.roi_centre)
+
+    @property
+    def roi_shape(self) -> tuple:
+        return (self.roi_n,) * 3
+
+
+# context 256^3 over the 32 mm field of view (0.125 mm) and an ROI of 256^3
+# over the central 8 mm (0.03125 mm, 4 times finer), on the 720-view
+# trajectory of the 512^3 workload
+ROI_FOCUS = RoiConfig("roi-256^3+256^3x4-768^2-720v", PERTURBED_512.scaled(n=256), roi_n=256, roi_box=8.0,
+                      roi_centre=(0.6, -0.4, 0.3))
+
+
+def roi_phantom(rcfg: RoiConfig, seed: Optional[int] = None, device: str = "cpu", sub: int = 2):
+    """(context volume, ROI volume): the objects of ``draw_objects(base)``
+    voxelised on both grids (sub^3 sub-samples per voxel), so the two
+    resolutions describe the same object."""
+    ells, blobs = draw_objects(rcfg.base, seed)
+    ctx = voxelize(rcfg.base, ells, blobs, sub=sub, device=device)
+    # the ROI grid as a cubic Config centred at the origin, objects shifted by -roi_centre
+    sh = np.asarray(rcfg.roi_centre, float)
+    ells_r = [Ellipsoid(e.centre - sh, e.semi_axes, e.rot, e.density, e.texture) for e in ells]
+    blobs_r = [Blob(b.centre - sh, b.sigma, b.amplitude) for b in blobs]
+    roi_grid = rcfg.base.scaled(n=rcfg.roi_n, box=rcfg.roi_box)
+    roi = voxelize(roi_grid, ells_r, blobs_r, sub=sub, device=device)
+    return ctx, roi
+
+
+# ---------------------------------------------------------------------------
 # Motion parameters
 # ---------------------------------------------------------------------------
 
