@@ -12,16 +12,13 @@
 // slab stays in L2 while it is being sampled.
 #include "atlas.cuh"
 #include "cylinder.cuh"
+#include "fwd_common.cuh"
 #include "joseph.cuh"
 #include "ray.cuh"
 #include "roi.cuh"
 
 namespace ctrex {
 
-constexpr int FWD_TX = 32;
-constexpr int FWD_TY = 4;
-
-enum FwdMode { MODE_PROJECT = 0, MODE_CORRECT = 1 };
 
 template <typename TV>
 __device__ __forceinline__ float LinearSampler<TV>::operator()(float gx, float gy, float gz, float &wsum) const
@@ -34,33 +31,6 @@ __device__ __forceinline__ float LinearSampler<TV>::interior(float gx, float gy,
 {
     float ws;
     return trilinear(vol, nx, ny, nz, gx, gy, gz, ws);
-}
-
-// Samples k of the interior range [ka, kb) have every trilinear tap inside the
-// grid: g0 + k sg in [eps, n - 1 - eps] on each axis, with a margin eps far
-// above the rounding of the sample positions, so the short path is exact.
-__device__ __forceinline__ void interior_range(const Grid &G, const Ray &R, int &ka, int &kb)
-{
-    const float eps = 1e-2f;
-    const int n[3] = {G.nx, G.ny, G.nz};
-    float lo = 0.0f, hi = (float)(R.K - 1);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float l = eps, h = (float)(n[a] - 1) - eps;
-        if (R.sg[a] != 0.0f) {
-            const float inv = 1.0f / R.sg[a];
-            const float t0 = (l - R.g0[a]) * inv, t1 = (h - R.g0[a]) * inv;
-            lo = fmaxf(lo, fminf(t0, t1));
-            hi = fminf(hi, fmaxf(t0, t1));
-        } else if (!(R.g0[a] >= l && R.g0[a] <= h)) {
-            hi = -1.0f;
-        }
-    }
-    ka = (int)ceilf(lo);
-    kb = (int)floorf(hi) + 1;
-    // keep one sample of rounding slack on each side in the exact path
-    ka = min(max(ka + 1, 0), R.K - 1);
-    kb = max(min(kb - 1, R.K - 1), ka);
 }
 
 // Integral of one pixel (mean over its sub-angle rays): value and row sum.
@@ -183,49 +153,8 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
     const bool inside = ok && in_pix;
     float val = 0.0f, rs = 0.0f;
     if (inside) pixel_integral<Sampler, MOTION>(G, views, mo, coef, vol, view, (float)iu, (float)iv, val, rs);
-    const size_t pix = ((size_t)k * G.nv + iv) * G.nu + iu;
-    if (MODE == MODE_PROJECT) {
-        if (in_pix) {  // a skipped (out-of-range) view gets zeros
-            Storage<TP>::store(out + pix, val);
-            if (rowsum_out) rowsum_out[pix] = rs;
-        }
-        return;
-    } else {
-        float e2 = 0.0f, p2 = 0.0f;
-        if (in_pix && !ok) Storage<TP>::store(out + pix, 0.0f);
-        if (inside) {
-            const float pm = Storage<TP>::load(p + (p_by_view ? ((size_t)view * G.nv + iv) * G.nu + iu : pix));
-            const float e = pm - val;
-            const float Rw = rs > G.eps_R ? 1.0f / rs : 0.0f;
-            Storage<TP>::store(out + pix, Rw * e);
-            e2 = e * e;
-            p2 = pm * pm;
-        }
-        // warp-shuffle then fixed-order CTA reduction of the residual norms
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            e2 += __shfl_xor_sync(0xffffffffu, e2, off);
-            p2 += __shfl_xor_sync(0xffffffffu, p2, off);
-        }
-        const int lane = threadIdx.x & 31;
-        const int warp = (threadIdx.y * FWD_TX + threadIdx.x) >> 5;
-        if (lane == 0) {
-            s_red[0][warp] = e2;
-            s_red[1][warp] = p2;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            float a = 0.0f, b = 0.0f;
-#pragma unroll
-            for (int w = 0; w < FWD_TX * FWD_TY / 32; ++w) {
-                a += s_red[0][w];
-                b += s_red[1][w];
-            }
-            const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-            partials[2 * bid] = a;
-            partials[2 * bid + 1] = b;
-        }
-    }
+    fwd_epilogue<TP, MODE>(G, k, view, ok, in_pix, iu, iv, val, rs, out, rowsum_out, p, partials, p_by_view,
+                           s_red);
 }
 
 // Second pass of the residual reduction: one CTA, fixed order, FP64.

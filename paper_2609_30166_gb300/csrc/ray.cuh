@@ -83,6 +83,33 @@ __device__ __forceinline__ bool setup_ray(const Grid &G, const ViewGPU &V, float
     return true;
 }
 
+// Samples k of the interior range [ka, kb) have every trilinear tap inside the
+// grid: g0 + k sg in [eps, n - 1 - eps] on each axis, with a margin eps far
+// above the rounding of the sample positions, so the short path is exact.
+__device__ __forceinline__ void interior_range(const Grid &G, const Ray &R, int &ka, int &kb)
+{
+    const float eps = 1e-2f;
+    const int n[3] = {G.nx, G.ny, G.nz};
+    float lo = 0.0f, hi = (float)(R.K - 1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float l = eps, h = (float)(n[a] - 1) - eps;
+        if (R.sg[a] != 0.0f) {
+            const float inv = 1.0f / R.sg[a];
+            const float t0 = (l - R.g0[a]) * inv, t1 = (h - R.g0[a]) * inv;
+            lo = fmaxf(lo, fminf(t0, t1));
+            hi = fminf(hi, fmaxf(t0, t1));
+        } else if (!(R.g0[a] >= l && R.g0[a] <= h)) {
+            hi = -1.0f;
+        }
+    }
+    ka = (int)ceilf(lo);
+    kb = (int)floorf(hi) + 1;
+    // keep one sample of rounding slack on each side in the exact path
+    ka = min(max(ka + 1, 0), R.K - 1);
+    kb = max(min(kb - 1, R.K - 1), ka);
+}
+
 // Zero-padded trilinear interpolation at index coordinate g (reading: taps
 // outside [0, n-1] contribute nothing).  wsum receives the summed weight of
 // the in-range taps (the interpolant of an all-ones volume, for row sums).
