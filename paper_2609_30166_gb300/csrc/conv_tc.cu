@@ -108,6 +108,15 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16-byte asynchronous copy global -> shared; src_bytes 0 writes zeros.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -167,6 +176,50 @@ __device__ __forceinline__ void load_im2col_rows(const __nv_bfloat16 *__restrict
             v = *reinterpret_cast<const uint4 *>(e);
         }
         *reinterpret_cast<uint4 *>(tile + swz(r, j)) = v;
+    }
+}
+
+// The same A chunk with asynchronous copies (channel counts that are
+// multiples of 8: every 16-byte chunk is one tap's eight channels).
+__device__ __forceinline__ void load_im2col_rows_async(const __nv_bfloat16 *__restrict__ x, const ConvShape &S,
+                                                       const int4 rc, long long k0, uint8_t *tile)
+{
+    const int r = threadIdx.x;
+    const int cin = S.cin;
+    // (tap, channel) of the chunk's first column, then stepped by 8 channels
+    int tap = (int)k0 / cin, ci = (int)k0 - tap * cin;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const __nv_bfloat16 *src = x;
+        int bytes = 0;
+        if (rc.x >= 0 && tap < 27) {
+            const int tz = tap / 9, ty = (tap - 9 * tz) / 3, tx = tap - 9 * tz - 3 * ty;
+            const int zz = rc.y + tz - 1, yy = rc.z + ty - 1, xs = rc.w + tx - 1;
+            if ((unsigned)zz < (unsigned)S.d && (unsigned)yy < (unsigned)S.h && (unsigned)xs < (unsigned)S.w) {
+                src = x + ((((long long)rc.x * S.d + zz) * S.h + yy) * S.w + xs) * cin + ci;
+                bytes = 16;
+            }
+        }
+        cp_async16(tile + swz(r, j), src, bytes);
+        ci += 8;
+        if (ci >= cin) {
+            ci -= cin;
+            ++tap;
+        }
+    }
+}
+
+// B chunk with asynchronous copies (K a multiple of 8).
+template <int BN>
+__device__ __forceinline__ void load_rows_kmajor_async(const __nv_bfloat16 *__restrict__ w, long long ktot,
+                                                       int nrows, int n0, long long k0, uint8_t *tile)
+{
+    for (int i = threadIdx.x; i < BN * 8; i += THREADS) {
+        const int r = i >> 3, j = i & 7;
+        const long long kb = k0 + 8 * j;
+        const int row = n0 + r;
+        const bool in = row < nrows && kb + 8 <= ktot;
+        cp_async16(tile + swz(r, j), in ? w + (long long)row * ktot + kb : w, in ? 16 : 0);
     }
 }
 
@@ -249,21 +302,28 @@ __device__ __forceinline__ void load_kvoxel_blocks(const __nv_bfloat16 *__restri
         }
         const int dz = tap / 9 - 1, dyy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
         uint4 in[8];
+        // the group's eight voxels are consecutive: decode the first, then step
+        const long long mg = k0 + 8 * vg;
+        int n = 0, z = 0, y = 0, x = 0;
+        if (mg < S.k_total) decode_voxel(S, mg, n, z, y, x);
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             in[t] = make_uint4(0u, 0u, 0u, 0u);
-            const long long m = k0 + 8 * vg + t;
-            if (rows_ok && m < S.k_total) {
-                int n, z, y, x;
-                decode_voxel(S, m, n, z, y, x);
-                if (IS_A) {
-                    z += dz;
-                    y += dyy;
-                    x += dx;
-                }
-                if ((unsigned)z < (unsigned)S.d && (unsigned)y < (unsigned)S.h && (unsigned)x < (unsigned)S.w)
+            if (rows_ok && mg + t < S.k_total) {
+                const int zz = IS_A ? z + dz : z, yy = IS_A ? y + dyy : y, xx = IS_A ? x + dx : x;
+                if ((unsigned)zz < (unsigned)S.d && (unsigned)yy < (unsigned)S.h && (unsigned)xx < (unsigned)S.w)
                     in[t] = __ldg(reinterpret_cast<const uint4 *>(
-                        src + ((((long long)n * S.d + z) * S.h + y) * S.w + x) * ch + c0));
+                        src + ((((long long)n * S.d + zz) * S.h + yy) * S.w + xx) * ch + c0));
+            }
+            if (++x == S.w) {  // next voxel in x-fastest order
+                x = 0;
+                if (++y == S.h) {
+                    y = 0;
+                    if (++z == S.d) {
+                        z = 0;
+                        ++n;
+                    }
+                }
             }
         }
         uint4 out[8];
@@ -419,10 +479,176 @@ __global__ void __launch_bounds__(THREADS) conv_tc_kernel(const __nv_bfloat16 *_
     }
 }
 
+// FWD with channel counts that are multiples of 8: the A (im2col) and B
+// (weight) chunks arrive by asynchronous copies, ST stages deep, so the
+// gathers of ST - 1 chunks are in flight while the tensor cores work.  Stage
+// s is refilled only after the MMAs that read it (committed to bars[s]) are
+// done.
+template <int BN, int ST>
+__global__ void __launch_bounds__(THREADS) conv_fwd_async_kernel(const __nv_bfloat16 *__restrict__ x,
+                                                                 const __nv_bfloat16 *__restrict__ w,
+                                                                 const float *__restrict__ bias, void *__restrict__ out,
+                                                                 int out_bf16, ConvShape S, int *__restrict__ status)
+{
+    constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
+    constexpr int TMEM_COLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : 128);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;                 // ST x A_BYTES
+    uint8_t *sB = smem + ST * A_BYTES;  // ST x B_BYTES
+    __shared__ uint64_t bars[ST];
+    __shared__ uint32_t tmem_base_s;
+
+    const int warp = threadIdx.x >> 5;
+    const long long m0 = (long long)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const int nk = (int)((S.k_total + BK - 1) / BK);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < ST; ++i) mbar_init(&bars[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base_s)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tmem_base_s;
+    constexpr uint32_t ID = idesc(BN);
+    int4 rc = make_int4(-1, 0, 0, 0);  // this thread's output voxel (n, z, y, x)
+    {
+        const long long m = m0 + threadIdx.x;
+        if (m < S.m_total) {
+            long long t = m;
+            rc.w = (int)(t % S.w);
+            t /= S.w;
+            rc.z = (int)(t % S.h);
+            t /= S.h;
+            rc.y = (int)(t % S.d);
+            rc.x = (int)(t / S.d);
+        }
+    }
+    auto issue = [&](int c) {
+        const int st = c % ST;
+        load_im2col_rows_async(x, S, rc, (long long)c * BK, sA + st * A_BYTES);
+        load_rows_kmajor_async<BN>(w, S.k_total, S.n_total, n0, (long long)c * BK, sB + st * B_BYTES);
+    };
+    // prologue: chunks 0 .. ST-2 in flight (one commit group each, empty past the end)
+#pragma unroll
+    for (int c = 0; c < ST - 1; ++c) {
+        if (c < nk) issue(c);
+        cp_async_commit();
+    }
+    bool ok = true;
+    int committed = -1;
+    for (int c = 0; c < nk; ++c) {
+        const int st = c % ST;
+        cp_async_wait<ST - 2>();  // this thread's copies of chunk c have landed
+        fence_async_smem();
+        tc_before_sync();
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        if (threadIdx.x == 0) {
+            tc_after_sync();
+            const uint32_t a_base = smem_addr(sA + st * A_BYTES), b_base = smem_addr(sB + st * B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                umma_bf16(tmem, sdesc(a_base + 32 * kk), sdesc(b_base + 32 * kk), ID, c > 0 || kk > 0);
+            umma_commit(&bars[st]);
+        }
+        committed = c;
+        // refill the stage chunk c - 1 used with chunk c + ST - 1
+        const int c2 = c + ST - 1;
+        if (c2 < nk) {
+            if (c2 >= ST && !mbar_wait(&bars[c2 % ST], (unsigned)((c2 / ST - 1) & 1))) ok = false;
+            if (ok) issue(c2);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    if (ok && nk > 0) {
+        const int last = nk - 1;
+        if (!mbar_wait(&bars[last % ST], (unsigned)((last / ST) & 1))) ok = false;
+    }
+    ok = __syncthreads_and(ok);
+    tc_after_sync();
+    if (ok && nk > 0) {
+        // epilogue: thread (warp w, lane l) owns accumulator row 32 w + l
+        const long long row = m0 + threadIdx.x;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(lane_addr + (uint32_t)c0, v);
+            if (row >= S.m_total || n0 + c0 >= S.n_total) continue;
+            float y[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int co = n0 + c0 + i;
+                y[i] = v[i] + ((bias && co < S.n_total) ? bias[co] : 0.0f);
+                if (S.relu) y[i] = fmaxf(y[i], 0.0f);
+            }
+            const long long o = row * S.n_total + n0 + c0;
+            if ((S.n_total & 15) == 0) {  // 16 whole channels, 16-byte aligned
+                if (out_bf16) {
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(y[2 * i], y[2 * i + 1]);
+                        pk[i] = *reinterpret_cast<const uint32_t *>(&h2);
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + o);
+                    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                } else {
+                    float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(out) + o);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) dst[i] = make_float4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    if (n0 + c0 + i >= S.n_total) continue;
+                    if (out_bf16)
+                        static_cast<__nv_bfloat16 *>(out)[o + i] = __float2bfloat16_rn(y[i]);
+                    else
+                        static_cast<float *>(out)[o + i] = y[i];
+                }
+            }
+        }
+    } else if (nk > 0) {
+        if (threadIdx.x == 0) {
+            atomicExch(status, 1);
+            if (committed >= 0) mbar_wait(&bars[committed % ST], (unsigned)((committed / ST) & 1));
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
 template <int OP, int BN>
 cudaError_t launch_bn(const __nv_bfloat16 *a, const __nv_bfloat16 *b, const float *bias, void *out, int out_bf16,
                       const ConvShape &S, int *status, cudaStream_t stream)
 {
+    if (OP == OP_FWD && (S.cin & 7) == 0) {
+        constexpr int ST = BN <= 64 ? 4 : 3;
+        const int smem = ST * (BM * 128 + BN * 128) + 1024;
+        cudaError_t e = cudaFuncSetAttribute(conv_fwd_async_kernel<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
+        if (e != cudaSuccess) return e;
+        const dim3 grid((unsigned)((S.m_total + BM - 1) / BM), (unsigned)((S.n_total + BN - 1) / BN), 1);
+        conv_fwd_async_kernel<BN, ST><<<grid, THREADS, smem, stream>>>(a, b, bias, out, out_bf16, S, status);
+        return cudaGetLastError();
+    }
     const int smem = STAGES * (BM * 128 + BN * 128) + 1024;
     cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<OP, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
