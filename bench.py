@@ -50,6 +50,21 @@ def parse():
     return ap.parse_args()
 
 
+def job_throughput(ms_local, units_per_rank, steps, world, device=None):
+    """(max-over-ranks ms, whole-job units/s / 1e9): the slowest rank's time
+    decides; every rank processed units_per_rank per step (weak scaling, no
+    data-path collective).  With world > 1 the process group must exist."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_per_rank * steps * world / (ms / 1e3) / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -415,12 +430,8 @@ def run_ours(args):
     fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
     bp_ms = [e[1].elapsed_time(e[2]) for e in evs]
     res = float((sums[0] / sums[1]).sqrt())
-    if world > 1:
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = job_throughput(ms, units, args.steps, world, device)
     sec = ms / 1e3
-    value = units * args.steps * world / sec / 1e9
 
     # end to end through the host-buffer C ABI entry point
     e2e = None
