@@ -748,6 +748,7 @@ int ctrex_set_roi(ctrex_ctx *c, const ctrex_vol_grid *roi)
         R.hi[a] = (float)((hi[a] - c->origin[a]) / c->vox[a]);
     }
     R.step_mm = F.step_mm;
+    for (int a = 0; a < 3; ++a) R.n[a] = n[a];
     c->roi = true;
     return CTREX_OK;
 }

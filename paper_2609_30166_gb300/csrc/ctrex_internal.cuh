@@ -70,6 +70,7 @@ struct RoiGPU {
     float sc[3], oc[3];
     float lo[3], hi[3];
     float step_mm;  // the ROI grid's step
+    int n[3];       // the ROI grid's voxels per axis
 };
 
 template <typename T> struct Storage;

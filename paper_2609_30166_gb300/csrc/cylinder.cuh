@@ -61,6 +61,33 @@ __device__ __forceinline__ bool setup_ray_cyl(const Grid &G, const CylGPU &C, co
     return true;
 }
 
+// Angle of (x, y) in [-pi, pi]: octant reduction to z = min/max in [0, 1],
+// atan(z) ~ z P(z^2) with P of degree 7 (coefficients fitted by weighted
+// least squares at Chebyshev nodes, refined by Lawson passes toward the
+// minimax fit: csrc/fit_atan.py; FP32 error below 2e-7 rad), then the octant
+// restored.  The quotient uses the hardware reciprocal plus one Newton step.
+__device__ __forceinline__ float cyl_angle(float x, float y)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(mx));
+    const float z = mx > 0.0f ? mn * (r0 * fmaf(-mx, r0, 2.0f)) : 0.0f;
+    const float t = z * z;
+    float p = -4.693705589e-03f;
+    p = fmaf(p, t, 2.425401658e-02f);
+    p = fmaf(p, t, -5.948881805e-02f);
+    p = fmaf(p, t, 9.914478660e-02f);
+    p = fmaf(p, t, -1.401955634e-01f);
+    p = fmaf(p, t, 1.996974051e-01f);
+    p = fmaf(p, t, -3.333199322e-01f);
+    p = fmaf(p, t, 9.999998808e-01f);
+    float a = p * z;
+    if (ay > ax) a = 1.57079632679f - a;
+    if (x < 0.0f) a = 3.14159265359f - a;
+    return copysignf(a, y);
+}
+
 // Trilinear interpolation on the cylindrical grid at frame point (qx, qy,
 // qz): r clamped at the first ring centre, phi periodic, zero outside in r
 // and z.  Two gathers per sample, FP32 weights.
@@ -77,8 +104,9 @@ struct CylSampler {
     __device__ __forceinline__ float operator()(float qx, float qy, float qz, float &wsum) const
     {
         const float nphi = (float)C.n_phi;
-        const float r = sqrtf(fmaf(qx, qx, qy * qy));
-        float gp = fmaf(atan2f(qy, qx), C.inv_dphi, -0.5f);
+        const float q2 = fmaf(qx, qx, qy * qy);
+        const float r = q2 > 0.0f ? q2 * rsqrtf(q2) : 0.0f;
+        float gp = fmaf(cyl_angle(qx, qy), C.inv_dphi, -0.5f);
         if (gp < 0.0f) gp += nphi;
         if (gp >= nphi) gp -= nphi;  // -tiny + N_phi rounded up to N_phi
         const float gr = fmaxf(fmaf(r, C.inv_dr, -0.5f), 0.0f);

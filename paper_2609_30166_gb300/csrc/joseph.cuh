@@ -52,47 +52,55 @@ __device__ __forceinline__ void joseph_axes(int m, int &a1, int &a2)
     a2 = m == 2 ? 1 : 2;
 }
 
+// Component i of a 3-vector by selects (no local-memory indexing).
+__device__ __forceinline__ float jsel(const float v[3], int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); }
+__device__ __forceinline__ int jsel(int a, int b, int c, int i) { return i == 0 ? a : (i == 1 ? b : c); }
+
 // Returns false if no slice crossing in front of the source has a tap
 // inside the grid.
 __device__ __forceinline__ bool joseph_setup(const Grid &G, const ViewGPU &V, float u, float v, JRay &J)
 {
     float X[3], dg[3], len;
     ray_line(G, V, u, v, X, dg, len);
-    const int n[3] = {G.nx, G.ny, G.nz};
     int m = 0;
     if (fabsf(dg[1]) > fabsf(dg[m])) m = 1;
     if (fabsf(dg[2]) > fabsf(dg[m])) m = 2;
     int a1, a2;
     joseph_axes(m, a1, a2);
-    const float inv = 1.0f / dg[m];  // mm per index unit along m (signed)
+    const float dm = jsel(dg, m), Xm = jsel(X, m);
+    const float inv = 1.0f / dm;  // mm per index unit along m (signed)
     J.m = m;
     J.dl = fabsf(inv);
-    J.r1 = dg[a1] * inv;
-    J.r2 = dg[a2] * inv;
-    J.p0 = fmaf(-X[m], J.r1, X[a1]);
-    J.q0 = fmaf(-X[m], J.r2, X[a2]);
+    J.r1 = jsel(dg, a1) * inv;
+    J.r2 = jsel(dg, a2) * inv;
+    J.p0 = fmaf(-Xm, J.r1, jsel(X, a1));
+    J.q0 = fmaf(-Xm, J.r2, jsel(X, a2));
+    const int nm = jsel(G.nx, G.ny, G.nz, m), n1 = jsel(G.nx, G.ny, G.nz, a1), n2 = jsel(G.nx, G.ny, G.nz, a2);
     // closed bounds: the grid's slices, in front of the source (t >= -len)
-    const float ksrc = fmaf(-len, dg[m], X[m]);
+    const float ksrc = fmaf(-len, dm, Xm);
     J.kmin = 0;
-    J.kmax = n[m] - 1;
+    J.kmax = nm - 1;
     if (inv > 0.0f)
         J.kmin = max(J.kmin, (int)ceilf(fmaxf(ksrc, -1.0f)));
     else
-        J.kmax = min(J.kmax, (int)floorf(fminf(ksrc, (float)n[m])));
+        J.kmax = min(J.kmax, (int)floorf(fminf(ksrc, (float)nm)));
     // open bounds: both in-slice coordinates in (-1, n_a)
     float lo = -INFINITY, hi = INFINITY;
-    const float r[2] = {J.r1, J.r2}, c0[2] = {J.p0, J.q0};
-    const int na[2] = {n[a1], n[a2]};
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        if (r[i] != 0.0f) {
-            const float ri = 1.0f / r[i];
-            const float ka = (-1.0f - c0[i]) * ri, kb = ((float)na[i] - c0[i]) * ri;
-            lo = fmaxf(lo, fminf(ka, kb));
-            hi = fminf(hi, fmaxf(ka, kb));
-        } else if (!(c0[i] > -1.0f && c0[i] < (float)na[i])) {
-            return false;
-        }
+    if (J.r1 != 0.0f) {
+        const float ri = 1.0f / J.r1;
+        const float ka = (-1.0f - J.p0) * ri, kb = ((float)n1 - J.p0) * ri;
+        lo = fmaxf(lo, fminf(ka, kb));
+        hi = fminf(hi, fmaxf(ka, kb));
+    } else if (!(J.p0 > -1.0f && J.p0 < (float)n1)) {
+        return false;
+    }
+    if (J.r2 != 0.0f) {
+        const float ri = 1.0f / J.r2;
+        const float ka = (-1.0f - J.q0) * ri, kb = ((float)n2 - J.q0) * ri;
+        lo = fmaxf(lo, fminf(ka, kb));
+        hi = fminf(hi, fmaxf(ka, kb));
+    } else if (!(J.q0 > -1.0f && J.q0 < (float)n2)) {
+        return false;
     }
     lo = fmaxf(lo, (float)J.kmin - 1.0f);  // keep the floats in int range
     hi = fminf(hi, (float)J.kmax + 1.0f);
@@ -114,11 +122,13 @@ __device__ __forceinline__ void joseph_integral(const Grid &G, const JosephSampl
     if (!joseph_setup(G, V, u, v, J)) return;
     int a1, a2;
     joseph_axes(J.m, a1, a2);
-    const int n1 = smp.n[a1], n2 = smp.n[a2];
+    const int n1 = jsel(smp.n[0], smp.n[1], smp.n[2], a1), n2 = jsel(smp.n[0], smp.n[1], smp.n[2], a2);
     const int k0 = max(J.klo - 1, J.kmin), k1 = min(J.khi + 1, J.kmax);
-    const int tb = smp.tbase[J.m];
+    const int tb = jsel(smp.tbase[0], smp.tbase[1], smp.tbase[2], J.m);
     const Atlas &A = smp.base.A;
     float acc = 0.0f, wacc = 0.0f;
+    // unrolled so that several independent gathers are in flight per thread
+#pragma unroll 4
     for (int k = k0; k <= k1; ++k) {
         const float p = fmaf((float)k, J.r1, J.p0), q = fmaf((float)k, J.r2, J.q0);
         const float fp = floorf(p), fq = floorf(q);

@@ -36,21 +36,57 @@ struct RoiSampler {
     __device__ __forceinline__ float interior(float, float, float) const { return 0.0f; }
 };
 
+// Samples k of [0, K-1) whose eight taps all lie inside a grid of n voxels
+// per axis: g(k) = X + (a + (k + 1/2) h) dg in [eps, n - 1 - eps] on each
+// axis (the margin eps is far above the rounding of the positions), with one
+// sample of slack at each end.
+__device__ __forceinline__ void piece_interior(const float X[3], const float dg[3], float a, float h, int K,
+                                               const int n[3], int &ka, int &kb)
+{
+    const float eps = 1e-2f;
+    float lo = 0.0f, hi = (float)(K - 2);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float g0 = fmaf(a + 0.5f * h, dg[ax], X[ax]), sg = h * dg[ax];
+        const float l = eps, u = (float)(n[ax] - 1) - eps;
+        if (sg != 0.0f) {
+            const float inv = 1.0f / sg;
+            const float t0 = (l - g0) * inv, t1 = (u - g0) * inv;
+            lo = fmaxf(lo, fminf(t0, t1));
+            hi = fminf(hi, fmaxf(t0, t1));
+        } else if (!(g0 >= l && g0 <= u)) {
+            hi = -1.0f;
+        }
+    }
+    ka = min(max((int)ceilf(lo) + 1, 0), K - 1);
+    kb = max(min((int)floorf(hi), K - 1), ka);
+}
+
 // Truncated-midpoint samples of the piece [a, b] (mm along the ray) of the
-// line g(t) = X + t dg in the index coordinates of grid `smp`, step h (mm).
-__device__ __forceinline__ void roi_piece(const AtlasSampler &smp, const float X[3], const float dg[3], float a,
-                                          float b, float h, float &val, float &rs)
+// line g(t) = X + t dg in the index coordinates of grid `smp` (n voxels per
+// axis), step h (mm); samples with all taps inside take the short path.
+__device__ __forceinline__ void roi_piece(const AtlasSampler &smp, const int n[3], const float X[3],
+                                          const float dg[3], float a, float b, float h, float &val, float &rs)
 {
     if (!(b > a)) return;
     int K = (int)ceilf((b - a) / h);
     if (K < 1) K = 1;
+    int ka, kb;
+    piece_interior(X, dg, a, h, K, n, ka, kb);
     float acc = 0.0f, wacc = 0.0f;
-    for (int k = 0; k < K - 1; ++k) {
+    auto general = [&](int k) {
         const float t = fmaf((float)k + 0.5f, h, a);
         float ws;
         acc += smp(fmaf(t, dg[0], X[0]), fmaf(t, dg[1], X[1]), fmaf(t, dg[2], X[2]), ws);
         wacc += ws;
+    };
+    for (int k = 0; k < ka; ++k) general(k);
+    for (int k = ka; k < kb; ++k) {
+        const float t = fmaf((float)k + 0.5f, h, a);
+        acc += smp.interior(fmaf(t, dg[0], X[0]), fmaf(t, dg[1], X[1]), fmaf(t, dg[2], X[2]));
     }
+    wacc += (float)(kb - ka);
+    for (int k = kb; k < K - 1; ++k) general(k);
     const float a_last = fmaf((float)(K - 1), h, a);
     const float t_last = 0.5f * (a_last + b), w_last = b - a_last;
     float ws;
@@ -103,8 +139,9 @@ __device__ __forceinline__ long long roi_integral(const Grid &G, const RoiSample
         if (t1 > r1) n += max((int)ceilf((t1 - r1) / hc), 1);
         return n;
     }
+    const int nc[3] = {G.nx, G.ny, G.nz}, nr[3] = {R.n[0], R.n[1], R.n[2]};
     if (!hit) {
-        roi_piece(smp.ctx, X, dg, t0, t1, hc, val, rs);
+        roi_piece(smp.ctx, nc, X, dg, t0, t1, hc, val, rs);
         return 0;
     }
     // ROI index coordinates: g_roi = g_ctx * sc + oc per axis
@@ -114,9 +151,9 @@ __device__ __forceinline__ long long roi_integral(const Grid &G, const RoiSample
         Xf[a] = fmaf(X[a], R.sc[a], R.oc[a]);
         dgf[a] = dg[a] * R.sc[a];
     }
-    roi_piece(smp.ctx, X, dg, t0, r0, hc, val, rs);
-    roi_piece(smp.roi, Xf, dgf, r0, r1, hf, val, rs);
-    roi_piece(smp.ctx, X, dg, r1, t1, hc, val, rs);
+    roi_piece(smp.ctx, nc, X, dg, t0, r0, hc, val, rs);
+    roi_piece(smp.roi, nr, Xf, dgf, r0, r1, hf, val, rs);
+    roi_piece(smp.ctx, nc, X, dg, r1, t1, hc, val, rs);
     return 0;
 }
 

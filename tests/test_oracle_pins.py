@@ -1131,3 +1131,4 @@ def test_roi_backprojection_is_per_grid():
     vox_idx = np.array([0, 17, nc - 1, nc, nc + 100, b.size - 1])
     bv, cv = oracle.backproject_voxels(pb, r, vox_idx)
     assert np.array_equal(bv, b[vox_idx]) and np.array_equal(cv, c[vox_idx])
+
