@@ -22,6 +22,10 @@ constexpr int BP_CHUNK = 128;
 #ifndef CTREX_BP_MIN_BLOCKS
 #define CTREX_BP_MIN_BLOCKS 8  // CTAs per SM the register budget is sized for (full occupancy)
 #endif
+#ifndef CTREX_BP_UNROLL
+#define CTREX_BP_UNROLL 2  // views per unrolled step of the view loop (2 measured fastest)
+#endif
+constexpr int BP_UNROLL = CTREX_BP_UNROLL;
 #ifndef CTREX_BP_SUBV_MIN_BLOCKS
 #define CTREX_BP_SUBV_MIN_BLOCKS 5  // the same for the sub-voxel variant (48 registers)
 #endif
@@ -173,6 +177,7 @@ __global__ void __launch_bounds__(BP_THREADS, SUBV ? CTREX_BP_SUBV_MIN_BLOCKS : 
         }
         __syncthreads();
         if (!inside) continue;
+#pragma unroll BP_UNROLL
         for (int m = 0; m < cnt; ++m) {
             const float4 p0 = sP[m][0], p1 = sP[m][1], p2 = sP[m][2];
             const typename Images::Slot slot = sImg[m];
