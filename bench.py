@@ -47,6 +47,8 @@ def parse():
                     help="override the number of views (small cases for ncu captures; not a bench line)")
     ap.add_argument("--domain", default="cartesian", choices=["cartesian", "cylinder"],
                     help="cylinder: the SIRT step on the aligned cylindrical vial domain (Sec. 3.5); not a bench line")
+    ap.add_argument("--projector", default="trilinear", choices=["trilinear", "joseph"],
+                    help="forward projector of the step (joseph: classical Joseph); not a bench line")
     return ap.parse_args()
 
 
@@ -148,11 +150,11 @@ def l2_copy_bandwidth(device, mib=16, iters=200):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
 # launch of the fused forward kernel, from the one-pass ncu capture summarised
-# in profiles/fwd_kernel_perturbed512.md.  Valid only for the kernel sources it
+# in profiles/fwd_kernel_perturbed512.md (traffic_full_v5).  Valid only for the kernel sources it
 # was taken on (hash below) and for the FP32 workload; otherwise null.
-FWD_TRAFFIC_BYTES = 2332405504 + 1694862080
-FWD_TRAFFIC_SOURCES = ("project.cu", "atlas.cuh", "ray.cuh", "cylinder.cuh")
-FWD_TRAFFIC_HASH = "f289f91e37e0fe10"
+FWD_TRAFFIC_BYTES = 2329623296 + 1694207488
+FWD_TRAFFIC_SOURCES = ("project.cu", "atlas.cuh", "ray.cuh", "cylinder.cuh", "joseph.cuh", "roi.cuh", "fwd_common.cuh", "ctrex_internal.cuh")
+FWD_TRAFFIC_HASH = "5924e71ab0ae8414"
 
 
 def fwd_traffic(dtype, views):
@@ -390,6 +392,8 @@ def run_ours(args):
             cfg = cfg.scaled(n_views=args.views, name=f"{cfg.name}-views{args.views}")
         geo = cfg
     ctx, P, phantom, p, tdt = build_workload(cfg, device, args.dtype)
+    if args.projector != "trilinear":
+        ctx.set_projector(args.projector)
     n_samples = ctx.count_samples()
     nz_, ny_, nx_ = cfg.vol_shape
     n_updates = nz_ * ny_ * nx_ * geo.n_views * geo.n_sub
@@ -477,7 +481,7 @@ def run_ours(args):
         "kernel_ms": {"fwd_correct": statistics.mean(fwd_ms), "back_project": statistics.mean(bp_ms)},
         "residual_after": res,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None if cyl else fwd_traffic(args.dtype, args.views),
+                     "frac": achieved / peak, "traffic": None if (cyl or args.projector != "trilinear") else fwd_traffic(args.dtype, args.views),
                      "kernel": "fwd_kernel (fused forward + correction)",
                      "l2_gather": {"peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
                                    "peak_method": "torch copy of 16 MiB buffers resident in L2, read+write bytes"},
@@ -491,7 +495,8 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_rows and not args.views and not args.small and not cyl:
+    if rank == 0 and world == 1 and not args.no_rows and not args.views and not args.small and not cyl \
+            and args.projector == "trilinear":
         sm_count = torch.cuda.get_device_properties(device).multi_processor_count
         sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
         # sub-voxel backprojection (2^3 points per voxel) of the last step's
