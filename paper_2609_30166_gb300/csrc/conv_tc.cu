@@ -10,8 +10,10 @@
 //   * operands are gathered from global memory by the CTA's 128 threads
 //     (implicit im2col, so no TMA tiled box fits them) and written straight
 //     into the 128-byte-swizzled K-major shared-memory layout the UMMA
-//     descriptors describe; two stages, so the gather of chunk c+1 overlaps
-//     the MMAs of chunk c;
+//     descriptors describe; for FWD with channel counts that are multiples
+//     of 8 by asynchronous 16-byte copies (conv_fwd_async_kernel), otherwise
+//     by loads and stores; the gather of chunk c+1 overlaps the MMAs of
+//     chunk c;
 //   * one thread issues four tcgen05.mma (K = 16 each) per chunk and commits
 //     them to the stage's mbarrier; the accumulator tile lives in TMEM and is
 //     read back with tcgen05.ld by the four warps (one row per thread) for
@@ -640,7 +642,9 @@ cudaError_t launch_bn(const __nv_bfloat16 *a, const __nv_bfloat16 *b, const floa
                       const ConvShape &S, int *status, cudaStream_t stream)
 {
     if (OP == OP_FWD && (S.cin & 7) == 0) {
-        constexpr int ST = BN <= 64 ? 4 : 3;
+        // 2 stages for tiles up to 64 wide (more CTAs per SM beat a deeper
+        // prefetch there), 3 for wider ones: measured on the U-Net's layers
+        constexpr int ST = BN <= 64 ? 2 : 3;
         const int smem = ST * (BM * 128 + BN * 128) + 1024;
         cudaError_t e = cudaFuncSetAttribute(conv_fwd_async_kernel<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              smem);
