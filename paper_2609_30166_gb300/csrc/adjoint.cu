@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
                    const float *__restrict__ coef_g, const int *__restrict__ view_idx,
                    const float *__restrict__ proj, float *__restrict__ vol, unsigned *devcheck)
 {
-    __shared__ float s_coef[MOTION ? NCOEF : 1];
+    __shared__ float4 s_coef[MOTION ? NCOEF / 3 : 1];  // padded: one vector load per coefficient
     const int k = blockIdx.y;
     const int view = view_idx ? view_idx[k] : k;
     if (view < 0 || view >= G.n_views) {
@@ -57,11 +57,12 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
         return;
     }
     MotionGPU mo;
-    const float *coef = nullptr;
+    const float4 *coef = nullptr;
     if (MOTION) {
         mo = motion[view];
         if (coef_g) {
-            for (int i = threadIdx.y * ADJ_TX + threadIdx.x; i < NCOEF; i += ADJ_TX * ADJ_TY) s_coef[i] = coef_g[i];
+            for (int i = threadIdx.y * ADJ_TX + threadIdx.x; i < NCOEF / 3; i += ADJ_TX * ADJ_TY)
+                s_coef[i] = make_float4(coef_g[3 * i], coef_g[3 * i + 1], coef_g[3 * i + 2], 0.0f);
             coef = s_coef;
         }
         __syncthreads();

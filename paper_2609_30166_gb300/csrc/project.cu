@@ -38,7 +38,7 @@ __device__ __forceinline__ float LinearSampler<TV>::interior(float gx, float gy,
 // every sample is mapped to (r, phi, z) by the sampler; the rest is shared.
 template <typename Sampler, bool MOTION>
 __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__restrict__ views,
-                                               const MotionGPU &mo, const float *coef,
+                                               const MotionGPU &mo, const float4 *coef,
                                                const Sampler &vol, int view, float u,
                                                float v, float &val, float &rs)
 {
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
                const int *__restrict__ view_idx, TP *__restrict__ out, float *__restrict__ rowsum_out,
                const TP *__restrict__ p, float *__restrict__ partials, unsigned *devcheck, int p_by_view)
 {
-    __shared__ float s_coef[MOTION ? 8 * 8 * 8 * 3 : 1];
+    __shared__ float4 s_coef[MOTION ? 8 * 8 * 8 : 1];  // padded: one vector load per coefficient
     __shared__ float s_red[2][FWD_TX * FWD_TY / 32];
     __shared__ float2 s_tile[Sampler::TILE_TABLE];
     Sampler vol = vol_in;
@@ -137,12 +137,12 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
         view = 0;
     }
     MotionGPU mo;
-    const float *coef = nullptr;
+    const float4 *coef = nullptr;
     if (MOTION) {
         mo = motion[view];
         if (coef_g != nullptr) {
-            for (int i = threadIdx.y * FWD_TX + threadIdx.x; i < 8 * 8 * 8 * 3; i += FWD_TX * FWD_TY)
-                s_coef[i] = coef_g[i];
+            for (int i = threadIdx.y * FWD_TX + threadIdx.x; i < 8 * 8 * 8; i += FWD_TX * FWD_TY)
+                s_coef[i] = make_float4(coef_g[3 * i], coef_g[3 * i + 1], coef_g[3 * i + 2], 0.0f);
             coef = s_coef;
         }
         __syncthreads();

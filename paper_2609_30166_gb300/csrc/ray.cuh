@@ -176,11 +176,26 @@ __device__ __forceinline__ void spline_coord(float gp, float scale, int &i0, flo
     f = xi - fl;
 }
 
+// Coefficient (cx, cy, cz) of an [8][8][8] coefficient block: float triples
+// (3 scalar loads) or float4 padded to 16 bytes (one vector load).
+__device__ __forceinline__ float3 coef_at(const float *coef, int cx, int cy, int cz)
+{
+    const float *c = coef + 3 * ((cz * 8 + cy) * 8 + cx);
+    return make_float3(c[0], c[1], c[2]);
+}
+__device__ __forceinline__ float3 coef_at(const float4 *coef, int cx, int cy, int cz)
+{
+    const float4 c = coef[(cz * 8 + cy) * 8 + cx];
+    return make_float3(c.x, c.y, c.z);
+}
+
 // Warp of one sample (Sec. 2.2.2 pose, then Sec. 3.1 displacement): index
 // coordinates in, index coordinates out.  coef: shared-memory copy of the
-// [8][8][8][3] coefficients in voxels, or nullptr.
-__device__ __forceinline__ void warp_sample(const Grid &G, const MotionGPU &m, const float *coef,
-                                            const float g[3], float y[3])
+// [8][8][8] coefficients in voxels (float triples or padded float4), or
+// nullptr.
+template <typename CoefT>
+__device__ __forceinline__ void warp_sample(const Grid &G, const MotionGPU &m, const CoefT *coef, const float g[3],
+                                            float y[3])
 {
     float gp[3];
 #pragma unroll
@@ -203,14 +218,14 @@ __device__ __forceinline__ void warp_sample(const Grid &G, const MotionGPU &m, c
             for (int j = 0; j < 4; ++j) {
                 const int cy = min(i0[1] - 1 + j, 7);
                 const float wyz = wz[k] * wy[j];
-                const float *row = coef + 3 * ((cz * 8 + cy) * 8);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int cx = min(i0[0] - 1 + i, 7);
                     const float wt = wyz * wx[i];
-                    u0 = fmaf(wt, row[3 * cx + 0], u0);
-                    u1 = fmaf(wt, row[3 * cx + 1], u1);
-                    u2 = fmaf(wt, row[3 * cx + 2], u2);
+                    const float3 c = coef_at(coef, cx, cy, cz);
+                    u0 = fmaf(wt, c.x, u0);
+                    u1 = fmaf(wt, c.y, u1);
+                    u2 = fmaf(wt, c.z, u2);
                 }
             }
         }
