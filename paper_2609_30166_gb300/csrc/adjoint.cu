@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
         }
         __syncthreads();
     }
-    const int iu = blockIdx.x * ADJ_TX + threadIdx.x;
-    const int iv = blockIdx.z * ADJ_TY + threadIdx.y;
+    int iu, iv;
+    tile_pixel<MOTION>(blockIdx.x * ADJ_TX, blockIdx.z * ADJ_TY, iu, iv);
     if (iu >= G.nu || iv >= G.nv) return;
     const float y = proj[((size_t)k * G.nv + iv) * G.nu + iu] * G.inv_sub;
     if (y == 0.0f) return;
@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
     }
     __syncthreads();
     float gM[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
-    const int iu = blockIdx.x * ADJ_TX + threadIdx.x;
-    const int iv = blockIdx.z * ADJ_TY + threadIdx.y;
+    int iu, iv;
+    tile_pixel<true>(blockIdx.x * ADJ_TX, blockIdx.z * ADJ_TY, iu, iv);
     const bool pix_ok = iu < G.nu && iv < G.nv;
     const float y = pix_ok ? gproj[((size_t)k * G.nv + iv) * G.nu + iu] * G.inv_sub : 0.0f;
     float *gco = (coef_g && grad_coef) ? s_gcoef : nullptr;

@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
         }
         __syncthreads();
     }
-    const int iu = blockIdx.x * FWD_TX + threadIdx.x;
-    const int iv = blockIdx.z * FWD_TY + threadIdx.y;
+    int iu, iv;
+    tile_pixel<MOTION>(blockIdx.x * FWD_TX, blockIdx.z * FWD_TY, iu, iv);
     const bool in_pix = iu < G.nu && iv < G.nv;
     const bool inside = ok && in_pix;
     float val = 0.0f, rs = 0.0f;

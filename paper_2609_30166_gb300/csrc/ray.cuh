@@ -176,6 +176,25 @@ __device__ __forceinline__ void spline_coord(float gp, float scale, int &i0, flo
     f = xi - fl;
 }
 
+// Pixel of this thread in a 32 x 4 pixel CTA tile.  Row layout: warp w is
+// detector row w of the tile.  Patch layout (the motion kernels): warp w is
+// the 8 x 4 pixel patch at columns 8w .. 8w + 7, so a warp's samples lie
+// closer together and more often in one spline cell, whose coefficient
+// loads are then shared by the warp.
+template <bool PATCH>
+__device__ __forceinline__ void tile_pixel(int tile_u0, int tile_v0, int &iu, int &iv)
+{
+    if (PATCH) {
+        const int tid = threadIdx.y * 32 + threadIdx.x;
+        const int w = tid >> 5, l = tid & 31;
+        iu = tile_u0 + 8 * w + (l & 7);
+        iv = tile_v0 + (l >> 3);
+    } else {
+        iu = tile_u0 + threadIdx.x;
+        iv = tile_v0 + threadIdx.y;
+    }
+}
+
 // Coefficient (cx, cy, cz) of an [8][8][8] coefficient block: float triples
 // (3 scalar loads) or float4 padded to 16 bytes (one vector load).
 __device__ __forceinline__ float3 coef_at(const float *coef, int cx, int cy, int cz)
