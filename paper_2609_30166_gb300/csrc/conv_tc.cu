@@ -34,6 +34,10 @@
 
 namespace {
 
+#ifndef CTREX_CONV_BRICK
+#define CTREX_CONV_BRICK 1
+#endif
+
 constexpr int BM = 128;
 constexpr int BK = 64;
 constexpr int STAGES = 2;
@@ -64,6 +68,19 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
     d |= (uint64_t)(1024u >> 4) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Shared-memory matrix descriptor, K-major without swizzle: core matrices of
+// 8 rows x 16 bytes stored contiguously; lbo = byte stride between core
+// matrices along K, sbo = byte stride between 8-row groups along M (or N).
+__device__ __forceinline__ uint64_t sdesc_none(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
     return d;
 }
 
@@ -138,6 +155,47 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
 
 // Byte offset of 16-byte chunk j of row r in a 128B-swizzled K-major tile.
 __device__ __forceinline__ uint32_t swz(int r, int j) { return (uint32_t)(r * 128 + ((j ^ (r & 7)) << 4)); }
+
+// FWD epilogue of 16 accumulator columns of one output voxel (row): bias,
+// optional ReLU, channels c .. c+15 of y[row] (those below n_total).
+__device__ __forceinline__ void store16_fwd(const float v[16], const float *__restrict__ bias, void *__restrict__ out,
+                                            int out_bf16, const ConvShape &S, long long row, int c)
+{
+    float y[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int co = c + i;
+        y[i] = v[i] + ((bias && co < S.n_total) ? bias[co] : 0.0f);
+        if (S.relu) y[i] = fmaxf(y[i], 0.0f);
+    }
+    const long long o = row * S.n_total + c;
+    if ((S.n_total & 15) == 0) {  // 16 whole channels, 16-byte aligned
+        if (out_bf16) {
+            uint32_t pk[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(y[2 * i], y[2 * i + 1]);
+                pk[i] = *reinterpret_cast<const uint32_t *>(&h2);
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + o);
+            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        } else {
+            float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(out) + o);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dst[i] = make_float4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (c + i >= S.n_total) continue;
+            if (out_bf16)
+                static_cast<__nv_bfloat16 *>(out)[o + i] = __float2bfloat16_rn(y[i]);
+            else
+                static_cast<float *>(out)[o + i] = y[i];
+        }
+    }
+}
 
 // -------- operand loaders (write one BK-wide chunk of a tile into smem) ----
 
@@ -588,39 +646,171 @@ __global__ void __launch_bounds__(THREADS) conv_fwd_async_kernel(const __nv_bflo
             float v[16];
             tmem_ld16(lane_addr + (uint32_t)c0, v);
             if (row >= S.m_total || n0 + c0 >= S.n_total) continue;
-            float y[16];
+            store16_fwd(v, bias, out, out_bf16, S, row, n0 + c0);
+        }
+    } else if (nk > 0) {
+        if (threadIdx.x == 0) {
+            atomicExch(status, 1);
+            if (committed >= 0) mbar_wait(&bars[committed % ST], (unsigned)((committed / ST) & 1));
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// FWD with the input staged once per tile as a "brick" (channel counts that
+// are multiples of 16).  The output tile is 16 rows (y) x 8 NT voxels (x) of
+// one (n, z) plane; NT accumulators of 128 rows (8 x 16) sit side by side in
+// TMEM.  A pipeline step stages, for 16 input channels and one of the three
+// input planes z - 1, z, z + 1 (dz), the plane's (8 NT + 2) x 18 window of
+// the input (zero outside the volume) in the non-swizzled K-major layout --
+// position p of channel block b at b * NP * 16 + p * 16 bytes -- and the nine
+// taps' weights of that plane and channel range.  The A operand of tap
+// (dy, dx) for accumulator t is then the brick itself, shifted by
+// dy * RW + dx + 8 t positions: MMA row m = 8 g + i reads position
+// (g + dy) * RW + 8 t + i + dx, so the 8-row groups are RW positions apart
+// (SBO) and the two 8-channel halves of K one block apart (LBO).  Each input
+// element is copied into shared memory about (RW * 18 * 3) / (128 NT) times
+// instead of 27 times as in the im2col form.
+template <int BN, int NT, int ST>
+__global__ void __launch_bounds__(THREADS) conv_fwd_brick_kernel(const __nv_bfloat16 *__restrict__ x,
+                                                                 const __nv_bfloat16 *__restrict__ w,
+                                                                 const float *__restrict__ bias, void *__restrict__ out,
+                                                                 int out_bf16, ConvShape S, int *__restrict__ status)
+{
+    constexpr int RW = 8 * NT + 2;                // brick row length (positions)
+    constexpr int NP = RW * 18;                   // positions of one plane's window
+    constexpr int A_BYTES = NP * 32;              // two 8-channel blocks
+    constexpr int B_BYTES = 9 * 2 * BN * 16;      // nine taps x two 8-channel blocks x BN rows
+    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    constexpr int ACC = NT * BN;
+    constexpr int TMEM_COLS = ACC <= 32 ? 32 : (ACC <= 64 ? 64 : (ACC <= 128 ? 128 : 256));
+    static_assert(ACC <= 256, "accumulator columns");
+    static_assert(A_BYTES % 16 == 0 && B_BYTES % 16 == 0, "16-byte stage layout");
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t bars[ST];
+    __shared__ uint32_t tmem_base_s;
+
+    const int warp = threadIdx.x >> 5;
+    // tile -> (n, z, y0, x0)
+    const int tiles_x = (S.w + 8 * NT - 1) / (8 * NT), tiles_y = (S.h + 15) / 16;
+    long long t = blockIdx.x;
+    const int tx = (int)(t % tiles_x);
+    t /= tiles_x;
+    const int ty = (int)(t % tiles_y);
+    t /= tiles_y;
+    const int z = (int)(t % S.d), nb = (int)(t / S.d);
+    const int x0 = tx * 8 * NT, y0 = ty * 16;
+    const int n0 = blockIdx.y * BN;
+    const int cin = S.cin;
+    const long long wrow = 27LL * cin;
+    const int nk = 3 * (cin >> 4);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < ST; ++i) mbar_init(&bars[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base_s)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tmem_base_s;
+    constexpr uint32_t ID = idesc(BN);
+    // step s: channels 16 (s / 3) .. + 16 of input plane z + s % 3 - 1
+    auto issue = [&](int s) {
+        uint8_t *sA = smem + (s % ST) * STAGE_BYTES, *sB = sA + A_BYTES;
+        const int c16 = (s / 3) << 4, dz = s % 3;
+        const int zz = z + dz - 1;
+        const bool zin = (unsigned)zz < (unsigned)S.d;
+        const __nv_bfloat16 *plane = x + ((long long)nb * S.d + zz) * S.h * S.w * cin + c16;
+        for (int i = threadIdx.x; i < 2 * NP; i += THREADS) {
+            const int b = i >= NP, p = i - b * NP;
+            const int py = p / RW, px = p - py * RW;
+            const int yy = y0 + py - 1, xx = x0 + px - 1;
+            const bool in = zin && (unsigned)yy < (unsigned)S.h && (unsigned)xx < (unsigned)S.w;
+            cp_async16(sA + i * 16, in ? plane + ((long long)yy * S.w + xx) * cin + 8 * b : x, in ? 16 : 0);
+        }
+        for (int i = threadIdx.x; i < 18 * BN; i += THREADS) {
+            const int r = i % BN, jb = i / BN;  // jb = 2 * tap-in-plane + channel block
+            const int co = n0 + r;
+            const bool in = co < S.n_total;
+            const __nv_bfloat16 *src = w + co * wrow + (long long)(9 * dz + (jb >> 1)) * cin + c16 + 8 * (jb & 1);
+            cp_async16(sB + i * 16, in ? src : w, in ? 16 : 0);
+        }
+    };
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int co = n0 + c0 + i;
-                y[i] = v[i] + ((bias && co < S.n_total) ? bias[co] : 0.0f);
-                if (S.relu) y[i] = fmaxf(y[i], 0.0f);
+    for (int c = 0; c < ST - 1; ++c) {
+        if (c < nk) issue(c);
+        cp_async_commit();
+    }
+    bool ok = true;
+    int committed = -1;
+    for (int c = 0; c < nk; ++c) {
+        const int st = c % ST;
+        cp_async_wait<ST - 2>();
+        fence_async_smem();
+        tc_before_sync();
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        if (threadIdx.x == 0) {
+            tc_after_sync();
+            const uint32_t a_base = smem_addr(smem + st * STAGE_BYTES), b_base = a_base + A_BYTES;
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int dy = j / 3, dx = j - 3 * (j / 3);
+                const uint64_t bd = sdesc_none(b_base + (uint32_t)(j * 2 * BN * 16), (uint32_t)(BN * 16), 128u);
+#pragma unroll
+                for (int q = 0; q < NT; ++q) {
+                    const uint64_t ad =
+                        sdesc_none(a_base + (uint32_t)((dy * RW + dx + 8 * q) * 16), (uint32_t)(NP * 16), (uint32_t)(RW * 16));
+                    umma_bf16(tmem + (uint32_t)(q * BN), ad, bd, ID, c > 0 || j > 0);
+                }
             }
-            const long long o = row * S.n_total + n0 + c0;
-            if ((S.n_total & 15) == 0) {  // 16 whole channels, 16-byte aligned
-                if (out_bf16) {
-                    uint32_t pk[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(y[2 * i], y[2 * i + 1]);
-                        pk[i] = *reinterpret_cast<const uint32_t *>(&h2);
-                    }
-                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + o);
-                    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                } else {
-                    float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(out) + o);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) dst[i] = make_float4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]);
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    if (n0 + c0 + i >= S.n_total) continue;
-                    if (out_bf16)
-                        static_cast<__nv_bfloat16 *>(out)[o + i] = __float2bfloat16_rn(y[i]);
-                    else
-                        static_cast<float *>(out)[o + i] = y[i];
-                }
+            umma_commit(&bars[st]);
+        }
+        committed = c;
+        const int c2 = c + ST - 1;
+        if (c2 < nk) {
+            if (c2 >= ST && !mbar_wait(&bars[c2 % ST], (unsigned)((c2 / ST - 1) & 1))) ok = false;
+            if (ok) issue(c2);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    if (ok && nk > 0) {
+        const int last = nk - 1;
+        if (!mbar_wait(&bars[last % ST], (unsigned)((last / ST) & 1))) ok = false;
+    }
+    ok = __syncthreads_and(ok);
+    tc_after_sync();
+    if (ok && nk > 0) {
+        // thread (warp w, lane l) owns accumulator row m = 32 w + l of every
+        // accumulator: voxel (y0 + m / 8, x0 + 8 q + m % 8)
+        const int m = threadIdx.x;
+        const int y = y0 + (m >> 3);
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int q = 0; q < NT; ++q) {
+            const int xo = x0 + 8 * q + (m & 7);
+            const bool in = y < S.h && xo < S.w;
+            const long long row = (((long long)nb * S.d + z) * S.h + y) * S.w + xo;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float v[16];
+                tmem_ld16(lane_addr + (uint32_t)(q * BN + c0), v);
+                if (!in || n0 + c0 >= S.n_total) continue;
+                store16_fwd(v, bias, out, out_bf16, S, row, n0 + c0);
             }
         }
     } else if (nk > 0) {
@@ -637,10 +827,34 @@ __global__ void __launch_bounds__(THREADS) conv_fwd_async_kernel(const __nv_bflo
     }
 }
 
+// Brick-staged FWD launch: 4 stages for narrow N tiles, 3 for wide ones
+// (shared memory per stage grows with BN).
+template <int BN, int NT>
+cudaError_t launch_brick(const __nv_bfloat16 *x, const __nv_bfloat16 *w, const float *bias, void *out, int out_bf16,
+                         const ConvShape &S, int *status, cudaStream_t stream)
+{
+    constexpr int ST = BN <= 32 ? 4 : 3;
+    constexpr int RW = 8 * NT + 2, NP = RW * 18;
+    const int smem = ST * (NP * 32 + 9 * 2 * BN * 16) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(conv_fwd_brick_kernel<BN, NT, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)S.nb * S.d * ((S.h + 15) / 16) * ((S.w + 8 * NT - 1) / (8 * NT));
+    if (tiles > 0x7FFFFFFFLL) return cudaErrorInvalidConfiguration;
+    const dim3 grid((unsigned)tiles, (unsigned)((S.n_total + BN - 1) / BN), 1);
+    conv_fwd_brick_kernel<BN, NT, ST><<<grid, THREADS, smem, stream>>>(x, w, bias, out, out_bf16, S, status);
+    return cudaGetLastError();
+}
+
 template <int OP, int BN>
 cudaError_t launch_bn(const __nv_bfloat16 *a, const __nv_bfloat16 *b, const float *bias, void *out, int out_bf16,
                       const ConvShape &S, int *status, cudaStream_t stream)
 {
+    if (OP == OP_FWD && (S.cin & 15) == 0 && CTREX_CONV_BRICK) {
+        // tiles 16 x 16 (NT = 2) unless the volume is at most 8 wide
+        if (S.w > 8) return launch_brick<BN, 2>(a, b, bias, out, out_bf16, S, status, stream);
+        return launch_brick<BN, 1>(a, b, bias, out, out_bf16, S, status, stream);
+    }
     if (OP == OP_FWD && (S.cin & 7) == 0) {
         // 2 stages for tiles up to 64 wide (more CTAs per SM beat a deeper
         // prefetch there), 3 for wider ones: measured on the U-Net's layers
