@@ -27,7 +27,9 @@
 //         split across CTAs, partial tiles added to dw[co][(tap, ci)] (FP32).
 // Every wait on an mbarrier is bounded; on expiry the kernel records an error
 // in the status word, releases its TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "ctrex.h"
@@ -36,6 +38,12 @@ namespace {
 
 #ifndef CTREX_CONV_BRICK
 #define CTREX_CONV_BRICK 1
+#endif
+#ifndef CTREX_CONV_TMA
+#define CTREX_CONV_TMA 1
+#endif
+#ifndef CTREX_CONV_FILL
+#define CTREX_CONV_FILL 1
 #endif
 
 constexpr int BM = 128;
@@ -827,13 +835,416 @@ __global__ void __launch_bounds__(THREADS) conv_fwd_brick_kernel(const __nv_bflo
     }
 }
 
-// Brick-staged FWD launch: 4 stages for narrow N tiles, 3 for wide ones
-// (shared memory per stage grows with BN).
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised brick FWD with TMA (channel counts that are
+// multiples of 16).  Same tiles, steps and shared-memory operand layout as
+// conv_fwd_brick_kernel, but:
+//   * one thread (warp 0) streams the steps of all the CTA's tiles through an
+//     ST-deep ring with cp.async.bulk.tensor: per step two 5D boxes of the
+//     input (8 channels x RW x 18 positions of one plane; the tensor map
+//     zero-fills the halo outside the volume, including planes outside the
+//     batch item) and 18 2D boxes of the weights (8 channels x BN rows per
+//     tap and channel block), completing on the stage's mbarrier;
+//   * one thread (warp 1) issues the MMAs of each step and commits them to
+//     the stage's "empty" barrier, and a tile's last commit to the
+//     accumulator's "full" barrier; two accumulators alternate in TMEM, so the
+//     MMAs of tile i + 1 overlap the epilogue of tile i;
+//   * four epilogue warps (2..5; warp w reads TMEM lanes 32 (w % 4) ..)
+//     drain an accumulator, store it and release it.
+// Every wait is bounded; on expiry a thread raises the shared abort flag,
+// which ends the other roles' waits, and the CTA drains its own copies and
+// MMAs (bounded) before it frees TMEM.
+constexpr int TMA_THREADS = 192;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// One lane of the warp (all lanes converged): 1 there, 0 elsewhere.
+__device__ __forceinline__ uint32_t elect_one()
+{
+    uint32_t p;
+    asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n selp.u32 %0, 1, 0, e;\n}\n" : "=r"(p));
+    return p;
+}
+// Variants issued only by the lane whose `leader` is nonzero, so that the
+// surrounding loop stays warp-uniform.
+__device__ __forceinline__ void expect_tx_p(uint32_t leader, uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{\n .reg .pred e;\n setp.ne.b32 e, %0, 0;\n @e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n}\n" ::"r"(
+                     leader),
+                 "r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_5d_p(uint32_t leader, uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                              int c2, int c3, int c4, uint64_t *bar)
+{
+    asm volatile(
+        "{\n .reg .pred e;\n setp.ne.b32 e, %0, 0;\n"
+        " @e cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%1], [%2, {%3, %4, %5, "
+        "%6, %7}], [%8];\n}\n" ::"r"(leader),
+        "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d_p(uint32_t leader, uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                              uint64_t *bar)
+{
+    asm volatile(
+        "{\n .reg .pred e;\n setp.ne.b32 e, %0, 0;\n"
+        " @e cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%1], [%2, {%3, %4}], "
+        "[%5];\n}\n" ::"r"(leader),
+        "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void umma_bf16_p(uint32_t leader, uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id,
+                                            uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n setp.ne.b32 e, %5, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate), "r"(leader));
+}
+__device__ __forceinline__ void umma_commit_p(uint32_t leader, uint64_t *bar)
+{
+    asm volatile(
+        "{\n .reg .pred e;\n setp.ne.b32 e, %0, 0;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%1];\n}\n" ::"r"(leader),
+        "r"(smem_addr(bar))
+        : "memory");
+}
+// Warp-wide bounded wait (every lane returns the same answer); with an abort
+// flag it also gives up once another role raised it, and raises it itself on
+// expiry.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, unsigned parity, volatile int *abort_flag)
+{
+    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+        if (__any_sync(0xffffffffu, mbar_test(bar, parity))) return true;
+        if (abort_flag && (i & 255) == 255 && __any_sync(0xffffffffu, *abort_flag != 0)) return false;
+    }
+    if (abort_flag) *abort_flag = 1;
+    return false;
+}
+
+// Shared-memory plan of the TMA kernel (bytes; every TMA destination
+// 128-byte aligned, every stage 1024-byte aligned).  RESW: the whole filter
+// of the (single) N tile stays resident, loaded once per CTA (W_MAX bytes at
+// most), and the ring carries only the input windows.
+template <int BN, int NT, bool RESW>
+struct TmaPlan {
+    static constexpr int RW = 8 * NT + 2;
+    static constexpr int NP = RW * 18;
+    static constexpr int A_BLK = (NP * 16 + 127) / 128 * 128;  // one 8-channel block of the window
+    static constexpr int B_BLK = BN * 16;                       // one tap's 8-channel block of BN rows
+    static constexpr int W_MAX = 112 * 1024;                    // resident filter budget
+    static constexpr int W_BYTES = RESW ? W_MAX : 0;
+    static constexpr int STAGE = (2 * A_BLK + (RESW ? 0 : 18 * B_BLK) + 1023) / 1024 * 1024;
+    static constexpr uint32_t TX = 2u * NP * 16 + (RESW ? 0u : 18u * B_BLK);  // bytes the TMA writes per step
+    static constexpr int ACC = NT * BN;  // columns of one accumulator
+    static constexpr int TMEM_COLS = 2 * ACC <= 32 ? 32 : (2 * ACC <= 64 ? 64 : (2 * ACC <= 128 ? 128 : (2 * ACC <= 256 ? 256 : 512)));
+    static constexpr int RING = 200 * 1024 - W_BYTES;
+    static constexpr int ST = RING / STAGE < 8 ? RING / STAGE : 8;
+    static constexpr int SMEM = W_BYTES + ST * STAGE + 1024;
+    static_assert(2 * ACC <= 512, "two accumulators must fit in TMEM");
+    static_assert(ST >= 2, "at least two stages");
+    static_assert(B_BLK % 128 == 0 && W_BYTES % 1024 == 0, "aligned weight boxes");
+};
+
+template <int BN, int NT, bool RESW>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    conv_fwd_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
+                        const float *__restrict__ bias, void *__restrict__ out, int out_bf16, ConvShape S,
+                        int *__restrict__ status)
+{
+    using PL = TmaPlan<BN, NT, RESW>;
+    constexpr int ST = PL::ST, RW = PL::RW;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *wres = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *smem = wres + PL::W_BYTES;  // the ring
+    __shared__ uint64_t full[ST], empty[ST], acc_full[2], acc_empty[2], drain, wbar;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_x = (S.w + 8 * NT - 1) / (8 * NT), tiles_y = (S.h + 15) / 16;
+    const int n_tiles = (S.n_total + BN - 1) / BN;  // 1 with RESW
+    const long long items = (long long)S.nb * S.d * tiles_y * tiles_x * n_tiles;
+    const int nk = 3 * (S.cin >> 4);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < ST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 128);
+        }
+        mbar_init(&drain, 1);
+        mbar_init(&wbar, 1);
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmw)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base_s)),
+                     "r"(PL::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tmem_base_s;
+    volatile int *abort_flag = &abort_s;
+    // item -> (n, z, y0, x0, n0)
+    auto decode = [&](long long it, int &nb, int &z, int &y0, int &x0, int &n0) {
+        const int nt = (int)(it % n_tiles);
+        long long t = it / n_tiles;
+        const int tx = (int)(t % tiles_x);
+        t /= tiles_x;
+        const int ty = (int)(t % tiles_y);
+        t /= tiles_y;
+        z = (int)(t % S.d);
+        nb = (int)(t / S.d);
+        x0 = tx * 8 * NT;
+        y0 = ty * 16;
+        n0 = nt * BN;
+    };
+
+    if (warp == 0) {
+        // producer warp: the loop runs warp-wide (uniform descriptors and
+        // coordinates); one elected lane issues each copy
+        const uint32_t leader = elect_one();
+        long long fill = 0;
+        bool ok = true;
+        if (RESW) {
+            // the whole filter: block (tap t, channel block kb) of BN rows at
+            // (t * cin / 8 + kb) * B_BLK
+            const int kbs = S.cin >> 3;
+            expect_tx_p(leader, &wbar, (uint32_t)(27 * kbs * PL::B_BLK));
+            const uint32_t wb = smem_addr(wres);
+            for (int t = 0; t < 27; ++t)
+                for (int kb = 0; kb < kbs; ++kb)
+                    tma_load_2d_p(leader, wb + (uint32_t)((t * kbs + kb) * PL::B_BLK), &tmw, t * S.cin + 8 * kb, 0,
+                                  &wbar);
+        }
+        for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+            int nb, z, y0, x0, n0;
+            decode(it, nb, z, y0, x0, n0);
+            for (int s = 0; s < nk; ++s, ++fill) {
+                const int st = (int)(fill % ST);
+                if (fill >= ST && !mbar_wait_warp(&empty[st], (unsigned)(((fill / ST) - 1) & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const int c16 = (s / 3) << 4, dz = s % 3;
+                const uint32_t a = smem_addr(smem + st * PL::STAGE), b = a + 2 * PL::A_BLK;
+                expect_tx_p(leader, &full[st], PL::TX);
+                tma_load_5d_p(leader, a, &tmx, c16, x0 - 1, y0 - 1, z + dz - 1, nb, &full[st]);
+                tma_load_5d_p(leader, a + PL::A_BLK, &tmx, c16 + 8, x0 - 1, y0 - 1, z + dz - 1, nb, &full[st]);
+                if (!RESW) {
+#pragma unroll
+                    for (int j = 0; j < 9; ++j)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            tma_load_2d_p(leader, b + (uint32_t)((2 * j + h) * PL::B_BLK), &tmw,
+                                          (9 * dz + j) * S.cin + c16 + 8 * h, n0, &full[st]);
+                }
+            }
+        }
+        if (!ok) {
+            if (lane == 0) atomicExch(status, 1);
+            // the copies already issued land on their own: wait for the last
+            // fill of every stage and the filter (bounded)
+            for (long long f = fill - 1; f >= 0 && f >= fill - ST; --f)
+                mbar_wait_warp(&full[f % ST], (unsigned)((f / ST) & 1), nullptr);
+            if (RESW) mbar_wait_warp(&wbar, 0u, nullptr);
+        }
+    } else if (warp == 1) {
+        // MMA warp: the loop runs warp-wide; one elected lane issues the MMAs
+        // and commits
+        const uint32_t leader = elect_one();
+        constexpr uint32_t ID = idesc(BN);
+        long long fill = 0;
+        int tile_i = 0;
+        bool ok = !RESW || mbar_wait_warp(&wbar, 0u, abort_flag), issued = false;
+        const int kbs = S.cin >> 3;
+        for (long long it = blockIdx.x; it < items && ok; it += gridDim.x, ++tile_i) {
+            const int acc = tile_i & 1;
+            if (tile_i >= 2 && !mbar_wait_warp(&acc_empty[acc], (unsigned)(((tile_i >> 1) - 1) & 1), abort_flag)) {
+                ok = false;
+                break;
+            }
+            tc_after_sync();
+            const uint32_t d = tmem + (uint32_t)(acc * PL::ACC);
+            for (int s = 0; s < nk; ++s, ++fill) {
+                const int st = (int)(fill % ST);
+                if (!mbar_wait_warp(&full[st], (unsigned)((fill / ST) & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_after_sync();
+                const uint32_t a_base = smem_addr(smem + st * PL::STAGE);
+                // weights of tap (dz, j), channel blocks 2c and 2c + 1
+                const uint32_t b_base = RESW ? smem_addr(wres) + (uint32_t)((9 * (s % 3) * kbs + 2 * (s / 3)) * PL::B_BLK)
+                                             : a_base + 2 * PL::A_BLK;
+                const uint32_t b_tap = RESW ? (uint32_t)(kbs * PL::B_BLK) : (uint32_t)(2 * PL::B_BLK);
+                // descriptors are affine in the start address (16-byte units in
+                // the low field, far from overflowing it): one base per operand,
+                // a constant offset per tap
+                const uint64_t a0 = sdesc_none(a_base, (uint32_t)PL::A_BLK, (uint32_t)(RW * 16));
+                const uint64_t b0 = sdesc_none(b_base, (uint32_t)PL::B_BLK, 128u);
+                const uint64_t b_step = b_tap >> 4;
+#pragma unroll
+                for (int j = 0; j < 9; ++j) {
+                    const int dy = j / 3, dx = j - 3 * (j / 3);
+                    const uint64_t bd = b0 + (uint64_t)j * b_step;
+#pragma unroll
+                    for (int q = 0; q < NT; ++q)
+                        umma_bf16_p(leader, d + (uint32_t)(q * BN), a0 + (uint64_t)(dy * RW + dx + 8 * q), bd, ID,
+                                    (s > 0 || j > 0) ? 1u : 0u);
+                }
+                umma_commit_p(leader, &empty[st]);
+                issued = true;
+            }
+            if (ok) umma_commit_p(leader, &acc_full[acc]);
+        }
+        if (!ok) {
+            if (lane == 0) atomicExch(status, 1);
+            if (issued) {
+                umma_commit_p(leader, &drain);  // tracks every MMA the elected lane issued
+                mbar_wait_warp(&drain, 0u, nullptr);
+            }
+        }
+    } else {
+        // epilogue warps 2..5: accumulator rows 32 (warp % 4) + lane
+        const int quarter = warp & 3;
+        const int m = 32 * quarter + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+        int tile_i = 0;
+        for (long long it = blockIdx.x; it < items; it += gridDim.x, ++tile_i) {
+            const int acc = tile_i & 1;
+            if (!mbar_wait_warp(&acc_full[acc], (unsigned)((tile_i >> 1) & 1), abort_flag)) {
+                if (lane == 0) atomicExch(status, 1);
+                break;
+            }
+            tc_after_sync();
+            int nb, z, y0, x0, n0;
+            decode(it, nb, z, y0, x0, n0);
+            const int y = y0 + (m >> 3);
+#pragma unroll 1
+            for (int q = 0; q < NT; ++q) {
+                const int xo = x0 + 8 * q + (m & 7);
+                const bool in = y < S.h && xo < S.w;
+                const long long row = (((long long)nb * S.d + z) * S.h + y) * S.w + xo;
+#pragma unroll 1
+                for (int c0 = 0; c0 < BN; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(lane_base + (uint32_t)(acc * PL::ACC + q * BN + c0), v);
+                    if (!in || n0 + c0 >= S.n_total) continue;
+                    store16_fwd(v, bias, out, out_bf16, S, row, n0 + c0);
+                }
+            }
+            tc_before_sync();
+            mbar_arrive(&acc_empty[acc]);
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PL::TMEM_COLS) : "memory");
+    }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null if the driver does not provide it.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled()
+{
+    static const EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeTiledFn) nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+// Persistent TMA brick FWD: one CTA per SM.  Returns cudaErrorNotSupported
+// (nothing launched) when the tensor maps cannot be made, so that the
+// caller falls back to the cp.async brick kernel.
+template <int BN, int NT, bool RESW>
+cudaError_t launch_tma(const __nv_bfloat16 *x, const __nv_bfloat16 *w, const float *bias, void *out, int out_bf16,
+                       const ConvShape &S, int *status, cudaStream_t stream)
+{
+    using PL = TmaPlan<BN, NT, RESW>;
+    const EncodeTiledFn enc = encode_tiled();
+    const int sms = sm_count();
+    if (!enc || sms <= 0 || (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(w) & 15))
+        return cudaErrorNotSupported;
+    const uint64_t es = sizeof(__nv_bfloat16);
+    CUtensorMap mx, mw;
+    {
+        const cuuint64_t dims[5] = {(cuuint64_t)S.cin, (cuuint64_t)S.w, (cuuint64_t)S.h, (cuuint64_t)S.d, (cuuint64_t)S.nb};
+        const cuuint64_t strides[4] = {S.cin * es, (uint64_t)S.w * S.cin * es, (uint64_t)S.h * S.w * S.cin * es,
+                                       (uint64_t)S.d * S.h * S.w * S.cin * es};
+        const cuuint32_t box[5] = {8, (cuuint32_t)PL::RW, 18, 1, 1};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(x), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+    }
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)(27LL * S.cin), (cuuint64_t)S.n_total};
+        const cuuint64_t strides[1] = {27ULL * S.cin * es};
+        const cuuint32_t box[2] = {8, (cuuint32_t)BN};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(w), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+    }
+    cudaError_t e =
+        cudaFuncSetAttribute(conv_fwd_tma_kernel<BN, NT, RESW>, cudaFuncAttributeMaxDynamicSharedMemorySize, PL::SMEM);
+    if (e != cudaSuccess) return e;
+    const long long items = (long long)S.nb * S.d * ((S.h + 15) / 16) * ((S.w + 8 * NT - 1) / (8 * NT)) *
+                            ((S.n_total + BN - 1) / BN);
+    const unsigned grid = (unsigned)(items < sms ? items : sms);
+    conv_fwd_tma_kernel<BN, NT, RESW><<<grid, TMA_THREADS, PL::SMEM, stream>>>(mx, mw, bias, out, out_bf16, S, status);
+    return cudaGetLastError();
+}
+
+// Brick-staged FWD launch, 3 stages (measured faster than 4 for the narrow
+// N tiles too: more CTAs stay resident).
 template <int BN, int NT>
 cudaError_t launch_brick(const __nv_bfloat16 *x, const __nv_bfloat16 *w, const float *bias, void *out, int out_bf16,
                          const ConvShape &S, int *status, cudaStream_t stream)
 {
-    constexpr int ST = BN <= 32 ? 4 : 3;
+    constexpr int ST = 3;
     constexpr int RW = 8 * NT + 2, NP = RW * 18;
     const int smem = ST * (NP * 32 + 9 * 2 * BN * 16) + 1024;
     cudaError_t e = cudaFuncSetAttribute(conv_fwd_brick_kernel<BN, NT, ST>,
@@ -852,6 +1263,18 @@ cudaError_t launch_bn(const __nv_bfloat16 *a, const __nv_bfloat16 *b, const floa
 {
     if (OP == OP_FWD && (S.cin & 15) == 0 && CTREX_CONV_BRICK) {
         // tiles 16 x 16 (NT = 2) unless the volume is at most 8 wide
+        if (CTREX_CONV_TMA) {
+            // the filter stays resident when the layer has one N tile and it fits
+            const bool resw = S.n_total <= BN && 27LL * S.cin * BN * 2 <= TmaPlan<BN, 2, true>::W_MAX;
+            cudaError_t e;
+            if (S.w > 8)
+                e = resw ? launch_tma<BN, 2, true>(a, b, bias, out, out_bf16, S, status, stream)
+                         : launch_tma<BN, 2, false>(a, b, bias, out, out_bf16, S, status, stream);
+            else
+                e = resw ? launch_tma<BN, 1, true>(a, b, bias, out, out_bf16, S, status, stream)
+                         : launch_tma<BN, 1, false>(a, b, bias, out, out_bf16, S, status, stream);
+            if (e != cudaErrorNotSupported) return e;
+        }
         if (S.w > 8) return launch_brick<BN, 2>(a, b, bias, out, out_bf16, S, status, stream);
         return launch_brick<BN, 1>(a, b, bias, out, out_bf16, S, status, stream);
     }
@@ -927,7 +1350,15 @@ int ctrex_conv3d_fwd(const void *x, const void *w, const float *bias, void *y, i
     S.n_total = cout;
     S.k_total = 27LL * cin;
     S.k_per_cta = S.k_total;
-    const int bn = pick_bn(cout);
+    int bn = pick_bn(cout);
+    if (CTREX_CONV_BRICK && CTREX_CONV_FILL && (cin & 15) == 0) {
+        // narrower N tiles while the grid would leave SMs idle (deep layers
+        // at small spatial sizes); measured: narrowing further, to two CTAs
+        // per SM, costs more in brick reloads than it gains
+        const int nt = wd > 8 ? 2 : 1;
+        const long long tiles = (long long)nb * d * ((h + 15) / 16) * ((wd + 8 * nt - 1) / (8 * nt));
+        while (bn > 32 && tiles * ((cout + bn - 1) / bn) < 152) bn = bn > 64 ? 64 : 32;
+    }
     cudaError_t e = launch_op<OP_FWD>(bn, static_cast<const __nv_bfloat16 *>(x), static_cast<const __nv_bfloat16 *>(w),
                                       bias, y, y_dtype == CTREX_BF16, S, status, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? CTREX_OK : CTREX_E_CUDA;

@@ -77,9 +77,9 @@ class UNet3D(torch.nn.Module):
         super().__init__()
         g = torch.Generator().manual_seed(seed)
         c1, c2, c3, c4 = base, 2 * base, 4 * base, 8 * base
-        # the single input channel is carried in a block of 8 (zeros beside
-        # it), the channel granularity of the tensor-core gathers
-        self.e1 = torch.nn.ModuleList([Conv3(8, c1, gen=g), Conv3(c1, c1, gen=g)])
+        # the single input channel is carried in a block of 16 (zeros beside
+        # it), the channel granularity of the brick-staged tensor-core conv
+        self.e1 = torch.nn.ModuleList([Conv3(16, c1, gen=g), Conv3(c1, c1, gen=g)])
         self.e2 = torch.nn.ModuleList([Conv3(c1, c2, gen=g), Conv3(c2, c2, gen=g)])
         self.e3 = torch.nn.ModuleList([Conv3(c2, c3, gen=g), Conv3(c3, c3, gen=g)])
         self.e4 = torch.nn.ModuleList([Conv3(c3, c4, gen=g), Conv3(c4, c4, gen=g)])
@@ -97,7 +97,7 @@ class UNet3D(torch.nn.Module):
 
     def forward(self, x):
         """x: [N, D, H, W] float32 (D, H, W divisible by 8); returns the same shape."""
-        xin = torch.nn.functional.pad(x.to(torch.bfloat16).unsqueeze(-1), (0, 7)).contiguous()
+        xin = torch.nn.functional.pad(x.to(torch.bfloat16).unsqueeze(-1), (0, 15)).contiguous()
         s1 = self._block(self.e1, xin)
         s2 = self._block(self.e2, _pool(s1))
         s3 = self._block(self.e3, _pool(s2))

@@ -27,12 +27,14 @@ def _bf(a):
 
 
 # channel counts: 1 (scalar gathers), 8 and 24 (16-byte im2col copies), the
-# rest multiples of 16 (brick-staged input); spatial sizes ragged against the
-# 16 x 16 and 16 x 8 output tiles, several tiles per plane
+# rest multiples of 16 (brick-staged input, TMA; filters resident or
+# streamed, several N tiles); spatial sizes ragged against the 16 x 16 and
+# 16 x 8 output tiles, several tiles per plane
 @pytest.mark.parametrize("shape,cin,cout", [((1, 6, 7, 9), 1, 16), ((1, 6, 7, 9), 16, 48), ((2, 5, 8, 6), 48, 32),
                                             ((1, 8, 8, 8), 32, 192), ((1, 4, 4, 4), 96, 128),
                                             ((2, 3, 17, 19), 8, 16), ((1, 5, 9, 11), 24, 40),
-                                            ((1, 4, 35, 21), 32, 24), ((2, 3, 18, 40), 16, 16)])
+                                            ((1, 4, 35, 21), 32, 24), ((2, 3, 18, 40), 16, 16),
+                                            ((1, 3, 20, 19), 32, 160), ((1, 2, 17, 18), 192, 64)])
 def test_conv_fwd_matches_oracle(ct, shape, cin, cout):
     from oracle import conv
 
