@@ -46,6 +46,7 @@ namespace {
 #define CTREX_CONV_FILL 1
 #endif
 
+
 constexpr int BM = 128;
 constexpr int BK = 64;
 constexpr int STAGES = 2;
