@@ -48,10 +48,16 @@ class _Conv3(torch.autograd.Function):
 
 
 class Conv3(torch.nn.Module):
-    def __init__(self, cin, cout, relu=True, gen=None):
+    def __init__(self, cin, cout, relu=True, gen=None, init_cin=None):
+        """init_cin: draw (He initialisation) the weights of only the first
+        init_cin input channels and start the others at zero."""
         super().__init__()
-        std = math.sqrt(2.0 / (27 * cin))
-        self.w = torch.nn.Parameter(torch.randn(cout, 27, cin, generator=gen) * std)
+        ci = init_cin or cin
+        std = math.sqrt(2.0 / (27 * ci))
+        w = torch.randn(cout, 27, ci, generator=gen) * std
+        if ci < cin:
+            w = torch.nn.functional.pad(w, (0, cin - ci))
+        self.w = torch.nn.Parameter(w)
         self.b = torch.nn.Parameter(torch.zeros(cout))
         self.relu = relu
 
@@ -78,8 +84,11 @@ class UNet3D(torch.nn.Module):
         g = torch.Generator().manual_seed(seed)
         c1, c2, c3, c4 = base, 2 * base, 4 * base, 8 * base
         # the single input channel is carried in a block of 16 (zeros beside
-        # it), the channel granularity of the brick-staged tensor-core conv
-        self.e1 = torch.nn.ModuleList([Conv3(16, c1, gen=g), Conv3(c1, c1, gen=g)])
+        # it), the channel granularity of the brick-staged tensor-core conv;
+        # the first layer is initialised as for a block of 8: the weights of
+        # the other 8 start at zero and, facing zero inputs, get zero
+        # gradients, so they stay zero
+        self.e1 = torch.nn.ModuleList([Conv3(16, c1, gen=g, init_cin=8), Conv3(c1, c1, gen=g)])
         self.e2 = torch.nn.ModuleList([Conv3(c1, c2, gen=g), Conv3(c2, c2, gen=g)])
         self.e3 = torch.nn.ModuleList([Conv3(c2, c3, gen=g), Conv3(c3, c3, gen=g)])
         self.e4 = torch.nn.ModuleList([Conv3(c3, c4, gen=g), Conv3(c4, c4, gen=g)])
