@@ -1168,6 +1168,199 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient with the brick scheme (cin a multiple of 16, cout of 8):
+//   dW[co][tap][ci] = sum_p dy[p][co] x[p + off(tap)][ci].
+// A job is (co tile of 128, ci chunk of CN, input plane offset dz); a CTA
+// runs one job over a contiguous range of 16 x 16 position tiles and keeps
+// the nine taps' D_tap[co][ci] (128 lanes x 9 CN columns) in TMEM across the
+// whole range, adding them to dW (FP32 atomics) once at the end.
+// Operands are MN-major (channels contiguous, K = voxels), non-swizzled: a
+// core matrix is 8 voxels x 8 channels, 128 contiguous bytes; SBO = stride
+// between 8-channel blocks, LBO = stride between 8-voxel groups (confirmed
+// by an in-bounds descriptor probe).  Per tile and stage:
+//   * dy rows as [row g][co block][16 voxels] x 16 B (one TMA box through a
+//     map whose dimensions are (8 channels, x, co block, y, plane)); the MMA
+//     of row g reads A = dy^T at g * CB * 256 with SBO 256, LBO 128: K = the
+//     row's 16 voxels, M = 128 co (rows past cout read other rows' data and
+//     land in accumulator lanes that are never stored; the region is padded
+//     so that they stay inside it);
+//   * the input window of plane z + dz - 1 for the CN channels, three
+//     times, shifted by kx = 0, 1, 2 voxels: copy kx holds rows y0 - 1 ..
+//     y0 + 16 and columns x0 + kx - 1 .. + 15 as [kx][8-channel block][18
+//     rows][16 voxels] x 16 B.  The blocks (kx, channel block) are then
+//     equally spaced, so one MMA with N = 3 CN (SBO = the block stride,
+//     LBO 128) takes the three kx taps of row ky at once: B starts at
+//     row g + ky of every copy.
+// 16 rows x 3 ky = 48 MMAs of 128 x 3 CN x 16 per tile; tap (ky, kx) lands
+// in TMEM columns (3 ky + kx) CN .. + CN.
+template <int CN>
+struct WgPlan {
+    static constexpr int COPY = 18 * 16 * 16;  // one 8-channel block of a window copy: 18 rows x 16 voxels x 16 B
+    static constexpr int X_BYTES = 3 * (CN / 8) * COPY;
+    static constexpr uint32_t X_TX = X_BYTES;  // the boxes fill the copies exactly
+    static constexpr int NK = 3 * CN;           // N of one MMA: the three kx taps x CN channels
+    static constexpr int TMEM_COLS = 9 * CN <= 256 ? 256 : 512;
+    static_assert(9 * CN <= 512 && NK <= 256 && NK % 16 == 0, "TMEM columns and MMA shape");
+};
+
+struct WgArgs {
+    int cb;          // 8-channel co blocks loaded per tile (min(16, cout / 8))
+    int dy_region;   // bytes of the dy part of a stage (with the padding)
+    int stage;       // bytes of a stage
+    int st;          // ring depth (<= WG_MAX_ST)
+    int splits;      // position-tile ranges per job (gridDim.x)
+    long long tiles; // 16 x 16 position tiles
+};
+constexpr int WG_MAX_ST = 8;
+
+template <int CN>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    conv_wgrad_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmdy,
+                          float *__restrict__ dw, ConvShape S, WgArgs G, int *__restrict__ status)
+{
+    using PL = WgPlan<CN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full[WG_MAX_ST], empty[WG_MAX_ST], done, drain;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ST = G.st;
+    // job -> (co tile, ci chunk, dz); split -> tile range
+    const int chunks = S.cin / CN;
+    const int dz = blockIdx.y % 3;
+    const int ci0 = (int)((blockIdx.y / 3) % chunks) * CN;
+    const int co0 = (int)(blockIdx.y / 3 / chunks) * 128;
+    const long long t_begin = G.tiles * blockIdx.x / G.splits, t_end = G.tiles * (blockIdx.x + 1) / G.splits;
+    const int tiles_x = (S.w + 15) / 16, tiles_y = (S.h + 15) / 16;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < ST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&done, 1);
+        mbar_init(&drain, 1);
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmdy)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base_s)),
+                     "r"(PL::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tmem_base_s;
+    volatile int *abort_flag = &abort_s;
+    const bool any = t_end > t_begin;
+
+    if (warp == 0 && any) {
+        const uint32_t leader = elect_one();
+        const uint32_t tx = (uint32_t)(4096 * G.cb) + PL::X_TX;
+        long long i = 0;
+        bool ok = true;
+        for (long long t = t_begin; t < t_end; ++t, ++i) {
+            const int st = (int)(i % ST);
+            if (i >= ST && !mbar_wait_warp(&empty[st], (unsigned)(((i / ST) - 1) & 1), abort_flag)) {
+                ok = false;
+                break;
+            }
+            long long u = t;
+            const int x0 = (int)(u % tiles_x) * 16;
+            u /= tiles_x;
+            const int y0 = (int)(u % tiles_y) * 16;
+            u /= tiles_y;
+            const int z = (int)(u % S.d), nb = (int)(u / S.d);
+            const uint32_t a = smem_addr(smem + (size_t)st * G.stage), b = a + (uint32_t)G.dy_region;
+            expect_tx_p(leader, &full[st], tx);
+            tma_load_5d_p(leader, a, &tmdy, 0, x0, co0 >> 3, y0, nb * S.d + z, &full[st]);
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                for (int h = 0; h < CN / 8; ++h)
+                    tma_load_5d_p(leader, b + (uint32_t)((kx * (CN / 8) + h) * PL::COPY), &tmx, ci0 + 8 * h, x0 + kx - 1,
+                                  y0 - 1, z + dz - 1, nb, &full[st]);
+        }
+        if (!ok) {
+            if (lane == 0) atomicExch(status, 1);
+            for (long long f = i - 1; f >= 0 && f >= i - ST; --f) mbar_wait_warp(&full[f % ST], (unsigned)((f / ST) & 1), nullptr);
+        }
+    } else if (warp == 1 && any) {
+        const uint32_t leader = elect_one();
+        // kind::f16, D F32, A and B BF16, both MN-major, N = 3 CN, M = 128
+        constexpr uint32_t ID = idesc(PL::NK) | (1u << 15) | (1u << 16);
+        long long i = 0;
+        bool ok = true, issued = false;
+        const uint32_t row_step = (uint32_t)(G.cb * 256) >> 4;  // descriptor units per dy row
+        for (long long t = t_begin; t < t_end; ++t, ++i) {
+            const int st = (int)(i % ST);
+            if (!mbar_wait_warp(&full[st], (unsigned)((i / ST) & 1), abort_flag)) {
+                ok = false;
+                break;
+            }
+            tc_after_sync();
+            const uint32_t a_base = smem_addr(smem + (size_t)st * G.stage);
+            const uint64_t a0 = sdesc_none(a_base, 128u, 256u);
+            const uint64_t b0 = sdesc_none(a_base + (uint32_t)G.dy_region, 128u, (uint32_t)PL::COPY);
+#pragma unroll 1
+            for (int g = 0; g < 16; ++g) {
+                const uint64_t ad = a0 + (uint64_t)(g * row_step);
+                const uint32_t acc = (i > 0 || g > 0) ? 1u : 0u;
+#pragma unroll
+                for (int ky = 0; ky < 3; ++ky)  // row g + ky of every copy: 16 voxels x 16 B
+                    umma_bf16_p(leader, tmem + (uint32_t)(ky * PL::NK), ad, b0 + (uint64_t)((g + ky) * 16), ID, acc);
+            }
+            umma_commit_p(leader, &empty[st]);
+            issued = true;
+        }
+        if (ok) {
+            umma_commit_p(leader, &done);
+        } else {
+            if (lane == 0) atomicExch(status, 1);
+            if (issued) {
+                umma_commit_p(leader, &drain);
+                mbar_wait_warp(&drain, 0u, nullptr);
+            }
+        }
+    } else if (warp >= 2 && any) {
+        // epilogue: lane row m = co0 + 32 (warp % 4) + lane, once per CTA
+        const int quarter = warp & 3;
+        const int co = co0 + 32 * quarter + lane;
+        if (mbar_wait_warp(&done, 0u, abort_flag)) {
+            tc_after_sync();
+            const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+            const long long krow = 27LL * S.cin;
+#pragma unroll 1
+            for (int j = 0; j < 9; ++j) {
+#pragma unroll 1
+                for (int c0 = 0; c0 < CN; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(lane_base + (uint32_t)(j * CN + c0), v);
+                    if (co < S.cout) {
+                        float *dst = dw + co * krow + (long long)(9 * dz + j) * S.cin + ci0 + c0;
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) atomicAdd(dst + q, v[q]);
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            atomicExch(status, 1);
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PL::TMEM_COLS) : "memory");
+    }
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library); null if the driver does not provide it.
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -1236,6 +1429,68 @@ cudaError_t launch_tma(const __nv_bfloat16 *x, const __nv_bfloat16 *w, const flo
                             ((S.n_total + BN - 1) / BN);
     const unsigned grid = (unsigned)(items < sms ? items : sms);
     conv_fwd_tma_kernel<BN, NT, RESW><<<grid, TMA_THREADS, PL::SMEM, stream>>>(mx, mw, bias, out, out_bf16, S, status);
+    return cudaGetLastError();
+}
+
+// Brick weight gradient: returns cudaErrorNotSupported (nothing launched)
+// when the tensor maps cannot be made.
+template <int CN>
+cudaError_t launch_wgrad_tma(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, float *dw, const ConvShape &S,
+                             int *status, cudaStream_t stream)
+{
+    using PL = WgPlan<CN>;
+    const EncodeTiledFn enc = encode_tiled();
+    const int sms = sm_count();
+    if (!enc || sms <= 0 || (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(dy) & 15))
+        return cudaErrorNotSupported;
+    const uint64_t es = sizeof(__nv_bfloat16);
+    CUtensorMap mx, mdy;
+    {
+        const cuuint64_t dims[5] = {(cuuint64_t)S.cin, (cuuint64_t)S.w, (cuuint64_t)S.h, (cuuint64_t)S.d, (cuuint64_t)S.nb};
+        const cuuint64_t strides[4] = {S.cin * es, (uint64_t)S.w * S.cin * es, (uint64_t)S.h * S.w * S.cin * es,
+                                       (uint64_t)S.d * S.h * S.w * S.cin * es};
+        const cuuint32_t box[5] = {8, 16, 18, 1, 1};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(x), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+    }
+    const int cb = S.cout / 8 < 16 ? S.cout / 8 : 16;
+    {
+        // (8 channels, x, 8-channel block, y, plane): the box lands as
+        // [y][block][x][8 channels]
+        const cuuint64_t dims[5] = {8, (cuuint64_t)S.w, (cuuint64_t)(S.cout / 8), (cuuint64_t)S.h,
+                                    (cuuint64_t)S.nb * S.d};
+        const cuuint64_t strides[4] = {S.cout * es, 16, (uint64_t)S.w * S.cout * es, (uint64_t)S.h * S.w * S.cout * es};
+        const cuuint32_t box[5] = {8, 16, (cuuint32_t)cb, 16, 1};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        if (enc(&mdy, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(dy), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+    }
+    WgArgs G{};
+    G.cb = cb;
+    // rows 0..15 of cb blocks each; row 15's 16 M blocks read up to
+    // 15 * cb * 256 + 16 * 256 bytes
+    G.dy_region = (256 * (15 * cb + 16) + 1023) / 1024 * 1024;
+    G.stage = (G.dy_region + PL::X_BYTES + 1023) / 1024 * 1024;
+    G.st = (200 * 1024) / G.stage;
+    if (G.st > WG_MAX_ST) G.st = WG_MAX_ST;
+    if (G.st < 2) return cudaErrorNotSupported;
+    const int smem = G.st * G.stage + 1024;
+    G.tiles = (long long)S.nb * S.d * ((S.h + 15) / 16) * ((S.w + 15) / 16);
+    const long long jobs = (long long)((S.cout + 127) / 128) * (S.cin / CN) * 3;
+    if (jobs > 65535) return cudaErrorNotSupported;
+    long long splits = sms / jobs;
+    if (splits < 1) splits = 1;
+    if (splits > G.tiles) splits = G.tiles;
+    G.splits = (int)splits;
+    cudaError_t e = cudaFuncSetAttribute(conv_wgrad_tma_kernel<CN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    conv_wgrad_tma_kernel<CN><<<dim3((unsigned)splits, (unsigned)jobs, 1), TMA_THREADS, smem, stream>>>(mx, mdy, dw, S, G,
+                                                                                                      status);
     return cudaGetLastError();
 }
 
@@ -1387,6 +1642,16 @@ int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, 
     per = ((per + BK - 1) / BK) * BK;
     if (per < BK) per = BK;
     S.k_per_cta = per;
+    if (CTREX_CONV_TMA && (cin & 15) == 0) {
+        // 32-channel chunks where two ring stages still fit beside the dy rows
+        const cudaError_t e = (cin & 31) == 0 && cout <= 64 ? launch_wgrad_tma<32>(static_cast<const __nv_bfloat16 *>(x),
+                                                                        static_cast<const __nv_bfloat16 *>(dy), dw, S,
+                                                                        status, static_cast<cudaStream_t>(stream))
+                                              : launch_wgrad_tma<16>(static_cast<const __nv_bfloat16 *>(x),
+                                                                        static_cast<const __nv_bfloat16 *>(dy), dw, S,
+                                                                        status, static_cast<cudaStream_t>(stream));
+        if (e != cudaErrorNotSupported) return e == cudaSuccess ? CTREX_OK : CTREX_E_CUDA;
+    }
     const int bn = pick_bn(cout);
     cudaError_t e = launch_op<OP_WGRAD>(bn, static_cast<const __nv_bfloat16 *>(x),
                                         static_cast<const __nv_bfloat16 *>(dy), nullptr, dw, 0, S, status,
