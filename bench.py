@@ -369,7 +369,7 @@ def measure_rows(device, gather_peak, sm_count, sm_mhz):
     rows["a12_conv3d_tcgen05"] = {"layers": convs, "best_fwd_tflops": best, "bf16_peak_tflops": bf16_peak,
                                   "best_fwd_frac": best / bf16_peak,
                                   "kernels": {"fwd": "conv_fwd_tma_kernel (persistent, TMA, brick-staged input)",
-                                              "wgrad": "conv_tc_kernel (split-K over voxels)"}}
+                                              "wgrad": "conv_wgrad_tma_kernel (MN-major brick, kx taps folded into N)"}}
     torch.cuda.empty_cache()
     return rows
 
