@@ -402,6 +402,7 @@ int ctrex_count_samples(ctrex_ctx *ctx, const int *view_idx, int n_idx, long lon
  *   status  DEVICE int, set to 1 if a tensor-core completion wait expired
  *           (the result is then invalid); never cleared by the library.
  *   stream  cudaStream_t (NULL = legacy default stream).
+ * x, wt and y must be 16-byte aligned (CTREX_E_ARG otherwise).
  * The input gradient is this same call on dy with the flipped, transposed
  * weights wt'[ci][26 - tap][co].  Errors: CTREX_E_ARG, CTREX_E_DTYPE,
  * CTREX_E_SHAPE, CTREX_E_CUDA.
@@ -412,10 +413,11 @@ int ctrex_conv3d_fwd(const void *x, const void *wt, const float *bias, void *y, 
 /*
  * Weight gradient of ctrex_conv3d_fwd: dw[co][tap][ci] += sum over voxels of
  * dy[voxel][co] * x[voxel + offset(tap)][ci] (zero outside).  The voxel sum
- * is split across CTAs and added with FP32 atomics (not bitwise
- * reproducible).  x bf16 [nb][d][h][w][cin], dy bf16 [nb][d][h][w][cout],
+ * is split across CTAs whose partial sums are added with FP32 atomics (not
+ * bitwise reproducible).  x bf16 [nb][d][h][w][cin], dy bf16 [nb][d][h][w][cout],
  * dw DEVICE float [cout][27][cin] (accumulated: zero it first).  cin and
- * cout must be multiples of 8 (CTREX_E_SHAPE otherwise).
+ * cout must be multiples of 8 (CTREX_E_SHAPE otherwise); x and dy must be
+ * 16-byte aligned (CTREX_E_ARG otherwise).
  */
 int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, int h, int w, int cin,
                        int cout, int *status, void *cuda_stream);

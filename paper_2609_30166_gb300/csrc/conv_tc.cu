@@ -4,29 +4,32 @@
 // tensor memory (TMEM).  The paper has no such operator; it motivates learned
 // components combined with the physics operators (Sec. 5).
 //
-// One kernel computes C[M][N] = sum_k A[M][k] B[N][k] tile by tile:
-//   * M tile 128 (one UMMA row block, cta_group::1), N tile = BN in {16..128},
-//     K staged 64 elements (one 128-byte row per operand row) at a time;
-//   * operands are gathered from global memory by the CTA's 128 threads
-//     (implicit im2col, so no TMA tiled box fits them) and written straight
-//     into the 128-byte-swizzled K-major shared-memory layout the UMMA
-//     descriptors describe; for FWD with channel counts that are multiples
-//     of 8 by asynchronous 16-byte copies (conv_fwd_async_kernel), otherwise
-//     by loads and stores; the gather of chunk c+1 overlaps the MMAs of
-//     chunk c;
-//   * one thread issues four tcgen05.mma (K = 16 each) per chunk and commits
-//     them to the stage's mbarrier; the accumulator tile lives in TMEM and is
-//     read back with tcgen05.ld by the four warps (one row per thread) for
-//     the epilogue.
-// Three operand layouts use it:
+// All kernels compute C[M][N] = sum_k A[M][k] B[N][k] with tcgen05.mma
+// (kind::f16, M = 128, cta_group::1), accumulators in TMEM read back with
+// tcgen05.ld for the epilogue.  Two families:
+//   * brick kernels (channel counts that are multiples of 16): TMA stages the
+//     input window a tile's taps reach once ("brick") and every tap's operand
+//     is the brick at a shifted descriptor start address, so no im2col is
+//     formed; persistent and warp-specialised (a TMA producer warp, an MMA
+//     warp, epilogue warps):
+//       conv_fwd_tma_kernel     forward and input gradient,
+//       conv_wgrad_tma_kernel   weight gradient (MN-major operands, K = voxels);
+//   * im2col kernels (other channel counts, and the fallback when no tensor
+//     map can be made): the CTA's 128 threads gather implicit-im2col chunks
+//     of 64 K elements into 128-byte-swizzled K-major tiles (16-byte cp.async
+//     copies for multiples of 8 channels: conv_fwd_async_kernel; loads and
+//     stores otherwise: conv_tc_kernel), one thread issues four MMAs per
+//     chunk.
+// Operand layouts:
 //   FWD   A = im2col(x)[m][(tap, ci)], B = w[co][(tap, ci)], C -> y[m][co]
 //         (+ bias, optional ReLU);  m runs over N*D*H*W output voxels (NDHWC).
 //   DGRAD the same with dy as input and the flipped, transposed weights
 //         w'[ci][(tap, co)] (prepared by the caller): dx = conv(dy, w').
-//   WGRAD A = im2col(x)^T[(tap, ci)][m], B = dy^T[co][m]: K runs over voxels,
-//         split across CTAs, partial tiles added to dw[co][(tap, ci)] (FP32).
+//   WGRAD dw[co][(tap, ci)] = sum over voxels of dy[m][co] x[m + off(tap)][ci]
+//         (FP32, partial sums added with atomics).
 // Every wait on an mbarrier is bounded; on expiry the kernel records an error
-// in the status word, releases its TMEM and returns.
+// in the status word, drains what it issued (bounded), releases its TMEM and
+// returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -36,9 +39,6 @@
 
 namespace {
 
-#ifndef CTREX_CONV_BRICK
-#define CTREX_CONV_BRICK 1
-#endif
 #ifndef CTREX_CONV_TMA
 #define CTREX_CONV_TMA 1
 #endif
@@ -671,190 +671,39 @@ __global__ void __launch_bounds__(THREADS) conv_fwd_async_kernel(const __nv_bflo
     }
 }
 
-// FWD with the input staged once per tile as a "brick" (channel counts that
-// are multiples of 16).  The output tile is 16 rows (y) x 8 NT voxels (x) of
-// one (n, z) plane; NT accumulators of 128 rows (8 x 16) sit side by side in
-// TMEM.  A pipeline step stages, for 16 input channels and one of the three
-// input planes z - 1, z, z + 1 (dz), the plane's (8 NT + 2) x 18 window of
-// the input (zero outside the volume) in the non-swizzled K-major layout --
-// position p of channel block b at b * NP * 16 + p * 16 bytes -- and the nine
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised FWD with the input staged as "bricks" by TMA
+// (channel counts that are multiples of 16).
+// Tiles: 16 rows (y) x 8 NT voxels (x) of one (n, z) plane; NT accumulators
+// of 128 rows (8 x 16) sit side by side in TMEM.  A pipeline step stages, for
+// 16 input channels and one of the three input planes z - 1, z, z + 1 (dz),
+// the plane's (8 NT + 2) x 18 window (zero outside the volume) in the
+// non-swizzled K-major layout -- position p of 8-channel block b at
+// b * A_BLK + p * 16 bytes -- plus, unless the filter is resident, the nine
 // taps' weights of that plane and channel range.  The A operand of tap
-// (dy, dx) for accumulator t is then the brick itself, shifted by
+// (dy, dx) for accumulator t is the window itself, shifted by
 // dy * RW + dx + 8 t positions: MMA row m = 8 g + i reads position
 // (g + dy) * RW + 8 t + i + dx, so the 8-row groups are RW positions apart
 // (SBO) and the two 8-channel halves of K one block apart (LBO).  Each input
 // element is copied into shared memory about (RW * 18 * 3) / (128 NT) times
-// instead of 27 times as in the im2col form.
-template <int BN, int NT, int ST>
-__global__ void __launch_bounds__(THREADS) conv_fwd_brick_kernel(const __nv_bfloat16 *__restrict__ x,
-                                                                 const __nv_bfloat16 *__restrict__ w,
-                                                                 const float *__restrict__ bias, void *__restrict__ out,
-                                                                 int out_bf16, ConvShape S, int *__restrict__ status)
-{
-    constexpr int RW = 8 * NT + 2;                // brick row length (positions)
-    constexpr int NP = RW * 18;                   // positions of one plane's window
-    constexpr int A_BYTES = NP * 32;              // two 8-channel blocks
-    constexpr int B_BYTES = 9 * 2 * BN * 16;      // nine taps x two 8-channel blocks x BN rows
-    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    constexpr int ACC = NT * BN;
-    constexpr int TMEM_COLS = ACC <= 32 ? 32 : (ACC <= 64 ? 64 : (ACC <= 128 ? 128 : 256));
-    static_assert(ACC <= 256, "accumulator columns");
-    static_assert(A_BYTES % 16 == 0 && B_BYTES % 16 == 0, "16-byte stage layout");
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t bars[ST];
-    __shared__ uint32_t tmem_base_s;
-
-    const int warp = threadIdx.x >> 5;
-    // tile -> (n, z, y0, x0)
-    const int tiles_x = (S.w + 8 * NT - 1) / (8 * NT), tiles_y = (S.h + 15) / 16;
-    long long t = blockIdx.x;
-    const int tx = (int)(t % tiles_x);
-    t /= tiles_x;
-    const int ty = (int)(t % tiles_y);
-    t /= tiles_y;
-    const int z = (int)(t % S.d), nb = (int)(t / S.d);
-    const int x0 = tx * 8 * NT, y0 = ty * 16;
-    const int n0 = blockIdx.y * BN;
-    const int cin = S.cin;
-    const long long wrow = 27LL * cin;
-    const int nk = 3 * (cin >> 4);
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < ST; ++i) mbar_init(&bars[i], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base_s)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_before_sync();
-    __syncthreads();
-    tc_after_sync();
-    const uint32_t tmem = tmem_base_s;
-    constexpr uint32_t ID = idesc(BN);
-    // step s: channels 16 (s / 3) .. + 16 of input plane z + s % 3 - 1
-    auto issue = [&](int s) {
-        uint8_t *sA = smem + (s % ST) * STAGE_BYTES, *sB = sA + A_BYTES;
-        const int c16 = (s / 3) << 4, dz = s % 3;
-        const int zz = z + dz - 1;
-        const bool zin = (unsigned)zz < (unsigned)S.d;
-        const __nv_bfloat16 *plane = x + ((long long)nb * S.d + zz) * S.h * S.w * cin + c16;
-        for (int i = threadIdx.x; i < 2 * NP; i += THREADS) {
-            const int b = i >= NP, p = i - b * NP;
-            const int py = p / RW, px = p - py * RW;
-            const int yy = y0 + py - 1, xx = x0 + px - 1;
-            const bool in = zin && (unsigned)yy < (unsigned)S.h && (unsigned)xx < (unsigned)S.w;
-            cp_async16(sA + i * 16, in ? plane + ((long long)yy * S.w + xx) * cin + 8 * b : x, in ? 16 : 0);
-        }
-        for (int i = threadIdx.x; i < 18 * BN; i += THREADS) {
-            const int r = i % BN, jb = i / BN;  // jb = 2 * tap-in-plane + channel block
-            const int co = n0 + r;
-            const bool in = co < S.n_total;
-            const __nv_bfloat16 *src = w + co * wrow + (long long)(9 * dz + (jb >> 1)) * cin + c16 + 8 * (jb & 1);
-            cp_async16(sB + i * 16, in ? src : w, in ? 16 : 0);
-        }
-    };
-#pragma unroll
-    for (int c = 0; c < ST - 1; ++c) {
-        if (c < nk) issue(c);
-        cp_async_commit();
-    }
-    bool ok = true;
-    int committed = -1;
-    for (int c = 0; c < nk; ++c) {
-        const int st = c % ST;
-        cp_async_wait<ST - 2>();
-        fence_async_smem();
-        tc_before_sync();
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
-        }
-        if (threadIdx.x == 0) {
-            tc_after_sync();
-            const uint32_t a_base = smem_addr(smem + st * STAGE_BYTES), b_base = a_base + A_BYTES;
-#pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                const int dy = j / 3, dx = j - 3 * (j / 3);
-                const uint64_t bd = sdesc_none(b_base + (uint32_t)(j * 2 * BN * 16), (uint32_t)(BN * 16), 128u);
-#pragma unroll
-                for (int q = 0; q < NT; ++q) {
-                    const uint64_t ad =
-                        sdesc_none(a_base + (uint32_t)((dy * RW + dx + 8 * q) * 16), (uint32_t)(NP * 16), (uint32_t)(RW * 16));
-                    umma_bf16(tmem + (uint32_t)(q * BN), ad, bd, ID, c > 0 || j > 0);
-                }
-            }
-            umma_commit(&bars[st]);
-        }
-        committed = c;
-        const int c2 = c + ST - 1;
-        if (c2 < nk) {
-            if (c2 >= ST && !mbar_wait(&bars[c2 % ST], (unsigned)((c2 / ST - 1) & 1))) ok = false;
-            if (ok) issue(c2);
-        }
-        cp_async_commit();
-    }
-    cp_async_wait<0>();
-    if (ok && nk > 0) {
-        const int last = nk - 1;
-        if (!mbar_wait(&bars[last % ST], (unsigned)((last / ST) & 1))) ok = false;
-    }
-    ok = __syncthreads_and(ok);
-    tc_after_sync();
-    if (ok && nk > 0) {
-        // thread (warp w, lane l) owns accumulator row m = 32 w + l of every
-        // accumulator: voxel (y0 + m / 8, x0 + 8 q + m % 8)
-        const int m = threadIdx.x;
-        const int y = y0 + (m >> 3);
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-        for (int q = 0; q < NT; ++q) {
-            const int xo = x0 + 8 * q + (m & 7);
-            const bool in = y < S.h && xo < S.w;
-            const long long row = (((long long)nb * S.d + z) * S.h + y) * S.w + xo;
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                float v[16];
-                tmem_ld16(lane_addr + (uint32_t)(q * BN + c0), v);
-                if (!in || n0 + c0 >= S.n_total) continue;
-                store16_fwd(v, bias, out, out_bf16, S, row, n0 + c0);
-            }
-        }
-    } else if (nk > 0) {
-        if (threadIdx.x == 0) {
-            atomicExch(status, 1);
-            if (committed >= 0) mbar_wait(&bars[committed % ST], (unsigned)((committed / ST) & 1));
-        }
-    }
-    tc_before_sync();
-    __syncthreads();
-    if (warp == 0) {
-        tc_after_sync();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Persistent, warp-specialised brick FWD with TMA (channel counts that are
-// multiples of 16).  Same tiles, steps and shared-memory operand layout as
-// conv_fwd_brick_kernel, but:
-//   * one thread (warp 0) streams the steps of all the CTA's tiles through an
-//     ST-deep ring with cp.async.bulk.tensor: per step two 5D boxes of the
-//     input (8 channels x RW x 18 positions of one plane; the tensor map
-//     zero-fills the halo outside the volume, including planes outside the
-//     batch item) and 18 2D boxes of the weights (8 channels x BN rows per
-//     tap and channel block), completing on the stage's mbarrier;
-//   * one thread (warp 1) issues the MMAs of each step and commits them to
-//     the stage's "empty" barrier, and a tile's last commit to the
-//     accumulator's "full" barrier; two accumulators alternate in TMEM, so the
-//     MMAs of tile i + 1 overlap the epilogue of tile i;
+// instead of 27 times as in the im2col form.  Roles:
+//   * warp 0 streams the steps of all the CTA's tiles through an ST-deep
+//     ring with cp.async.bulk.tensor: per step two 5D boxes of the input
+//     (8 channels x RW x 18 positions of one plane; the tensor map zero-fills
+//     the halo outside the volume, including planes outside the batch item)
+//     and, unless resident, 18 2D boxes of the weights (8 channels x BN rows
+//     per tap and channel block), completing on the stage's mbarrier;
+//   * warp 1 issues the MMAs of each step and commits them to the stage's
+//     "empty" barrier, and a tile's last commit to the accumulator's "full"
+//     barrier; two accumulators alternate in TMEM, so the MMAs of tile i + 1
+//     overlap the epilogue of tile i;
 //   * four epilogue warps (2..5; warp w reads TMEM lanes 32 (w % 4) ..)
 //     drain an accumulator, store it and release it.
-// Every wait is bounded; on expiry a thread raises the shared abort flag,
-// which ends the other roles' waits, and the CTA drains its own copies and
-// MMAs (bounded) before it frees TMEM.
+// The producer and MMA loops run warp-wide with one elected lane issuing,
+// so that descriptors and coordinates stay warp-uniform.  Every wait is
+// bounded; on expiry a thread raises the shared abort flag, which ends the
+// other roles' waits, and the CTA drains its own copies and MMAs (bounded)
+// before it frees TMEM.
 constexpr int TMA_THREADS = 192;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -1389,7 +1238,7 @@ int sm_count()
 
 // Persistent TMA brick FWD: one CTA per SM.  Returns cudaErrorNotSupported
 // (nothing launched) when the tensor maps cannot be made, so that the
-// caller falls back to the cp.async brick kernel.
+// caller falls back to the im2col kernel.
 template <int BN, int NT, bool RESW>
 cudaError_t launch_tma(const __nv_bfloat16 *x, const __nv_bfloat16 *w, const float *bias, void *out, int out_bf16,
                        const ConvShape &S, int *status, cudaStream_t stream)
@@ -1494,45 +1343,22 @@ cudaError_t launch_wgrad_tma(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, fl
     return cudaGetLastError();
 }
 
-// Brick-staged FWD launch, 3 stages (measured faster than 4 for the narrow
-// N tiles too: more CTAs stay resident).
-template <int BN, int NT>
-cudaError_t launch_brick(const __nv_bfloat16 *x, const __nv_bfloat16 *w, const float *bias, void *out, int out_bf16,
-                         const ConvShape &S, int *status, cudaStream_t stream)
-{
-    constexpr int ST = 3;
-    constexpr int RW = 8 * NT + 2, NP = RW * 18;
-    const int smem = ST * (NP * 32 + 9 * 2 * BN * 16) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(conv_fwd_brick_kernel<BN, NT, ST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    const long long tiles = (long long)S.nb * S.d * ((S.h + 15) / 16) * ((S.w + 8 * NT - 1) / (8 * NT));
-    if (tiles > 0x7FFFFFFFLL) return cudaErrorInvalidConfiguration;
-    const dim3 grid((unsigned)tiles, (unsigned)((S.n_total + BN - 1) / BN), 1);
-    conv_fwd_brick_kernel<BN, NT, ST><<<grid, THREADS, smem, stream>>>(x, w, bias, out, out_bf16, S, status);
-    return cudaGetLastError();
-}
-
 template <int OP, int BN>
 cudaError_t launch_bn(const __nv_bfloat16 *a, const __nv_bfloat16 *b, const float *bias, void *out, int out_bf16,
                       const ConvShape &S, int *status, cudaStream_t stream)
 {
-    if (OP == OP_FWD && (S.cin & 15) == 0 && CTREX_CONV_BRICK) {
-        // tiles 16 x 16 (NT = 2) unless the volume is at most 8 wide
-        if (CTREX_CONV_TMA) {
-            // the filter stays resident when the layer has one N tile and it fits
-            const bool resw = S.n_total <= BN && 27LL * S.cin * BN * 2 <= TmaPlan<BN, 2, true>::W_MAX;
-            cudaError_t e;
-            if (S.w > 8)
-                e = resw ? launch_tma<BN, 2, true>(a, b, bias, out, out_bf16, S, status, stream)
-                         : launch_tma<BN, 2, false>(a, b, bias, out, out_bf16, S, status, stream);
-            else
-                e = resw ? launch_tma<BN, 1, true>(a, b, bias, out, out_bf16, S, status, stream)
-                         : launch_tma<BN, 1, false>(a, b, bias, out, out_bf16, S, status, stream);
-            if (e != cudaErrorNotSupported) return e;
-        }
-        if (S.w > 8) return launch_brick<BN, 2>(a, b, bias, out, out_bf16, S, status, stream);
-        return launch_brick<BN, 1>(a, b, bias, out, out_bf16, S, status, stream);
+    if (OP == OP_FWD && (S.cin & 15) == 0 && CTREX_CONV_TMA) {
+        // tiles 16 x 16 (NT = 2) unless the volume is at most 8 wide; the
+        // filter stays resident when the layer has one N tile and it fits
+        const bool resw = S.n_total <= BN && 27LL * S.cin * BN * 2 <= TmaPlan<BN, 2, true>::W_MAX;
+        cudaError_t e;
+        if (S.w > 8)
+            e = resw ? launch_tma<BN, 2, true>(a, b, bias, out, out_bf16, S, status, stream)
+                     : launch_tma<BN, 2, false>(a, b, bias, out, out_bf16, S, status, stream);
+        else
+            e = resw ? launch_tma<BN, 1, true>(a, b, bias, out, out_bf16, S, status, stream)
+                     : launch_tma<BN, 1, false>(a, b, bias, out, out_bf16, S, status, stream);
+        if (e != cudaErrorNotSupported) return e;  // else: the im2col kernel below
     }
     if (OP == OP_FWD && (S.cin & 7) == 0) {
         // 2 stages for tiles up to 64 wide (more CTAs per SM beat a deeper
@@ -1592,6 +1418,8 @@ int ctrex_conv3d_fwd(const void *x, const void *w, const float *bias, void *y, i
                      int wd, int cin, int cout, int relu, int *status, void *stream)
 {
     if (!x || !w || !y || !status) return CTREX_E_ARG;
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(y)) & 15)
+        return CTREX_E_ARG;  // 16-byte copies and stores
     if (y_dtype != CTREX_F32 && y_dtype != CTREX_BF16) return CTREX_E_DTYPE;
     if (!shape_ok(nb, d, h, wd, cin, cout)) return CTREX_E_SHAPE;
     ConvShape S{};
@@ -1607,7 +1435,7 @@ int ctrex_conv3d_fwd(const void *x, const void *w, const float *bias, void *y, i
     S.k_total = 27LL * cin;
     S.k_per_cta = S.k_total;
     int bn = pick_bn(cout);
-    if (CTREX_CONV_BRICK && CTREX_CONV_FILL && (cin & 15) == 0) {
+    if (CTREX_CONV_TMA && CTREX_CONV_FILL && (cin & 15) == 0) {
         // narrower N tiles while the grid would leave SMs idle (deep layers
         // at small spatial sizes); measured: narrowing further, to two CTAs
         // per SM, costs more in brick reloads than it gains
@@ -1624,6 +1452,7 @@ int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, 
                        int *status, void *stream)
 {
     if (!x || !dy || !dw || !status) return CTREX_E_ARG;
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(dy)) & 15) return CTREX_E_ARG;
     if (!shape_ok(nb, d, h, wd, cin, cout) || (cin & 7) || (cout & 7)) return CTREX_E_SHAPE;
     ConvShape S{};
     S.nb = nb;

@@ -68,3 +68,24 @@ def test_binding_refuses_to_run_without_library(tmp_path):
             ctrex.load_library(str(tmp_path / "missing.so"))
     finally:
         ctrex._lib = saved
+
+
+def test_conv_argument_checks_answer_without_gpu(lib):
+    """The conv entry points refuse null and unaligned pointers (their
+    kernels copy 16-byte channel vectors) and bad shapes before any CUDA
+    call; the pointers below are never dereferenced."""
+    vp = ctypes.c_void_p
+    st = vp(0x1000)
+    a, b, c = vp(0x10000), vp(0x20000), vp(0x30000)
+    odd = vp(0x10002)  # 2-byte aligned: a bf16 element, not a 16-byte vector
+    E_ARG, E_SHAPE = -1, -2
+    fwd = lib.ctrex_conv3d_fwd
+    assert fwd(None, b, None, c, 0, 1, 4, 4, 4, 16, 16, 0, st, None) == E_ARG
+    assert fwd(odd, b, None, c, 0, 1, 4, 4, 4, 16, 16, 0, st, None) == E_ARG
+    assert fwd(a, vp(0x20008), None, c, 0, 1, 4, 4, 4, 16, 16, 0, st, None) == E_ARG
+    assert fwd(a, b, None, vp(0x30004), 0, 1, 4, 4, 4, 16, 16, 0, st, None) == E_ARG
+    assert fwd(a, b, None, c, 0, 0, 4, 4, 4, 16, 16, 0, st, None) == E_SHAPE
+    wg = lib.ctrex_conv3d_wgrad
+    assert wg(odd, b, c, 1, 4, 4, 4, 16, 16, st, None) == E_ARG
+    assert wg(a, vp(0x20002), c, 1, 4, 4, 4, 16, 16, st, None) == E_ARG
+    assert wg(a, b, c, 1, 4, 4, 4, 12, 16, st, None) == E_SHAPE
