@@ -1,6 +1,8 @@
 """One small invocation of the hot path on cuda:0, checked against the FP64
 oracle: fused forward projection + correction, weighted backprojection with
-normalisation and update (one SIRT iteration of Eq. (1))."""
+normalisation and update (one SIRT iteration of Eq. (1)); then one 3x3x3
+convolution of the warm-start network and its weight gradient on the
+tensor cores against the FP64 conv oracle."""
 
 import numpy as np
 import torch
@@ -30,4 +32,21 @@ def run():
     ctx.close()
     if not (err_p <= 1e-5 and err_x <= 1e-5 and done == 2):
         raise AssertionError(f"smoke parity failed: projection {err_p:.3e}, SIRT volume {err_x:.3e}")
-    print(f"smoke ok: projection rel.L2 {err_p:.2e}, 2-iteration SIRT rel.L2 {err_x:.2e}")
+
+    from oracle import conv
+
+    rng = np.random.default_rng(3)
+    xc = torch.as_tensor(rng.normal(size=(1, 4, 18, 20, 16)), dtype=torch.float32).to(torch.bfloat16)
+    wc = torch.as_tensor(rng.normal(size=(16, 27, 16)) / 20.0, dtype=torch.float32).to(torch.bfloat16)
+    dyc = torch.as_tensor(rng.normal(size=(1, 4, 18, 20, 16)), dtype=torch.float32).to(torch.bfloat16)
+    y_ref = conv.conv3d(xc.double().numpy(), wc.double().numpy())
+    _, dw_ref = conv.conv3d_grads(xc.double().numpy(), wc.double().numpy(), dyc.double().numpy())
+    y = ctrex.conv3d(xc.to(dev), wc.to(dev), out_dtype=torch.float32)
+    dw = ctrex.conv3d_wgrad(xc.to(dev), dyc.to(dev))
+    ctrex.conv_status_check(dev)
+    err_y = float(np.linalg.norm(y.double().cpu().numpy() - y_ref) / np.linalg.norm(y_ref))
+    err_w = float(np.linalg.norm(dw.double().cpu().numpy() - dw_ref) / np.linalg.norm(dw_ref))
+    if not (err_y <= 1e-4 and err_w <= 1e-4):
+        raise AssertionError(f"smoke conv parity failed: forward {err_y:.3e}, weight gradient {err_w:.3e}")
+    print(f"smoke ok: projection rel.L2 {err_p:.2e}, 2-iteration SIRT rel.L2 {err_x:.2e}, "
+          f"conv {err_y:.2e}, conv weight gradient {err_w:.2e}")

@@ -483,8 +483,9 @@ def conv3d(x, wt, bias=None, relu=False, out_dtype=torch.bfloat16):
     if bias is not None:
         bias = bias.float().contiguous()
     stream = torch.cuda.current_stream(x.device).cuda_stream
-    rc = lib.ctrex_conv3d_fwd(_ptr(x), _ptr(wt), _ptr(bias), _ptr(y), _dt(y), nb, d, h, w, cin, cout, int(relu),
-                              _ptr(_status(x.device)), ctypes.c_void_p(stream))
+    with torch.cuda.device(x.device):  # the library launches on the current device
+        rc = lib.ctrex_conv3d_fwd(_ptr(x), _ptr(wt), _ptr(bias), _ptr(y), _dt(y), nb, d, h, w, cin, cout, int(relu),
+                                  _ptr(_status(x.device)), ctypes.c_void_p(stream))
     if rc != OK:
         raise CtrexError(rc, f"ctrex_conv3d_fwd failed for x {tuple(x.shape)}, wt {tuple(wt.shape)}")
     return y
@@ -500,8 +501,9 @@ def conv3d_wgrad(x, dy, dw=None):
     if dw is None:
         dw = torch.zeros((cout, 27, cin), dtype=torch.float32, device=x.device)
     stream = torch.cuda.current_stream(x.device).cuda_stream
-    rc = lib.ctrex_conv3d_wgrad(_ptr(x), _ptr(dy), _ptr(dw), nb, d, h, w, cin, cout, _ptr(_status(x.device)),
-                                ctypes.c_void_p(stream))
+    with torch.cuda.device(x.device):
+        rc = lib.ctrex_conv3d_wgrad(_ptr(x), _ptr(dy), _ptr(dw), nb, d, h, w, cin, cout, _ptr(_status(x.device)),
+                                    ctypes.c_void_p(stream))
     if rc != OK:
         raise CtrexError(rc, "ctrex_conv3d_wgrad failed")
     return dw
