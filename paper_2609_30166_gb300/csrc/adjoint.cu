@@ -7,6 +7,12 @@
 // Sec. 4.1 projector with the Sec. 2.2.2 / 3.1 warp.
 #include "ray.cuh"
 
+// 4 resident CTAs per SM for the motion gradient: registers capped at 128
+// (a few bytes of spills), measured faster than 167 registers at 3 CTAs
+#ifndef CTREX_MGRAD_MIN_BLOCKS
+#define CTREX_MGRAD_MIN_BLOCKS 4
+#endif
+
 namespace ctrex {
 
 constexpr int ADJ_TX = 32, ADJ_TY = 4;
@@ -301,7 +307,7 @@ __device__ __forceinline__ void grad_sample(const Grid &G, const MotionGPU &m, c
 }
 
 template <typename TV>
-__global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
+__global__ void __launch_bounds__(ADJ_TX *ADJ_TY, CTREX_MGRAD_MIN_BLOCKS)
     motion_grad_kernel(Grid G, const ViewGPU *__restrict__ views, const MotionGPU *__restrict__ motion,
                        const float *__restrict__ coef_g, const int *__restrict__ view_idx,
                        const TV *__restrict__ vol, const float *__restrict__ gproj,
