@@ -47,6 +47,7 @@ namespace {
 #endif
 
 
+
 constexpr int BM = 128;
 constexpr int BK = 64;
 constexpr int STAGES = 2;
@@ -93,10 +94,11 @@ __device__ __forceinline__ uint64_t sdesc_none(uint32_t saddr, uint32_t lbo, uin
     return d;
 }
 
-// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major.
-__host__ __device__ constexpr uint32_t idesc(int n)
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major,
+// N = n, M = m (64 or 128).
+__host__ __device__ constexpr uint32_t idesc(int n, int m = BM)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
@@ -1031,9 +1033,9 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
 //   * dy rows as [row g][co block][16 voxels] x 16 B (one TMA box through a
 //     map whose dimensions are (8 channels, x, co block, y, plane)); the MMA
 //     of row g reads A = dy^T at g * CB * 256 with SBO 256, LBO 128: K = the
-//     row's 16 voxels, M = 128 co (rows past cout read other rows' data and
-//     land in accumulator lanes that are never stored; the region is padded
-//     so that they stay inside it);
+//     row's 16 voxels, M = 128 co, or 64 when cout <= 64 (rows past cout
+//     read other rows' data and land in accumulator lanes that are never
+//     stored; the region is padded so that they stay inside it);
 //   * the input window of plane z + dz - 1 for the CN channels, three
 //     times, shifted by kx = 0, 1, 2 voxels: copy kx holds rows y0 - 1 ..
 //     y0 + 16 and columns x0 + kx - 1 .. + 15 as [kx][8-channel block][18
@@ -1063,7 +1065,7 @@ struct WgArgs {
 };
 constexpr int WG_MAX_ST = 8;
 
-template <int CN>
+template <int CN, bool M64>
 __global__ void __launch_bounds__(TMA_THREADS, 1)
     conv_wgrad_tma_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmdy,
                           float *__restrict__ dw, ConvShape S, WgArgs G, int *__restrict__ status)
@@ -1142,8 +1144,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         }
     } else if (warp == 1 && any) {
         const uint32_t leader = elect_one();
-        // kind::f16, D F32, A and B BF16, both MN-major, N = 3 CN, M = 128
-        constexpr uint32_t ID = idesc(PL::NK) | (1u << 15) | (1u << 16);
+        // kind::f16, D F32, A and B BF16, both MN-major, N = 3 CN, M = 64 or 128
+        constexpr uint32_t ID = idesc(PL::NK, M64 ? 64 : 128) | (1u << 15) | (1u << 16);
         long long i = 0;
         bool ok = true, issued = false;
         const uint32_t row_step = (uint32_t)(G.cb * 256) >> 4;  // descriptor units per dy row
@@ -1178,9 +1180,11 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             }
         }
     } else if (warp >= 2 && any) {
-        // epilogue: lane row m = co0 + 32 (warp % 4) + lane, once per CTA
+        // epilogue, once per CTA: accumulator row m = co - co0 sits in TMEM lane
+        // m (M = 128) or 32 (m / 16) + m % 16 (M = 64: lanes 16..31 of each
+        // quarter hold no row)
         const int quarter = warp & 3;
-        const int co = co0 + 32 * quarter + lane;
+        const int co = M64 ? (lane < 16 ? co0 + 16 * quarter + lane : S.cout) : co0 + 32 * quarter + lane;
         if (mbar_wait_warp(&done, 0u, abort_flag)) {
             tc_after_sync();
             const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
@@ -1283,7 +1287,7 @@ cudaError_t launch_tma(const __nv_bfloat16 *x, const __nv_bfloat16 *w, const flo
 
 // Brick weight gradient: returns cudaErrorNotSupported (nothing launched)
 // when the tensor maps cannot be made.
-template <int CN>
+template <int CN, bool M64>
 cudaError_t launch_wgrad_tma(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, float *dw, const ConvShape &S,
                              int *status, cudaStream_t stream)
 {
@@ -1321,9 +1325,9 @@ cudaError_t launch_wgrad_tma(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, fl
     }
     WgArgs G{};
     G.cb = cb;
-    // rows 0..15 of cb blocks each; row 15's 16 M blocks read up to
-    // 15 * cb * 256 + 16 * 256 bytes
-    G.dy_region = (256 * (15 * cb + 16) + 1023) / 1024 * 1024;
+    // rows 0..15 of cb blocks each; row 15's 16 (M = 64: 8) M blocks read up
+    // to 15 * cb * 256 + 16 (8) * 256 bytes
+    G.dy_region = (256 * (15 * cb + (M64 ? 8 : 16)) + 1023) / 1024 * 1024;
     G.stage = (G.dy_region + PL::X_BYTES + 1023) / 1024 * 1024;
     G.st = (200 * 1024) / G.stage;
     if (G.st > WG_MAX_ST) G.st = WG_MAX_ST;
@@ -1336,10 +1340,11 @@ cudaError_t launch_wgrad_tma(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, fl
     if (splits < 1) splits = 1;
     if (splits > G.tiles) splits = G.tiles;
     G.splits = (int)splits;
-    cudaError_t e = cudaFuncSetAttribute(conv_wgrad_tma_kernel<CN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(conv_wgrad_tma_kernel<CN, M64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    conv_wgrad_tma_kernel<CN><<<dim3((unsigned)splits, (unsigned)jobs, 1), TMA_THREADS, smem, stream>>>(mx, mdy, dw, S, G,
-                                                                                                      status);
+    conv_wgrad_tma_kernel<CN, M64><<<dim3((unsigned)splits, (unsigned)jobs, 1), TMA_THREADS, smem, stream>>>(
+        mx, mdy, dw, S, G, status);
     return cudaGetLastError();
 }
 
@@ -1472,13 +1477,16 @@ int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, 
     if (per < BK) per = BK;
     S.k_per_cta = per;
     if (CTREX_CONV_TMA && (cin & 15) == 0) {
-        // 32-channel chunks where two ring stages still fit beside the dy rows
-        const cudaError_t e = (cin & 31) == 0 && cout <= 64 ? launch_wgrad_tma<32>(static_cast<const __nv_bfloat16 *>(x),
-                                                                        static_cast<const __nv_bfloat16 *>(dy), dw, S,
-                                                                        status, static_cast<cudaStream_t>(stream))
-                                              : launch_wgrad_tma<16>(static_cast<const __nv_bfloat16 *>(x),
-                                                                        static_cast<const __nv_bfloat16 *>(dy), dw, S,
-                                                                        status, static_cast<cudaStream_t>(stream));
+        // 32-channel chunks where two ring stages still fit beside the dy
+        // rows; M = 64 MMAs (half the dy operand reads) for up to 64 outputs
+        const auto *xb = static_cast<const __nv_bfloat16 *>(x);
+        const auto *db = static_cast<const __nv_bfloat16 *>(dy);
+        const cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const bool c32 = (cin & 31) == 0 && cout <= 64, m64 = cout <= 64;
+        const cudaError_t e = c32 ? (m64 ? launch_wgrad_tma<32, true>(xb, db, dw, S, status, st)
+                                         : launch_wgrad_tma<32, false>(xb, db, dw, S, status, st))
+                                  : (m64 ? launch_wgrad_tma<16, true>(xb, db, dw, S, status, st)
+                                         : launch_wgrad_tma<16, false>(xb, db, dw, S, status, st));
         if (e != cudaErrorNotSupported) return e == cudaSuccess ? CTREX_OK : CTREX_E_CUDA;
     }
     const int bn = pick_bn(cout);
