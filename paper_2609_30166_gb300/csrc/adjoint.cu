@@ -22,20 +22,23 @@ constexpr int NCOEF = 8 * 8 * 8 * 3;
 // Adjoint: scatter y_i * w_k * trilinear weight into the 8 taps (FP32 atomics)
 // ---------------------------------------------------------------------------
 
-// Each (y, z) row of the 2 x 2 x 2 footprint adds w0, w1 to the neighbours
-// x0, x0 + 1, consecutive floats.  When both lie in one 16-byte-aligned quad
-// of the volume (x0 % 4 != 3 in element terms; 3 cases in 4), one vector
-// reduction adds (.., w0, w1, ..) with zeros in the other two lanes, so a
-// sample issues about 5 reductions instead of 8 (the reductions' L1/TEX path
-// bounds the kernel without motion; with motion the spline evaluation does).  The zero lanes belong to neighbouring voxels
+// Trilinear scatter of val at the point with centred index coordinates gc
+// (index coordinates minus the integer grid centre c: floor and fraction are
+// exact in them).  Each (y, z) row of the 2 x 2 x 2 footprint adds w0, w1 to
+// the neighbours x0, x0 + 1, consecutive floats.  When both lie in one
+// 16-byte-aligned quad of the volume (x0 % 4 != 3 in element terms; 3 cases
+// in 4), one vector reduction adds (.., w0, w1, ..) with zeros in the other
+// two lanes, so a sample issues about 5 reductions instead of 8 (the
+// reductions' L1/TEX path bounds the kernel without motion; with motion the
+// spline evaluation does).  The zero lanes belong to neighbouring voxels
 // (possibly of the adjacent row) inside the volume; adding +0 leaves them
 // unchanged.  vec: the volume is 16-byte aligned; nvox: its element count.
-__device__ __forceinline__ void scatter_trilinear(float *__restrict__ vol, int nx, int ny, int nz,
-                                                  const float g[3], float val, bool vec, long long nvox)
+__device__ __forceinline__ void scatter_trilinear(float *__restrict__ vol, int nx, int ny, int nz, const float c[3],
+                                                  const float gc[3], float val, bool vec, long long nvox)
 {
-    const float fx = floorf(g[0]), fy = floorf(g[1]), fz = floorf(g[2]);
-    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
-    const float ax = g[0] - fx, ay = g[1] - fy, az = g[2] - fz;
+    const float fx = floorf(gc[0]), fy = floorf(gc[1]), fz = floorf(gc[2]);
+    const int ix = (int)fx + (int)c[0], iy = (int)fy + (int)c[1], iz = (int)fz + (int)c[2];
+    const float ax = gc[0] - fx, ay = gc[1] - fy, az = gc[2] - fz;
     const float wx[2] = {1.0f - ax, ax}, wy[2] = {1.0f - ay, ay}, wz[2] = {1.0f - az, az};
     const bool in0 = (unsigned)ix < (unsigned)nx, in1 = (unsigned)(ix + 1) < (unsigned)nx;
 #pragma unroll
@@ -102,9 +105,11 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
     if (y == 0.0f) return;
     const bool vec = (reinterpret_cast<uintptr_t>(vol) & 15) == 0;
     const long long nvox = (long long)G.nx * G.ny * G.nz;
+    float cen[3];
+    grid_centre(G, cen);
     for (int s = 0; s < G.n_sub; ++s) {
-        Ray R;
-        if (!setup_ray(G, views[view * G.n_sub + s], (float)iu, (float)iv, R)) continue;
+        Ray R;  // sample positions relative to the grid centre
+        if (!setup_ray(G, views[view * G.n_sub + s], (float)iu, (float)iv, R, cen)) continue;
         const float ys = y * G.step_mm;
         for (int kk = 0; kk < R.K; ++kk) {
             float g[3];
@@ -120,17 +125,18 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
                 g[2] = R.g_last[2];
                 val = y * R.w_last;
             }
+            float gc[3];
             if (MOTION) {
-                float yy[3];
-                warp_sample(G, mo, coef, g, yy);
-                g[0] = yy[0];
-                g[1] = yy[1];
-                g[2] = yy[2];
+                warp_sample_c(G, mo, coef, g, gc);
+            } else {
+                gc[0] = g[0];
+                gc[1] = g[1];
+                gc[2] = g[2];
             }
-            if (!(g[0] >= -1.0f && g[0] < (float)G.nx && g[1] >= -1.0f && g[1] < (float)G.ny &&
-                  g[2] >= -1.0f && g[2] < (float)G.nz))
+            if (!(gc[0] >= -1.0f - cen[0] && gc[0] < (float)G.nx - cen[0] && gc[1] >= -1.0f - cen[1] &&
+                  gc[1] < (float)G.ny - cen[1] && gc[2] >= -1.0f - cen[2] && gc[2] < (float)G.nz - cen[2]))
                 continue;
-            scatter_trilinear(vol, G.nx, G.ny, G.nz, g, val, vec, nvox);
+            scatter_trilinear(vol, G.nx, G.ny, G.nz, cen, gc, val, vec, nvox);
         }
     }
 }
@@ -423,6 +429,7 @@ cudaError_t launch_motion_grad(const FwdArgs &a, const float *gproj, float *grad
 struct Frame {
     double vox[3];
     double origin[3];
+    double cen[3];  // integer grid centre floor((n - 1) / 2) per axis (index coordinates)
 };
 
 // Rodrigues R = I + a K + b K^2 and dR/domega_i (FP64, one thread per view).
@@ -494,7 +501,16 @@ __global__ void motion_setup_kernel(const float *__restrict__ theta, const float
             m.M[3 * r + c] = (float)(Mw[3 * r + c] * F.vox[c] / F.vox[r]);
             acc += Mw[3 * r + c] * F.origin[c];
         }
-        m.b[r] = (float)(acc / F.vox[r]);
+        const double b = acc / F.vox[r];
+        m.b[r] = (float)b;
+        double bc = b;
+        for (int c = 0; c < 3; ++c) {
+            const double Mrc = Mw[3 * r + c] * F.vox[c] / F.vox[r];
+            const double Drc = Mrc - (r == c ? 1.0 : 0.0);
+            m.D[3 * r + c] = (float)Drc;
+            bc += Drc * F.cen[c];
+        }
+        m.bc[r] = (float)bc;
     }
     m.s = s_view ? s_view[v] : 0.0f;
     m.pad[0] = m.pad[1] = m.pad[2] = 0.0f;
@@ -509,13 +525,15 @@ __global__ void coef_to_index_kernel(const float *__restrict__ coef, Frame F, fl
 }
 
 cudaError_t launch_motion_setup(const float *theta, const float *coef, const float *s_view, int n_views,
-                                const Grid &, const double vox[3], const double origin[3], MotionGPU *motion,
+                                const Grid &G, const double vox[3], const double origin[3], MotionGPU *motion,
                                 float *coef_idx, float *dRdw, cudaStream_t stream)
 {
     Frame F;
+    const int n[3] = {G.nx, G.ny, G.nz};
     for (int a = 0; a < 3; ++a) {
         F.vox[a] = vox[a];
         F.origin[a] = origin[a];
+        F.cen[a] = (double)((n[a] - 1) / 2);
     }
     motion_setup_kernel<<<(n_views + 127) / 128, 128, 0, stream>>>(theta, s_view, n_views, F, motion, dRdw);
     cudaError_t e = cudaGetLastError();

@@ -34,9 +34,14 @@ struct MotionGPU {
     float M[9];
     float b[3];
     float s;
+    // centred form y - c = (g - c) + D (g - c) + bc about the integer grid
+    // centre c = floor((n - 1) / 2) per axis: D = M - I and bc = M c + b - c,
+    // both formed in FP64 and rounded once (small for a near-identity pose)
+    float bc[3];
+    float D[9];
     float pad[3];
 };
-static_assert(sizeof(MotionGPU) == 64, "MotionGPU layout");
+static_assert(sizeof(MotionGPU) == 112, "MotionGPU layout");
 
 struct Grid {
     int nx, ny, nz;

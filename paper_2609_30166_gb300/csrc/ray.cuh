@@ -61,8 +61,12 @@ __device__ __forceinline__ void finish_ray(const Grid &G, const float X[3], cons
 }
 
 // Sets up the ray of view parameters V through detector point (u, v).
-// Returns false if the half line from the source misses the clip box.
-__device__ __forceinline__ bool setup_ray(const Grid &G, const ViewGPU &V, float u, float v, Ray &R)
+// Returns false if the half line from the source misses the clip box.  With
+// an offset off, the sample positions come out as index coordinates minus
+// off (the clip itself is unchanged): for off = the integer grid centre they
+// are formed at magnitudes up to n / 2, which halves their rounding.
+__device__ __forceinline__ bool setup_ray(const Grid &G, const ViewGPU &V, float u, float v, Ray &R,
+                                          const float *off = nullptr)
 {
     float X[3], dg[3], len;
     ray_line(G, V, u, v, X, dg, len);
@@ -79,7 +83,12 @@ __device__ __forceinline__ bool setup_ray(const Grid &G, const ViewGPU &V, float
         }
     }
     if (!(t1 > t0)) return false;
-    finish_ray(G, X, dg, t0, t1, R);
+    if (off) {
+        const float Xo[3] = {X[0] - off[0], X[1] - off[1], X[2] - off[2]};
+        finish_ray(G, Xo, dg, t0, t1, R);
+    } else {
+        finish_ray(G, X, dg, t0, t1, R);
+    }
     return true;
 }
 
@@ -208,25 +217,41 @@ __device__ __forceinline__ float3 coef_at(const float4 *coef, int cx, int cy, in
     return make_float3(c.x, c.y, c.z);
 }
 
-// Warp of one sample (Sec. 2.2.2 pose, then Sec. 3.1 displacement): index
-// coordinates in, index coordinates out.  coef: shared-memory copy of the
+// Integer grid centre c = floor((n - 1) / 2) per axis (index coordinates).
+__device__ __forceinline__ void grid_centre(const Grid &G, float c[3])
+{
+    c[0] = (float)((G.nx - 1) >> 1);
+    c[1] = (float)((G.ny - 1) >> 1);
+    c[2] = (float)((G.nz - 1) >> 1);
+}
+
+// Warp of one sample (Sec. 2.2.2 pose, then Sec. 3.1 displacement), in
+// coordinates centred on the integer grid centre c: gc = g - c in (g index
+// coordinates), yc = y - c out, with y = M g + b + s u(M g + b).  It runs as
+// yc = gc + (D gc + bc + s u) with gc = g - c, D = M - I, bc = M c + b - c:
+// the bracket is a displacement of a few voxels for a near-identity pose,
+// so its roundings are small, and only the last addition rounds at the
+// magnitude of the coordinate (up to n / 2).  Since c is an integer, floor
+// and fraction of y follow exactly from yc.  coef: shared-memory copy of the
 // [8][8][8] coefficients in voxels (float triples or padded float4), or
 // nullptr.
 template <typename CoefT>
-__device__ __forceinline__ void warp_sample(const Grid &G, const MotionGPU &m, const CoefT *coef, const float g[3],
-                                            float y[3])
+__device__ __forceinline__ void warp_sample_c(const Grid &G, const MotionGPU &m, const CoefT *coef, const float gc[3],
+                                              float yc[3])
 {
-    float gp[3];
+    float c[3];
+    grid_centre(G, c);
+    float d[3];  // displacement D gc + bc (+ s u below)
 #pragma unroll
     for (int r = 0; r < 3; ++r)
-        gp[r] = fmaf(m.M[3 * r], g[0], fmaf(m.M[3 * r + 1], g[1], fmaf(m.M[3 * r + 2], g[2], m.b[r])));
+        d[r] = fmaf(m.D[3 * r], gc[0], fmaf(m.D[3 * r + 1], gc[1], fmaf(m.D[3 * r + 2], gc[2], m.bc[r])));
     float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
     if (coef != nullptr && m.s != 0.0f) {
         int i0[3];
         float f[3], wx[4], wy[4], wz[4];
         bool act[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) spline_coord(gp[a], G.spl_scale[a], i0[a], f[a], act[a]);
+        for (int a = 0; a < 3; ++a) spline_coord(gc[a] + d[a] + c[a], G.spl_scale[a], i0[a], f[a], act[a]);
         bspline_weights(f[0], wx);
         bspline_weights(f[1], wy);
         bspline_weights(f[2], wz);
@@ -241,17 +266,31 @@ __device__ __forceinline__ void warp_sample(const Grid &G, const MotionGPU &m, c
                 for (int i = 0; i < 4; ++i) {
                     const int cx = min(i0[0] - 1 + i, 7);
                     const float wt = wyz * wx[i];
-                    const float3 c = coef_at(coef, cx, cy, cz);
-                    u0 = fmaf(wt, c.x, u0);
-                    u1 = fmaf(wt, c.y, u1);
-                    u2 = fmaf(wt, c.z, u2);
+                    const float3 cf = coef_at(coef, cx, cy, cz);
+                    u0 = fmaf(wt, cf.x, u0);
+                    u1 = fmaf(wt, cf.y, u1);
+                    u2 = fmaf(wt, cf.z, u2);
                 }
             }
         }
     }
-    y[0] = fmaf(m.s, u0, gp[0]);
-    y[1] = fmaf(m.s, u1, gp[1]);
-    y[2] = fmaf(m.s, u2, gp[2]);
+    yc[0] = gc[0] + fmaf(m.s, u0, d[0]);
+    yc[1] = gc[1] + fmaf(m.s, u1, d[1]);
+    yc[2] = gc[2] + fmaf(m.s, u2, d[2]);
+}
+
+// The same warp in plain index coordinates.
+template <typename CoefT>
+__device__ __forceinline__ void warp_sample(const Grid &G, const MotionGPU &m, const CoefT *coef, const float g[3],
+                                            float y[3])
+{
+    float c[3];
+    grid_centre(G, c);
+    const float gc[3] = {g[0] - c[0], g[1] - c[1], g[2] - c[2]};
+    warp_sample_c(G, m, coef, gc, y);
+    y[0] += c[0];
+    y[1] += c[1];
+    y[2] += c[2];
 }
 
 }  // namespace ctrex

@@ -168,3 +168,69 @@ def test_fullsize_motion_projector():
     err = rel_l2(got, ref)
     print(f"motion projector 256^3, sampled rays: rel.L2 {err:.3e}")
     assert err <= TOL32
+
+
+def test_fullsize_motion_adjoint_and_gradient():
+    """Matched adjoint and motion gradient of the motion workload (256^3,
+    384^2, 360 views) through the launches bench.py times (all 360 views).
+    One view carries random detector values, the others zeros; the oracle
+    computes that view alone: the whole adjoint volume, the view's 15 pose
+    derivatives and the 1536 coefficient derivatives.  The adjoint identity
+    <A x, g> = <x, A^T g> is checked over all 360 views with positive g.
+
+    Tolerances: with positive detector values the adjoint sums ~10^2
+    same-sign contributions per voxel (TOL32).  With zero-mean values they
+    cancel, and the FP32 rounding of the sample positions (index coordinates
+    up to 256: up to 1.5e-5 voxel, moving trilinear weights by as much) no
+    longer averages out: a few 1e-5, bound 1e-4.  Each
+    coefficient derivative sums ~10^7 mixed-sign per-sample terms in FP32
+    (warp sums, then per-CTA shared-memory and global atomics); with random
+    g the result is a random walk ~sqrt(n) times one term while the rounding
+    grows with sum |terms| ~ n terms, so the relative error scales like
+    sqrt(n) u ~ 3e-4: the bound is 1e-3.  The pose derivatives of one view
+    are checked at the same bound."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_30166_gb300 import _build, ctrex
+
+    _build.build_library()
+    cfg = inputs.MOTION_256
+    P = inputs.projection_matrices(cfg)
+    th, co, sv = inputs.motion_params(cfg)
+    ctx = ctrex.context_for(cfg, P=P)
+    f = lambda a: torch.as_tensor(a, dtype=torch.float32).cuda().contiguous()  # noqa: E731
+    ctx.set_motion(f(th), f(co), f(sv), cfg.margin)
+    vol = inputs.phantom(cfg, device="cuda").float().contiguous()
+    pb = oracle.Problem(P, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin, (cfg.nu, cfg.nv), cfg.step_vox, theta=th,
+                        coef=co, s_view=sv, margin=cfg.margin)
+    rng = np.random.default_rng(360)
+    v = 137
+    gv = rng.normal(size=(cfg.nv, cfg.nu))
+    g = torch.zeros((cfg.n_views, cfg.nv, cfg.nu), device="cuda")
+    g[v] = torch.as_tensor(gv, dtype=torch.float32)
+    one = np.array([v], dtype=np.int32)
+    adj = ctx.adjoint_project(g)
+    adj_ref = oracle.adjoint(pb, gv[None], views=one)
+    e_adj = rel_l2(adj.double().cpu().numpy(), adj_ref)
+    gpos = rng.uniform(0.5, 1.5, size=(cfg.nv, cfg.nu))
+    g2 = torch.zeros_like(g)
+    g2[v] = torch.as_tensor(gpos, dtype=torch.float32)
+    e_pos = rel_l2(ctx.adjoint_project(g2).double().cpu().numpy(), oracle.adjoint(pb, gpos[None], views=one))
+    gt, gc = ctx.motion_grad(vol, g)
+    vol64 = vol.double().cpu().numpy()
+    gt_ref, gc_ref = oracle.motion_grad(pb, vol64, gv[None], views=one)
+    e_t = rel_l2(gt.double().cpu().numpy()[v], gt_ref[v])
+    e_c = rel_l2(gc.double().cpu().numpy(), gc_ref)
+    others = torch.ones(cfg.n_views, dtype=torch.bool)
+    others[v] = False
+    other = float(gt[others.cuda()].abs().max())  # views with zero g get exactly zero
+    print(f"motion 256^3 full size, view {v}: adjoint rel.L2 {e_pos:.3e} (positive g), {e_adj:.3e} (zero-mean g), "
+          f"pose derivatives {e_t:.3e}, coefficient derivatives {e_c:.3e}")
+    assert np.abs(adj_ref).max() > 0 and np.abs(gc_ref).max() > 0
+    assert e_pos <= TOL32 and e_adj <= 1e-4 and e_t <= 1e-3 and e_c <= 1e-3 and other == 0.0
+    # adjoint identity over all views (positive g: no cancellation)
+    gp = torch.rand((cfg.n_views, cfg.nv, cfg.nu), device="cuda", generator=torch.Generator(device="cuda").manual_seed(7))
+    lhs = float((ctx.fwd_project(vol).double() * gp.double()).sum())
+    rhs = float((vol.double() * ctx.adjoint_project(gp).double()).sum())
+    print(f"<A x, g> = {lhs:.6e}, <x, A^T g> = {rhs:.6e}, rel. difference {abs(lhs - rhs) / abs(lhs):.2e}")
+    assert abs(lhs - rhs) <= TOL32 * abs(lhs)
