@@ -279,18 +279,49 @@ __device__ __forceinline__ void warp_sample_c(const Grid &G, const MotionGPU &m,
     yc[2] = gc[2] + fmaf(m.s, u2, d[2]);
 }
 
-// The same warp in plain index coordinates.
+// The same warp in plain index coordinates, as the forward projector uses it:
+// y = M g + b + s u(M g + b) formed directly (fewer operations; the forward
+// averages the position rounding out along the ray, so it needs no centring).
 template <typename CoefT>
 __device__ __forceinline__ void warp_sample(const Grid &G, const MotionGPU &m, const CoefT *coef, const float g[3],
                                             float y[3])
 {
-    float c[3];
-    grid_centre(G, c);
-    const float gc[3] = {g[0] - c[0], g[1] - c[1], g[2] - c[2]};
-    warp_sample_c(G, m, coef, gc, y);
-    y[0] += c[0];
-    y[1] += c[1];
-    y[2] += c[2];
+    float gp[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        gp[r] = fmaf(m.M[3 * r], g[0], fmaf(m.M[3 * r + 1], g[1], fmaf(m.M[3 * r + 2], g[2], m.b[r])));
+    float u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
+    if (coef != nullptr && m.s != 0.0f) {
+        int i0[3];
+        float f[3], wx[4], wy[4], wz[4];
+        bool act[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) spline_coord(gp[a], G.spl_scale[a], i0[a], f[a], act[a]);
+        bspline_weights(f[0], wx);
+        bspline_weights(f[1], wy);
+        bspline_weights(f[2], wz);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int cz = min(i0[2] - 1 + k, 7);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int cy = min(i0[1] - 1 + j, 7);
+                const float wyz = wz[k] * wy[j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int cx = min(i0[0] - 1 + i, 7);
+                    const float wt = wyz * wx[i];
+                    const float3 cf = coef_at(coef, cx, cy, cz);
+                    u0 = fmaf(wt, cf.x, u0);
+                    u1 = fmaf(wt, cf.y, u1);
+                    u2 = fmaf(wt, cf.z, u2);
+                }
+            }
+        }
+    }
+    y[0] = fmaf(m.s, u0, gp[0]);
+    y[1] = fmaf(m.s, u1, gp[1]);
+    y[2] = fmaf(m.s, u2, gp[2]);
 }
 
 }  // namespace ctrex
