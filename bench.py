@@ -521,6 +521,20 @@ def run_ours(args):
                       "back_project_ms": t_jb * 1e3, "gups": (ns_j + n_updates) / (t_jf + t_jb) / 1e9,
                       "fwd_tex_gather_frac": ns_j / t_jf / gather_peak,
                       "trilinear_fwd_correct_ms": statistics.mean(fwd_ms)}
+        # BF16 storage of the volume, the projections and the correction
+        # images (FP32 accumulation): the same SIRT step on the same workload
+        bf16_row = None
+        if tdt == torch.float32:
+            x16, p16 = x.to(torch.bfloat16), p.to(torch.bfloat16)
+            r16, s16 = torch.empty_like(p16), torch.empty(2, dtype=torch.float64, device=device)
+            t_bf = _time(lambda: ctx.fwd_correct(x16, p16, r=r16, sums=s16), reps=2)
+            t_bb = _time(lambda: ctx.back_project(r16, vol=x16, alpha=1.0, normalize=True, accumulate=True), reps=2)
+            bf16_row = {"workload": cfg.name, "storage": "bf16", "accumulation": "f32",
+                        "fwd_correct_ms": t_bf * 1e3, "back_project_ms": t_bb * 1e3,
+                        "gups": units / (t_bf + t_bb) / 1e9,
+                        "fwd_tex_gather_frac": n_samples / t_bf / gather_peak,
+                        "bp_tex_gather_frac": n_updates / t_bb / gather_peak}
+            del x16, p16, r16
         del x, r
         torch.cuda.empty_cache()
         out["rows"] = measure_rows(device, gather_peak, sm_count, sm_mhz)
@@ -529,6 +543,8 @@ def run_ours(args):
                                           "tex_gather_frac": sv_points / t_sv / gather_peak,
                                           "centre_bp_ms": statistics.mean(bp_ms)}
         out["rows"]["a16_joseph_sirt_step"] = joseph_row
+        if bf16_row:
+            out["rows"]["a11_bf16_sirt_step"] = bf16_row
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not cyl:
         vol_np = phantom.double().cpu().numpy()
         ncpu_units, ncpu_s, desc = oracle_sample_run(cfg, P, vol_np, n_fwd_views=1 if not args.small else 8,
