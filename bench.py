@@ -263,7 +263,7 @@ MOTION_OPS_PER_SAMPLE = 64 * 4 + 16 + 3 * 10 + 12 + 30
 
 
 def measure_rows(device, gather_peak, sm_count, sm_mhz):
-    """Throughput of the survey rows the SIRT step does not exercise, each on
+    """Throughput of the hot-path rows the SIRT step does not exercise, each on
     its full-size workload, with the ceiling that bounds it."""
     import torch
 

@@ -1,4 +1,4 @@
-// probe.cu -- measured ceilings used to judge the projectors: the texture
+// probe.cu -- measured ceilings the projectors are rated against: the texture
 // unit's gather throughput on an L1-resident texture (the projectors are
 // bound by the texture return path, not by HBM).
 #include "atlas.cuh"

@@ -1,7 +1,7 @@
 """tcgen05 implicit-GEMM 3x3x3 convolution vs the FP64 conv oracle, fed the
 same BF16-rounded inputs.  Products of BF16 values are exact and the tensor
 cores accumulate in FP32, so FP32 outputs agree to 1e-4 relative L2 (the
-survey's bound for the conv kernels); BF16 outputs add one rounding (4e-3)."""
+bound set for the conv kernels); BF16 outputs add one rounding (4e-3)."""
 
 import numpy as np
 import pytest

@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances: FP32 storage 1e-5 relative L2 (the survey's contract for every
+Tolerances: FP32 storage 1e-5 relative L2 (the contract for every
 projector, correction and backprojection result); BF16 storage is compared
 against the oracle run on the same BF16-rounded inputs at 4e-3 relative L2
 (one output rounding is 2^-9 relative; sums stay FP32).
