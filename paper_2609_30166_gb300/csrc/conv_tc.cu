@@ -45,6 +45,9 @@ namespace {
 #ifndef CTREX_CONV_FILL
 #define CTREX_CONV_FILL 1
 #endif
+#ifndef CTREX_CONV_WG_CHUNK
+#define CTREX_CONV_WG_CHUNK 32
+#endif
 
 
 
@@ -1064,6 +1067,7 @@ struct WgArgs {
     long long tiles; // 16 x 16 position tiles
 };
 constexpr int WG_MAX_ST = 8;
+constexpr long long WG_CHUNK = CTREX_CONV_WG_CHUNK;  // tiles per CTA at most (see the launcher)
 
 template <int CN, bool M64>
 __global__ void __launch_bounds__(TMA_THREADS, 1)
@@ -1336,9 +1340,19 @@ cudaError_t launch_wgrad_tma(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, fl
     G.tiles = (long long)S.nb * S.d * ((S.h + 15) / 16) * ((S.w + 15) / 16);
     const long long jobs = (long long)((S.cout + 127) / 128) * (S.cin / CN) * 3;
     if (jobs > 65535) return cudaErrorNotSupported;
-    long long splits = sms / jobs;
+    // The tensor core's FP32 accumulation loses about 2^-24 of the partial
+    // sum per K step in a long chain (measured: 5e-4 relative after 5.2 k
+    // steps of positive terms), so a CTA accumulates at most WG_CHUNK tiles
+    // (16 K steps each) in TMEM before its partial sums go to dW with FP32
+    // atomics; and at least one CTA per SM.
+    // The grid is rounded up to whole waves of one CTA per SM, the tiles
+    // spread evenly over them.
+    const long long need = (G.tiles + WG_CHUNK - 1) / WG_CHUNK * jobs;
+    const long long waves = (need + sms - 1) / sms;
+    long long splits = waves * sms / jobs;
     if (splits < 1) splits = 1;
     if (splits > G.tiles) splits = G.tiles;
+    if (splits > 0x7FFFFFFFLL) return cudaErrorNotSupported;
     G.splits = (int)splits;
     cudaError_t e =
         cudaFuncSetAttribute(conv_wgrad_tma_kernel<CN, M64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
