@@ -1483,10 +1483,14 @@ int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, 
     S.m_total = 27LL * cin;
     S.n_total = cout;
     S.k_total = (long long)nb * d * h * wd;
-    // split K so that the grid fills the GPU about twice
+    // split K so that the grid fills the GPU about twice, and so that no CTA
+    // accumulates more than 8192 voxels (512 K steps) in TMEM: the tensor
+    // core's FP32 accumulation drifts over long chains
     const long long mt = (S.m_total + BM - 1) / BM;
     long long splits = (2 * 152 + mt - 1) / mt;
     long long per = (S.k_total + splits - 1) / splits;
+    if (per > 8192) per = 8192;
+    if ((S.k_total + per - 1) / per > 65535) per = (S.k_total + 65534) / 65535;  // grid z limit
     per = ((per + BK - 1) / BK) * BK;
     if (per < BK) per = BK;
     S.k_per_cta = per;
