@@ -496,7 +496,10 @@ def run_ours(args):
                                     "peak_method": "ctrex_probe_gather_rate: tex2Dgather on an L1-resident texture"},
                      "note": f"algorithmic gather bytes = 8 taps x {elt} B per sample; peak = HBM copy "
                              f"bandwidth ({peak_kind}); the gather is served mostly from L1/L2"},
-        "gpu_launches": 3 * args.steps,
+        # per step: volume atlas upload (two kernels for the Joseph atlas),
+        # fused forward + correction, residual finish, correction-image atlas
+        # upload, backprojection + update
+        "gpu_launches": (6 if args.projector == "joseph" else 5) * args.steps,
         "e2e": e2e,
         "clocks": clk,
     }
