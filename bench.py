@@ -149,8 +149,8 @@ def l2_copy_bandwidth(device, mib=16, iters=200):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
-# launch of the fused forward kernel, from the one-pass ncu capture summarised
-# in profiles/fwd_kernel_perturbed512.md (traffic_full_v10).  Valid only for the kernel sources it
+# launch of the fused forward kernel, from a one-pass ncu capture of that
+# kernel (summary kept under profiles/).  Valid only for the kernel sources it
 # was taken on (hash below) and for the FP32 workload; otherwise null.
 FWD_TRAFFIC_BYTES = 2331578112 + 1694034944
 FWD_TRAFFIC_SOURCES = ("project.cu", "atlas.cuh", "ray.cuh", "cylinder.cuh", "joseph.cuh", "roi.cuh", "fwd_common.cuh", "ctrex_internal.cuh")

@@ -15,6 +15,7 @@ Each wrapper names the paper passage its C routine follows:
   alpha, Eq. (1) term 3; Sec. 3.2 / 4.3.2 voxel weights.
 * ``adjoint``, ``motion_grad``  -- transpose and chain rule of ``forward``
   (Sec. 5 motivates geometry refinement; no formula is printed).
+* ``displacement``              -- the Sec. 3.1 deformation field on its own.
 * ``sirt``                      -- Eq. (1) iterated, all views in one subset.
 * ``os_sirt``                   -- Eq. (1) on ordered subsets of views (Sec. 2.3.2).
 
@@ -109,6 +110,7 @@ def _declare(lib):
     lib.or_backproject_voxels.argtypes = [pp, _dp, _ip, ctypes.c_int, _lp, ctypes.c_long, _dp, _dp]
     lib.or_adjoint.argtypes = [pp, _dp, _ip, ctypes.c_int, _dp]
     lib.or_motion_grad.argtypes = [pp, _dp, _dp, _ip, ctypes.c_int, _dp, _dp]
+    lib.or_displacement.argtypes = [pp, ctypes.c_long, _dp, _dp, _dp]
     lib.or_sirt.argtypes = [pp, _dp, _dp, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_double,
                             ctypes.c_double, ctypes.c_double, _dp, _ip]
     lib.or_os_sirt.argtypes = [pp, _dp, _dp, _ip, _ip, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp,
@@ -353,6 +355,17 @@ def motion_grad(pb, vol, g, views=None):
     _check(lib.or_motion_grad(ctypes.byref(pb._c), _ptr(vol), _ptr(g), _ptr(v, _ip), n, _ptr(gt),
                               _ptr(gc)))
     return gt, gc
+
+
+def displacement(pb, pts):
+    """(u [n, 3], du/dx' [n, 3, 3]) of the B-spline deformation (Sec. 3.1,
+    reading R6) at world points pts [n, 3] (mm), from ``pb.coef``."""
+    lib = _load()
+    pts = _f64(pts).reshape(-1, 3)
+    u = np.zeros_like(pts)
+    J = np.zeros((len(pts), 3, 3))
+    _check(lib.or_displacement(ctypes.byref(pb._c), len(pts), _ptr(pts), _ptr(u), _ptr(J)))
+    return u, J
 
 
 def sirt(pb, p, max_iter, alpha=1.0, w=None, tol=0.0, x0=None, eps_C=EPS_C):

@@ -27,7 +27,7 @@
  *                 above (the paper motivates geometry refinement in Sec. 5 but
  *                 prints no formula).
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *   R1 the ray is the half line t >= 0 from the source; P is sign-normalised
  *      so that the depth of the volume centre is positive;
  *   R2 fixed step, truncated-midpoint quadrature starting at the entry face;
@@ -483,6 +483,18 @@ static void displacement(const or_problem *pb, const double xp[3], double u[3], 
                     }
                 }
             }
+}
+
+/*
+ * Displacement field u(x') and its Jacobian at n points (Sec. 3.1 deformation,
+ * reading R6), exported so that its control-grid placement can be checked on
+ * its own: xp [n][3] mm, u [n][3], J [n][9] (row = component, column = axis).
+ */
+int or_displacement(const or_problem *pb, long n, const double *xp, double *u, double *J)
+{
+    if (!pb->coef) return -1;
+    for (long q = 0; q < n; ++q) displacement(pb, xp + 3 * q, u + 3 * q, J ? J + 9 * q : NULL);
+    return 0;
 }
 
 /* Motion of view v applied to a nominal sample point x (mm): returns y. */

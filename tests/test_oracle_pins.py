@@ -252,6 +252,117 @@ def test_p5_backprojector_column_sums(dense8):
     assert (B >= 0).all()
 
 
+def _frame_projection(frame, X):
+    """Detector coordinates (u, v) of points X [..., 3] and whether each lies
+    in front of the source, by line/plane intersection with the detector
+    plane of one frame (s, d0, u_axis, v_axis): no projection matrix."""
+    s, d0, ua, va = frame
+    nrm = np.cross(ua, va)
+    den = (X - s) @ nrm
+    t = ((d0 - s) @ nrm) / np.where(den == 0, np.inf, den)
+    rel = s + t[..., None] * (X - s) - d0
+    G = np.array([[ua @ ua, ua @ va], [ua @ va, va @ va]])
+    uv = np.linalg.solve(G, np.stack([rel @ ua, rel @ va], axis=-1)[..., None])[..., 0]
+    return uv[..., 0], uv[..., 1], t > 0
+
+
+def _dense_bp_independent(frames, shape, vox, origin, nu, nv):
+    """Dense backprojector B [voxels, rays] from its definition (Sec. 4.1
+    backprojection operator, reading R4): the voxel centre projected through
+    each (view, sub-angle) frame, bilinear weights on the four neighbouring
+    pixels, pixels outside [0, nu-1] x [0, nv-1] and points behind the source
+    contributing nothing, each sub-angle weighted 1/S.  Also returns how many
+    (voxel, frame) footprints straddle the detector edge."""
+    nz, ny, nx = shape
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    pts = np.stack([origin[0] + X * vox[0], origin[1] + Y * vox[1], origin[2] + Z * vox[2]], -1).reshape(-1, 3)
+    n_views, n_sub = len(frames), len(frames[0])
+    B = np.zeros((len(pts), n_views * nv * nu))
+    straddle = total = 0
+    for k in range(n_views):
+        for sub in range(n_sub):
+            u, v, front = _frame_projection(frames[k][sub], pts)
+            for j in range(len(pts)):
+                if not front[j]:
+                    continue
+                iu0, iv0 = math.floor(u[j]), math.floor(v[j])
+                fu, fv = u[j] - iu0, v[j] - iv0
+                inside = 0
+                for dv, wv in ((0, 1.0 - fv), (1, fv)):
+                    for du, wu in ((0, 1.0 - fu), (1, fu)):
+                        iu, iv = iu0 + du, iv0 + dv
+                        if 0 <= iu <= nu - 1 and 0 <= iv <= nv - 1:
+                            inside += 1
+                            B[j, (k * nv + iv) * nu + iu] += wu * wv / n_sub
+                total += 1
+                straddle += 0 < inside < 4
+    return B, straddle, total
+
+
+def _dense_bp_oracle(pb, n_views):
+    nray = n_views * pb.nv * pb.nu
+    B = np.zeros((pb.nx * pb.ny * pb.nz, nray))
+    for i in range(nray):
+        e = np.zeros(nray)
+        e[i] = 1.0
+        B[:, i] = oracle.backproject(pb, e.reshape(n_views, pb.nv, pb.nu))[1].ravel()
+    return B
+
+
+def test_p5_backprojector_equals_independent_dense_definition():
+    # A detector narrower than the projected volume, so that many footprints
+    # cross its edges, with perturbed views and two sub-angles per view.
+    cfg = small(n=8, nu=5, nv=4, n_views=3, trajectory="perturbed", seed=5, det_width=40.0)
+    srcs, ctrs, us, vs = inputs.detector_frames(cfg)
+    P1 = inputs.projection_matrices(cfg)
+    # second sub-angle: the same frame rotated by 7 degrees about z
+    Rz = inputs.rot_z(math.radians(7.0))
+    frames, P = [], np.zeros((cfg.n_views, 2, 3, 4))
+    for k in range(cfg.n_views):
+        f = []
+        for sub, R in enumerate((np.eye(3), Rz)):
+            s, c, ua, va = R @ srcs[k, 0], R @ ctrs[k, 0], R @ us[k, 0], R @ vs[k, 0]
+            d0 = c - 0.5 * (cfg.nu - 1) * ua - 0.5 * (cfg.nv - 1) * va
+            f.append((s, d0, ua, va))
+            P[k, sub] = inputs.cone_matrix(s, c, ua, va, cfg.nu, cfg.nv)
+        frames.append(f)
+    assert np.allclose(P[:, 0], P1[:, 0])
+    pb = oracle.Problem(P, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin, (cfg.nu, cfg.nv), cfg.step_vox)
+    B_ind, straddle, total = _dense_bp_independent(frames, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin,
+                                                   cfg.nu, cfg.nv)
+    assert straddle >= 0.2 * total
+    B = _dense_bp_oracle(pb, cfg.n_views)
+    assert np.max(np.abs(B - B_ind)) <= 1e-13
+    _, _, c = oracle.backproject(pb, np.ones((cfg.n_views, cfg.nv, cfg.nu)))
+    assert np.allclose(c.ravel(), B_ind.sum(axis=1), rtol=0, atol=1e-13)
+
+
+def test_p5_backprojector_skips_points_behind_the_source():
+    # Sources inside the volume: the voxels behind each source get nothing
+    # from that view (depth <= 0), the rest follow the bilinear definition.
+    shape, vox, nu, nv = (8, 8, 8), (4.0, 4.0, 4.0), 12, 11
+    origin = (-14.0, -14.0, -14.0)
+    frames, P = [], []
+    for ang, src in ((0.0, (-3.0, 0.5, 0.2)), (2.1, (1.5, -2.5, -0.7))):
+        R = inputs.rot_z(ang)
+        s = R @ np.array([src[0], 0.0, 0.0]) + np.array([0.0, src[1], src[2]])
+        c = s + R @ np.array([60.0, 0.0, 0.0])
+        ua, va = R @ np.array([0.0, 6.0, 0.0]), np.array([0.0, 0.0, 6.0])
+        d0 = c - 0.5 * (nu - 1) * ua - 0.5 * (nv - 1) * va
+        frames.append([(s, d0, ua, va)])
+        P.append(inputs.cone_matrix(s, c, ua, va, nu, nv)[None])
+    P = np.stack(P)
+    pb = oracle.Problem(P, shape, vox, origin, (nu, nv), 0.5)
+    B_ind, _, _ = _dense_bp_independent(frames, shape, vox, origin, nu, nv)
+    Z, Y, X = np.meshgrid(*(np.arange(8),) * 3, indexing="ij")
+    pts = np.stack([origin[0] + X * 4.0, origin[1] + Y * 4.0, origin[2] + Z * 4.0], -1).reshape(-1, 3)
+    behind = ~_frame_projection(frames[0][0], pts)[2]
+    assert 0.2 * len(pts) < behind.sum() < 0.8 * len(pts)
+    B = _dense_bp_oracle(pb, 2)
+    assert np.max(np.abs(B - B_ind)) <= 1e-13
+    assert not B[behind, : nu * nv].any()
+
+
 def test_p5_sirt_step_is_dense_formula(dense8):
     cfg, pb, A, B = dense8
     rng = np.random.default_rng(6)
@@ -389,6 +500,49 @@ def test_p7_rotation_and_affine_conventions(motion_case):
     c, _ = oracle.forward(oracle_problem(cfg, theta=th2, coef=zero, s_view=np.zeros(cfg.n_views)), vol)
     d, _ = oracle.forward(pb_s, np.ascontiguousarray(vol.transpose(0, 2, 1)))
     assert np.allclose(c, d, rtol=0, atol=1e-12 * c.max())
+
+
+def test_p7_bspline_control_grid_reproduces_linear_fields():
+    """Sec. 3.1 deformation on an 8^3 control grid, reading R6: point i of
+    axis a sits at box_min_a + (i - 1) * box_a / 5.  A cubic B-spline
+    reproduces linear functions, so coefficients c_i = a + G x_i (x_i the
+    control-point positions from that statement) give u(x') = a + G x' and
+    du/dx' = G inside the box; beyond it the coordinate is clamped to the box
+    face, where u takes its face value and the clamped axis' column of the
+    Jacobian vanishes."""
+    shape, vox = (6, 7, 9), (1.3, 0.8, 1.1)          # (nz, ny, nx); vox (x, y, z)
+    origin = (-4.0, 2.5, -3.0)
+    n_xyz = shape[::-1]
+    lo = np.array([origin[a] - 0.5 * vox[a] for a in range(3)])
+    box = np.array([n_xyz[a] * vox[a] for a in range(3)])
+    rng = np.random.default_rng(31)
+    a0 = rng.normal(size=3)
+    G = rng.normal(size=(3, 3)) * 0.05
+    idx = np.arange(8)
+    ctrl = [lo[a] + (idx - 1) * box[a] / 5.0 for a in range(3)]
+    K, J_, I = np.meshgrid(idx, idx, idx, indexing="ij")      # coef[k][j][i]
+    xc = np.stack([ctrl[0][I], ctrl[1][J_], ctrl[2][K]], axis=-1)
+    coef = a0 + xc @ G.T
+    cfg = small(n=8, nu=8, nv=8, n_views=2)
+    pb = oracle.Problem(inputs.projection_matrices(cfg), shape, vox, origin, (8, 8), 0.5, coef=coef,
+                        theta=inputs.identity_theta(2), s_view=np.ones(2))
+    inside = lo + rng.uniform(0.0, 1.0, size=(400, 3)) * box
+    u, J = oracle.displacement(pb, inside)
+    assert np.max(np.abs(u - (a0 + inside @ G.T))) <= 1e-12
+    assert np.max(np.abs(J - G)) <= 1e-12
+    # beyond the box on one axis at a time: the face value, that column zero
+    for ax in range(3):
+        out = lo + rng.uniform(0.1, 0.9, size=(50, 3)) * box
+        out[:25, ax] = lo[ax] - rng.uniform(0.2, 3.0, size=25)
+        out[25:, ax] = lo[ax] + box[ax] + rng.uniform(0.2, 3.0, size=25)
+        clamped = out.copy()
+        clamped[:25, ax] = lo[ax]
+        clamped[25:, ax] = lo[ax] + box[ax]
+        u, J = oracle.displacement(pb, out)
+        assert np.max(np.abs(u - (a0 + clamped @ G.T))) <= 1e-12
+        G0 = G.copy()
+        G0[:, ax] = 0.0
+        assert np.max(np.abs(J - G0)) <= 1e-12
 
 
 def test_p7_repeated_subangles_equal_single():
