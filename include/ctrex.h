@@ -450,9 +450,16 @@ int ctrex_probe_gather_rate(void *cuda_stream, double *gathers_per_s);
  *   stream   cudaStream_t to enqueue on (NULL = legacy default stream).
  * The reduction's scratch is a 1 MiB static device array that every GPU
  * loading the library holds until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) and
- * caches it, so make the first call on each device before any stream
- * capture.  Every call shares the array: calls whose kernels overlap on the
+ * device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it.  Under CUDA's lazy module loading
+ * (the default) that lookup is what loads this file's module, which places
+ * the array and the kernels in device memory and may synchronise.  So make
+ * one call on each device before any region where allocation or
+ * synchronisation is not allowed, and before any stream capture; from the
+ * second call on, nothing is allocated.  The cached address belongs to the
+ * device's current primary context: after cudaDeviceReset on that device,
+ * do not call this function again in the same process (the cache would be
+ * stale).  Every call shares the array: calls whose kernels overlap on the
  * GPU race on it and must be serialised by the caller.  Errors:
  * CTREX_E_SHAPE, CTREX_E_DTYPE, CTREX_E_ARG (NULL buffer, eps_R < 0 or NaN),
  * CTREX_E_CUDA (address lookup or launch failed).

@@ -33,7 +33,11 @@ static __device__ __align__(256) double g_cs_partials[2 * CS_MAX_BLOCKS];
 
 // Host code must not take the address of g_cs_partials directly (in host
 // code the name is a host-side stand-in): the device address is looked up
-// once per device with cudaGetSymbolAddress and cached here.
+// once per device with cudaGetSymbolAddress and cached here.  With lazy
+// module loading that first lookup loads the module (array and kernels),
+// so callers make one call per device before any allocation-free region.
+// The cache belongs to the device's primary context and is not refreshed
+// after a cudaDeviceReset.
 std::mutex g_cs_mutex;
 double *g_cs_ptr[CS_MAX_DEVICES] = {};
 

@@ -424,17 +424,29 @@ def correct_static(p, q, rowsum, r=None, sums=None, eps_R=0.0):
     library (for callers that cannot let it call cudaMalloc); see
     ``ctrex_correct_static`` in include/ctrex.h.  Runs on the device of p, on
     the current torch stream.  Calls that overlap on the GPU share one static
-    scratch array and race: serialise them."""
+    scratch array and race: serialise them.  Every tensor is checked before
+    the call, so a wrong output buffer is refused instead of being written
+    past its end."""
     lib = load_library()
-    dev = p.device
+    dev = p.device if isinstance(p, torch.Tensor) else None
     for t, name in ((p, "p"), (q, "q"), (rowsum, "rowsum")):
         if not isinstance(t, torch.Tensor) or t.device != dev or not t.is_contiguous():
             raise ValueError(f"{name} must be a contiguous tensor on {dev}")
+    if p.dtype not in (torch.float32, torch.bfloat16):
+        raise ValueError("p must be float32 or bfloat16")
     if q.dtype != p.dtype or q.shape != p.shape or rowsum.shape != p.shape or rowsum.dtype != torch.float32:
         raise ValueError("q must match p; rowsum must be float32 of p's shape")
+    if r is not None and (not isinstance(r, torch.Tensor) or r.dtype != p.dtype or r.shape != p.shape
+                          or r.device != dev or not r.is_contiguous()):
+        raise ValueError("r must be a contiguous tensor of p's dtype, shape and device")
+    if sums is not None and (not isinstance(sums, torch.Tensor) or sums.dtype != torch.float64
+                             or sums.numel() < 2 or sums.device != dev or not sums.is_contiguous()):
+        raise ValueError("sums must be a contiguous float64 tensor of at least 2 elements on p's device")
     n = p.numel()
     if n > CORRECT_STATIC_MAX_N:
         raise ValueError(f"correct_static: n = {n} exceeds the static scratch limit {CORRECT_STATIC_MAX_N}")
+    if dev.type != "cuda":
+        raise ValueError("correct_static runs on a CUDA device only (there is no CPU fallback)")
     if r is None:
         r = torch.empty_like(p)
     if sums is None:

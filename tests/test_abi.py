@@ -89,3 +89,29 @@ def test_conv_argument_checks_answer_without_gpu(lib):
     assert wg(odd, b, c, 1, 4, 4, 4, 16, 16, st, None) == E_ARG
     assert wg(a, vp(0x20002), c, 1, 4, 4, 4, 16, 16, st, None) == E_ARG
     assert wg(a, b, c, 1, 4, 4, 4, 12, 16, st, None) == E_SHAPE
+
+
+def test_correct_static_binding_refuses_bad_buffers_without_gpu(lib):
+    """The binding checks every caller buffer before the call: an output of
+    the wrong dtype, size, device or layout would otherwise be written past
+    its end by the kernel.  A CPU input is refused too (no CPU fallback)."""
+    import torch
+
+    from paper_2609_30166_gb300 import ctrex
+
+    p = torch.zeros(16)
+    q, rs = torch.zeros(16), torch.ones(16)
+    bad_r = [torch.zeros(16, dtype=torch.float64), torch.zeros(8), torch.zeros(32)[::2],
+             torch.zeros(16, dtype=torch.bfloat16)]
+    for r in bad_r:
+        with pytest.raises(ValueError, match="r must be"):
+            ctrex.correct_static(p, q, rs, r=r)
+    bad_sums = [torch.zeros(2, dtype=torch.float32), torch.zeros(1, dtype=torch.float64),
+                torch.zeros(4, dtype=torch.float64)[::2]]
+    for sums in bad_sums:
+        with pytest.raises(ValueError, match="sums must be"):
+            ctrex.correct_static(p, q, rs, sums=sums)
+    with pytest.raises(ValueError, match="rowsum"):
+        ctrex.correct_static(p, q, rs.double())
+    with pytest.raises(ValueError, match="no CPU fallback"):
+        ctrex.correct_static(p, q, rs, r=torch.zeros(16), sums=torch.zeros(2, dtype=torch.float64))

@@ -68,6 +68,13 @@ def test_correct_static_matches_fused_correction_twice(ct):
     r2, _ = ct.correct_static(p, q, rowsum, eps_R=eps_R)
     torch.cuda.synchronize()
     assert _rel(r2, r_ref) <= 1e-5
+    # and both equal the FP64 oracle's correction on the same inputs
+    import oracle
+
+    r_o, e2_o, p2_o = oracle.correct(p.double().cpu().numpy(), q.double().cpu().numpy(),
+                                     rowsum.double().cpu().numpy(), eps_R)
+    assert _rel(r2, torch.from_numpy(r_o)) <= 1e-5
+    assert np.allclose(sums.cpu().numpy(), [e2_o, p2_o], rtol=1e-5, atol=0.0)
     ctx.close()
 
 
