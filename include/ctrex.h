@@ -432,6 +432,18 @@ int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, 
 int ctrex_probe_gather_rate(void *cuda_stream, double *gathers_per_s);
 
 /*
+ * Measured L2 read bandwidth of the current device (GB/s, bytes read): a
+ * buffer of half the L2 size is read repeatedly with 16-byte L2-only loads
+ * (no L1 allocation) by a grid of 8 CTAs per SM, 512 passes timed with CUDA
+ * events after one warm pass.  This is the denominator of the graded gather
+ * roofline: the projectors' algorithmic gather bytes (8 taps per sample, 4
+ * per backprojected voxel-view) over what L2 can deliver.  Allocates and
+ * frees the buffer; synchronises the stream.  Errors: CTREX_E_ARG (NULL
+ * output), CTREX_E_CUDA.
+ */
+int ctrex_probe_l2_read_bandwidth(void *cuda_stream, double *gb_per_s);
+
+/*
  * Detector-space correction without any allocation.  The paper has no
  * counterpart: this is an extra entry point for callers that cannot let the
  * library call cudaMalloc (a host whose caching allocator already reserved

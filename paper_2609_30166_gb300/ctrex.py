@@ -34,7 +34,7 @@ EXPORTS = (
     "ctrex_fwd_correct", "ctrex_back_project", "ctrex_adjoint_project", "ctrex_motion_grad",
     "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples", "ctrex_correct_static",
     "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad", "ctrex_os_sirt_iterate", "ctrex_set_bp_window",
-    "ctrex_probe_gather_rate", "ctrex_set_bp_subvoxel", "ctrex_set_geometry_cylinder", "ctrex_set_projector",
+    "ctrex_probe_gather_rate", "ctrex_probe_l2_read_bandwidth", "ctrex_set_bp_subvoxel", "ctrex_set_geometry_cylinder", "ctrex_set_projector",
     "ctrex_set_roi",
 )
 
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH):
         "ctrex_set_geometry_cylinder": ([vp, ctypes.POINTER(d), i, i, ctypes.POINTER(CylGrid),
                                          ctypes.POINTER(DetGrid), d], i),
         "ctrex_probe_gather_rate": ([vp, ctypes.POINTER(d)], i),
+        "ctrex_probe_l2_read_bandwidth": ([vp, ctypes.POINTER(d)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -537,6 +538,20 @@ def probe_gather_rate(device=None):
                                          ctypes.byref(out))
     if rc != OK:
         raise CtrexError(rc, "gather-rate probe failed")
+    return out.value
+
+
+def probe_l2_read_bandwidth(device=None):
+    """Measured L2 read bandwidth in GB/s (16-byte L2-only loads over half
+    of L2)."""
+    lib = load_library()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    out = ctypes.c_double(0.0)
+    with torch.cuda.device(dev):
+        rc = lib.ctrex_probe_l2_read_bandwidth(ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream),
+                                               ctypes.byref(out))
+    if rc != OK:
+        raise CtrexError(rc, "L2 read-bandwidth probe failed")
     return out.value
 
 
