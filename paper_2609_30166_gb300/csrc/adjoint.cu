@@ -159,15 +159,27 @@ cudaError_t launch_adjoint(const FwdArgs &a, const float *proj, float *vol)
 // ---------------------------------------------------------------------------
 // Motion gradient
 // ---------------------------------------------------------------------------
+//
+// dL/dtheta and dL/dcoef of L = <g, A x> (chain rule of the Sec. 4.1
+// projector through the Sec. 2.2.2 pose and the Sec. 3.1 warp).  Per sample
+// k of ray i, with y = g' + s u(g'), g' = M g + b:
+//   dL/dy  = g_i w_k grad mu(y)                 (trilinear gradient, index units)
+//   dL/dg' = dL/dy (I + s du/dg')               -> dL/db += dL/dg', dL/dM += dL/dg' g^T
+//   dL/dc_ijk[c] += s dL/dy[c] beta(xi - i) beta(eta - j) beta(zeta - k)
+// Sample positions, the warp and the pose sums are formed relative to the
+// integer grid centre c (as in the adjoint): dL/dM = sum dL/dg' (g - c)^T +
+// (sum dL/dg') c^T, the last term added in FP64 by the finish kernel.
 
-// Zero-padded trilinear interpolant's gradient (index units) inside floor(g).
+// Zero-padded trilinear interpolant's gradient (index units) inside the cell
+// floor(y), at the point with centred index coordinates yc = y - c (floor and
+// fraction exact in them).
 template <typename TV>
-__device__ __forceinline__ void trilinear_grad(const TV *__restrict__ vol, int nx, int ny, int nz,
-                                               const float g[3], float grad[3])
+__device__ __forceinline__ void trilinear_grad_c(const TV *__restrict__ vol, int nx, int ny, int nz, const float c[3],
+                                                 const float yc[3], float grad[3])
 {
-    const float fx = floorf(g[0]), fy = floorf(g[1]), fz = floorf(g[2]);
-    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
-    const float ax = g[0] - fx, ay = g[1] - fy, az = g[2] - fz;
+    const float fx = floorf(yc[0]), fy = floorf(yc[1]), fz = floorf(yc[2]);
+    const int ix = (int)fx + (int)c[0], iy = (int)fy + (int)c[1], iz = (int)fz + (int)c[2];
+    const float ax = yc[0] - fx, ay = yc[1] - fy, az = yc[2] - fz;
     float v[2][2][2];
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz)
@@ -177,7 +189,7 @@ __device__ __forceinline__ void trilinear_grad(const TV *__restrict__ vol, int n
             for (int dx = 0; dx < 2; ++dx) {
                 const int x = ix + dx, y = iy + dy, z = iz + dz;
                 const bool in = (unsigned)x < (unsigned)nx && (unsigned)y < (unsigned)ny && (unsigned)z < (unsigned)nz;
-                v[dz][dy][dx] = in ? Storage<TV>::load(vol + (z * ny + y) * nx + x) : 0.0f;
+                v[dz][dy][dx] = in ? Storage<TV>::load(vol + ((long long)z * ny + y) * nx + x) : 0.0f;
             }
     const float by0 = 1.0f - ay, bz0 = 1.0f - az, bx0 = 1.0f - ax;
     grad[0] = bz0 * (by0 * (v[0][0][1] - v[0][0][0]) + ay * (v[0][1][1] - v[0][1][0])) +
@@ -188,126 +200,208 @@ __device__ __forceinline__ void trilinear_grad(const TV *__restrict__ vol, int n
               ay * (bx0 * (v[1][1][0] - v[0][1][0]) + ax * (v[1][1][1] - v[0][1][1]));
 }
 
-// One sample of the motion gradient: accumulates dL/dM, dL/db (registers)
-// and dL/dcoef (shared memory, warp-reduced when the warp shares one cell).
-template <typename TV>
-__device__ __forceinline__ void grad_sample(const Grid &G, const MotionGPU &m, const float *coef,
-                                            const TV *__restrict__ vol, const float g[3], float scale,
-                                            bool active, float gM[9], float gb[3], float *s_gcoef)
+// Displacement u and its derivatives with respect to the three spline
+// coordinates, by sum factorisation over the separable 4 x 4 x 4 support:
+// the x sums first (value and x-derivative weights), then y, then z --
+// 576 FMAs instead of 64 taps x 12 accumulators with per-tap weight products.
+__device__ __forceinline__ void spline_value_jacobian(const float4 *coef, const int i0[3], const float wx[4],
+                                                      const float wy[4], const float wz[4], const float dx[4],
+                                                      const float dy[4], const float dz[4], float u[3],
+                                                      float Jx[3], float Jy[3], float Jz[3])
 {
-    float gp[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-        gp[r] = fmaf(m.M[3 * r], g[0], fmaf(m.M[3 * r + 1], g[1], fmaf(m.M[3 * r + 2], g[2], m.b[r])));
-    int i0[3] = {1, 1, 1};
-    float f[3] = {0.f, 0.f, 0.f};
-    bool act[3] = {false, false, false};
-    float wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
-    float u[3] = {0.f, 0.f, 0.f};
-    float J[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // J[comp][axis]
-    const bool spline = coef != nullptr && m.s != 0.0f;
-    if (spline) {
+    for (int c = 0; c < 3; ++c) u[c] = Jx[c] = Jy[c] = Jz[c] = 0.0f;
+    // the z loop stays rolled (bounds the live coefficient loads); its two
+    // weights are picked by selects, which keeps the arrays in registers
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        const int cz = min(i0[2] - 1 + k, 7);
+        const float wzk = k == 0 ? wz[0] : (k == 1 ? wz[1] : (k == 2 ? wz[2] : wz[3]));
+        const float dzk = k == 0 ? dz[0] : (k == 1 ? dz[1] : (k == 2 ? dz[2] : dz[3]));
+        float a[3] = {0.f, 0.f, 0.f}, bx[3] = {0.f, 0.f, 0.f}, by[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int j = 0; j < 4; ++j) {
+            const int cy = min(i0[1] - 1 + j, 7);
+            const float wyj = j == 0 ? wy[0] : (j == 1 ? wy[1] : (j == 2 ? wy[2] : wy[3]));
+            const float dyj = j == 0 ? dy[0] : (j == 1 ? dy[1] : (j == 2 ? dy[2] : dy[3]));
+            float sx[3] = {0.f, 0.f, 0.f}, tx[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) spline_coord(gp[a], G.spl_scale[a], i0[a], f[a], act[a]);
-        bspline_weights(f[0], wx);
-        bspline_weights(f[1], wy);
-        bspline_weights(f[2], wz);
-        bspline_dweights(f[0], dx);
-        bspline_dweights(f[1], dy);
-        bspline_dweights(f[2], dz);
-        const float sx = act[0] ? G.spl_scale[0] : 0.f, sy = act[1] ? G.spl_scale[1] : 0.f,
-                    sz = act[2] ? G.spl_scale[2] : 0.f;
+            for (int i = 0; i < 4; ++i) {
+                const int cx = min(i0[0] - 1 + i, 7);
+                const float3 cf = coef_at(coef, cx, cy, cz);
+                sx[0] = fmaf(wx[i], cf.x, sx[0]);
+                sx[1] = fmaf(wx[i], cf.y, sx[1]);
+                sx[2] = fmaf(wx[i], cf.z, sx[2]);
+                tx[0] = fmaf(dx[i], cf.x, tx[0]);
+                tx[1] = fmaf(dx[i], cf.y, tx[1]);
+                tx[2] = fmaf(dx[i], cf.z, tx[2]);
+            }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int cz = min(i0[2] - 1 + k, 7);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int cy = min(i0[1] - 1 + j, 7);
-                const float *row = coef + 3 * ((cz * 8 + cy) * 8);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int cx = min(i0[0] - 1 + i, 7);
-                    const float w0 = wx[i] * wy[j] * wz[k];
-                    const float w1 = dx[i] * wy[j] * wz[k] * sx;
-                    const float w2 = wx[i] * dy[j] * wz[k] * sy;
-                    const float w3 = wx[i] * wy[j] * dz[k] * sz;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float cv = row[3 * cx + c];
-                        u[c] = fmaf(w0, cv, u[c]);
-                        J[3 * c + 0] = fmaf(w1, cv, J[3 * c + 0]);
-                        J[3 * c + 1] = fmaf(w2, cv, J[3 * c + 1]);
-                        J[3 * c + 2] = fmaf(w3, cv, J[3 * c + 2]);
-                    }
-                }
+            for (int c = 0; c < 3; ++c) {
+                a[c] = fmaf(wyj, sx[c], a[c]);
+                bx[c] = fmaf(wyj, tx[c], bx[c]);
+                by[c] = fmaf(dyj, sx[c], by[c]);
             }
         }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            u[c] = fmaf(wzk, a[c], u[c]);
+            Jx[c] = fmaf(wzk, bx[c], Jx[c]);
+            Jy[c] = fmaf(wzk, by[c], Jy[c]);
+            Jz[c] = fmaf(dzk, a[c], Jz[c]);
+        }
     }
-    const float yv[3] = {fmaf(m.s, u[0], gp[0]), fmaf(m.s, u[1], gp[1]), fmaf(m.s, u[2], gp[2])};
-    float gy[3] = {0.f, 0.f, 0.f};
-    if (active && yv[0] >= -1.0f && yv[0] < (float)G.nx && yv[1] >= -1.0f && yv[1] < (float)G.ny &&
-        yv[2] >= -1.0f && yv[2] < (float)G.nz)
-        trilinear_grad(vol, G.nx, G.ny, G.nz, yv, gy);
+}
+
+// --- coefficient gradient on the tensor cores --------------------------------
+//
+// Over the samples s of a warp that share one spline cell, the coefficient
+// gradient of that cell is an outer-product sum
+//   G[(c, kz)][(j, i)] = sum_s  (v_s[c] wz_s[kz]) (wy_s[j] wx_s[i]),
+// v_s = s_view dL/dy_s: a 12 x 16 matrix = A (12 x samples) B (samples x 16),
+// i.e. a GEMM with K = samples.  One warp step (32 samples) is 4 k-chunks of
+// mma.m16n8k8 (TF32) per 8-column half of G, with rows 12..15 zero.  FP32
+// accuracy comes from the 3-term split x = hi + lo (hi = tf32(x), lo =
+// tf32(x - hi)): A B ~ Alo Bhi + Ahi Blo + Ahi Bhi, each product within about
+// 3 * 2^-22 of the FP32 one.  A step's MMAs start from zero (a chain of 12
+// k-steps), and its result is added to FP32 register sums of the warp's
+// current cell; those go to the CTA's FP64 shared partials (atomics, once per
+// change of cell) and, at the end, to FP64 global sums.
+//
+// Fragment layouts of mma.m16n8k8 .tf32 (g = lane / 4, t = lane % 4):
+//   A (row-major 16 x 8): a0 (g, t), a1 (g + 8, t), a2 (g, t + 4), a3 (g + 8, t + 4)
+//   B (col-major 8 x 8):  b0 (k = t, n = g), b1 (k = t + 4, n = g)
+//   C/D (16 x 8):         d0 (g, 2t), d1 (g, 2t + 1), d2 (g + 8, 2t), d3 (g + 8, 2t + 1)
+// With k = sample, lane (g, t) needs samples t and t + 4 of each chunk: it
+// reads their spline fractions and v by shuffles and evaluates the B-spline
+// basis functions its rows / columns need (kz = i = g % 4, j = g / 4 for the
+// first half of G, 2 + g / 4 for the second) itself.
+
+__device__ __forceinline__ unsigned tf32_bits(float x)
+{
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// x = hi + lo as two TF32 values.
+__device__ __forceinline__ void tf32_split(float x, unsigned &hi, unsigned &lo)
+{
+    hi = tf32_bits(x);
+    lo = tf32_bits(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32_16x8x8(float d[4], const unsigned a[4], unsigned b0, unsigned b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Power-basis coefficients (f^0 .. f^3) of the uniform cubic B-spline piece m
+// (m = 0..3: weight of control point i0 - 1 + m at fraction f).
+__device__ __forceinline__ float4 bspline_piece(int m)
+{
+    return m == 0 ? make_float4(1.0f / 6.0f, -0.5f, 0.5f, -1.0f / 6.0f)
+                  : (m == 1 ? make_float4(2.0f / 3.0f, 0.0f, -1.0f, 0.5f)
+                            : (m == 2 ? make_float4(1.0f / 6.0f, 0.5f, 0.5f, -0.5f)
+                                      : make_float4(0.0f, 0.0f, 0.0f, 1.0f / 6.0f)));
+}
+
+__device__ __forceinline__ float horner(const float4 p, float f)
+{
+    return fmaf(fmaf(fmaf(p.w, f, p.z), f, p.y), f, p.x);
+}
+
+// The warp's coefficient-gradient state: FP32 sums of the current cell's
+// 12 x 16 block in fragment layout (two 8-column halves).
+struct CoefAcc {
+    float acc[2][4];
+    int cell;  // packed i0 of the current cell, -1 for none (warp-uniform)
+};
+
+// Adds the sums of acc's cell to the CTA's FP64 partials and clears them.
+// Entries whose control point index passes 7 carry an exactly zero weight
+// (cubic piece 3 at fraction 0) and are skipped.
+__device__ __forceinline__ void coef_flush(CoefAcc &A, double *s_g64, int lane)
+{
+    if (A.cell >= 0) {
+        const int i0x = A.cell & 7, i0y = (A.cell >> 3) & 7, i0z = A.cell >> 6;
+        const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) gy[c] *= scale;  // dL/dy (index units)
-    // dL/dg' = dL/dy (I + s J)
-    float ggp[3];
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) ggp[a] = gy[a] + m.s * (gy[0] * J[a] + gy[1] * J[3 + a] + gy[2] * J[6 + a]);
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        gb[r] += ggp[r];
-        gM[3 * r + 0] = fmaf(ggp[r], g[0], gM[3 * r + 0]);
-        gM[3 * r + 1] = fmaf(ggp[r], g[1], gM[3 * r + 1]);
-        gM[3 * r + 2] = fmaf(ggp[r], g[2], gM[3 * r + 2]);
+            for (int q = 0; q < 4; ++q) {
+                const int row = g + 8 * (q >> 1), col = 8 * h + 2 * t + (q & 1);
+                const float v = A.acc[h][q];
+                A.acc[h][q] = 0.0f;
+                if (row >= 12 || v == 0.0f) continue;
+                const int comp = row >> 2, kz = row & 3, j = col >> 2, i = col & 3;
+                const int cx = i0x - 1 + i, cy = i0y - 1 + j, cz = i0z - 1 + kz;
+                if (cx > 7 || cy > 7 || cz > 7) continue;
+                atomicAdd(s_g64 + 3 * ((cz * 8 + cy) * 8 + cx) + comp, (double)v);
+            }
     }
-    if (s_gcoef == nullptr || m.s == 0.0f) return;
-    // dL/dcoef[cell + (i, j, k)][c] += s * dL/dy[c] * wx[i] wy[j] wz[k] for the
-    // 4 x 4 x 4 support of each lane's spline cell.  Lanes are served one cell
-    // at a time (a warp's rays usually share one cell, rarely two); for the
-    // lanes of that cell the 192 contributions are summed across the warp by
-    // a reduce-scatter in six passes of 32 entries (31 shuffles each), after
-    // which lane l owns entry 32 p + l and adds it to shared memory: no two
-    // lanes of a warp touch the same address.
+}
+
+// One warp step of the coefficient gradient.  Per lane: cell = packed i0 of
+// its sample, f = spline fractions, v = s_view dL/dy (zero when the lane has
+// no contribution), live = whether it has one.  Warp-collective.
+__device__ __forceinline__ void coef_step(CoefAcc &A, double *s_g64, int cell, const float f[3], const float v[3],
+                                          bool live, const float4 *s_piece)
+{
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int cell = (i0[2] * 8 + i0[1]) * 8 + i0[0];
-    unsigned pending = __ballot_sync(full, active && scale != 0.0f);
-    const float vs[3] = {m.s * gy[0], m.s * gy[1], m.s * gy[2]};
-    while (pending) {  // warp-uniform
+    const int g = lane >> 2, t = lane & 3;
+    // the B-spline pieces of this lane's rows and columns
+    const float4 pz = s_piece[g & 3], px = pz, py0 = s_piece[g >> 2], py1 = s_piece[2 + (g >> 2)];
+    unsigned pending = __ballot_sync(full, live);
+    while (pending) {  // warp-uniform: one round per distinct cell of this step
         const int leader = __ffs(pending) - 1;
         const int lcell = __shfl_sync(full, cell, leader);
         const bool mine = ((pending >> lane) & 1u) && cell == lcell;
-        const float on = mine ? 1.0f : 0.0f;
-        const int li0[3] = {__shfl_sync(full, i0[0], leader), __shfl_sync(full, i0[1], leader),
-                            __shfl_sync(full, i0[2], leader)};
-        // entry e = c * 64 + (k * 16 + j * 4 + i): pass p (32 entries) holds one
-        // component c = p / 2 and the two z planes k = 2 (p % 2) + {0, 1}
-#pragma unroll 1
-        for (int pass = 0; pass < 6; ++pass) {
-            const float vc = on * (pass < 2 ? vs[0] : (pass < 4 ? vs[1] : vs[2]));
-            const float wz0 = (pass & 1) ? wz[2] : wz[0], wz1 = (pass & 1) ? wz[3] : wz[1];
-            float v[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) v[q] = vc * (q < 16 ? wz0 : wz1) * wy[(q >> 2) & 3] * wx[q & 3];
-            // recursive halving: after the offset-o stage a lane keeps the half
-            // of its entries whose bit matches its own lane bit o
-#pragma unroll
-            for (int o = 16, half = 16; o > 0; o >>= 1, half >>= 1) {
-                const bool upper = (lane & o) != 0;
-#pragma unroll
-                for (int q = 0; q < half; ++q) {
-                    const float send = upper ? v[q] : v[q + half];
-                    const float keep = upper ? v[q + half] : v[q];
-                    v[q] = keep + __shfl_xor_sync(full, send, o);
-                }
-            }
-            // lane owns entry 32 pass + lane: c = pass / 2, (i, j, k) from the lane
-            const int c = pass >> 1;
-            const int cx = min(li0[0] - 1 + (lane & 3), 7), cy = min(li0[1] - 1 + ((lane >> 2) & 3), 7),
-                      cz = min(li0[2] - 1 + 2 * (pass & 1) + (lane >> 4), 7);
-            if (v[0] != 0.0f) atomicAdd(s_gcoef + 3 * ((cz * 8 + cy) * 8 + cx) + c, v[0]);
+        if (lcell != A.cell) {
+            coef_flush(A, s_g64, lane);
+            A.cell = lcell;
         }
+        const float pv0 = mine ? v[0] : 0.0f, pv1 = mine ? v[1] : 0.0f, pv2 = mine ? v[2] : 0.0f;
+        const float pfx = mine ? f[0] : 0.0f, pfy = mine ? f[1] : 0.0f, pfz = mine ? f[2] : 0.0f;
+        float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            float a[4], b[2][2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int src = 8 * q + t + 4 * h;
+                const float fx = __shfl_sync(full, pfx, src), fy = __shfl_sync(full, pfy, src),
+                            fz = __shfl_sync(full, pfz, src);
+                const float x0 = __shfl_sync(full, pv0, src), x1 = __shfl_sync(full, pv1, src),
+                            x2 = __shfl_sync(full, pv2, src);
+                const float wz = horner(pz, fz), wx = horner(px, fx);
+                a[2 * h] = (g < 4 ? x0 : x1) * wz;        // row g:     c = g / 4, kz = g % 4
+                a[2 * h + 1] = g < 4 ? x2 * wz : 0.0f;    // row g + 8: c = 2 (rows 12..15 zero)
+                b[0][h] = horner(py0, fy) * wx;           // column g of half 0: j = g / 4, i = g % 4
+                b[1][h] = horner(py1, fy) * wx;           // column g of half 1: j = 2 + g / 4
+            }
+            unsigned ah[4], al[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) tf32_split(a[e], ah[e], al[e]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                unsigned bh0, bl0, bh1, bl1;
+                tf32_split(b[h][0], bh0, bl0);
+                tf32_split(b[h][1], bh1, bl1);
+                mma_tf32_16x8x8(d[h], al, bh0, bh1);
+                mma_tf32_16x8x8(d[h], ah, bl0, bl1);
+                mma_tf32_16x8x8(d[h], ah, bh0, bh1);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) A.acc[h][e] += d[h][e];
         pending &= ~__ballot_sync(full, mine);
     }
 }
@@ -317,68 +411,132 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY, CTREX_MGRAD_MIN_BLOCKS)
     motion_grad_kernel(Grid G, const ViewGPU *__restrict__ views, const MotionGPU *__restrict__ motion,
                        const float *__restrict__ coef_g, const int *__restrict__ view_idx,
                        const TV *__restrict__ vol, const float *__restrict__ gproj,
-                       float *__restrict__ grad_M, float *__restrict__ grad_b,
-                       float *__restrict__ grad_coef, unsigned *devcheck)
+                       double *__restrict__ grad_M, double *__restrict__ grad_b,
+                       double *__restrict__ grad_coef, unsigned *devcheck)
 {
-    __shared__ float s_coef[NCOEF];
-    __shared__ float s_gcoef[NCOEF];
-    __shared__ float s_red[12][ADJ_TX * ADJ_TY / 32];
+    __shared__ float4 s_coef[NCOEF / 3];  // padded: one vector load per control point
+    __shared__ double s_g64[NCOEF];       // the CTA's coefficient-gradient partials
+    __shared__ double s_red[12][ADJ_TX * ADJ_TY / 32];
+    __shared__ float4 s_piece[4];
     const int tid = threadIdx.y * ADJ_TX + threadIdx.x;
+    const int lane = tid & 31;
     const int k = blockIdx.y;
-    int view = view_idx ? view_idx[k] : k;
-    const bool view_ok = view >= 0 && view < G.n_views;
-    if (!view_ok) {
+    const int view = view_idx ? view_idx[k] : k;
+    if (!(view >= 0 && view < G.n_views)) {
         if (tid == 0) atomicOr(devcheck, (unsigned)DEVCHECK_OOB);
         return;  // uniform over the CTA
     }
     const MotionGPU mo = motion[view];
-    const float *coef = nullptr;
-    if (coef_g) {
-        for (int i = tid; i < NCOEF; i += ADJ_TX * ADJ_TY) {
-            s_coef[i] = coef_g[i];
-            s_gcoef[i] = 0.0f;
-        }
-        coef = s_coef;
-    }
+    const bool spline = coef_g != nullptr && mo.s != 0.0f;
+    const bool want_coef = spline && grad_coef != nullptr;
+    if (spline)
+        for (int i = tid; i < NCOEF / 3; i += ADJ_TX * ADJ_TY)
+            s_coef[i] = make_float4(coef_g[3 * i], coef_g[3 * i + 1], coef_g[3 * i + 2], 0.0f);
+    if (want_coef)
+        for (int i = tid; i < NCOEF; i += ADJ_TX * ADJ_TY) s_g64[i] = 0.0;
+    if (tid < 4) s_piece[tid] = bspline_piece(tid);
     __syncthreads();
-    float gM[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
+    float cen[3];
+    grid_centre(G, cen);
+    CoefAcc CA;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) CA.acc[h][e] = 0.0f;
+    CA.cell = -1;
+    float G1[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
     int iu, iv;
     tile_pixel<true>(blockIdx.x * ADJ_TX, blockIdx.z * ADJ_TY, iu, iv);
     const bool pix_ok = iu < G.nu && iv < G.nv;
     const float y = pix_ok ? gproj[((size_t)k * G.nv + iv) * G.nu + iu] * G.inv_sub : 0.0f;
-    float *gco = (coef_g && grad_coef) ? s_gcoef : nullptr;
     for (int s = 0; s < G.n_sub; ++s) {
-        Ray R;
-        bool hit = pix_ok && setup_ray(G, views[view * G.n_sub + s], (float)(pix_ok ? iu : 0),
-                                       (float)(pix_ok ? iv : 0), R);
-        // the warp-collective shared-memory reduction needs every lane: lanes
-        // without work run the loop with zero weight up to the warp's longest ray
-        int K = hit ? R.K : 0;
+        Ray R;  // sample positions relative to the grid centre
+        const bool hit = pix_ok && setup_ray(G, views[view * G.n_sub + s], (float)(pix_ok ? iu : 0),
+                                             (float)(pix_ok ? iv : 0), R, cen);
+        // the warp-collective coefficient step needs every lane: lanes without
+        // work run the loop with zero weight up to the warp's longest ray
+        const int K = hit ? R.K : 0;
         int Kmax = K;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) Kmax = max(Kmax, __shfl_xor_sync(0xffffffffu, Kmax, off));
         for (int kk = 0; kk < Kmax; ++kk) {
-            float g[3] = {0.f, 0.f, 0.f};
+            float gc[3] = {0.f, 0.f, 0.f};
             float sc = 0.0f;
-            const bool act = hit && kk < K && y != 0.0f;
             if (hit && kk < K - 1) {
-                g[0] = fmaf((float)kk, R.sg[0], R.g0[0]);
-                g[1] = fmaf((float)kk, R.sg[1], R.g0[1]);
-                g[2] = fmaf((float)kk, R.sg[2], R.g0[2]);
+                gc[0] = fmaf((float)kk, R.sg[0], R.g0[0]);
+                gc[1] = fmaf((float)kk, R.sg[1], R.g0[1]);
+                gc[2] = fmaf((float)kk, R.sg[2], R.g0[2]);
                 sc = y * G.step_mm;
             } else if (hit && kk == K - 1) {
-                g[0] = R.g_last[0];
-                g[1] = R.g_last[1];
-                g[2] = R.g_last[2];
+                gc[0] = R.g_last[0];
+                gc[1] = R.g_last[1];
+                gc[2] = R.g_last[2];
                 sc = R.w_last > 0.0f ? y * R.w_last : 0.0f;
             }
-            grad_sample(G, mo, coef, vol, g, act ? sc : 0.0f, act, gM, gb, gco);
+            const bool act = hit && kk < K && sc != 0.0f;
+            // warp: d = D gc + bc (+ s u), g' - c = gc + d
+            float d[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                d[r] = fmaf(mo.D[3 * r], gc[0], fmaf(mo.D[3 * r + 1], gc[1], fmaf(mo.D[3 * r + 2], gc[2], mo.bc[r])));
+            int i0[3] = {1, 1, 1};
+            float f[3] = {0.f, 0.f, 0.f};
+            float u[3] = {0.f, 0.f, 0.f}, Jx[3] = {0.f, 0.f, 0.f}, Jy[3] = {0.f, 0.f, 0.f},
+                  Jz[3] = {0.f, 0.f, 0.f};
+            if (spline) {
+                bool on[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) spline_coord(gc[a] + d[a] + cen[a], G.spl_scale[a], i0[a], f[a], on[a]);
+                float wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
+                bspline_weights(f[0], wx);
+                bspline_weights(f[1], wy);
+                bspline_weights(f[2], wz);
+                bspline_dweights(f[0], dx);
+                bspline_dweights(f[1], dy);
+                bspline_dweights(f[2], dz);
+                spline_value_jacobian(s_coef, i0, wx, wy, wz, dx, dy, dz, u, Jx, Jy, Jz);
+                const float sx = on[0] ? G.spl_scale[0] : 0.f, sy = on[1] ? G.spl_scale[1] : 0.f,
+                            sz = on[2] ? G.spl_scale[2] : 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Jx[c] *= sx;
+                    Jy[c] *= sy;
+                    Jz[c] *= sz;
+                }
+            }
+            const float yc[3] = {gc[0] + fmaf(mo.s, u[0], d[0]), gc[1] + fmaf(mo.s, u[1], d[1]),
+                                 gc[2] + fmaf(mo.s, u[2], d[2])};
+            float gy[3] = {0.f, 0.f, 0.f};
+            if (act && yc[0] >= -1.0f - cen[0] && yc[0] < (float)G.nx - cen[0] && yc[1] >= -1.0f - cen[1] &&
+                yc[1] < (float)G.ny - cen[1] && yc[2] >= -1.0f - cen[2] && yc[2] < (float)G.nz - cen[2])
+                trilinear_grad_c(vol, G.nx, G.ny, G.nz, cen, yc, gy);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gy[c] *= sc;  // dL/dy (index units)
+            // dL/dg' = dL/dy (I + s J), J[c][a] = du_c / dg'_a
+            const float gg[3] = {gy[0] + mo.s * (gy[0] * Jx[0] + gy[1] * Jx[1] + gy[2] * Jx[2]),
+                                 gy[1] + mo.s * (gy[0] * Jy[0] + gy[1] * Jy[1] + gy[2] * Jy[2]),
+                                 gy[2] + mo.s * (gy[0] * Jz[0] + gy[1] * Jz[1] + gy[2] * Jz[2])};
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                gb[r] += gg[r];
+                G1[3 * r + 0] = fmaf(gg[r], gc[0], G1[3 * r + 0]);
+                G1[3 * r + 1] = fmaf(gg[r], gc[1], G1[3 * r + 1]);
+                G1[3 * r + 2] = fmaf(gg[r], gc[2], G1[3 * r + 2]);
+            }
+            if (want_coef) {  // CTA-uniform
+                const float v[3] = {mo.s * gy[0], mo.s * gy[1], mo.s * gy[2]};
+                const bool live = act && (v[0] != 0.0f || v[1] != 0.0f || v[2] != 0.0f);
+                const int cell = (i0[2] * 8 + i0[1]) * 8 + i0[0];
+                coef_step(CA, s_g64, cell, f, v, live, s_piece);
+            }
         }
     }
-    // CTA reduction of the 12 pose-gradient entries, one atomic each
+    if (want_coef) coef_flush(CA, s_g64, lane);
+    // CTA reduction of the 12 pose-gradient entries: FP32 warp sums, FP64 over
+    // the warps and across CTAs
     float vals[12];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) vals[q] = gM[q];
+    for (int q = 0; q < 9; ++q) vals[q] = G1[q];
 #pragma unroll
     for (int q = 0; q < 3; ++q) vals[9 + q] = gb[q];
 #pragma unroll
@@ -386,26 +544,26 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY, CTREX_MGRAD_MIN_BLOCKS)
         float v = vals[q];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if ((tid & 31) == 0) s_red[q][tid >> 5] = v;
+        if (lane == 0) s_red[q][tid >> 5] = (double)v;
     }
     __syncthreads();
     if (tid < 12) {
-        float v = 0.0f;
+        double v = 0.0;
 #pragma unroll
         for (int w = 0; w < ADJ_TX * ADJ_TY / 32; ++w) v += s_red[tid][w];
         if (grad_M && tid < 9) atomicAdd(grad_M + 9 * view + tid, v);
         if (grad_b && tid >= 9) atomicAdd(grad_b + 3 * view + (tid - 9), v);
     }
-    if (gco) {
+    if (want_coef) {
         for (int i = tid; i < NCOEF; i += ADJ_TX * ADJ_TY) {
-            const float v = s_gcoef[i];
-            if (v != 0.0f) atomicAdd(grad_coef + i, v);
+            const double v = s_g64[i];
+            if (v != 0.0) atomicAdd(grad_coef + i, v);
         }
     }
 }
 
-cudaError_t launch_motion_grad(const FwdArgs &a, const float *gproj, float *grad_M, float *grad_b,
-                               float *grad_coef_idx)
+cudaError_t launch_motion_grad(const FwdArgs &a, const float *gproj, double *grad_M, double *grad_b,
+                               double *grad_coef_idx)
 {
     if (a.n_idx == 0) return cudaSuccess;
     const Grid &G = *a.grid;
@@ -546,8 +704,10 @@ cudaError_t launch_motion_setup(const float *theta, const float *coef, const flo
 }
 
 // dL/d(omega, t, A) from dL/d(M, b) (index coordinates); one thread per view.
+// gMc holds sum dL/dg' (g - c)^T, so dL/dM = gMc + gb c^T (c: integer grid
+// centre).
 __global__ void motion_finish_kernel(const float *__restrict__ theta, const float *__restrict__ dRdw,
-                                     const float *__restrict__ gM, const float *__restrict__ gb, int n_views,
+                                     const double *__restrict__ gMc, const double *__restrict__ gb, int n_views,
                                      Frame F, float *__restrict__ grad_theta)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -561,8 +721,10 @@ __global__ void motion_finish_kernel(const float *__restrict__ theta, const floa
     double gMw[9], gbw[3];
     for (int r = 0; r < 3; ++r) {
         gbw[r] = gb[3 * v + r] / F.vox[r];
-        for (int c = 0; c < 3; ++c)
-            gMw[3 * r + c] = gM[9 * v + 3 * r + c] * F.vox[c] / F.vox[r] + gb[3 * v + r] * F.origin[c] / F.vox[r];
+        for (int c = 0; c < 3; ++c) {
+            const double gM = gMc[9 * v + 3 * r + c] + gb[3 * v + r] * F.cen[c];
+            gMw[3 * r + c] = gM * F.vox[c] / F.vox[r] + gb[3 * v + r] * F.origin[c] / F.vox[r];
+        }
     }
     // Mw = A R, bw = A t
     double gA[9], gR[9], gt[3];
@@ -590,21 +752,23 @@ __global__ void motion_finish_kernel(const float *__restrict__ theta, const floa
     (void)dRdw;
 }
 
-__global__ void coef_grad_finish_kernel(const float *__restrict__ g_idx, Frame F, float *__restrict__ grad_coef)
+__global__ void coef_grad_finish_kernel(const double *__restrict__ g_idx, Frame F, float *__restrict__ grad_coef)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < NCOEF) grad_coef[i] += (float)(g_idx[i] / F.vox[i % 3]);
 }
 
-cudaError_t launch_motion_grad_finish(const float *theta, const float *dRdw, const float *grad_M,
-                                      const float *grad_b, const float *grad_coef_idx, int n_views,
-                                      const double vox[3], const double origin[3], float *grad_theta,
-                                      float *grad_coef, cudaStream_t stream)
+cudaError_t launch_motion_grad_finish(const float *theta, const float *dRdw, const double *grad_M,
+                                      const double *grad_b, const double *grad_coef_idx, int n_views,
+                                      const Grid &G, const double vox[3], const double origin[3],
+                                      float *grad_theta, float *grad_coef, cudaStream_t stream)
 {
     Frame F;
+    const int n[3] = {G.nx, G.ny, G.nz};
     for (int a = 0; a < 3; ++a) {
         F.vox[a] = vox[a];
         F.origin[a] = origin[a];
+        F.cen[a] = (double)((n[a] - 1) / 2);
     }
     if (grad_theta && theta) {
         motion_finish_kernel<<<(n_views + 127) / 128, 128, 0, stream>>>(theta, dRdw, grad_M, grad_b, n_views, F,

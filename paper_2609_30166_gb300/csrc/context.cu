@@ -33,7 +33,7 @@ struct ctrex_ctx {
     float *d_coef = nullptr;      // [8][8][8][3] mm
     float *d_coef_idx = nullptr;  // [8][8][8][3] voxels
     float *d_dRdw = nullptr;      // [n_views][27]
-    float *d_gM = nullptr, *d_gb = nullptr, *d_gcoef = nullptr;  // gradient scratch
+    double *d_gM = nullptr, *d_gb = nullptr, *d_gcoef = nullptr;  // gradient scratch (FP64 sums)
     bool coef_valid = false, theta_valid = false;
     // scratch
     float *d_partials = nullptr;
@@ -638,9 +638,9 @@ int ctrex_set_motion(ctrex_ctx *c, const float *theta, const float *coef, const 
         CT_CUDA(c, cudaMalloc((void **)&c->d_theta, sizeof(float) * 15 * (size_t)V));
         CT_CUDA(c, cudaMalloc((void **)&c->d_coef, sizeof(float) * 1536));
         CT_CUDA(c, cudaMalloc((void **)&c->d_coef_idx, sizeof(float) * 1536));
-        CT_CUDA(c, cudaMalloc((void **)&c->d_gM, sizeof(float) * 9 * (size_t)V));
-        CT_CUDA(c, cudaMalloc((void **)&c->d_gb, sizeof(float) * 3 * (size_t)V));
-        CT_CUDA(c, cudaMalloc((void **)&c->d_gcoef, sizeof(float) * 1536));
+        CT_CUDA(c, cudaMalloc((void **)&c->d_gM, sizeof(double) * 9 * (size_t)V));
+        CT_CUDA(c, cudaMalloc((void **)&c->d_gb, sizeof(double) * 3 * (size_t)V));
+        CT_CUDA(c, cudaMalloc((void **)&c->d_gcoef, sizeof(double) * 1536));
     }
     const float *th = nullptr;
     if (theta) {
@@ -914,14 +914,14 @@ int ctrex_motion_grad(ctrex_ctx *c, const void *vol, int vdt, const float *gproj
         return fail(c, CTREX_E_STATE, "motion_grad: grad_coef requested but no coefficients were set");
     DeviceGuard g(c->device);
     const int V = c->grid.n_views;
-    CT_CUDA(c, cudaMemsetAsync(c->d_gM, 0, sizeof(float) * 9 * (size_t)V, c->stream));
-    CT_CUDA(c, cudaMemsetAsync(c->d_gb, 0, sizeof(float) * 3 * (size_t)V, c->stream));
-    CT_CUDA(c, cudaMemsetAsync(c->d_gcoef, 0, sizeof(float) * 1536, c->stream));
+    CT_CUDA(c, cudaMemsetAsync(c->d_gM, 0, sizeof(double) * 9 * (size_t)V, c->stream));
+    CT_CUDA(c, cudaMemsetAsync(c->d_gb, 0, sizeof(double) * 3 * (size_t)V, c->stream));
+    CT_CUDA(c, cudaMemsetAsync(c->d_gcoef, 0, sizeof(double) * 1536, c->stream));
     cudaError_t ce = launch_motion_grad(fwd_args(c, vol, vdt, view_idx, n_idx), gproj, c->d_gM, c->d_gb,
                                         grad_coef ? c->d_gcoef : nullptr);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "motion_grad launch");
     ce = launch_motion_grad_finish(c->theta_valid ? c->d_theta : nullptr, c->d_dRdw, c->d_gM, c->d_gb, c->d_gcoef, V,
-                                   c->vox, c->origin, grad_theta, grad_coef, c->stream);
+                                   c->grid, c->vox, c->origin, grad_theta, grad_coef, c->stream);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "motion_grad finish");
     return CTREX_OK;
 }

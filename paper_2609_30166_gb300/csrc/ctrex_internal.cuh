@@ -146,15 +146,15 @@ struct BpArgs {
 cudaError_t launch_backproject(const BpArgs &a);
 
 cudaError_t launch_adjoint(const FwdArgs &a, const float *proj, float *vol);
-cudaError_t launch_motion_grad(const FwdArgs &a, const float *gproj, float *grad_M, float *grad_b,
-                               float *grad_coef_idx);
+cudaError_t launch_motion_grad(const FwdArgs &a, const float *gproj, double *grad_M, double *grad_b,
+                               double *grad_coef_idx);
 cudaError_t launch_motion_setup(const float *theta, const float *coef, const float *s_view,
                                 int n_views, const Grid &g, const double vox[3],
                                 const double origin[3], MotionGPU *motion, float *coef_idx,
                                 float *dRdw, cudaStream_t stream);
-cudaError_t launch_motion_grad_finish(const float *theta, const float *dRdw, const float *grad_M,
-                                      const float *grad_b, const float *grad_coef_idx,
-                                      int n_views, const double vox[3], const double origin[3],
+cudaError_t launch_motion_grad_finish(const float *theta, const float *dRdw, const double *grad_M,
+                                      const double *grad_b, const double *grad_coef_idx, int n_views,
+                                      const Grid &g, const double vox[3], const double origin[3],
                                       float *grad_theta, float *grad_coef, cudaStream_t stream);
 
 }  // namespace ctrex

@@ -178,19 +178,26 @@ def test_fullsize_motion_adjoint_and_gradient():
     derivatives and the 1536 coefficient derivatives.  The adjoint identity
     <A x, g> = <x, A^T g> is checked over all 360 views with positive g.
 
-    Tolerances: with positive detector values the adjoint sums ~10^2
+    Tolerances.  With positive detector values the adjoint sums ~10^2
     same-sign contributions per voxel (TOL32).  With zero-mean values they
     cancel, and the FP32 rounding of the sample positions (index coordinates
-    up to 256: up to 1.5e-5 voxel, moving trilinear weights by as much) no
-    longer averages out: a few 1e-5, bound 1e-4.  Each
-    coefficient derivative sums ~10^7 mixed-sign per-sample terms in FP32
-    (warp sums, then per-CTA shared-memory and global atomics); with random
-    g the result is a random walk ~sqrt(n) times one term while the rounding
-    grows with sum |terms| ~ n terms, so the relative error scales like
-    sqrt(n) u ~ 3e-4: the bound is 1e-3.  The pose derivatives of one view
-    are checked at the same bound."""
+    up to 256: ~1e-5 voxel) no longer averages out: a few 1e-5, bound 1e-4.
+
+    The motion gradient samples grad mu of the trilinear interpolant, which
+    jumps at every cell face (by the second difference of the volume).  On
+    this phantom (ellipsoids with one-voxel edges) and zero-mean g the exact
+    result is ill-conditioned in the sample positions: the FP64 oracle's own
+    gradient moves by more than 1e-4 when the pose is shifted rigidly by
+    1e-5 voxel, less than the FP32 position rounding (checked below).  The
+    GPU's FP32 positions therefore cannot agree better than that; the bound
+    is 1e-3.  The well-conditioned case -- a smooth volume (the phantom
+    blurred by a Gaussian of 2 voxels) and positive g, where a 1e-5-voxel
+    perturbation moves the oracle by ~1e-6 -- is held to TOL32 and checks the
+    FP64 accumulation of the ~10^7 per-sample terms."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    from scipy.ndimage import gaussian_filter
+
     from paper_2609_30166_gb300 import _build, ctrex
 
     _build.build_library()
@@ -201,8 +208,10 @@ def test_fullsize_motion_adjoint_and_gradient():
     f = lambda a: torch.as_tensor(a, dtype=torch.float32).cuda().contiguous()  # noqa: E731
     ctx.set_motion(f(th), f(co), f(sv), cfg.margin)
     vol = inputs.phantom(cfg, device="cuda").float().contiguous()
-    pb = oracle.Problem(P, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin, (cfg.nu, cfg.nv), cfg.step_vox, theta=th,
-                        coef=co, s_view=sv, margin=cfg.margin)
+    problem = lambda theta: oracle.Problem(P, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin,  # noqa: E731
+                                           (cfg.nu, cfg.nv), cfg.step_vox, theta=theta, coef=co, s_view=sv,
+                                           margin=cfg.margin)
+    pb = problem(th)
     rng = np.random.default_rng(360)
     v = 137
     gv = rng.normal(size=(cfg.nv, cfg.nu))
@@ -221,13 +230,31 @@ def test_fullsize_motion_adjoint_and_gradient():
     gt_ref, gc_ref = oracle.motion_grad(pb, vol64, gv[None], views=one)
     e_t = rel_l2(gt.double().cpu().numpy()[v], gt_ref[v])
     e_c = rel_l2(gc.double().cpu().numpy(), gc_ref)
+    # conditioning of that case: the oracle itself under a 1e-5-voxel shift
+    th_s = th.copy()
+    th_s[v, 3:6] += 1e-5 * cfg.vox * np.array([1.0, -0.7, 0.4])
+    gt_s, gc_s = oracle.motion_grad(problem(th_s), vol64, gv[None], views=one)
+    k_t, k_c = rel_l2(gt_s[v], gt_ref[v]), rel_l2(gc_s, gc_ref)
     others = torch.ones(cfg.n_views, dtype=torch.bool)
     others[v] = False
     other = float(gt[others.cuda()].abs().max())  # views with zero g get exactly zero
-    print(f"motion 256^3 full size, view {v}: adjoint rel.L2 {e_pos:.3e} (positive g), {e_adj:.3e} (zero-mean g), "
-          f"pose derivatives {e_t:.3e}, coefficient derivatives {e_c:.3e}")
+    # the well-conditioned case: smooth volume, positive g
+    vs64 = gaussian_filter(inputs.phantom(cfg).double().numpy(), 2.0)
+    vs = torch.as_tensor(vs64, dtype=torch.float32).cuda().contiguous()
+    vs64 = vs.double().cpu().numpy()
+    gts, gcs = ctx.motion_grad(vs, g2)
+    gts_ref, gcs_ref = oracle.motion_grad(pb, vs64, gpos[None], views=one)
+    e_ts = rel_l2(gts.double().cpu().numpy()[v], gts_ref[v])
+    e_cs = rel_l2(gcs.double().cpu().numpy(), gcs_ref)
+    print(f"motion 256^3 full size, view {v}: adjoint rel.L2 {e_pos:.3e} (positive g), {e_adj:.3e} (zero-mean g); "
+          f"gradient, phantom, zero-mean g: pose {e_t:.3e}, coefficients {e_c:.3e} (oracle moved by "
+          f"{k_t:.3e} / {k_c:.3e} under a 1e-5-voxel shift); smooth volume, positive g: pose {e_ts:.3e}, "
+          f"coefficients {e_cs:.3e}")
     assert np.abs(adj_ref).max() > 0 and np.abs(gc_ref).max() > 0
-    assert e_pos <= TOL32 and e_adj <= 1e-4 and e_t <= 1e-3 and e_c <= 1e-3 and other == 0.0
+    assert e_pos <= TOL32 and e_adj <= 1e-4 and other == 0.0
+    assert k_t > 1e-4 and k_c > 1e-4  # ill-conditioned at the FP32 position level
+    assert e_t <= 1e-3 and e_c <= 1e-3
+    assert e_ts <= TOL32 and e_cs <= TOL32
     # adjoint identity over all views (positive g: no cancellation)
     gp = torch.rand((cfg.n_views, cfg.nv, cfg.nu), device="cuda", generator=torch.Generator(device="cuda").manual_seed(7))
     lhs = float((ctx.fwd_project(vol).double() * gp.double()).sum())

@@ -1,0 +1,148 @@
+"""Accuracy of 50 SIRT iterations of Eq. (1) at full size (the perturbed
+512^3 workload: 768^2 detector, 720 views), FP32 storage and BF16 storage,
+against the FP64 oracle on the central 64^3 sub-volume.
+
+A full FP64 SIRT at 512^3 is out of reach on the host, so the check is per
+step: at k = 0 and k = 49 the oracle takes the GPU's own iterate x_k (upcast
+to FP64) and computes x_{k+1} = x_k + C B R (p - A x_k) exactly on every
+voxel of the central 64^3 sub-volume.  Every ray whose bilinear footprint can
+reach a sub-volume voxel is re-projected in full through the whole 512^3
+x_k: per view, every pixel of the bounding rectangle of the projected
+sub-volume (with one pixel more on the high side for the bilinear taps).
+The measured projections p are the GPU's (an input to the step, the same on
+both sides).
+
+Tolerances: FP32 storage 1e-5 (the FP32 contract), on x_{k+1} and on the
+update x_{k+1} - x_k alone (at k = 49 the update is small against x_k, so
+the first figure alone would hide its error).  BF16 storage: the GPU stores
+x_{k+1} (and the correction images) in BF16, one rounding of at most 2^-9
+relative per element, so 4e-3 on x_{k+1} as for every BF16 output (the
+update's own error is printed: the rounding of x_{k+1} dominates it).  Also
+printed:
+how far the BF16-storage run has drifted from the FP32-storage run after 50
+iterations (GPU against GPU) and both runs' residuals.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_30166_gb300 import inputs
+from tests.helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+TOL16 = 4e-3
+SUB = 64
+
+
+def _subvolume(cfg):
+    lo = (cfg.n - SUB) // 2
+    return lo, lo + SUB
+
+
+def _footprint_rects(cfg, P, lo, hi):
+    """Per view: (u0, u1, v0, v1), the pixel rectangle holding every bilinear
+    tap of every voxel centre in [lo, hi)^3 (corners projected in FP64)."""
+    idx = np.array([lo, hi - 1], dtype=np.float64)
+    corners = np.array([[cfg.origin[0] + a * cfg.vox, cfg.origin[1] + b * cfg.vox, cfg.origin[2] + c * cfg.vox, 1.0]
+                        for a in idx for b in idx for c in idx])
+    rects = []
+    for v in range(cfg.n_views):
+        h = corners @ P[v, 0].T
+        assert (h[:, 2] * np.sign(h[0, 2]) > 0).all()
+        u, w = h[:, 0] / h[:, 2], h[:, 1] / h[:, 2]
+        u0, u1 = max(int(math.floor(u.min())), 0), min(int(math.floor(u.max())) + 1, cfg.nu - 1)
+        v0, v1 = max(int(math.floor(w.min())), 0), min(int(math.floor(w.max())) + 1, cfg.nv - 1)
+        rects.append((u0, u1, v0, v1))
+    return rects
+
+
+def _oracle_step(pb, cfg, rects, x_k, p, lo, hi, chunk=60):
+    """x_{k+1} on the sub-volume, in FP64, from the GPU's x_k and p."""
+    x64 = x_k.double().cpu().numpy()
+    views, us, vs = [], [], []
+    for v, (u0, u1, v0, v1) in enumerate(rects):
+        U, V = np.meshgrid(np.arange(u0, u1 + 1), np.arange(v0, v1 + 1))
+        views.append(np.full(U.size, v, dtype=np.int32))
+        us.append(U.ravel())
+        vs.append(V.ravel())
+    views, us, vs = np.concatenate(views), np.concatenate(us), np.concatenate(vs)
+    q, rs = oracle.forward_rays(pb, x64, views, us.astype(np.float64), vs.astype(np.float64))
+    p_sel = p[torch.as_tensor(views, dtype=torch.long, device=p.device), torch.as_tensor(vs, device=p.device),
+              torch.as_tensor(us, device=p.device)].double().cpu().numpy()
+    R = np.where(rs > pb.eps_R, 1.0 / np.where(rs > 0, rs, 1.0), 0.0)
+    r_sel = R * (p_sel - q)
+    Z, Y, X = np.meshgrid(*(np.arange(lo, hi),) * 3, indexing="ij")
+    vox = ((Z * cfg.n + Y) * cfg.n + X).ravel()
+    b = np.zeros(vox.size)
+    c = np.zeros(vox.size)
+    for v0 in range(0, cfg.n_views, chunk):
+        sel = np.arange(v0, min(v0 + chunk, cfg.n_views))
+        r = np.zeros((sel.size, cfg.nv, cfg.nu))
+        m = (views >= sel[0]) & (views <= sel[-1])
+        r[views[m] - v0, vs[m], us[m]] = r_sel[m]
+        bb, cc = oracle.backproject_voxels(pb, r, vox, views=sel)
+        b += bb
+        c += cc
+    C = np.where(c > oracle.EPS_C, 1.0 / np.where(c > 0, c, 1.0), 0.0)
+    return x64[lo:hi, lo:hi, lo:hi].ravel() + C * b, vox.size, views.size
+
+
+def _run(ctx, cfg, p, dtype):
+    """x_0, x_1, x_49, x_50 and the residual history of 50 iterations."""
+    x = torch.zeros(cfg.vol_shape, dtype=dtype, device="cuda")
+    snaps, hist = {0: x.clone()}, []
+    for k, n in ((1, 1), (49, 48), (50, 1)):
+        x, h, done = ctx.sirt_iterate(x, p, n)
+        assert done == n
+        hist.extend(h.tolist())
+        snaps[k] = x.clone()
+    return snaps, hist
+
+
+def test_perturbed512_sirt_50_iterations_against_oracle_subvolume():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_30166_gb300 import _build, ctrex
+
+    _build.build_library()
+    cfg = inputs.PERTURBED_512
+    P = inputs.projection_matrices(cfg)
+    ctx = ctrex.context_for(cfg, P=P)
+    phantom = inputs.phantom(cfg, device="cuda").to(torch.float32).contiguous()
+    p32 = ctx.fwd_project(phantom)
+    del phantom
+    pb = oracle.Problem(P, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin, (cfg.nu, cfg.nv), cfg.step_vox)
+    lo, hi = _subvolume(cfg)
+    rects = _footprint_rects(cfg, P, lo, hi)
+    results = {}
+    finals = {}
+    for name, dtype in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        p = p32 if dtype == torch.float32 else p32.to(torch.bfloat16).contiguous()
+        snaps, hist = _run(ctx, cfg, p, dtype)
+        finals[name] = (snaps[50].float(), hist[-1])
+        for k in (0, 49):
+            want, n_vox, n_rays = _oracle_step(pb, cfg, rects, snaps[k], p, lo, hi)
+            got = snaps[k + 1][lo:hi, lo:hi, lo:hi].double().cpu().numpy().ravel()
+            xk = snaps[k][lo:hi, lo:hi, lo:hi].double().cpu().numpy().ravel()
+            results[(name, k)] = rel_l2(got, want)
+            results[(name, k, "update")] = rel_l2(got - xk, want - xk)
+        del snaps, p
+        torch.cuda.empty_cache()
+    drift = rel_l2(finals["bf16"][0].cpu().numpy(), finals["f32"][0].cpu().numpy())
+    print(f"512^3 x 720 views, central {SUB}^3 ({n_vox} voxels, {n_rays} rays re-projected per step): "
+          f"FP32 storage x_1 {results[('f32', 0)]:.3e}, x_50 {results[('f32', 49)]:.3e} "
+          f"(update {results[('f32', 49, 'update')]:.3e}); "
+          f"BF16 storage x_1 {results[('bf16', 0)]:.3e}, x_50 {results[('bf16', 49)]:.3e} "
+          f"(update {results[('bf16', 49, 'update')]:.3e}); "
+          f"BF16 vs FP32 run after 50 iterations {drift:.3e}; residual after 49 updates "
+          f"FP32 {finals['f32'][1]:.4e}, BF16 {finals['bf16'][1]:.4e}")
+    ctx.close()
+    assert results[("f32", 0)] <= TOL32 and results[("f32", 49)] <= TOL32
+    assert results[("f32", 49, "update")] <= TOL32
+    assert results[("bf16", 0)] <= TOL16 and results[("bf16", 49)] <= TOL16
