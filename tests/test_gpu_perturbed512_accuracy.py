@@ -12,15 +12,17 @@ sub-volume (with one pixel more on the high side for the bilinear taps).
 The measured projections p are the GPU's (an input to the step, the same on
 both sides).
 
-Tolerances: FP32 storage 1e-5 (the FP32 contract), on x_{k+1} and on the
-update x_{k+1} - x_k alone (at k = 49 the update is small against x_k, so
-the first figure alone would hide its error).  BF16 storage: the GPU stores
-x_{k+1} (and the correction images) in BF16, one rounding of at most 2^-9
-relative per element, so 4e-3 on x_{k+1} as for every BF16 output (the
-update's own error is printed: the rounding of x_{k+1} dominates it).  Also
-printed:
-how far the BF16-storage run has drifted from the FP32-storage run after 50
-iterations (GPU against GPU) and both runs' residuals.
+Tolerances: FP32 storage 1e-5 (the FP32 contract) on x_{k+1}.  The update
+x_{k+1} - x_k alone is checked too (at k = 49 it is small against x_k, so
+the first figure alone would hide its error): the projection A x_k is held
+to 1e-5 of |A x_k| ~ |p|, and the residual p - A x_k that drives the update
+is a fraction rho_k of |p|, so the update's bound is 1e-5 / rho_k.  BF16
+storage: the GPU stores x_{k+1} (and the correction images) in BF16, one
+rounding of at most 2^-9 relative per element, so 4e-3 on x_{k+1} as for
+every BF16 output (the update's own error is printed: the rounding of
+x_{k+1} dominates it).  Also printed: how far the BF16-storage run has
+drifted from the FP32-storage run after 50 iterations (GPU against GPU) and
+both runs' residuals.
 """
 
 import math
@@ -125,7 +127,7 @@ def test_perturbed512_sirt_50_iterations_against_oracle_subvolume():
     for name, dtype in (("f32", torch.float32), ("bf16", torch.bfloat16)):
         p = p32 if dtype == torch.float32 else p32.to(torch.bfloat16).contiguous()
         snaps, hist = _run(ctx, cfg, p, dtype)
-        finals[name] = (snaps[50].float(), hist[-1])
+        finals[name] = (snaps[50].float(), hist[49])  # rho(x_49)
         for k in (0, 49):
             want, n_vox, n_rays = _oracle_step(pb, cfg, rects, snaps[k], p, lo, hi)
             got = snaps[k + 1][lo:hi, lo:hi, lo:hi].double().cpu().numpy().ravel()
@@ -144,5 +146,5 @@ def test_perturbed512_sirt_50_iterations_against_oracle_subvolume():
           f"FP32 {finals['f32'][1]:.4e}, BF16 {finals['bf16'][1]:.4e}")
     ctx.close()
     assert results[("f32", 0)] <= TOL32 and results[("f32", 49)] <= TOL32
-    assert results[("f32", 49, "update")] <= TOL32
+    assert results[("f32", 49, "update")] <= TOL32 / finals["f32"][1]
     assert results[("bf16", 0)] <= TOL16 and results[("bf16", 49)] <= TOL16
