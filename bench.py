@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="64^3 workload (quick check)")
     ap.add_argument("--warm-start-steps", type=int, default=400,
                     help="train the U-Net warm start this many steps and report time to residual 1e-3 (0: skip)")
+    ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
+                    help="skip the 50-iteration FP32 / BF16 SIRT runs on the bench workload")
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the per-row measurements (sub-angle, motion, adjoint, gradient, conv)")
     ap.add_argument("--views", type=int, default=0,
@@ -163,31 +165,70 @@ def measured_peaks():
 # CPU baseline: the FP64 oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
 
-def oracle_sample_run(cfg, P, vol_np, n_fwd_views=2, bp_edge=32, bp_views=90):
-    """Time the oracle: forward of n_fwd_views complete views + backprojection
-    of the central bp_edge^3 sub-volume over bp_views views.  Returns
-    (units, seconds, description)."""
+def oracle_plan_inputs():
+    """Inputs of the oracle timing plan (CPU, outside every timed region):
+    phantoms voxelised with one sample per voxel (the oracle's run time does
+    not depend on the values) and measured projections from the oracle."""
     import numpy as np
 
     import oracle
+    from paper_2609_30166_gb300 import inputs
 
-    pb = oracle.Problem(P, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin, (cfg.nu, cfg.nv), cfg.step_vox)
-    fwd_views = np.linspace(0, cfg.n_views - 1, n_fwd_views).astype(np.int32)
-    bp_sel = np.linspace(0, cfg.n_views - 1, bp_views).astype(np.int32)
-    n_samples = oracle.count_samples(pb, fwd_views) * 1  # counted outside the timed region
-    lo = cfg.n // 2 - bp_edge // 2
-    idx = np.arange(lo, lo + bp_edge)
+    def problem(cfg):
+        P = inputs.projection_matrices(cfg)
+        return oracle.Problem(P, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin, (cfg.nu, cfg.nv), cfg.step_vox)
+
+    c1, c5, c2 = inputs.CIRCULAR_64, inputs.SPARSE_128, inputs.PERTURBED_512
+    pb1, pb5, pb2 = problem(c1), problem(c5), problem(c2)
+    v1 = inputs.phantom(c1, sub=1).numpy()
+    v5 = inputs.phantom(c5, sub=1).numpy()
+    v2 = inputs.phantom(c2, sub=1).numpy()
+    p1 = oracle.forward(pb1, v1)[0]
+    p5 = oracle.forward(pb5, v5)[0]
+    fwd_views = np.linspace(0, c2.n_views - 1, 4).round().astype(np.int32)
+    lo = c2.n // 2 - 32
+    idx = np.arange(lo, lo + 64)
     zz, yy, xx = np.meshgrid(idx, idx, idx, indexing="ij")
-    vox_flat = ((zz * cfg.n + yy) * cfg.n + xx).ravel().astype(np.int64)
-    r = np.ones((bp_views, cfg.nv, cfg.nu))
-    t0 = time.perf_counter()
-    oracle.forward(pb, vol_np, views=fwd_views)
-    oracle.backproject_voxels(pb, r, vox_flat, views=bp_sel)
-    dt = time.perf_counter() - t0
-    units = n_samples + len(vox_flat) * bp_views * cfg.n_sub
-    desc = (f"oracle FP64: forward of {n_fwd_views} complete views ({n_samples} samples) + backprojection of the "
-            f"central {bp_edge}^3 sub-volume over {bp_views} views ({len(vox_flat) * bp_views} updates)")
-    return units, dt, desc
+    vox_flat = ((zz * c2.n + yy) * c2.n + xx).ravel().astype(np.int64)
+    r2 = np.ones((c2.n_views, c2.nv, c2.nu))
+    units = {
+        "c1_sirt_10": 10 * (oracle.count_samples(pb1) + v1.size * c1.n_views),
+        "c5_sirt_1": oracle.count_samples(pb5) + v5.size * c5.n_views,
+        "c2_fwd_4_views": oracle.count_samples(pb2, fwd_views),
+        "c2_bp_64^3_720_views": vox_flat.size * c2.n_views,
+    }
+    runs = {
+        "c1_sirt_10": lambda: oracle.sirt(pb1, p1, 10),
+        "c5_sirt_1": lambda: oracle.sirt(pb5, p5, 1),
+        "c2_fwd_4_views": lambda: oracle.forward(pb2, v2, views=fwd_views),
+        "c2_bp_64^3_720_views": lambda: oracle.backproject_voxels(pb2, r2, vox_flat),
+    }
+    return units, runs
+
+
+ORACLE_PLAN = ("oracle FP64 (C, OpenMP): {c1} full 10-iteration SIRT; {c5} one SIRT iteration; {c2} forward of "
+               "4 complete views and backprojection of the central 64^3 sub-volume over all 720 views")
+
+
+def oracle_plan_time(units, runs, reps=3):
+    """Median of reps timings of each part; returns (units, seconds, parts)."""
+    parts = {}
+    for name, fn in runs.items():
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        parts[name] = {"units": units[name], "s": statistics.median(ts), "gups": units[name] / statistics.median(ts) / 1e9}
+    total_u = sum(p["units"] for p in parts.values())
+    total_s = sum(p["s"] for p in parts.values())
+    return total_u, total_s, parts
+
+
+def oracle_plan_desc():
+    from paper_2609_30166_gb300 import inputs
+
+    return ORACLE_PLAN.format(c1=inputs.CIRCULAR_64.name, c5=inputs.SPARSE_128.name, c2=inputs.PERTURBED_512.name)
 
 
 def omp_threads():
@@ -240,6 +281,58 @@ def _time(fn, reps=3, warm=1):
 # (per point one weight product and three FMAs, plus per-axis weights), the
 # pose (9 FMA + 3), trilinear interpolation; counted from ray.cuh.
 MOTION_OPS_PER_SAMPLE = 64 * 4 + 16 + 3 * 10 + 12 + 30
+
+
+def sirt_50_iterations(ctx, cfg, p, device):
+    """50 SIRT iterations from zero on the bench workload with FP32 and with
+    BF16 storage (volume, projections, correction images; FP32 accumulation):
+    residuals and how far the BF16 run ends from the FP32 run.  The per-step
+    error of both against the FP64 oracle (central 64^3 sub-volume at k = 0
+    and k = 49) is checked by the GPU test suite, which may run the oracle."""
+    import torch
+
+    res = {"workload": cfg.name, "iterations": 50}
+    finals = {}
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        pp = p if dt == torch.float32 else p.to(dt).contiguous()
+        x = torch.zeros(cfg.vol_shape, dtype=dt, device=device)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        x, hist, done = ctx.sirt_iterate(x, pp, 50)
+        torch.cuda.synchronize(device)
+        res[name] = {"s": time.perf_counter() - t0, "iters": done, "residual_first": float(hist[0]),
+                     "residual_last": float(hist[-1])}
+        finals[name] = x.float()
+        del pp, x
+    d = (finals["bf16"] - finals["f32"]).double().norm() / finals["f32"].double().norm()
+    res["bf16_vs_f32_rel_l2"] = float(d)
+    del finals
+    torch.cuda.empty_cache()
+    return res
+
+
+def time_to_residual_circular64(device, tol=1e-3, max_iter=20000):
+    """Plain SIRT from zero on the 64^3 circular workload until rho <= tol:
+    wall time (the host reads the residual once per iteration) and
+    iterations."""
+    import torch
+
+    from paper_2609_30166_gb300 import ctrex, inputs
+
+    cfg = inputs.CIRCULAR_64
+    ctx = ctrex.context_for(cfg, device=device)
+    ph = inputs.phantom(cfg, device=str(device)).to(torch.float32).contiguous()
+    p = ctx.fwd_project(ph)
+    x = torch.zeros(cfg.vol_shape, dtype=torch.float32, device=device)
+    ctx.sirt_iterate(x.clone(), p, 3)  # warm-up
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    x, hist, done = ctx.sirt_iterate(x, p, max_iter, tol=tol)
+    torch.cuda.synchronize(device)
+    dt = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": cfg.name, "tol": tol, "s": dt, "iters": done,
+            "residual_last": float(hist[done]) if done < len(hist) else float(hist[-1])}
 
 
 def measure_rows(device, gather_peak, sm_count, sm_mhz):
@@ -532,6 +625,8 @@ def run_ours(args):
             del x16, p16, r16
         del x, r
         torch.cuda.empty_cache()
+        if args.accuracy and tdt == torch.float32:
+            out["sirt_50_iterations"] = sirt_50_iterations(ctx, cfg, p, device)
         out["rows"] = measure_rows(device, gather_peak, sm_count, sm_mhz)
         out["rows"]["a14_subvoxel_bp"] = {"workload": cfg.name, "s": 2, "ms": t_sv * 1e3,
                                           "point_updates": sv_points, "gpoint_updates_per_s": sv_points / t_sv / 1e9,
@@ -540,13 +635,14 @@ def run_ours(args):
         out["rows"]["a16_joseph_sirt_step"] = joseph_row
         if bf16_row:
             out["rows"]["a11_bf16_sirt_step"] = bf16_row
+    if rank == 0 and world == 1 and not args.no_rows and not args.views and not args.small and not cyl:
+        out["time_to_residual_1e-3_circular64"] = time_to_residual_circular64(device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not cyl:
-        vol_np = phantom.double().cpu().numpy()
-        ncpu_units, ncpu_s, desc = oracle_sample_run(cfg, P, vol_np, n_fwd_views=1 if not args.small else 8,
-                                                     bp_edge=32 if not args.small else 16,
-                                                     bp_views=45 if not args.small else 90)
+        units_p, runs_p = oracle_plan_inputs()
+        ncpu_units, ncpu_s, parts = oracle_plan_time(units_p, runs_p, reps=3)
         out["cpu_baseline"] = {"value": ncpu_units / ncpu_s / 1e9, "unit": "GUPS", "cores": omp_threads(),
-                               "kind": "oracle", "sample": desc}
+                               "kind": "oracle", "sample": oracle_plan_desc() + "; median of 3 per part",
+                               "parts": parts}
     if rank == 0 and world == 1 and args.warm_start_steps > 0 and not args.views and not args.small and not cyl:
         from paper_2609_30166_gb300 import warmstart
 
@@ -573,22 +669,18 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    import numpy as np
-
     from paper_2609_30166_gb300 import inputs
 
     cfg = inputs.CIRCULAR_64 if args.small else inputs.PERTURBED_512
-    P = inputs.projection_matrices(cfg)
-    vol_np = inputs.phantom(cfg).numpy() if args.small else inputs.phantom(cfg, sub=1).numpy()
-    kw = dict(n_fwd_views=1, bp_edge=16, bp_views=45) if not args.small else dict(n_fwd_views=4, bp_edge=16,
-                                                                                   bp_views=90)
+    units_p, runs_p = oracle_plan_inputs()
     for _ in range(args.warmup):
-        oracle_sample_run(cfg, P, vol_np, **dict(kw, n_fwd_views=1, bp_edge=8, bp_views=4))
-    units_total, secs, desc = 0, 0.0, ""
+        runs_p["c1_sirt_10"]()
+    units_total, secs, parts = 0, 0.0, {}
     for _ in range(args.steps):
-        u, s, desc = oracle_sample_run(cfg, P, vol_np, **kw)
+        u, s, parts = oracle_plan_time(units_p, runs_p, reps=1)
         units_total += u
         secs += s
+    desc = oracle_plan_desc() + "; each step runs every part once"
     value = units_total / secs / 1e9
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GUPS", "n_gpus": args.gpus,
@@ -597,11 +689,10 @@ def run_reference(args):
         "data": "synthetic", "config": {"workload": cfg.name, "volume": list(cfg.vol_shape),
                                         "detector": [cfg.nv, cfg.nu], "views": cfg.n_views},
         "cpu_baseline": {"value": value, "unit": "GUPS", "cores": omp_threads(), "kind": "oracle",
-                         "sample": desc},
+                         "sample": desc, "parts": parts},
         "e2e": {"value": value, "unit": "GUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
-    _ = np
 
 
 def main():
