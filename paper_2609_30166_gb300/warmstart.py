@@ -3,7 +3,7 @@ textured phantoms, 60 views, 192^2 detector): trains the U-Net on
 (5-iteration SIRT, phantom) pairs made by the library, then measures wall time
 and iterations to relative data residual 1e-3 on held-out phantoms.
 
-    python -m paper_2609_30166_gb300.warmstart [--steps 400] [--train 56] [--test 8]
+    python -m paper_2609_30166_gb300.warmstart [--steps 1200] [--train 56] [--test 8]
 prints one JSON object.
 """
 
@@ -19,7 +19,7 @@ import torch
 from . import ctrex, inputs, unet
 
 
-def run(n_train=56, n_test=8, steps=400, batch=2, tol=1e-3, max_iter=4000, seed=0, log=None):
+def run(n_train=56, n_test=8, steps=1200, batch=2, tol=1e-3, max_iter=4000, seed=0, log=None):
     cfg = inputs.SPARSE_128
     ctx = ctrex.context_for(cfg)
     t0 = time.perf_counter()
@@ -48,7 +48,7 @@ def run(n_train=56, n_test=8, steps=400, batch=2, tol=1e-3, max_iter=4000, seed=
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=1200)
     ap.add_argument("--train", type=int, default=56)
     ap.add_argument("--test", type=int, default=8)
     a = ap.parse_args()

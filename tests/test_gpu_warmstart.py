@@ -1,8 +1,8 @@
 """What the learned warm start gains over plain SIRT: on held-out phantoms
 the trained U-Net's output is far closer to the truth than its 5-iteration
 SIRT input, and SIRT started from it reaches relative data residual 1e-3 in
-fewer iterations and less wall time than SIRT from zero (time includes the
-input iterations and the network)."""
+at most 0.7 of the wall time of SIRT from zero (time includes the input
+iterations and the network; measured about 0.26 over 8 held-out phantoms)."""
 
 import pytest
 import torch
@@ -16,7 +16,7 @@ def test_warm_start_beats_plain_sirt():
     from paper_2609_30166_gb300 import _build, warmstart
 
     _build.build_library()
-    res = warmstart.run(n_train=56, n_test=2, steps=400)
+    res = warmstart.run(n_train=56, n_test=2)
     print({k: v for k, v in res.items() if k != "per_phantom"})
     for r in res["per_phantom"]:
         print(r)
@@ -25,4 +25,4 @@ def test_warm_start_beats_plain_sirt():
     for r in res["per_phantom"]:
         assert r["plain_rho"] <= 1e-3 and r["warm_rho"] <= 1e-3
     assert res["warm_iters"] < res["plain_iters"]
-    assert res["warm_s"] < res["plain_s"]
+    assert res["warm_s"] <= 0.7 * res["plain_s"]
