@@ -16,6 +16,9 @@ Each wrapper names the paper passage its C routine follows:
 * ``adjoint``, ``motion_grad``  -- transpose and chain rule of ``forward``
   (Sec. 5 motivates geometry refinement; no formula is printed).
 * ``displacement``              -- the Sec. 3.1 deformation field on its own.
+* ``Problem(dyrect=...)``       -- Sec. 3.3 event-based 4D model (initial and
+  final values, transition times) in the projector, backprojector, adjoint
+  and SIRT.
 * ``sirt``                      -- Eq. (1) iterated, all views in one subset.
 * ``os_sirt``                   -- Eq. (1) on ordered subsets of views (Sec. 2.3.2).
 
@@ -93,7 +96,7 @@ class _CProblem(ctypes.Structure):
         ("cyl", ctypes.c_int), ("cyl_dr", ctypes.c_double), ("cyl_dz", ctypes.c_double),
         ("cyl_pose", _dp), ("joseph", ctypes.c_int),
         ("roi", ctypes.c_int), ("roi_n", ctypes.c_int * 3), ("roi_vox", ctypes.c_double * 3),
-        ("roi_origin", ctypes.c_double * 3),
+        ("roi_origin", ctypes.c_double * 3), ("dyr_tau", _dp), ("dyr_t", _dp),
     ]
 
 
@@ -134,11 +137,14 @@ class Problem:
     order, mm; det (nu, nv); theta [n_views, 15]; coef [8, 8, 8, 3]; s_view
     [n_views].  cyl = (dr, dz, pose[3, 4]) switches to the aligned cylindrical
     domain (reading R13): vol_shape is then (N_z, N_phi, N_r) and vox, origin
-    are unused.
+    are unused.  dyrect = (tau [nz, ny, nx], t_view [n_views]) switches on the
+    event-based 4D model (Sec. 3.3, reading R16): volumes are then
+    [2, nz, ny, nx], the initial values followed by the final values.
     """
 
     def __init__(self, P, vol_shape, vox, origin, det, step_vox=0.5, theta=None, coef=None,
-                 s_view=None, margin=0.0, bp_window=None, bp_subvoxel=1, cyl=None, joseph=False, roi=None):
+                 s_view=None, margin=0.0, bp_window=None, bp_subvoxel=1, cyl=None, joseph=False, roi=None,
+                 dyrect=None):
         P = _f64(P)
         if P.ndim == 3:
             P = P[:, None]
@@ -161,6 +167,12 @@ class Problem:
             rshape, rvox, rorg = roi
             self.roi = (tuple(int(v) for v in rshape), tuple(float(v) for v in rvox),
                         tuple(float(v) for v in rorg))
+        self.dyrect = None
+        if dyrect is not None:
+            tau, tv = dyrect
+            tau, tv = _f64(tau), _f64(tv)
+            assert tau.shape == (self.nz, self.ny, self.nx) and tv.shape == (self.n_views,)
+            self.dyrect = (tau, tv)
         self.cyl = None
         if cyl is not None:
             dr, dz, pose = cyl
@@ -174,7 +186,9 @@ class Problem:
                             1 if self.joseph else 0, 1 if self.roi else 0,
                             (ctypes.c_int * 3)(*(self.roi[0][::-1] if self.roi else (0, 0, 0))),
                             (ctypes.c_double * 3)(*(self.roi[1] if self.roi else (0.0, 0.0, 0.0))),
-                            (ctypes.c_double * 3)(*(self.roi[2] if self.roi else (0.0, 0.0, 0.0))))
+                            (ctypes.c_double * 3)(*(self.roi[2] if self.roi else (0.0, 0.0, 0.0))),
+                            _ptr(self.dyrect[0] if self.dyrect else None),
+                            _ptr(self.dyrect[1] if self.dyrect else None))
 
     @property
     def grid_shape(self):
@@ -187,6 +201,8 @@ class Problem:
         if self.roi:
             rz, ry, rx = self.roi[0]
             return (self.nz * self.ny * self.nx + rz * ry * rx,)
+        if self.dyrect:
+            return (2, self.nz, self.ny, self.nx)
         return (self.nz, self.ny, self.nx)
 
     @property
@@ -203,7 +219,8 @@ class Problem:
         args = dict(P=self.P, vol_shape=self.grid_shape, vox=self.vox, origin=self.origin,
                     det=(self.nu, self.nv), step_vox=self.step_vox, theta=self.theta, coef=self.coef,
                     s_view=self.s_view, margin=self.margin, bp_window=self.bp_window,
-                    bp_subvoxel=self.bp_subvoxel, cyl=self.cyl, joseph=self.joseph, roi=self.roi)
+                    bp_subvoxel=self.bp_subvoxel, cyl=self.cyl, joseph=self.joseph, roi=self.roi,
+                    dyrect=self.dyrect)
         args.update(kw)
         return Problem(**args)
 
@@ -225,6 +242,10 @@ class Problem:
     def with_joseph(self, on=True):
         """The same problem with the classical Joseph projector (reading R14)."""
         return self._replace(joseph=on)
+
+    def with_dyrect(self, tau, t_view):
+        """The same problem with the event-based 4D model (reading R16)."""
+        return self._replace(dyrect=(tau, t_view))
 
     def with_window(self, bp_window):
         """The same problem whose backprojector sees per-view detector windows
@@ -323,13 +344,15 @@ def backproject(pb, r, views=None, w=None, alpha=1.0, x=None, eps_C=EPS_C):
 
 
 def backproject_voxels(pb, r, vox_flat, views=None):
-    """(b, c) at the listed flat voxel indices."""
+    """(b, c) at the listed flat voxel indices (with the event-based model:
+    arrays [2, n], the initial-value parts then the final-value parts)."""
     lib = _load()
     r = _f64(r)
     v, n = _views(pb, views)
     vox_flat = np.ascontiguousarray(vox_flat, dtype=np.int64)
-    b = np.zeros(len(vox_flat))
-    c = np.zeros(len(vox_flat))
+    shape = (2, len(vox_flat)) if pb.dyrect else (len(vox_flat),)
+    b = np.zeros(shape)
+    c = np.zeros(shape)
     _check(lib.or_backproject_voxels(ctypes.byref(pb._c), _ptr(r), _ptr(v, _ip), n,
                                      _ptr(vox_flat, _lp), len(vox_flat), _ptr(b), _ptr(c)))
     return b, c

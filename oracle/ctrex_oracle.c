@@ -57,7 +57,17 @@
  *      these, zero outside in r (beyond ring N_r - 1) and z.  Rays are
  *      clipped to the bounding cylinder r <= N_r dr, |q_z| <= N_z dz / 2;
  *      the step is step_vox * min(dr, dz); the rest of the projector and the
- *      backprojector (at the voxel centres mapped back to world) is as above.
+ *      backprojector (at the voxel centres mapped back to world) is as above;
+ *   R16 event-based 4D model (Sec. 3.3): three fields per voxel, the initial
+ *      value mu0_j, the final value mu1_j and the transition time tau_j; view
+ *      v, acquired at time t_v, sees mu0_j where t_v < tau_j and mu1_j
+ *      otherwise (one irreversible change per voxel).  The projector
+ *      samples that per-view volume (the selection is made per trilinear
+ *      tap).  The backprojector splits Eq. (1) term 3 by the same rule: the
+ *      views before tau_j update mu0_j, normalised by their own column sum,
+ *      the views from tau_j on update mu1_j.  tau is an input (its update
+ *      rule is not part of this paper).  Cartesian trilinear projector
+ *      without motion, ROI, Joseph or sub-voxel backprojection.
  *
  * Conventions: volume vol[iz][iy][ix] (x fastest), voxel (0,0,0) centred at
  * origin (mm), index coordinate g = (x - origin) / vox.  Projection images
@@ -100,6 +110,11 @@ typedef struct {
     int roi;
     int roi_n[3];
     double roi_vox[3], roi_origin[3];
+    /* event-based 4D model (Sec. 3.3, reading R16): when dyr_tau is set,
+     * volumes hold the initial values mu0 followed by the final values mu1
+     * (2 nx ny nz each) */
+    const double *dyr_tau; /* [nz][ny][nx] transition times, or NULL */
+    const double *dyr_t;   /* [n_views] acquisition time of each view */
 } or_problem;
 
 /* Per (view, sub-angle) quantities derived from P (Sec. 2.2.1). */
@@ -291,6 +306,41 @@ static double trilinear(const or_problem *pb, const double *vol, const double g[
         grad[1] = gy;
         grad[2] = gz;
     }
+    return val;
+}
+
+/*
+ * Reading R16: the zero-padded trilinear interpolant of the volume that a view
+ * acquired at time t sees: each tap takes mu0 (the first half of vol) where
+ * t < tau at that voxel, else mu1 (the second half).  wsum as for trilinear().
+ */
+static double dyr_trilinear(const or_problem *pb, const double *vol, const double g[3], double t, double *wsum)
+{
+    const int n[3] = {pb->nx, pb->ny, pb->nz};
+    const size_t nvox = (size_t)n[0] * n[1] * n[2];
+    *wsum = 0.0;
+    for (int a = 0; a < 3; ++a)
+        if (!(g[a] >= -1.0 && g[a] < (double)n[a])) return 0.0;
+    int i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double fl = floor(g[a]);
+        i0[a] = (int)fl;
+        f[a] = g[a] - fl;
+    }
+    double val = 0.0, ws = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                int ix = i0[0] + dx, iy = i0[1] + dy, iz = i0[2] + dz;
+                if (ix < 0 || ix >= n[0] || iy < 0 || iy >= n[1] || iz < 0 || iz >= n[2]) continue;
+                double wgt = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                size_t j = ((size_t)iz * n[1] + iy) * n[0] + ix;
+                if (vol) val += wgt * (t < pb->dyr_tau[j] ? vol[j] : vol[nvox + j]);
+                else val += wgt;
+                ws += wgt;
+            }
+    *wsum = ws;
     return val;
 }
 
@@ -653,6 +703,9 @@ static void fwd_sample(void *vctx, const double x[3], double w)
         world_to_cyl(c->pb, y, q);
         cyl_index(c->pb, q, g);
         c->val += w * cyl_interp(c->pb, c->vol, g, &ws);
+    } else if (c->pb->dyr_tau) {
+        to_index(c->pb, y, g);
+        c->val += w * dyr_trilinear(c->pb, c->vol, g, c->pb->dyr_t[c->view], &ws);
     } else {
         to_index(c->pb, y, g);
         c->val += w * trilinear(c->pb, c->vol, g, &ws, NULL);
@@ -805,6 +858,8 @@ static void pixel_value(const or_problem *pb, const or_view *ov, const double *v
 static int joseph_unsupported(const or_problem *pb)
 {
     if (pb->roi && (pb->joseph || pb->cyl || pb->theta || pb->coef)) return 1; /* R15: trilinear, no motion */
+    if (pb->dyr_tau && (pb->roi || pb->joseph || pb->cyl || pb->theta || pb->coef || pb->bp_subvoxel > 1))
+        return 1; /* R16: Cartesian trilinear projector, no motion */
     return pb->joseph && (pb->cyl || pb->theta || pb->coef);
 }
 
@@ -921,13 +976,16 @@ int or_correct(long n, const double *p, const double *q, const double *rowsum, d
  * [n_sel][nv][nu] in the order of views[].
  */
 static void bp_point(const or_problem *pb, const or_view *ov, const double *r, const int *views, int n_sel,
-                     const double X[3], double *b_out, double *c_out)
+                     const double X[3], double tau, double b_out[2], double c_out[2])
 {
-    double b = 0.0, c = 0.0;
+    double bb[2] = {0.0, 0.0}, cc[2] = {0.0, 0.0};
     size_t npix = (size_t)pb->nu * pb->nv;
     for (int k = 0; k < n_sel; ++k) {
         int view = views ? views[k] : k;
         const double *img = r + k * npix;
+        /* reading R16: views from the transition on update the final value */
+        const int part = (pb->dyr_tau && !(pb->dyr_t[view] < tau)) ? 1 : 0;
+        double b = 0.0, c = 0.0;
         for (int s = 0; s < pb->n_sub; ++s) {
             const double *P = ov[(size_t)view * pb->n_sub + s].P;
             double h[3];
@@ -956,17 +1014,22 @@ static void bp_point(const or_problem *pb, const or_view *ov, const double *r, c
                     c += wgt / pb->n_sub;
                 }
         }
+        bb[part] += b;
+        cc[part] += c;
     }
-    *b_out = b;
-    *c_out = c;
+    b_out[0] = bb[0];
+    b_out[1] = bb[1];
+    c_out[0] = cc[0];
+    c_out[1] = cc[1];
 }
 
 static void bp_voxel(const or_problem *pb, const or_view *ov, const double *r, const int *views,
-                     int n_sel, int ix, int iy, int iz, double *b_out, double *c_out)
+                     int n_sel, int ix, int iy, int iz, double b_out[2], double c_out[2])
 {
     const int sv = pb->bp_subvoxel > 1 ? pb->bp_subvoxel : 1;
     const int i[3] = {ix, iy, iz};
-    double b = 0.0, c = 0.0;
+    const double tau = pb->dyr_tau ? pb->dyr_tau[((size_t)iz * pb->ny + iy) * pb->nx + ix] : 0.0;
+    double b[2] = {0.0, 0.0}, c[2] = {0.0, 0.0};
     for (int az = 0; az < sv; ++az)
         for (int ay = 0; ay < sv; ++ay)
             for (int ax = 0; ax < sv; ++ax) {
@@ -986,13 +1049,17 @@ static void bp_voxel(const or_problem *pb, const or_view *ov, const double *r, c
                     for (int d = 0; d < 3; ++d)
                         X[d] = pb->origin[d] + (i[d] + (a[d] + 0.5) / sv - 0.5) * pb->vox[d];
                 }
-                double bb, cc;
-                bp_point(pb, ov, r, views, n_sel, X, &bb, &cc);
-                b += bb;
-                c += cc;
+                double bb[2], cc[2];
+                bp_point(pb, ov, r, views, n_sel, X, tau, bb, cc);
+                for (int q = 0; q < 2; ++q) {
+                    b[q] += bb[q];
+                    c[q] += cc[q];
+                }
             }
-    *b_out = b / ((double)sv * sv * sv);
-    *c_out = c / ((double)sv * sv * sv);
+    for (int q = 0; q < 2; ++q) {
+        b_out[q] = b[q] / ((double)sv * sv * sv);
+        c_out[q] = c[q] / ((double)sv * sv * sv);
+    }
 }
 
 /*
@@ -1000,28 +1067,38 @@ static void bp_voxel(const or_problem *pb, const or_view *ov, const double *r, c
  * c_j > eps_C else 0.  x may be NULL (then only b, c are produced); w may be
  * NULL (w = 1); b, c may be NULL.
  */
+static int dyrect_unsupported_bp(const or_problem *pb)
+{
+    return pb->dyr_tau && (pb->cyl || pb->roi || pb->bp_subvoxel > 1);
+}
+
 int or_backproject(const or_problem *pb, const double *r, const int *views, int n_sel,
                    const double *w, double alpha, double eps_C, double *x, double *b_out,
                    double *c_out)
 {
+    if (dyrect_unsupported_bp(pb)) return OR_E_ARG;
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;
     long nc = grid_voxels(pb);
     or_problem f = pb->roi ? roi_part(pb) : *pb;
     long nvox = nc + (pb->roi ? grid_voxels(&f) : 0);
+    const int parts = pb->dyr_tau ? 2 : 1; /* reading R16: mu0 then mu1 */
 #pragma omp parallel for schedule(dynamic, 64)
     for (long j = 0; j < nvox; ++j) {
         const or_problem *g = j < nc ? pb : &f; /* reading R15: the ROI voxels follow */
         long jj = j < nc ? j : j - nc;
         int ix = (int)(jj % g->nx), iy = (int)((jj / g->nx) % g->ny), iz = (int)(jj / ((long)g->nx * g->ny));
-        double b, c;
-        bp_voxel(g, ov, r, views, n_sel, ix, iy, iz, &b, &c);
-        if (b_out) b_out[j] = b;
-        if (c_out) c_out[j] = c;
-        if (x) {
-            double C = c > eps_C ? 1.0 / c : 0.0;
-            x[j] += alpha * (w ? w[j] : 1.0) * C * b;
+        double b[2], c[2];
+        bp_voxel(g, ov, r, views, n_sel, ix, iy, iz, b, c);
+        for (int q = 0; q < parts; ++q) {
+            long jo = j + q * nvox;
+            if (b_out) b_out[jo] = b[q];
+            if (c_out) c_out[jo] = c[q];
+            if (x) {
+                double C = c[q] > eps_C ? 1.0 / c[q] : 0.0;
+                x[jo] += alpha * (w ? w[jo] : 1.0) * C * b[q];
+            }
         }
     }
     free(ov);
@@ -1032,6 +1109,7 @@ int or_backproject(const or_problem *pb, const double *r, const int *views, int 
 int or_backproject_voxels(const or_problem *pb, const double *r, const int *views, int n_sel,
                           const long *vox, long n_vox, double *b_out, double *c_out)
 {
+    if (dyrect_unsupported_bp(pb)) return OR_E_ARG;
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;
@@ -1043,7 +1121,14 @@ int or_backproject_voxels(const or_problem *pb, const double *r, const int *view
         const or_problem *g = (pb->roi && j >= nc) ? &f : pb;
         if (g == &f) j -= nc;
         int ix = (int)(j % g->nx), iy = (int)((j / g->nx) % g->ny), iz = (int)(j / ((long)g->nx * g->ny));
-        bp_voxel(g, ov, r, views, n_sel, ix, iy, iz, &b_out[q], &c_out[q]);
+        double b[2], c[2];
+        bp_voxel(g, ov, r, views, n_sel, ix, iy, iz, b, c);
+        b_out[q] = b[0];
+        c_out[q] = c[0];
+        if (pb->dyr_tau) { /* reading R16: the mu1 parts follow the mu0 parts */
+            b_out[n_vox + q] = b[1];
+            c_out[n_vox + q] = c[1];
+        }
     }
     free(ov);
     return 0;
@@ -1077,13 +1162,17 @@ static void adj_sample(void *vctx, const double x[3], double w)
         i0[a] = (int)fl;
         f[a] = g[a] - fl;
     }
+    const size_t nvox = (size_t)n[0] * n[1] * n[2];
     for (int dz = 0; dz < 2; ++dz)
         for (int dy = 0; dy < 2; ++dy)
             for (int dx = 0; dx < 2; ++dx) {
                 int ix = i0[0] + dx, iy = i0[1] + dy, iz = i0[2] + dz;
                 if (ix < 0 || ix >= n[0] || iy < 0 || iy >= n[1] || iz < 0 || iz >= n[2]) continue;
                 double wt = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
-                c->acc[((size_t)iz * n[1] + iy) * n[0] + ix] += c->y * w * wt;
+                size_t j = ((size_t)iz * n[1] + iy) * n[0] + ix;
+                /* reading R16: the tap's value came from mu1 from the transition on */
+                if (pb->dyr_tau && !(pb->dyr_t[c->view] < pb->dyr_tau[j])) j += nvox;
+                c->acc[j] += c->y * w * wt;
             }
 }
 
@@ -1091,11 +1180,11 @@ static void adj_sample(void *vctx, const double x[3], double w)
 int or_adjoint(const or_problem *pb, const double *y, const int *views, int n_sel, double *vol_out)
 {
     /* the transpose of the trilinear projector on the Cartesian grid only */
-    if (pb->cyl || pb->joseph || pb->roi) return OR_E_ARG;
+    if (pb->cyl || pb->joseph || pb->roi || joseph_unsupported(pb)) return OR_E_ARG;
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;
-    size_t nvox = (size_t)pb->nx * pb->ny * pb->nz;
+    size_t nvox = (size_t)pb->nx * pb->ny * pb->nz * (pb->dyr_tau ? 2 : 1);
     long npix = (long)pb->nu * pb->nv;
     int nth = 1;
 #ifdef _OPENMP
@@ -1219,7 +1308,7 @@ static void grad_sample(void *vctx, const double x[3], double w)
 int or_motion_grad(const or_problem *pb, const double *vol, const double *g, const int *views,
                    int n_sel, double *grad_theta, double *grad_coef)
 {
-    if (pb->cyl || pb->joseph || pb->roi) return OR_E_ARG; /* trilinear projector, one Cartesian grid */
+    if (pb->cyl || pb->joseph || pb->roi || pb->dyr_tau) return OR_E_ARG; /* trilinear projector, one Cartesian grid */
     int err;
     or_view *ov = setup_all_views(pb, &err);
     if (!ov) return err;

@@ -322,6 +322,58 @@ def phantom(cfg: Config, seed: Optional[int] = None, device: str = "cpu", sub: i
 
 
 # ---------------------------------------------------------------------------
+# Event-based 4D scenes (Sec. 3.3): initial values, final values, transition
+# times per voxel, for a scan during which regions change irreversibly
+# ---------------------------------------------------------------------------
+
+def view_times(cfg: Config) -> np.ndarray:
+    """Acquisition time of each view: t_v = v / (V - 1), the scan running
+    from 0 to 1."""
+    return np.arange(cfg.n_views, dtype=np.float64) / max(cfg.n_views - 1, 1)
+
+
+def dyrect_fields(cfg: Config, seed: Optional[int] = None, n_events: int = 8, device: str = "cpu", sub: int = 4):
+    """(mu0, mu1, tau) of a scene in which n_events ellipsoidal regions change
+    attenuation once during the scan (fluid invading a pore network, a phase
+    transition): mu0 = the configuration's phantom; region k adds delta_k to
+    it (voxelised like the phantom), and a planar front sweeps through the
+    region, so a voxel changes when the front reaches its centre:
+        tau = t0_k + dur_k ((x - c_k) . n_k + r_k) / (2 r_k),
+    r_k the region's largest semi-axis.  Voxels outside every region get
+    tau = 2 (after the scan); overlapping regions keep the earliest time.
+    Draws from PCG64(seed or cfg.seed, offset 1000), per region in this
+    order: full axes U[4, 16] mm (3), rotation (4 normals), centre in the
+    box shrunk by r_k (3), delta_k U[-0.4, 0.6], front direction (3
+    normals), start t0_k U[0.05, 0.6], duration dur_k U[0.2, 0.5].
+    Returns float64 torch tensors [n, n, n] on device."""
+    import torch
+
+    mu0 = phantom(cfg, seed, device, sub)
+    rng = np.random.Generator(np.random.PCG64((cfg.seed if seed is None else seed) + 1000))
+    half = 0.5 * cfg.box
+    mu1 = mu0.clone()
+    tau = torch.full(cfg.vol_shape, 2.0, dtype=torch.float64, device=device)
+    idx = torch.arange(cfg.n, dtype=torch.float64, device=device)
+    xc = cfg.origin[0] + idx * cfg.vox
+    for _ in range(n_events):
+        semi = 0.5 * rng.uniform(4.0, 16.0, size=3)
+        rot = random_rotation(rng)
+        r = float(semi.max())
+        centre = rng.uniform(-half + r, half - r, size=3)
+        delta = float(rng.uniform(-0.4, 0.6))
+        nrm = rng.normal(size=3)
+        nrm /= np.linalg.norm(nrm)
+        t0 = float(rng.uniform(0.05, 0.6))
+        dur = float(rng.uniform(0.2, 0.5))
+        region = voxelize(cfg, [Ellipsoid(centre, semi, rot, delta)], [], sub=sub, device=device)
+        mu1 += region
+        front = t0 + dur * ((xc[None, None, :] - centre[0]) * nrm[0] + (xc[None, :, None] - centre[1]) * nrm[1]
+                            + (xc[:, None, None] - centre[2]) * nrm[2] + r) / (2.0 * r)
+        tau = torch.where(region != 0, torch.minimum(tau, front), tau)
+    return mu0, mu1, tau
+
+
+# ---------------------------------------------------------------------------
 # Aligned cylindrical domain (Sec. 3.5): a vial on the scanner's trajectory
 # ---------------------------------------------------------------------------
 
