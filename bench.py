@@ -311,6 +311,39 @@ def sirt_50_iterations(ctx, cfg, p, device):
     return res
 
 
+def dyrect_sirt_step(ctx, cfg, device, n_samples, n_updates, gather_peak):
+    """One SIRT step of the event-based 4D model (Sec. 3.3) on the bench
+    workload: the event scene's initial and final values and transition
+    times, measured data simulated by the event-model projector, the fused
+    forward + correction and the split backprojection timed.  Samples and
+    voxel-view updates are those of the static step (each tap and each
+    voxel-view pair serves one of the two value fields); a sample costs six
+    gathers (initial value, final value, transition time; two slices)."""
+    import torch
+
+    from paper_2609_30166_gb300 import inputs
+
+    mu0, mu1, tau = inputs.dyrect_fields(cfg, device=str(device))
+    tv = torch.as_tensor(inputs.view_times(cfg), dtype=torch.float32, device=device)
+    ctx.set_dyrect(tau.to(torch.float32).contiguous(), tv)
+    x_true = torch.stack([mu0, mu1]).to(torch.float32).contiguous()
+    del mu0, mu1, tau
+    pd = ctx.fwd_project(x_true)
+    x = torch.zeros_like(x_true)
+    del x_true
+    r = torch.empty_like(pd)
+    sums = torch.empty(2, dtype=torch.float64, device=device)
+    t_f = _time(lambda: ctx.fwd_correct(x, pd, r=r, sums=sums), reps=2)
+    t_b = _time(lambda: ctx.back_project(r, vol=x, alpha=1.0, normalize=True, accumulate=True), reps=2)
+    ctx.set_dyrect(None)
+    del x, r, pd
+    torch.cuda.empty_cache()
+    return {"workload": cfg.name + " (event scene: 8 changing regions)", "fwd_correct_ms": t_f * 1e3,
+            "back_project_ms": t_b * 1e3, "gups": (n_samples + n_updates) / (t_f + t_b) / 1e9,
+            "fwd_tex_gather_frac": 6 * n_samples / t_f / gather_peak,
+            "bp_tex_gather_frac": n_updates / t_b / gather_peak}
+
+
 def time_to_residual_circular64(device, tol=1e-3, max_iter=20000):
     """Plain SIRT from zero on the 64^3 circular workload until rho <= tol:
     wall time (the host reads the residual once per iteration) and
@@ -627,7 +660,11 @@ def run_ours(args):
         torch.cuda.empty_cache()
         if args.accuracy and tdt == torch.float32:
             out["sirt_50_iterations"] = sirt_50_iterations(ctx, cfg, p, device)
+        dyr_row = dyrect_sirt_step(ctx, cfg, device, n_samples, n_updates, gather_peak) \
+            if tdt == torch.float32 else None
         out["rows"] = measure_rows(device, gather_peak, sm_count, sm_mhz)
+        if dyr_row:
+            out["rows"]["a18_dyrect_sirt_step"] = dyr_row
         out["rows"]["a14_subvoxel_bp"] = {"workload": cfg.name, "s": 2, "ms": t_sv * 1e3,
                                           "point_updates": sv_points, "gpoint_updates_per_s": sv_points / t_sv / 1e9,
                                           "tex_gather_frac": sv_points / t_sv / gather_peak,

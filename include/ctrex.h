@@ -261,6 +261,35 @@ int ctrex_set_bp_subvoxel(ctrex_ctx *ctx, int s);
  */
 int ctrex_set_roi(ctrex_ctx *ctx, const ctrex_vol_grid *roi);
 
+/*
+ * Event-based 4D reconstruction (Sec. 3.3): temporal behaviour is
+ * parameterised per voxel by three fields, an initial value mu0, a final
+ * value mu1 and a transition time tau, and the projector and backprojector
+ * act on them directly.  Reading: view v, acquired at time t_view[v], sees
+ * mu0_j where t_view[v] < tau_j and mu1_j elsewhere (one irreversible change
+ * per voxel); the forward projector samples that per-view volume (the choice
+ * is made per trilinear tap; weights and row sums are those of the static
+ * projector); the backprojector splits Eq. (1) term 3 by the same rule: the
+ * views before tau_j update mu0_j, normalised by their own column sum, the
+ * others update mu1_j.  tau is an input: its update rule is not part of the
+ * paper.  Once set, every volume buffer (vol, w) of fwd_project,
+ * fwd_correct, back_project, adjoint_project (the exact transpose with
+ * respect to (mu0, mu1)), sirt_iterate, os_sirt_iterate and sirt_host holds
+ * mu0 followed by mu1 (2 nx ny nz elements).
+ *   tau     DEVICE float [nz][ny][nx] transition times, or NULL to switch
+ *           the model off.
+ *   t_view  DEVICE float [n_views] acquisition time of each view (same
+ *           unit as tau).
+ * Both are copied on the stream (the caller may free them once the stream
+ * has passed this call).  Defined for the trilinear projector on the
+ * Cartesian grid without motion, ROI or sub-voxel backprojection:
+ * CTREX_E_STATE otherwise (and set_motion, set_roi, set_projector(Joseph),
+ * set_bp_subvoxel(s > 1) and motion_grad return CTREX_E_STATE while it is
+ * on).  CTREX_E_SHAPE if the volume exceeds the device's 2D texture limits.
+ * set_geometry and set_geometry_cylinder switch it off.
+ */
+int ctrex_set_dyrect(ctrex_ctx *ctx, const float *tau, const float *t_view);
+
 #define CTREX_PROJ_TRILINEAR 0
 #define CTREX_PROJ_JOSEPH 1
 int ctrex_set_projector(ctrex_ctx *ctx, int kind);

@@ -74,11 +74,42 @@ __device__ __forceinline__ void scatter_trilinear(float *__restrict__ vol, int n
     }
 }
 
-template <bool MOTION>
+// Event-based 4D model (Sec. 3.3): the transpose sends each tap's share to
+// mu0 (vol[j]) if the view's time t precedes the voxel's transition time
+// tau_j, else to mu1 (vol[nvox + j]); scalar reductions.
+__device__ __forceinline__ void scatter_trilinear_dyrect(float *__restrict__ vol, int nx, int ny, int nz,
+                                                         const float c[3], const float gc[3], float val,
+                                                         const float *__restrict__ tau, float t, long long nvox)
+{
+    const float fx = floorf(gc[0]), fy = floorf(gc[1]), fz = floorf(gc[2]);
+    const int ix = (int)fx + (int)c[0], iy = (int)fy + (int)c[1], iz = (int)fz + (int)c[2];
+    const float ax = gc[0] - fx, ay = gc[1] - fy, az = gc[2] - fz;
+    const float wx[2] = {1.0f - ax, ax}, wy[2] = {1.0f - ay, ay}, wz[2] = {1.0f - az, az};
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz) {
+        const int z = iz + dz;
+        if ((unsigned)z >= (unsigned)nz) continue;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const int y = iy + dy;
+            if ((unsigned)y >= (unsigned)ny) continue;
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int x = ix + dx;
+                if ((unsigned)x >= (unsigned)nx) continue;
+                const long long j = ((long long)z * ny + y) * nx + x;
+                atomicAdd(vol + (t < __ldg(tau + j) ? j : nvox + j), val * wz[dz] * wy[dy] * wx[dx]);
+            }
+        }
+    }
+}
+
+template <bool MOTION, bool DYR>
 __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
     adjoint_kernel(Grid G, const ViewGPU *__restrict__ views, const MotionGPU *__restrict__ motion,
                    const float *__restrict__ coef_g, const int *__restrict__ view_idx,
-                   const float *__restrict__ proj, float *__restrict__ vol, unsigned *devcheck)
+                   const float *__restrict__ proj, float *__restrict__ vol, unsigned *devcheck,
+                   const float *__restrict__ tau, const float *__restrict__ t_view)
 {
     __shared__ float4 s_coef[MOTION ? NCOEF / 3 : 1];  // padded: one vector load per coefficient
     const int k = blockIdx.y;
@@ -105,6 +136,7 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
     if (y == 0.0f) return;
     const bool vec = (reinterpret_cast<uintptr_t>(vol) & 15) == 0;
     const long long nvox = (long long)G.nx * G.ny * G.nz;
+    const float t = DYR ? __ldg(t_view + view) : 0.0f;
     float cen[3];
     grid_centre(G, cen);
     for (int s = 0; s < G.n_sub; ++s) {
@@ -136,7 +168,10 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
             if (!(gc[0] >= -1.0f - cen[0] && gc[0] < (float)G.nx - cen[0] && gc[1] >= -1.0f - cen[1] &&
                   gc[1] < (float)G.ny - cen[1] && gc[2] >= -1.0f - cen[2] && gc[2] < (float)G.nz - cen[2]))
                 continue;
-            scatter_trilinear(vol, G.nx, G.ny, G.nz, cen, gc, val, vec, nvox);
+            if (DYR)
+                scatter_trilinear_dyrect(vol, G.nx, G.ny, G.nz, cen, gc, val, tau, t, nvox);
+            else
+                scatter_trilinear(vol, G.nx, G.ny, G.nz, cen, gc, val, vec, nvox);
         }
     }
 }
@@ -147,12 +182,16 @@ cudaError_t launch_adjoint(const FwdArgs &a, const float *proj, float *vol)
     const Grid &G = *a.grid;
     const dim3 grid((G.nu + ADJ_TX - 1) / ADJ_TX, a.n_idx, (G.nv + ADJ_TY - 1) / ADJ_TY);
     const dim3 block(ADJ_TX, ADJ_TY);
+    if (a.dyr && a.motion) return cudaErrorInvalidValue;  // the event model is defined without motion
     if (a.motion)
-        adjoint_kernel<true><<<grid, block, 0, a.stream>>>(G, a.views, a.motion, a.coef_idx, a.view_idx,
-                                                          proj, vol, a.devcheck);
+        adjoint_kernel<true, false><<<grid, block, 0, a.stream>>>(G, a.views, a.motion, a.coef_idx, a.view_idx,
+                                                                 proj, vol, a.devcheck, nullptr, nullptr);
+    else if (a.dyr)
+        adjoint_kernel<false, true><<<grid, block, 0, a.stream>>>(G, a.views, nullptr, nullptr, a.view_idx, proj,
+                                                                 vol, a.devcheck, a.dyr->tau, a.dyr->t_view);
     else
-        adjoint_kernel<false><<<grid, block, 0, a.stream>>>(G, a.views, nullptr, nullptr, a.view_idx, proj,
-                                                           vol, a.devcheck);
+        adjoint_kernel<false, false><<<grid, block, 0, a.stream>>>(G, a.views, nullptr, nullptr, a.view_idx, proj,
+                                                                  vol, a.devcheck, nullptr, nullptr);
     return cudaGetLastError();
 }
 

@@ -66,6 +66,7 @@ struct AtlasSampler {
     static constexpr bool CYLINDER = false;
     static constexpr bool JOSEPH = false;
     static constexpr bool ROI = false;
+    static constexpr bool DYRECT = false;
     // Fills the per-CTA tile-origin table (all threads call; barrier inside).
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads)
     {
@@ -188,6 +189,7 @@ struct LinearSampler {
     static constexpr bool CYLINDER = false;
     static constexpr bool JOSEPH = false;
     static constexpr bool ROI = false;
+    static constexpr bool DYRECT = false;
     __device__ __forceinline__ void bind(float2 *, int, int) {}
     __device__ __forceinline__ float interior(float gx, float gy, float gz) const;
     __device__ __forceinline__ float operator()(float gx, float gy, float gz, float &wsum) const;

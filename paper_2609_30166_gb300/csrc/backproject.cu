@@ -29,6 +29,9 @@ constexpr int BP_UNROLL = CTREX_BP_UNROLL;
 #ifndef CTREX_BP_SUBV_MIN_BLOCKS
 #define CTREX_BP_SUBV_MIN_BLOCKS 5  // the same for the sub-voxel variant (48 registers)
 #endif
+#ifndef CTREX_BP_DYR_MIN_BLOCKS
+#define CTREX_BP_DYR_MIN_BLOCKS 5  // the event-model variant: eight accumulators (48 registers)
+#endif
 
 // Bilinear sample of one correction image at (u, v) = (iu + au, iv + av),
 // zero outside the detector (taps outside get zero weight).  A Slot holds what
@@ -247,6 +250,128 @@ __global__ void __launch_bounds__(BP_THREADS, SUBV ? CTREX_BP_SUBV_MIN_BLOCKS : 
     }
 }
 
+// Event-based 4D model (Sec. 3.3): vol (and w) hold mu0 followed by mu1.
+// Eq. (1) term 3 splits by the voxel's transition time tau_j: the views
+// acquired before tau_j (t_v < tau_j) backproject into mu0_j and the others
+// into mu1_j, each part normalised by its own column sum.  Cartesian grid,
+// voxel centres, two z-neighbouring voxels per thread as in bp_kernel.
+template <typename Images, typename TV, bool WINDOW>
+__global__ void __launch_bounds__(BP_THREADS, CTREX_BP_DYR_MIN_BLOCKS)
+    bp_dyrect_kernel(Grid G, const ViewGPU *__restrict__ views, const int *__restrict__ view_idx, int n_idx,
+                     const Images img, const int4 *__restrict__ window, TV *__restrict__ vol,
+                     const float *__restrict__ w, float alpha, int normalize, int accumulate,
+                     const float *__restrict__ tau, const float *__restrict__ t_view)
+{
+    __shared__ float4 sP[BP_CHUNK][3];
+    __shared__ typename Images::Slot sImg[BP_CHUNK];
+    __shared__ float sT[BP_CHUNK];
+    __shared__ float4 sWin[WINDOW ? BP_CHUNK : 1];
+    const int tid = (threadIdx.z * BP_TY + threadIdx.y) * BP_TX + threadIdx.x;
+    const int ix = blockIdx.x * BP_TX + threadIdx.x;
+    const int iy = blockIdx.y * BP_TY + threadIdx.y;
+    const int iz = (blockIdx.z * BP_TZ + threadIdx.z) * BP_VZ;
+    const bool inside = ix < G.nx && iy < G.ny && iz < G.nz;
+    const size_t nvox = (size_t)G.nx * G.ny * G.nz;
+    const size_t j0 = ((size_t)iz * G.ny + iy) * G.nx + ix;
+    const float tau0 = inside ? __ldg(tau + j0) : 0.0f;
+    const float tau1 = inside && iz + 1 < G.nz ? __ldg(tau + j0 + (size_t)G.nx * G.ny) : 0.0f;
+    const float fx = (float)ix, fy = (float)iy, fz = (float)iz;
+    float2 lo = make_float2(0.0f, 0.0f), hi = make_float2((float)(G.nu - 1), (float)(G.nv - 1));
+    // [voxel][part]: part 0 = views before the transition (mu0), 1 = after (mu1)
+    float b00 = 0.f, c00 = 0.f, b01 = 0.f, c01 = 0.f, b10 = 0.f, c10 = 0.f, b11 = 0.f, c11 = 0.f;
+    const int total = n_idx * G.n_sub;
+    for (int base = 0; base < total; base += BP_CHUNK) {
+        const int cnt = min(BP_CHUNK, total - base);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += BP_THREADS) {
+            const int q = base + t;
+            const int k = q / G.n_sub, s = q - k * G.n_sub;
+            int view = view_idx ? view_idx[k] : k;
+            const bool ok = view >= 0 && view < G.n_views;
+            if (!ok) view = 0;
+            const float *P = views[view * G.n_sub + s].P;
+            sP[t][0] = make_float4(P[0], P[1], P[2], P[3]);
+            sP[t][1] = make_float4(P[4], P[5], P[6], P[7]);
+            sP[t][2] = ok ? make_float4(P[8], P[9], P[10], P[11]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            sImg[t] = img.slot(k);
+            sT[t] = __ldg(t_view + view);
+            if (WINDOW) {
+                const int4 wd = window[view];
+                sWin[t] = make_float4((float)wd.x, (float)wd.y, (float)wd.z, (float)wd.w);
+            }
+        }
+        __syncthreads();
+        if (!inside) continue;
+#pragma unroll BP_UNROLL
+        for (int m = 0; m < cnt; ++m) {
+            const float4 p0 = sP[m][0], p1 = sP[m][1], p2 = sP[m][2];
+            const typename Images::Slot slot = sImg[m];
+            const float tv = sT[m];
+            if (WINDOW) {
+                const float4 wd = sWin[m];
+                lo = make_float2(wd.x, wd.z);
+                hi = make_float2(wd.y, wd.w);
+            }
+            const float h3 = fmaf(p2.x, fx, fmaf(p2.y, fy, fmaf(p2.z, fz, p2.w)));
+            const float h1 = fmaf(p0.x, fx, fmaf(p0.y, fy, fmaf(p0.z, fz, p0.w)));
+            const float h2 = fmaf(p1.x, fx, fmaf(p1.y, fy, fmaf(p1.z, fz, p1.w)));
+            float tb = 0.0f, tc = 0.0f;
+            bp_term(img, slot, h1, h2, h3, lo, hi, tb, tc);
+            const bool e0 = tv < tau0;
+            b00 += e0 ? tb : 0.0f;
+            c00 += e0 ? tc : 0.0f;
+            b01 += e0 ? 0.0f : tb;
+            c01 += e0 ? 0.0f : tc;
+            tb = 0.0f;
+            tc = 0.0f;
+            bp_term(img, slot, h1 + p0.z, h2 + p1.z, h3 + p2.z, lo, hi, tb, tc);
+            const bool e1 = tv < tau1;
+            b10 += e1 ? tb : 0.0f;
+            c10 += e1 ? tc : 0.0f;
+            b11 += e1 ? 0.0f : tb;
+            c11 += e1 ? 0.0f : tc;
+        }
+    }
+    if (!inside) return;
+    const float mean = G.inv_sub;
+#pragma unroll
+    for (int q = 0; q < BP_VZ; ++q) {
+        if (iz + q >= G.nz) break;
+        const size_t j = j0 + (size_t)q * G.nx * G.ny;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            const float b = (q == 0 ? (part == 0 ? b00 : b01) : (part == 0 ? b10 : b11)) * mean;
+            const float c = (q == 0 ? (part == 0 ? c00 : c01) : (part == 0 ? c10 : c11)) * mean;
+            const size_t jo = j + (size_t)part * nvox;
+            float scale = alpha;
+            if (normalize) scale *= (c > 1e-6f ? 1.0f / c : 0.0f);
+            if (w) scale *= __ldg(w + jo);
+            const float upd = scale * b;
+            const float out = accumulate ? Storage<TV>::load(vol + jo) + upd : upd;
+            Storage<TV>::store(vol + jo, out);
+        }
+    }
+}
+
+template <typename Images, typename TV>
+static cudaError_t bp_launch_dyrect(const BpArgs &a, const Images &img)
+{
+    const Grid &G = *a.grid;
+    const dim3 block(BP_TX, BP_TY, BP_TZ);
+    const dim3 grid((G.nx + BP_TX - 1) / BP_TX, (G.ny + BP_TY - 1) / BP_TY,
+                    (G.nz + BP_TZ * BP_VZ - 1) / (BP_TZ * BP_VZ));
+    if (a.cyl || a.subvox > 1) return cudaErrorInvalidValue;
+    if (a.window)
+        bp_dyrect_kernel<Images, TV, true><<<grid, block, 0, a.stream>>>(
+            G, a.views, a.view_idx, a.n_idx, img, a.window, static_cast<TV *>(a.vol), a.w, a.alpha, a.normalize,
+            a.accumulate, a.dyr->tau, a.dyr->t_view);
+    else
+        bp_dyrect_kernel<Images, TV, false><<<grid, block, 0, a.stream>>>(
+            G, a.views, a.view_idx, a.n_idx, img, nullptr, static_cast<TV *>(a.vol), a.w, a.alpha, a.normalize,
+            a.accumulate, a.dyr->tau, a.dyr->t_view);
+    return cudaGetLastError();
+}
+
 template <typename Images, typename TV, bool SUBV, bool CYL>
 static void bp_launch_window(const BpArgs &a, const Images &img, dim3 grid, dim3 block)
 {
@@ -287,6 +412,10 @@ static cudaError_t bp_launch(const BpArgs &a, const Images &img)
 template <typename Images>
 static cudaError_t bp_dispatch_vol(const BpArgs &a, const Images &img)
 {
+    if (a.dyr) {
+        if (a.vol_dtype == CTREX_F32) return bp_launch_dyrect<Images, float>(a, img);
+        return bp_launch_dyrect<Images, __nv_bfloat16>(a, img);
+    }
     if (a.vol_dtype == CTREX_F32) return bp_launch<Images, float>(a, img);
     return bp_launch<Images, __nv_bfloat16>(a, img);
 }

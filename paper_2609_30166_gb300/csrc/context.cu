@@ -73,6 +73,15 @@ struct ctrex_ctx {
     RoiGPU roig{};
     AtlasStore roi_atlas;
     Atlas roi_atlas_view;
+    // event-based 4D model (set by ctrex_set_dyrect): volume buffers hold
+    // the initial values followed by the final values
+    bool dyr = false;
+    float *d_tau = nullptr;     // [nz][ny][nx] transition times
+    float *d_tview = nullptr;   // [n_views] acquisition times
+    AtlasStore dyr_atlas1;      // the final values (the volume atlas holds the initial ones)
+    AtlasStore tau_atlas;
+    Atlas dyr_atlas1_view, tau_atlas_view;
+    DyrArgs dyra{};
     // ordered-subset SIRT: concatenated subset view lists, per-subset norms
     int *d_subset_views = nullptr;
     size_t subset_views_bytes = 0;
@@ -179,15 +188,27 @@ FwdArgs fwd_args(ctrex_ctx *c, const void *vol, int vdt, const int *view_idx, in
     a.cyl = c->cyl ? &c->cylg : nullptr;
     a.joseph = c->projector == CTREX_PROJ_JOSEPH ? 1 : 0;
     a.roi = c->roi ? &c->roig : nullptr;
+    a.dyr = c->dyr ? &c->dyra : nullptr;
     return a;
 }
 
 size_t grid_voxels(const Grid &G) { return (size_t)G.nx * G.ny * G.nz; }
 
-// Elements of a volume buffer: the grid, then the ROI grid if one is set.
+// Elements of a volume buffer: the grid, then the ROI grid if one is set;
+// with the event-based model the grid's initial then final values.
 size_t volume_elems(const ctrex_ctx *c)
 {
-    return grid_voxels(c->grid) + (c->roi ? grid_voxels(c->roi_grid) : 0);
+    return grid_voxels(c->grid) * (c->dyr ? 2 : 1) + (c->roi ? grid_voxels(c->roi_grid) : 0);
+}
+
+void dyr_release(ctrex_ctx *c)
+{
+    c->dyr = false;
+    if (c->d_tau) cudaFree(c->d_tau);
+    if (c->d_tview) cudaFree(c->d_tview);
+    c->d_tau = c->d_tview = nullptr;
+    atlas_release(c->dyr_atlas1);
+    atlas_release(c->tau_atlas);
 }
 
 // Uploads vol into the context's texture atlas and points a.atlas at it; if
@@ -208,6 +229,29 @@ int prepare_atlas(ctrex_ctx *c, FwdArgs &a, const void *vol, int vdt)
         if (e != cudaSuccess) return cuda_fail(c, e, "Joseph atlas upload");
         c->jos_atlas_view = atlas_view(c->jos_atlas);
         a.atlas = &c->jos_atlas_view;
+        return CTREX_OK;
+    }
+    if (c->dyr) {
+        // initial values into the volume atlas, final values into their own;
+        // the transition times were uploaded by set_dyrect; no row-major fallback
+        const size_t off = grid_voxels(c->grid) * dtype_size(vdt);
+        AtlasStore *st[2] = {&c->vol_atlas, &c->dyr_atlas1};
+        Atlas *vw[2] = {&c->vol_atlas_view, &c->dyr_atlas1_view};
+        for (int i = 0; i < 2; ++i) {
+            cudaError_t e = atlas_ensure(*st[i], c->grid.nx, c->grid.ny, c->grid.nz, vdt == CTREX_BF16, c->device,
+                                         false);
+            if (e == cudaErrorInvalidValue) {
+                cudaGetLastError();
+                return fail(c, CTREX_E_SHAPE, "event model: the volume exceeds the 2D texture limits of the device");
+            }
+            if (e != cudaSuccess) return cuda_fail(c, e, "event-model atlas allocation");
+            e = atlas_upload(*st[i], static_cast<const char *>(vol) + (i ? off : 0), c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "event-model atlas upload");
+            *vw[i] = atlas_view(*st[i]);
+        }
+        c->dyra.mu1 = &c->dyr_atlas1_view;
+        c->dyra.tau_atlas = &c->tau_atlas_view;
+        a.atlas = &c->vol_atlas_view;
         return CTREX_OK;
     }
     if (c->roi) {
@@ -360,6 +404,7 @@ int ctrex_destroy(ctrex_ctx *c)
         atlas_release(c->jos_atlas);
         atlas_release(c->roi_atlas);
         dfree(c->d_views_roi);
+        dyr_release(c);
     }
     delete c;
     return CTREX_OK;
@@ -461,6 +506,7 @@ static int build_geometry(ctrex_ctx *c, const double *P, int n_views, int n_sub,
     dfree(c->d_views_roi);
     c->roi = false;
     atlas_release(c->roi_atlas);
+    dyr_release(c);
     dfree(c->d_window);
     c->has_window = false;
     // motion buffers are sized by n_views: drop them with the old geometry
@@ -617,9 +663,9 @@ int ctrex_set_motion(ctrex_ctx *c, const float *theta, const float *coef, const 
 {
     if (!c) return CTREX_E_ARG;
     if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_motion before set_geometry");
-    if ((c->cyl || c->roi || c->projector == CTREX_PROJ_JOSEPH) && (theta || coef || s_view))
+    if ((c->cyl || c->roi || c->dyr || c->projector == CTREX_PROJ_JOSEPH) && (theta || coef || s_view))
         return fail(c, CTREX_E_STATE, "set_motion: the motion model is defined for the trilinear projector on the "
-                                      "Cartesian grid only");
+                                      "Cartesian grid only, without the event model");
     double box = 0.0;
     const int nn[3] = {c->grid.nx, c->grid.ny, c->grid.nz};
     for (int a = 0; a < 3; ++a) box = fmax(box, nn[a] * c->vox[a]);
@@ -700,9 +746,9 @@ int ctrex_set_roi(ctrex_ctx *c, const ctrex_vol_grid *roi)
         atlas_release(c->roi_atlas);
         return CTREX_OK;
     }
-    if (c->cyl || c->has_motion || c->projector != CTREX_PROJ_TRILINEAR)
+    if (c->cyl || c->has_motion || c->dyr || c->projector != CTREX_PROJ_TRILINEAR)
         return fail(c, CTREX_E_STATE, "set_roi: the ROI projector is the trilinear one on a Cartesian grid without "
-                                      "motion");
+                                      "motion or the event model");
     if (roi->nx < 1 || roi->ny < 1 || roi->nz < 1 ||
         (long long)roi->nx * roi->ny * roi->nz + (long long)grid_voxels(c->grid) >= (1LL << 31))
         return fail(c, CTREX_E_SHAPE, "set_roi: grid %d x %d x %d unsupported", roi->nx, roi->ny, roi->nz);
@@ -758,9 +804,9 @@ int ctrex_set_projector(ctrex_ctx *c, int kind)
     if (!c) return CTREX_E_ARG;
     if (kind != CTREX_PROJ_TRILINEAR && kind != CTREX_PROJ_JOSEPH)
         return fail(c, CTREX_E_ARG, "set_projector: unknown projector %d", kind);
-    if (kind == CTREX_PROJ_JOSEPH && (c->cyl || c->has_motion || c->roi))
+    if (kind == CTREX_PROJ_JOSEPH && (c->cyl || c->has_motion || c->roi || c->dyr))
         return fail(c, CTREX_E_STATE, "set_projector: the Joseph projector is defined on the Cartesian grid "
-                                      "without motion");
+                                      "without motion or the event model");
     c->projector = kind;
     if (kind != CTREX_PROJ_JOSEPH) atlas_release(c->jos_atlas);
     return CTREX_OK;
@@ -770,7 +816,46 @@ int ctrex_set_bp_subvoxel(ctrex_ctx *c, int s)
 {
     if (!c) return CTREX_E_ARG;
     if (s < 1 || s > CTREX_MAX_SUBVOXEL) return fail(c, CTREX_E_ARG, "set_bp_subvoxel: s must be in [1, 8]");
+    if (s > 1 && c->dyr) return fail(c, CTREX_E_STATE, "set_bp_subvoxel: not defined with the event model");
     c->bp_subvoxel = s;
+    return CTREX_OK;
+}
+
+int ctrex_set_dyrect(ctrex_ctx *c, const float *tau, const float *t_view)
+{
+    if (!c) return CTREX_E_ARG;
+    if (!c->has_geom) return fail(c, CTREX_E_STATE, "set_dyrect before set_geometry");
+    DeviceGuard g(c->device);
+    if (!tau) {
+        dyr_release(c);
+        return CTREX_OK;
+    }
+    if (!t_view) return fail(c, CTREX_E_ARG, "set_dyrect: t_view is NULL");
+    if (c->cyl || c->roi || c->has_motion || c->projector != CTREX_PROJ_TRILINEAR || c->bp_subvoxel > 1)
+        return fail(c, CTREX_E_STATE, "set_dyrect: the event model is defined for the trilinear projector on one "
+                                      "Cartesian grid, without motion, ROI or sub-voxel backprojection");
+    if (2 * (long long)grid_voxels(c->grid) >= (1LL << 31))
+        return fail(c, CTREX_E_SHAPE, "set_dyrect: the two value fields exceed 2^31 elements");
+    const size_t nvox = grid_voxels(c->grid), V = (size_t)c->grid.n_views;
+    if (!c->d_tau) CT_CUDA(c, cudaMalloc((void **)&c->d_tau, sizeof(float) * nvox));
+    if (!c->d_tview) CT_CUDA(c, cudaMalloc((void **)&c->d_tview, sizeof(float) * V));
+    CT_CUDA(c, cudaMemcpyAsync(c->d_tau, tau, sizeof(float) * nvox, cudaMemcpyDeviceToDevice, c->stream));
+    CT_CUDA(c, cudaMemcpyAsync(c->d_tview, t_view, sizeof(float) * V, cudaMemcpyDeviceToDevice, c->stream));
+    cudaError_t e = atlas_ensure(c->tau_atlas, c->grid.nx, c->grid.ny, c->grid.nz, false, c->device, false);
+    if (e == cudaErrorInvalidValue) {
+        cudaGetLastError();
+        dyr_release(c);
+        return fail(c, CTREX_E_SHAPE, "set_dyrect: the volume exceeds the 2D texture limits of the device");
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "transition-time atlas allocation");
+    e = atlas_upload(c->tau_atlas, c->d_tau, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "transition-time atlas upload");
+    c->tau_atlas_view = atlas_view(c->tau_atlas);
+    c->dyra.tau = c->d_tau;
+    c->dyra.t_view = c->d_tview;
+    c->dyra.tau_atlas = &c->tau_atlas_view;
+    c->dyra.mu1 = &c->dyr_atlas1_view;
+    c->dyr = true;
     return CTREX_OK;
 }
 
@@ -854,6 +939,7 @@ int ctrex_back_project(ctrex_ctx *c, const void *r, int rdt, void *vol, int vdt,
     a.window = c->has_window ? c->d_window : nullptr;
     a.subvox = c->bp_subvoxel;
     a.cyl = c->cyl ? &c->cylg : nullptr;
+    a.dyr = c->dyr ? &c->dyra : nullptr;
     if (n_idx > 0 && !c->img_atlas_unfit) {
         cudaError_t ae = atlas_ensure(c->img_atlas, c->grid.nu, c->grid.nv, n_idx, rdt == CTREX_BF16, c->device);
         if (ae == cudaErrorInvalidValue) {
@@ -904,7 +990,7 @@ int ctrex_motion_grad(ctrex_ctx *c, const void *vol, int vdt, const float *gproj
     if (!c) return CTREX_E_ARG;
     int e = check_views(c, view_idx, n_idx);
     if (e) return e;
-    if (!c->has_motion) return fail(c, CTREX_E_STATE, "motion_grad: set_motion has not been called");
+    if (!c->has_motion || c->dyr) return fail(c, CTREX_E_STATE, "motion_grad: set_motion has not been called");
     if (n_idx == 0) return CTREX_OK;
     if (!vol || !gproj) return fail(c, CTREX_E_ARG, "motion_grad: NULL buffer");
     if (!dtype_ok(vdt)) return fail(c, CTREX_E_DTYPE, "motion_grad: bad dtype");

@@ -98,6 +98,16 @@ enum : unsigned { DEVCHECK_OOB = 1u };
 
 struct Atlas;
 
+// Event-based 4D model (Sec. 3.3): with these set, volume buffers hold mu0
+// followed by mu1 (2 nx ny nz elements) and view v sees mu0 at the voxels
+// whose transition time tau exceeds t_view[v], mu1 elsewhere.
+struct DyrArgs {
+    const Atlas *mu1 = nullptr;     // atlas of the final values (the forward's atlas holds mu0)
+    const Atlas *tau_atlas = nullptr;
+    const float *tau = nullptr;     // device [nz][ny][nx]
+    const float *t_view = nullptr;  // device [n_views]
+};
+
 struct FwdArgs {
     const Grid *grid;           // host copy
     const Atlas *atlas = nullptr;  // volume uploaded into a texture atlas, or nullptr
@@ -115,6 +125,7 @@ struct FwdArgs {
     int joseph = 0;               // classical Joseph projector; atlas = the three-stack atlas
     const RoiGPU *roi = nullptr;  // multi-resolution ROI: atlas = context grid, roi_atlas = ROI grid
     const Atlas *roi_atlas = nullptr;
+    const DyrArgs *dyr = nullptr;  // event-based 4D model, or nullptr
 };
 
 cudaError_t launch_forward(const FwdArgs &a, void *proj, int proj_dtype, float *rowsum);
@@ -141,6 +152,7 @@ struct BpArgs {
     int accumulate;
     int subvox = 1;  // sub-voxel points per axis (1 = voxel centre only)
     const CylGPU *cyl = nullptr;  // cylindrical domain, or nullptr (Cartesian grid)
+    const DyrArgs *dyr = nullptr;  // event-based 4D model: vol and w hold mu0 then mu1
     cudaStream_t stream;
 };
 cudaError_t launch_backproject(const BpArgs &a);

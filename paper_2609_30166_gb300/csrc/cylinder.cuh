@@ -98,6 +98,7 @@ struct CylSampler {
     static constexpr bool CYLINDER = true;
     static constexpr bool JOSEPH = false;
     static constexpr bool ROI = false;
+    static constexpr bool DYRECT = false;
 
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads) { base.bind(table, tid, nthreads); }
 

@@ -25,6 +25,7 @@ struct JosephSampler {
     static constexpr bool CYLINDER = false;
     static constexpr bool JOSEPH = true;
     static constexpr bool ROI = false;
+    static constexpr bool DYRECT = false;
 
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads) { base.bind(table, tid, nthreads); }
     // unused: the Joseph path never samples trilinearly

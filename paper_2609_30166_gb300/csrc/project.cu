@@ -12,6 +12,7 @@
 // slab stays in L2 while it is being sampled.
 #include "atlas.cuh"
 #include "cylinder.cuh"
+#include "dyrect.cuh"
 #include "fwd_common.cuh"
 #include "joseph.cuh"
 #include "ray.cuh"
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
         ok = false;
         view = 0;
     }
+    if constexpr (Sampler::DYRECT) vol.set_view(view);  // the view's acquisition time
     MotionGPU mo;
     const float4 *coef = nullptr;
     if (MOTION) {
@@ -240,7 +242,7 @@ static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, flo
 {
     const Grid &G = *a.grid;
     const dim3 grid = fwd_grid(G, a.n_idx), block(FWD_TX, FWD_TY);
-    if constexpr (!Sampler::CYLINDER && !Sampler::JOSEPH && !Sampler::ROI) {
+    if constexpr (!Sampler::CYLINDER && !Sampler::JOSEPH && !Sampler::ROI && !Sampler::DYRECT) {
         if (a.motion) {
             fwd_kernel<Sampler, TP, MODE, true><<<grid, block, 0, a.stream>>>(
                 G, a.views, a.motion, a.coef_idx, smp, a.view_idx, out, rowsum, p, partials, a.devcheck,
@@ -264,6 +266,11 @@ static cudaError_t fwd_dispatch_sampler(const FwdArgs &a, TP *out, float *rowsum
         if (!a.atlas || !a.roi_atlas || a.cyl || a.joseph) return cudaErrorInvalidValue;
         RoiSampler rs{AtlasSampler{*a.atlas}, AtlasSampler{*a.roi_atlas}, *a.roi};
         return fwd_launch<RoiSampler, TP, MODE>(a, rs, out, rowsum, p, partials);
+    }
+    if (a.dyr) {  // mu0 from the volume atlas, mu1 and tau from their own
+        if (!a.atlas || !a.dyr->mu1 || !a.dyr->tau_atlas || a.cyl || a.joseph) return cudaErrorInvalidValue;
+        DyrectSampler ds{*a.atlas, *a.dyr->mu1, *a.dyr->tau_atlas, a.dyr->t_view};
+        return fwd_launch<DyrectSampler, TP, MODE>(a, ds, out, rowsum, p, partials);
     }
     if (a.joseph) {  // the Joseph projector reads its three-stack atlas only
         if (!a.atlas || a.cyl) return cudaErrorInvalidValue;

@@ -21,6 +21,7 @@ struct RoiSampler {
     static constexpr bool CYLINDER = false;
     static constexpr bool JOSEPH = false;
     static constexpr bool ROI = true;
+    static constexpr bool DYRECT = false;
 
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads)
     {

@@ -34,7 +34,7 @@ EXPORTS = (
     "ctrex_fwd_correct", "ctrex_back_project", "ctrex_adjoint_project", "ctrex_motion_grad",
     "ctrex_sirt_iterate", "ctrex_sirt_host", "ctrex_count_samples", "ctrex_correct_static",
     "ctrex_conv3d_fwd", "ctrex_conv3d_wgrad", "ctrex_os_sirt_iterate", "ctrex_set_bp_window",
-    "ctrex_probe_gather_rate", "ctrex_probe_l2_read_bandwidth", "ctrex_set_bp_subvoxel", "ctrex_set_geometry_cylinder", "ctrex_set_projector",
+    "ctrex_probe_gather_rate", "ctrex_probe_l2_read_bandwidth", "ctrex_set_dyrect", "ctrex_set_bp_subvoxel", "ctrex_set_geometry_cylinder", "ctrex_set_projector",
     "ctrex_set_roi",
 )
 
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
                                          ctypes.POINTER(DetGrid), d], i),
         "ctrex_probe_gather_rate": ([vp, ctypes.POINTER(d)], i),
         "ctrex_probe_l2_read_bandwidth": ([vp, ctypes.POINTER(d)], i),
+        "ctrex_set_dyrect": ([vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -280,6 +281,22 @@ class Context:
         """Forward projector: "trilinear" (default) or "joseph"."""
         k = {"trilinear": PROJ_TRILINEAR, "joseph": PROJ_JOSEPH}[kind]
         self._check(self.lib.ctrex_set_projector(self._h, k))
+
+    def set_dyrect(self, tau=None, t_view=None):
+        """Event-based 4D model (Sec. 3.3): tau [nz, ny, nx] transition times
+        and t_view [n_views] acquisition times (float32 device tensors);
+        volumes then become [2, nz, ny, nx] = (initial values, final values).
+        None switches it off."""
+        self._sync_stream()
+        if tau is None:
+            self._check(self.lib.ctrex_set_dyrect(self._h, None, None))
+            self.vol_shape = self.grid_shape
+            return
+        tau = self._dev(tau, "tau", self.grid_shape, dtypes=(torch.float32,))
+        t_view = self._dev(t_view, "t_view", (self.n_views,), dtypes=(torch.float32,))
+        self._dyr_keep = (tau, t_view)  # copied on the stream
+        self._check(self.lib.ctrex_set_dyrect(self._h, _ptr(tau), _ptr(t_view)))
+        self.vol_shape = (2,) + tuple(self.grid_shape)
 
     def set_bp_subvoxel(self, s=1):
         """Sub-voxel backprojection: s^3 points per voxel (1 = off)."""
