@@ -131,12 +131,18 @@ class ClockSampler:
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
-# launch of the fused forward kernel, from a one-pass ncu capture of that
-# kernel (summary kept under profiles/).  Valid only for the kernel sources it
-# was taken on (hash below) and for the FP32 workload; otherwise null.
-FWD_TRAFFIC_BYTES = 2331578112 + 1694034944
-FWD_TRAFFIC_SOURCES = ("project.cu", "atlas.cuh", "ray.cuh", "cylinder.cuh", "joseph.cuh", "roi.cuh", "fwd_common.cuh", "ctrex_internal.cuh")
-FWD_TRAFFIC_HASH = "ff65172063c78fe6"
+# launch of the fused forward kernel, from one-pass ncu captures of that
+# kernel on 16 and 180 views of the workload (summary kept under profiles/):
+# the launch reads the volume atlas once and each view's measured image and
+# writes its correction image, so traffic = a + b * views, with a and b from
+# the two captures, evaluated at 720 views.  Valid only for the kernel
+# sources it was taken on (hash below) and for the FP32 workload; otherwise
+# null.
+_T16, _T180 = 585101312 + 33152512, 983686144 + 396029696
+FWD_TRAFFIC_BYTES = int(_T16 + (_T180 - _T16) * (720 - 16) / (180 - 16))
+FWD_TRAFFIC_SOURCES = ("project.cu", "atlas.cuh", "ray.cuh", "cylinder.cuh", "joseph.cuh", "roi.cuh", "fwd_common.cuh",
+                       "ctrex_internal.cuh", "dyrect.cuh")
+FWD_TRAFFIC_HASH = "615f77780c263ae1"
 
 
 def fwd_traffic(dtype, views):
