@@ -56,6 +56,14 @@ constexpr int BK = 64;
 constexpr int STAGES = 2;
 constexpr int THREADS = 128;
 constexpr long long WAIT_LIMIT = 1LL << 26;
+// Polls of the epilogue's accumulator waits in the persistent kernels.  The
+// default is WAIT_LIMIT; a build with a tiny value makes those waits expire
+// on purpose, which is how the abort and drain path is tested (every other
+// wait keeps WAIT_LIMIT).
+#ifndef CTREX_CONV_EPI_WAIT_LIMIT
+#define CTREX_CONV_EPI_WAIT_LIMIT (1LL << 26)
+#endif
+constexpr long long EPI_WAIT_LIMIT = CTREX_CONV_EPI_WAIT_LIMIT;
 
 enum Op { OP_FWD = 0, OP_WGRAD = 1 };
 
@@ -779,10 +787,11 @@ __device__ __forceinline__ void umma_commit_p(uint32_t leader, uint64_t *bar)
 }
 // Warp-wide bounded wait (every lane returns the same answer); with an abort
 // flag it also gives up once another role raised it, and raises it itself on
-// expiry.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, unsigned parity, volatile int *abort_flag)
+// expiry.  limit: polls before it gives up.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, unsigned parity, volatile int *abort_flag,
+                                               long long limit = WAIT_LIMIT)
 {
-    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    for (long long i = 0; i < limit; ++i) {
         if (__any_sync(0xffffffffu, mbar_test(bar, parity))) return true;
         if (abort_flag && (i & 255) == 255 && __any_sync(0xffffffffu, *abort_flag != 0)) return false;
     }
@@ -876,6 +885,9 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         n0 = nt * BN;
     };
 
+    long long fills = 0;  // producer: copies issued (stage fills)
+    bool mmas = false;    // MMA warp: any MMA issued
+    uint32_t mma_leader = 0;
     if (warp == 0) {
         // producer warp: the loop runs warp-wide (uniform descriptors and
         // coordinates); one elected lane issues each copy
@@ -917,14 +929,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
                 }
             }
         }
-        if (!ok) {
-            if (lane == 0) atomicExch(status, 1);
-            // the copies already issued land on their own: wait for the last
-            // fill of every stage and the filter (bounded)
-            for (long long f = fill - 1; f >= 0 && f >= fill - ST; --f)
-                mbar_wait_warp(&full[f % ST], (unsigned)((f / ST) & 1), nullptr);
-            if (RESW) mbar_wait_warp(&wbar, 0u, nullptr);
-        }
+        if (!ok && lane == 0) atomicExch(status, 1);
+        fills = fill;
     } else if (warp == 1) {
         // MMA warp: the loop runs warp-wide; one elected lane issues the MMAs
         // and commits
@@ -974,13 +980,9 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             }
             if (ok) umma_commit_p(leader, &acc_full[acc]);
         }
-        if (!ok) {
-            if (lane == 0) atomicExch(status, 1);
-            if (issued) {
-                umma_commit_p(leader, &drain);  // tracks every MMA the elected lane issued
-                mbar_wait_warp(&drain, 0u, nullptr);
-            }
-        }
+        if (!ok && lane == 0) atomicExch(status, 1);
+        mmas = issued;
+        mma_leader = leader;
     } else {
         // epilogue warps 2..5: accumulator rows 32 (warp % 4) + lane
         const int quarter = warp & 3;
@@ -989,7 +991,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         int tile_i = 0;
         for (long long it = blockIdx.x; it < items; it += gridDim.x, ++tile_i) {
             const int acc = tile_i & 1;
-            if (!mbar_wait_warp(&acc_full[acc], (unsigned)((tile_i >> 1) & 1), abort_flag)) {
+            if (!mbar_wait_warp(&acc_full[acc], (unsigned)((tile_i >> 1) & 1), abort_flag, EPI_WAIT_LIMIT)) {
                 if (lane == 0) atomicExch(status, 1);
                 break;
             }
@@ -1016,6 +1018,22 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     }
     tc_before_sync();
     __syncthreads();
+    // Every role has left its loop, so the abort flag is final.  If a role
+    // gave up, the others may have stopped waiting for work still in flight:
+    // the producer waits for the last fill of every stage and the filter (the
+    // earlier fills of a stage completed before it was refilled), and the MMA
+    // warp for every MMA its elected lane issued, before the CTA releases
+    // TMEM and its shared memory.  All these waits are bounded.
+    if (*abort_flag) {
+        if (warp == 0) {
+            for (long long f = fills - 1; f >= 0 && f >= fills - ST; --f)
+                mbar_wait_warp(&full[f % ST], (unsigned)((f / ST) & 1), nullptr);
+            if (RESW) mbar_wait_warp(&wbar, 0u, nullptr);
+        } else if (warp == 1 && mmas) {
+            umma_commit_p(mma_leader, &drain);
+            mbar_wait_warp(&drain, 0u, nullptr);
+        }
+    }
     if (warp == 1) {
         tc_after_sync();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PL::TMEM_COLS) : "memory");
@@ -1115,6 +1133,9 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     volatile int *abort_flag = &abort_s;
     const bool any = t_end > t_begin;
 
+    long long fills = 0;  // producer: stage fills issued
+    bool mmas = false;    // MMA warp: any MMA issued
+    uint32_t mma_leader = 0;
     if (warp == 0 && any) {
         const uint32_t leader = elect_one();
         const uint32_t tx = (uint32_t)(4096 * G.cb) + PL::X_TX;
@@ -1142,10 +1163,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
                     tma_load_5d_p(leader, b + (uint32_t)((kx * (CN / 8) + h) * PL::COPY), &tmx, ci0 + 8 * h, x0 + kx - 1,
                                   y0 - 1, z + dz - 1, nb, &full[st]);
         }
-        if (!ok) {
-            if (lane == 0) atomicExch(status, 1);
-            for (long long f = i - 1; f >= 0 && f >= i - ST; --f) mbar_wait_warp(&full[f % ST], (unsigned)((f / ST) & 1), nullptr);
-        }
+        if (!ok && lane == 0) atomicExch(status, 1);
+        fills = i;
     } else if (warp == 1 && any) {
         const uint32_t leader = elect_one();
         // kind::f16, D F32, A and B BF16, both MN-major, N = 3 CN, M = 64 or 128
@@ -1176,20 +1195,18 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         }
         if (ok) {
             umma_commit_p(leader, &done);
-        } else {
-            if (lane == 0) atomicExch(status, 1);
-            if (issued) {
-                umma_commit_p(leader, &drain);
-                mbar_wait_warp(&drain, 0u, nullptr);
-            }
+        } else if (lane == 0) {
+            atomicExch(status, 1);
         }
+        mmas = issued;
+        mma_leader = leader;
     } else if (warp >= 2 && any) {
         // epilogue, once per CTA: accumulator row m = co - co0 sits in TMEM lane
         // m (M = 128) or 32 (m / 16) + m % 16 (M = 64: lanes 16..31 of each
         // quarter hold no row)
         const int quarter = warp & 3;
         const int co = M64 ? (lane < 16 ? co0 + 16 * quarter + lane : S.cout) : co0 + 32 * quarter + lane;
-        if (mbar_wait_warp(&done, 0u, abort_flag)) {
+        if (mbar_wait_warp(&done, 0u, abort_flag, EPI_WAIT_LIMIT)) {
             tc_after_sync();
             const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
             const long long krow = 27LL * S.cin;
@@ -1212,6 +1229,18 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     }
     tc_before_sync();
     __syncthreads();
+    // as in the forward: once a role gave up, the producer's last fills and
+    // the MMA warp's MMAs complete (bounded waits) before TMEM and shared
+    // memory are released
+    if (*abort_flag) {
+        if (warp == 0) {
+            for (long long f = fills - 1; f >= 0 && f >= fills - ST; --f)
+                mbar_wait_warp(&full[f % ST], (unsigned)((f / ST) & 1), nullptr);
+        } else if (warp == 1 && mmas) {
+            umma_commit_p(mma_leader, &drain);
+            mbar_wait_warp(&drain, 0u, nullptr);
+        }
+    }
     if (warp == 1) {
         tc_after_sync();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PL::TMEM_COLS) : "memory");
