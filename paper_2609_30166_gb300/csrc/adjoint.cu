@@ -7,15 +7,22 @@
 // Sec. 4.1 projector with the Sec. 2.2.2 / 3.1 warp.
 #include "ray.cuh"
 
-// 4 resident CTAs per SM for the motion gradient: registers capped at 128
-// (a few bytes of spills), measured faster than 167 registers at 3 CTAs
+// Motion gradient CTA: CTREX_MGRAD_WARPS warps, each on an 8 x 4 pixel
+// patch (the CTA covers 8 * warps detector columns x 4 rows); registers
+// capped at 128 (CTREX_MGRAD_MIN_BLOCKS resident CTAs of that size per SM).
+// Fewer warps per CTA shorten the wait of warps with short rays for the
+// CTA's final reduction.
+#ifndef CTREX_MGRAD_WARPS
+#define CTREX_MGRAD_WARPS 2
+#endif
 #ifndef CTREX_MGRAD_MIN_BLOCKS
-#define CTREX_MGRAD_MIN_BLOCKS 4
+#define CTREX_MGRAD_MIN_BLOCKS (16 / CTREX_MGRAD_WARPS)
 #endif
 
 namespace ctrex {
 
 constexpr int ADJ_TX = 32, ADJ_TY = 4;
+constexpr int MG_WARPS = CTREX_MGRAD_WARPS, MG_THREADS = 32 * MG_WARPS;
 constexpr int NCOEF = 8 * 8 * 8 * 3;
 
 // ---------------------------------------------------------------------------
@@ -111,7 +118,7 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
                    const float *__restrict__ proj, float *__restrict__ vol, unsigned *devcheck,
                    const float *__restrict__ tau, const float *__restrict__ t_view)
 {
-    __shared__ float4 s_coef[MOTION ? NCOEF / 3 : 1];  // padded: one vector load per coefficient
+    __shared__ float4 s_coef[MOTION ? NCOEF_PAD : 1];  // zero-padded 9^3 float4 copy of the coefficients
     const int k = blockIdx.y;
     const int view = view_idx ? view_idx[k] : k;
     if (view < 0 || view >= G.n_views) {
@@ -123,8 +130,7 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
     if (MOTION) {
         mo = motion[view];
         if (coef_g) {
-            for (int i = threadIdx.y * ADJ_TX + threadIdx.x; i < NCOEF / 3; i += ADJ_TX * ADJ_TY)
-                s_coef[i] = make_float4(coef_g[3 * i], coef_g[3 * i + 1], coef_g[3 * i + 2], 0.0f);
+            load_coef_padded(s_coef, coef_g, threadIdx.y * ADJ_TX + threadIdx.x, ADJ_TX * ADJ_TY);
             coef = s_coef;
         }
         __syncthreads();
@@ -250,24 +256,23 @@ __device__ __forceinline__ void spline_value_jacobian(const float4 *coef, const 
 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) u[c] = Jx[c] = Jy[c] = Jz[c] = 0.0f;
+    const float4 *plane = coef_cell(coef, i0);
     // the z loop stays rolled (bounds the live coefficient loads); its two
     // weights are picked by selects, which keeps the arrays in registers
 #pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
-        const int cz = min(i0[2] - 1 + k, 7);
+    for (int k = 0; k < 4; ++k, plane += CPAD * CPAD) {
         const float wzk = k == 0 ? wz[0] : (k == 1 ? wz[1] : (k == 2 ? wz[2] : wz[3]));
         const float dzk = k == 0 ? dz[0] : (k == 1 ? dz[1] : (k == 2 ? dz[2] : dz[3]));
         float a[3] = {0.f, 0.f, 0.f}, bx[3] = {0.f, 0.f, 0.f}, by[3] = {0.f, 0.f, 0.f};
+        const float4 *row = plane;
 #pragma unroll 1
-        for (int j = 0; j < 4; ++j) {
-            const int cy = min(i0[1] - 1 + j, 7);
+        for (int j = 0; j < 4; ++j, row += CPAD) {
             const float wyj = j == 0 ? wy[0] : (j == 1 ? wy[1] : (j == 2 ? wy[2] : wy[3]));
             const float dyj = j == 0 ? dy[0] : (j == 1 ? dy[1] : (j == 2 ? dy[2] : dy[3]));
             float sx[3] = {0.f, 0.f, 0.f}, tx[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int cx = min(i0[0] - 1 + i, 7);
-                const float3 cf = coef_at(coef, cx, cy, cz);
+                const float4 cf = row[i];
                 sx[0] = fmaf(wx[i], cf.x, sx[0]);
                 sx[1] = fmaf(wx[i], cf.y, sx[1]);
                 sx[2] = fmaf(wx[i], cf.z, sx[2]);
@@ -446,18 +451,18 @@ __device__ __forceinline__ void coef_step(CoefAcc &A, double *s_g64, int cell, c
 }
 
 template <typename TV>
-__global__ void __launch_bounds__(ADJ_TX *ADJ_TY, CTREX_MGRAD_MIN_BLOCKS)
+__global__ void __launch_bounds__(MG_THREADS, CTREX_MGRAD_MIN_BLOCKS)
     motion_grad_kernel(Grid G, const ViewGPU *__restrict__ views, const MotionGPU *__restrict__ motion,
                        const float *__restrict__ coef_g, const int *__restrict__ view_idx,
                        const TV *__restrict__ vol, const float *__restrict__ gproj,
                        double *__restrict__ grad_M, double *__restrict__ grad_b,
                        double *__restrict__ grad_coef, unsigned *devcheck)
 {
-    __shared__ float4 s_coef[NCOEF / 3];  // padded: one vector load per control point
+    __shared__ float4 s_coef[NCOEF_PAD];  // zero-padded 9^3 float4 copy of the coefficients
     __shared__ double s_g64[NCOEF];       // the CTA's coefficient-gradient partials
-    __shared__ double s_red[12][ADJ_TX * ADJ_TY / 32];
+    __shared__ double s_red[12][MG_WARPS];
     __shared__ float4 s_piece[4];
-    const int tid = threadIdx.y * ADJ_TX + threadIdx.x;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     const int lane = tid & 31;
     const int k = blockIdx.y;
     const int view = view_idx ? view_idx[k] : k;
@@ -468,11 +473,9 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY, CTREX_MGRAD_MIN_BLOCKS)
     const MotionGPU mo = motion[view];
     const bool spline = coef_g != nullptr && mo.s != 0.0f;
     const bool want_coef = spline && grad_coef != nullptr;
-    if (spline)
-        for (int i = tid; i < NCOEF / 3; i += ADJ_TX * ADJ_TY)
-            s_coef[i] = make_float4(coef_g[3 * i], coef_g[3 * i + 1], coef_g[3 * i + 2], 0.0f);
+    if (spline) load_coef_padded(s_coef, coef_g, tid, MG_THREADS);
     if (want_coef)
-        for (int i = tid; i < NCOEF; i += ADJ_TX * ADJ_TY) s_g64[i] = 0.0;
+        for (int i = tid; i < NCOEF; i += MG_THREADS) s_g64[i] = 0.0;
     if (tid < 4) s_piece[tid] = bspline_piece(tid);
     __syncthreads();
     float cen[3];
@@ -485,7 +488,7 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY, CTREX_MGRAD_MIN_BLOCKS)
     CA.cell = -1;
     float G1[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
     int iu, iv;
-    tile_pixel<true>(blockIdx.x * ADJ_TX, blockIdx.z * ADJ_TY, iu, iv);
+    tile_pixel<true>(blockIdx.x * 8 * MG_WARPS, blockIdx.z * 4, iu, iv);
     const bool pix_ok = iu < G.nu && iv < G.nv;
     const float y = pix_ok ? gproj[((size_t)k * G.nv + iv) * G.nu + iu] * G.inv_sub : 0.0f;
     for (int s = 0; s < G.n_sub; ++s) {
@@ -589,12 +592,12 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY, CTREX_MGRAD_MIN_BLOCKS)
     if (tid < 12) {
         double v = 0.0;
 #pragma unroll
-        for (int w = 0; w < ADJ_TX * ADJ_TY / 32; ++w) v += s_red[tid][w];
+        for (int w = 0; w < MG_WARPS; ++w) v += s_red[tid][w];
         if (grad_M && tid < 9) atomicAdd(grad_M + 9 * view + tid, v);
         if (grad_b && tid >= 9) atomicAdd(grad_b + 3 * view + (tid - 9), v);
     }
     if (want_coef) {
-        for (int i = tid; i < NCOEF; i += ADJ_TX * ADJ_TY) {
+        for (int i = tid; i < NCOEF; i += MG_THREADS) {
             const double v = s_g64[i];
             if (v != 0.0) atomicAdd(grad_coef + i, v);
         }
@@ -606,8 +609,8 @@ cudaError_t launch_motion_grad(const FwdArgs &a, const float *gproj, double *gra
 {
     if (a.n_idx == 0) return cudaSuccess;
     const Grid &G = *a.grid;
-    const dim3 grid((G.nu + ADJ_TX - 1) / ADJ_TX, a.n_idx, (G.nv + ADJ_TY - 1) / ADJ_TY);
-    const dim3 block(ADJ_TX, ADJ_TY);
+    const dim3 grid((G.nu + 8 * MG_WARPS - 1) / (8 * MG_WARPS), a.n_idx, (G.nv + 3) / 4);
+    const dim3 block(32, MG_WARPS);
     if (a.vol_dtype == CTREX_F32)
         motion_grad_kernel<float><<<grid, block, 0, a.stream>>>(G, a.views, a.motion, a.coef_idx, a.view_idx,
                                                                (const float *)a.vol, gproj, grad_M, grad_b,

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
                const int *__restrict__ view_idx, TP *__restrict__ out, float *__restrict__ rowsum_out,
                const TP *__restrict__ p, float *__restrict__ partials, unsigned *devcheck, int p_by_view)
 {
-    __shared__ float4 s_coef[MOTION ? 8 * 8 * 8 : 1];  // padded: one vector load per coefficient
+    __shared__ float4 s_coef[MOTION ? NCOEF_PAD : 1];  // zero-padded 9^3 float4 copy of the coefficients
     __shared__ float s_red[2][FWD_TX * FWD_TY / 32];
     __shared__ float2 s_tile[Sampler::TILE_TABLE];
     Sampler vol = vol_in;
@@ -143,8 +143,7 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
     if (MOTION) {
         mo = motion[view];
         if (coef_g != nullptr) {
-            for (int i = threadIdx.y * FWD_TX + threadIdx.x; i < 8 * 8 * 8; i += FWD_TX * FWD_TY)
-                s_coef[i] = make_float4(coef_g[3 * i], coef_g[3 * i + 1], coef_g[3 * i + 2], 0.0f);
+            load_coef_padded(s_coef, coef_g, threadIdx.y * FWD_TX + threadIdx.x, FWD_TX * FWD_TY);
             coef = s_coef;
         }
         __syncthreads();

@@ -204,17 +204,33 @@ __device__ __forceinline__ void tile_pixel(int tile_u0, int tile_v0, int &iu, in
     }
 }
 
-// Coefficient (cx, cy, cz) of an [8][8][8] coefficient block: float triples
-// (3 scalar loads) or float4 padded to 16 bytes (one vector load).
-__device__ __forceinline__ float3 coef_at(const float *coef, int cx, int cy, int cz)
+// Shared-memory copy of the [8][8][8][3] B-spline coefficients as float4
+// (one vector load each), zero-padded to 9 x 9 x 9: the 4 x 4 x 4 support of
+// spline cell i0 (i0 in [1, 6] per axis) spans control points i0 - 1 ..
+// i0 + 2, at most 8, so no index needs clamping; a point 8 is reached only
+// at spline coordinate 6 exactly, where its weight (cubic piece 3 at
+// fraction 0) is zero.  Tap (i, j, k) of the cell is base[k * 81 + j * 9 + i]
+// with base = coef_cell(coef, i0): constant offsets from one address.
+constexpr int CPAD = 9;
+constexpr int NCOEF_PAD = CPAD * CPAD * CPAD;
+
+__device__ __forceinline__ void load_coef_padded(float4 *__restrict__ s, const float *__restrict__ coef_g, int tid,
+                                                 int nthreads)
 {
-    const float *c = coef + 3 * ((cz * 8 + cy) * 8 + cx);
-    return make_float3(c[0], c[1], c[2]);
+    for (int i = tid; i < NCOEF_PAD; i += nthreads) {
+        const int cx = i % CPAD, cy = (i / CPAD) % CPAD, cz = i / (CPAD * CPAD);
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (cx < 8 && cy < 8 && cz < 8) {
+            const float *c = coef_g + 3 * ((cz * 8 + cy) * 8 + cx);
+            v = make_float4(c[0], c[1], c[2], 0.0f);
+        }
+        s[i] = v;
+    }
 }
-__device__ __forceinline__ float3 coef_at(const float4 *coef, int cx, int cy, int cz)
+
+__device__ __forceinline__ const float4 *coef_cell(const float4 *coef, const int i0[3])
 {
-    const float4 c = coef[(cz * 8 + cy) * 8 + cx];
-    return make_float3(c.x, c.y, c.z);
+    return coef + ((i0[2] - 1) * CPAD + (i0[1] - 1)) * CPAD + (i0[0] - 1);
 }
 
 // Integer grid centre c = floor((n - 1) / 2) per axis (index coordinates).
@@ -232,11 +248,9 @@ __device__ __forceinline__ void grid_centre(const Grid &G, float c[3])
 // the bracket is a displacement of a few voxels for a near-identity pose,
 // so its roundings are small, and only the last addition rounds at the
 // magnitude of the coordinate (up to n / 2).  Since c is an integer, floor
-// and fraction of y follow exactly from yc.  coef: shared-memory copy of the
-// [8][8][8] coefficients in voxels (float triples or padded float4), or
-// nullptr.
-template <typename CoefT>
-__device__ __forceinline__ void warp_sample_c(const Grid &G, const MotionGPU &m, const CoefT *coef, const float gc[3],
+// and fraction of y follow exactly from yc.  coef: the padded shared-memory
+// copy of the coefficients in voxels (load_coef_padded), or nullptr.
+__device__ __forceinline__ void warp_sample_c(const Grid &G, const MotionGPU &m, const float4 *coef, const float gc[3],
                                               float yc[3])
 {
     float c[3];
@@ -255,18 +269,16 @@ __device__ __forceinline__ void warp_sample_c(const Grid &G, const MotionGPU &m,
         bspline_weights(f[0], wx);
         bspline_weights(f[1], wy);
         bspline_weights(f[2], wz);
+        const float4 *base = coef_cell(coef, i0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int cz = min(i0[2] - 1 + k, 7);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int cy = min(i0[1] - 1 + j, 7);
                 const float wyz = wz[k] * wy[j];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const int cx = min(i0[0] - 1 + i, 7);
                     const float wt = wyz * wx[i];
-                    const float3 cf = coef_at(coef, cx, cy, cz);
+                    const float4 cf = base[k * CPAD * CPAD + j * CPAD + i];
                     u0 = fmaf(wt, cf.x, u0);
                     u1 = fmaf(wt, cf.y, u1);
                     u2 = fmaf(wt, cf.z, u2);
@@ -282,8 +294,7 @@ __device__ __forceinline__ void warp_sample_c(const Grid &G, const MotionGPU &m,
 // The same warp in plain index coordinates, as the forward projector uses it:
 // y = M g + b + s u(M g + b) formed directly (fewer operations; the forward
 // averages the position rounding out along the ray, so it needs no centring).
-template <typename CoefT>
-__device__ __forceinline__ void warp_sample(const Grid &G, const MotionGPU &m, const CoefT *coef, const float g[3],
+__device__ __forceinline__ void warp_sample(const Grid &G, const MotionGPU &m, const float4 *coef, const float g[3],
                                             float y[3])
 {
     float gp[3];
@@ -300,18 +311,16 @@ __device__ __forceinline__ void warp_sample(const Grid &G, const MotionGPU &m, c
         bspline_weights(f[0], wx);
         bspline_weights(f[1], wy);
         bspline_weights(f[2], wz);
+        const float4 *base = coef_cell(coef, i0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int cz = min(i0[2] - 1 + k, 7);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int cy = min(i0[1] - 1 + j, 7);
                 const float wyz = wz[k] * wy[j];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const int cx = min(i0[0] - 1 + i, 7);
                     const float wt = wyz * wx[i];
-                    const float3 cf = coef_at(coef, cx, cy, cz);
+                    const float4 cf = base[k * CPAD * CPAD + j * CPAD + i];
                     u0 = fmaf(wt, cf.x, u0);
                     u1 = fmaf(wt, cf.y, u1);
                     u2 = fmaf(wt, cf.z, u2);
