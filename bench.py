@@ -474,14 +474,21 @@ def measure_rows(device, gather_peak, sm_count, sm_mhz):
         flops = 2.0 * x.numel() / cin * 27 * cin * cout
         t_fw = _time(lambda: ctrex.conv3d(x, wt, relu=True))
         t_wg = _time(lambda: ctrex.conv3d_wgrad(x, dy))
+        # compulsory HBM bytes: x and y (forward) or x and dy (weight gradient)
+        hbm = 2.0 * x.numel() / cin * (cin + cout)
+        hbm_peak = measured_peaks()[0] * 1e9
         convs[f"{n}^3 x2, {cin}->{cout}"] = {"fwd_ms": t_fw * 1e3, "fwd_tflops": flops / t_fw / 1e12,
-                                             "wgrad_ms": t_wg * 1e3, "wgrad_tflops": flops / t_wg / 1e12}
+                                             "fwd_hbm_frac": hbm / t_fw / hbm_peak,
+                                             "wgrad_ms": t_wg * 1e3, "wgrad_tflops": flops / t_wg / 1e12,
+                                             "wgrad_hbm_frac": hbm / t_wg / hbm_peak}
     ctrex.conv_status_check(device)
     best = max(v["fwd_tflops"] for v in convs.values())
     rows["a12_conv3d_tcgen05"] = {"layers": convs, "best_fwd_tflops": best, "bf16_peak_tflops": bf16_peak,
                                   "best_fwd_frac": best / bf16_peak,
                                   "kernels": {"fwd": "conv_fwd_tma_kernel (persistent, TMA, brick-staged input)",
-                                              "wgrad": "conv_wgrad_tma_kernel (MN-major brick, kx taps folded into N)"}}
+                                              "wgrad": "conv_wgrad_tma_kernel (MN-major brick, kx taps folded into N); "
+                                                       "16 output channels: conv_wgrad_c16_kernel (mma.m16n8k16 "
+                                                       "with register-resident operands)"}}
     torch.cuda.empty_cache()
     return rows
 

@@ -1247,6 +1247,227 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient of layers with 16 output channels (the U-Net's first and
+// last level): dW[co][tap][ci] = sum_p dy[p][co] x[p + off(tap)][ci].
+// With cout = 16 the tcgen05 form above wastes most of each MMA (M is at
+// least 64) and re-reads both operands from shared memory for every MMA.
+// Here each warp keeps its nine taps' 16 x 16 sums in registers and runs
+// mma.m16n8k16 (BF16, FP32 accumulation; M = co, N = ci, K = 16 voxels of an
+// output row) with register-resident operands:
+//   * a CTA owns a column of the volume -- 16 input channels, one batch item,
+//     W16_TH rows x 32 columns -- and walks a range of planes z.  For plane z
+//     it needs the input planes z - 1, z, z + 1 over (W16_TH + 2) x 34 voxels
+//     (halo included, zero outside the volume) and the dy tile of plane z; the
+//     input planes live in a ring of four slots and the dy tiles in two, so
+//     each step loads one new input plane and one dy tile (16-byte cp.async)
+//     while the previous step computes.  A staged voxel takes 48 bytes (32
+//     of data), so the eight rows of an ldmatrix are spread over all banks;
+//   * warp (kz, chunk) walks the W16_TH + 2 rows of input plane z + kz - 1 for its
+//     16-column chunk: per row it loads the three kx-shifted x operands once
+//     (ldmatrix.trans at shifted row addresses -- the shift costs nothing)
+//     and the dy row of the same index, keeps the last three dy rows, and
+//     issues the 18 MMAs that pair x row y with dy rows y, y - 1, y - 2 (taps
+//     ky = 0, 1, 2): each staged operand feeds up to 18 MMAs;
+//   * the register sums go to dW (FP32 atomics) every 32 planes and at the
+//     end, so no sum chains more than 512 MMA steps (the tensor core's FP32
+//     accumulation drifts over long chains).
+// Fragment layouts of mma.m16n8k16 (g = lane / 4, t = lane % 4): A (16 x 16,
+// row = co, col = voxel k) a0 (g, 2t..2t+1), a1 (g + 8, 2t..), a2 (g, 2t+8..),
+// a3 (g + 8, 2t+8..); B (16 x 8, row = voxel k, col = ci) b0 (2t..2t+1, g),
+// b1 (2t+8..2t+9, g); D d0, d1 (g, 2t..2t+1), d2, d3 (g + 8, 2t..2t+1).  With
+// voxels as the rows of the staged 8 x 8 matrices, ldmatrix.trans hands each
+// lane exactly these pairs.
+// tile rows: 8 keeps the staging ring at 90 KB, two CTAs per SM (measured
+// faster than 16 rows at one CTA per SM: 0.248 vs 0.300 ms on 2 x 128^3, 16 -> 16)
+#ifndef CTREX_W16_ROWS
+#define CTREX_W16_ROWS 8
+#endif
+constexpr int W16_TW = 32, W16_TH = CTREX_W16_ROWS;   // tile: columns (two 16-voxel chunks) x rows
+constexpr int W16_XR = W16_TH + 2, W16_XC = W16_TW + 2;  // staged input rows / columns (halo)
+constexpr int W16_VS = 48;                             // bytes per staged voxel
+constexpr int W16_XPLANE = W16_XR * W16_XC * W16_VS;   // 16 320 bytes for 8 rows
+constexpr int W16_DYB = W16_TH * W16_TW * W16_VS;      // 12 288
+constexpr int W16_SMEM = 4 * W16_XPLANE + 2 * W16_DYB;  // 89 856
+constexpr int W16_CTAS = W16_SMEM <= 110 * 1024 ? 2 : 1;  // resident CTAs per SM the budget allows
+constexpr int W16_THREADS = 192;                        // 6 warps: plane kz (3) x column chunk (2)
+constexpr int W16_FLUSH = 32;                           // planes between flushes of the register sums
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t r[4])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Issues (no wait) the copies of input plane zz into a ring slot, or of the
+// dy tile of plane zz: 16-byte cp.async per half voxel, zeros outside.
+__device__ __forceinline__ void w16_stage_plane(const __nv_bfloat16 *__restrict__ x, const ConvShape &S, int nb,
+                                                int zz, int y0, int x0, int ci0, uint8_t *slot)
+{
+    for (int i = threadIdx.x; i < W16_XR * W16_XC * 2; i += W16_THREADS) {
+        const int h = i & 1, v = (i >> 1) % W16_XC, row = (i >> 1) / W16_XC;
+        const int yy = y0 - 1 + row, xx = x0 - 1 + v;
+        const __nv_bfloat16 *src = x;
+        int bytes = 0;
+        if ((unsigned)zz < (unsigned)S.d && (unsigned)yy < (unsigned)S.h && (unsigned)xx < (unsigned)S.w) {
+            src = x + ((((long long)nb * S.d + zz) * S.h + yy) * S.w + xx) * S.cin + ci0 + 8 * h;
+            bytes = 16;
+        }
+        cp_async16(slot + (row * W16_XC + v) * W16_VS + 16 * h, src, bytes);
+    }
+}
+
+__device__ __forceinline__ void w16_stage_dy(const __nv_bfloat16 *__restrict__ dy, const ConvShape &S, int nb,
+                                             int z, int y0, int x0, uint8_t *slot)
+{
+    for (int i = threadIdx.x; i < W16_TH * W16_TW * 2; i += W16_THREADS) {
+        const int h = i & 1, v = (i >> 1) % W16_TW, row = (i >> 1) / W16_TW;
+        const int yy = y0 + row, xx = x0 + v;
+        const __nv_bfloat16 *src = dy;
+        int bytes = 0;
+        if (z < S.d && yy < S.h && xx < S.w) {
+            src = dy + ((((long long)nb * S.d + z) * S.h + yy) * S.w + xx) * 16 + 8 * h;
+            bytes = 16;
+        }
+        cp_async16(slot + (row * W16_TW + v) * W16_VS + 16 * h, src, bytes);
+    }
+}
+
+__global__ void __launch_bounds__(W16_THREADS, W16_CTAS)
+    conv_wgrad_c16_kernel(const __nv_bfloat16 *__restrict__ x, const __nv_bfloat16 *__restrict__ dy,
+                          float *__restrict__ dw, ConvShape S, int segs)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+    uint8_t *planes = smem, *dys = smem + 4 * W16_XPLANE;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int kz = warp % 3, chunk = warp / 3;
+    const int g = lane >> 2, t = lane & 3;
+    // CTA -> (column, plane segment); column -> (ci chunk, n, y band, x chunk)
+    const int tiles_x = (S.w + W16_TW - 1) / W16_TW, tiles_y = (S.h + W16_TH - 1) / W16_TH;
+    long long col = blockIdx.x / segs;
+    const int seg = (int)(blockIdx.x % segs);
+    const int x0 = (int)(col % tiles_x) * W16_TW;
+    col /= tiles_x;
+    const int y0 = (int)(col % tiles_y) * W16_TH;
+    col /= tiles_y;
+    const int nb = (int)(col % S.nb), ci0 = (int)(col / S.nb) * 16;
+    const int zb = (int)((long long)S.d * seg / segs), ze = (int)((long long)S.d * (seg + 1) / segs);
+    // this lane's ldmatrix row: matrix mi = lane / 8, row r = lane % 8
+    const int mi = lane >> 3, r8 = lane & 7;
+    // dy (A): matrices (voxels 0-7, co 0-7), (0-7, 8-15), (8-15, 0-7), (8-15, 8-15)
+    const uint32_t a_off = (uint32_t)((16 * chunk + 8 * (mi >> 1) + r8) * W16_VS + 16 * (mi & 1));
+    // x (B): matrices (voxels 0-7, ci 0-7), (8-15, 0-7), (0-7, 8-15), (8-15, 8-15)
+    const uint32_t b_off = (uint32_t)((16 * chunk + 8 * (mi & 1) + r8) * W16_VS + 16 * (mi >> 1));
+    float acc[9][2][4];
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[q][h][e] = 0.0f;
+    auto flush = [&]() {
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int co = g + 8 * (e >> 1), ci = ci0 + 8 * h + 2 * t + (e & 1);
+                    const float v = acc[q][h][e];
+                    acc[q][h][e] = 0.0f;
+                    if (v != 0.0f) atomicAdd(dw + ((long long)co * 27 + kz * 9 + q) * S.cin + ci, v);
+                }
+    };
+    if (zb >= ze) return;  // uniform over the CTA
+    // prologue: input planes zb - 1, zb, zb + 1 in slots 0, 1, 2; dy of zb in slot 0
+    for (int q = 0; q < 3; ++q) w16_stage_plane(x, S, nb, zb - 1 + q, y0, x0, ci0, planes + q * W16_XPLANE);
+    w16_stage_dy(dy, S, nb, zb, y0, x0, dys);
+    cp_async_commit();
+    for (int z = zb; z < ze; ++z) {
+        const int j = z - zb;
+        // prefetch: input plane z + 2 into the free slot, dy of z + 1
+        if (z + 1 < ze) {
+            w16_stage_plane(x, S, nb, z + 2, y0, x0, ci0, planes + ((j + 3) & 3) * W16_XPLANE);
+            w16_stage_dy(dy, S, nb, z + 1, y0, x0, dys + ((j + 1) & 1) * W16_DYB);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();  // everything but the prefetch just issued has landed
+        __syncthreads();
+        const uint32_t xs = smem_addr(planes + ((j + kz) & 3) * W16_XPLANE);  // input plane z + kz - 1
+        const uint32_t ds = smem_addr(dys + (j & 1) * W16_DYB);
+        uint32_t a0[4] = {0u, 0u, 0u, 0u}, a1[4] = {0u, 0u, 0u, 0u}, a2[4] = {0u, 0u, 0u, 0u};  // dy rows yp, yp-1, yp-2
+#pragma unroll 1
+        for (int yp = 0; yp < W16_XR; ++yp) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                a2[e] = a1[e];
+                a1[e] = a0[e];
+            }
+            if (yp < W16_TH) ldsm_x4_trans(ds + (uint32_t)(yp * W16_TW * W16_VS) + a_off, a0);
+            uint32_t b[3][4];
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx)
+                ldsm_x4_trans(xs + (uint32_t)((yp * W16_XC + kx) * W16_VS) + b_off, b[kx]);
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+                if (yp < W16_TH) {  // ky = 0: output row yp
+                    mma_bf16_16816(acc[kx][0], a0, b[kx][0], b[kx][1]);
+                    mma_bf16_16816(acc[kx][1], a0, b[kx][2], b[kx][3]);
+                }
+                if (yp >= 1 && yp <= W16_TH) {  // ky = 1: output row yp - 1
+                    mma_bf16_16816(acc[3 + kx][0], a1, b[kx][0], b[kx][1]);
+                    mma_bf16_16816(acc[3 + kx][1], a1, b[kx][2], b[kx][3]);
+                }
+                if (yp >= 2) {  // ky = 2: output row yp - 2
+                    mma_bf16_16816(acc[6 + kx][0], a2, b[kx][0], b[kx][1]);
+                    mma_bf16_16816(acc[6 + kx][1], a2, b[kx][2], b[kx][3]);
+                }
+            }
+        }
+        if ((j + 1) % W16_FLUSH == 0) flush();
+        __syncthreads();  // the slots read here are refilled by the next step's prefetch
+    }
+    cp_async_wait<0>();
+    flush();
+}
+
+int sm_count();
+
+cudaError_t launch_wgrad_c16(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, float *dw, const ConvShape &S,
+                             cudaStream_t stream)
+{
+    const long long cols = (long long)(S.cin / 16) * S.nb * ((S.h + W16_TH - 1) / W16_TH) *
+                           ((S.w + W16_TW - 1) / W16_TW);
+    // split the planes so that the grid covers about three waves of resident
+    // CTAs, with at least 8 planes per segment
+    long long segs = (3LL * W16_CTAS * sm_count() + cols - 1) / cols;
+    const long long max_segs = S.d / 8 > 1 ? S.d / 8 : 1;
+    if (segs > max_segs) segs = max_segs;
+    if (segs < 1) segs = 1;
+    const long long grid = cols * segs;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(conv_wgrad_c16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   W16_SMEM + 128);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    conv_wgrad_c16_kernel<<<(unsigned)grid, W16_THREADS, W16_SMEM + 128, stream>>>(x, dy, dw, S, (int)segs);
+    return cudaGetLastError();
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library); null if the driver does not provide it.
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -1523,6 +1744,12 @@ int ctrex_conv3d_wgrad(const void *x, const void *dy, float *dw, int nb, int d, 
     per = ((per + BK - 1) / BK) * BK;
     if (per < BK) per = BK;
     S.k_per_cta = per;
+    if (cout == 16 && (cin & 15) == 0) {  // register-blocked MMAs: no padded M
+        const cudaError_t e = launch_wgrad_c16(static_cast<const __nv_bfloat16 *>(x),
+                                               static_cast<const __nv_bfloat16 *>(dy), dw, S,
+                                               static_cast<cudaStream_t>(stream));
+        return e == cudaSuccess ? CTREX_OK : CTREX_E_CUDA;
+    }
     if (CTREX_CONV_TMA && (cin & 15) == 0) {
         // 32-channel chunks where two ring stages still fit beside the dy
         // rows; M = 64 MMAs (half the dy operand reads) for up to 64 outputs

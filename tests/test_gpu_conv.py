@@ -53,10 +53,13 @@ def test_conv_fwd_matches_oracle(ct, shape, cin, cout):
 # weight gradient: input channels 16, 48 (16-channel chunks), 32 (32-channel
 # chunks), 8 and 24 (the split-K kernel); 136 output channels span two 128-row
 # tiles, the second mostly empty; ragged spatial sizes against the 16 x 16
-# position tiles
+# position tiles; 16 output channels (the register-blocked kernel) with
+# ragged 16 x 32 tiles, and with three input-channel chunks whose tiles a
+# CTA's range crosses
 @pytest.mark.parametrize("shape,cin,cout", [((1, 6, 7, 9), 16, 16), ((2, 5, 6, 7), 48, 32), ((1, 8, 8, 8), 32, 64),
                                             ((1, 3, 17, 18), 32, 136), ((2, 4, 5, 6), 8, 16),
-                                            ((1, 3, 19, 33), 24, 24)])
+                                            ((1, 3, 19, 33), 24, 24), ((2, 7, 35, 40), 16, 16),
+                                            ((2, 16, 40, 70), 48, 16)])
 def test_conv_grads_match_oracle(ct, shape, cin, cout):
     from oracle import conv
 
