@@ -54,11 +54,13 @@ def test_expired_epilogue_wait_recovers(variant):
     dev = torch.device("cuda", torch.cuda.current_device())
     rng = np.random.default_rng(21)
     # 2 x 64^3 x 16 channels: 2048 output tiles, several per CTA, so the MMA
-    # warp also reaches its accumulator-release waits
-    nb, d, h, w, cin, cout = 2, 64, 64, 64, 16, 16
+    # warp also reaches its accumulator-release waits.  The weight gradient
+    # takes 32 output channels: layers with 16 use the register-blocked kernel,
+    # which has no mbarrier waits.
+    nb, d, h, w, cin, cout, cg = 2, 64, 64, 64, 16, 16, 32
     x = torch.as_tensor(rng.normal(size=(nb, d, h, w, cin)), dtype=torch.float32).to(torch.bfloat16).to(dev)
     wt = torch.as_tensor(rng.normal(size=(cout, 27, cin)) / 20.0, dtype=torch.float32).to(torch.bfloat16).to(dev)
-    dy = torch.as_tensor(rng.normal(size=(nb, d, h, w, cout)), dtype=torch.float32).to(torch.bfloat16).to(dev)
+    dy = torch.as_tensor(rng.normal(size=(nb, d, h, w, cg)), dtype=torch.float32).to(torch.bfloat16).to(dev)
     stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
     # forward with the one-poll epilogue
     st = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -69,8 +71,8 @@ def test_expired_epilogue_wait_recovers(variant):
     fwd_status = int(st.item())
     # weight gradient with the one-poll epilogue
     st.zero_()
-    dw = torch.zeros((cout, 27, cin), dtype=torch.float32, device=dev)
-    rc = lib.ctrex_conv3d_wgrad(_p(x), _p(dy), _p(dw), nb, d, h, w, cin, cout, _p(st), stream)
+    dw = torch.zeros((cg, 27, cin), dtype=torch.float32, device=dev)
+    rc = lib.ctrex_conv3d_wgrad(_p(x), _p(dy), _p(dw), nb, d, h, w, cin, cg, _p(st), stream)
     torch.cuda.synchronize()
     assert rc == 0
     wg_status = int(st.item())
@@ -80,7 +82,8 @@ def test_expired_epilogue_wait_recovers(variant):
     xs, ws_, dys = x[:1, :24, :20, :18], wt, dy[:1, :24, :20, :18]
     xs, dys = xs.contiguous(), dys.contiguous()
     y_ref = conv.conv3d(xs.double().cpu().numpy(), ws_.double().cpu().numpy())
-    _, dw_ref = conv.conv3d_grads(xs.double().cpu().numpy(), ws_.double().cpu().numpy(), dys.double().cpu().numpy())
+    w32 = rng.normal(size=(cg, 27, cin))  # dW does not depend on the weights
+    _, dw_ref = conv.conv3d_grads(xs.double().cpu().numpy(), w32, dys.double().cpu().numpy())
     y2 = ct.conv3d(xs, ws_, out_dtype=torch.float32)
     dw2 = ct.conv3d_wgrad(xs, dys)
     ct.conv_status_check(dev)
