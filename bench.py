@@ -138,11 +138,11 @@ class ClockSampler:
 # the two captures, evaluated at 720 views.  Valid only for the kernel
 # sources it was taken on (hash below) and for the FP32 workload; otherwise
 # null.
-_T16, _T180 = 585101312 + 33152512, 983686144 + 396029696
+_T16, _T180 = 585478400 + 33003264, 980367872 + 395119616
 FWD_TRAFFIC_BYTES = int(_T16 + (_T180 - _T16) * (720 - 16) / (180 - 16))
 FWD_TRAFFIC_SOURCES = ("project.cu", "atlas.cuh", "ray.cuh", "cylinder.cuh", "joseph.cuh", "roi.cuh", "fwd_common.cuh",
                        "ctrex_internal.cuh", "dyrect.cuh")
-FWD_TRAFFIC_HASH = "615f77780c263ae1"
+FWD_TRAFFIC_HASH = "65167ed01d5f8c82"
 
 
 def fwd_traffic(dtype, views):

@@ -8,15 +8,17 @@
 #include "ray.cuh"
 
 // Motion gradient CTA: CTREX_MGRAD_WARPS warps, each on an 8 x 4 pixel
-// patch (the CTA covers 8 * warps detector columns x 4 rows); registers
-// capped at 128 (CTREX_MGRAD_MIN_BLOCKS resident CTAs of that size per SM).
-// Fewer warps per CTA shorten the wait of warps with short rays for the
-// CTA's final reduction.
+// patch (the CTA covers 8 * warps detector columns x 4 rows), with
+// CTREX_MGRAD_MIN_BLOCKS resident CTAs per SM (two warps and six CTAs cap
+// the registers at 168, enough for the unrolled y loop of the spline without
+// spills; 5 or 4 CTAs with more registers, or 4-warp CTAs, were no faster).
+// Few warps per CTA shorten the wait of warps with short rays for the CTA's
+// final reduction.
 #ifndef CTREX_MGRAD_WARPS
 #define CTREX_MGRAD_WARPS 2
 #endif
 #ifndef CTREX_MGRAD_MIN_BLOCKS
-#define CTREX_MGRAD_MIN_BLOCKS (16 / CTREX_MGRAD_WARPS)
+#define CTREX_MGRAD_MIN_BLOCKS (12 / CTREX_MGRAD_WARPS)
 #endif
 
 namespace ctrex {
@@ -258,17 +260,17 @@ __device__ __forceinline__ void spline_value_jacobian(const float4 *coef, const 
     for (int c = 0; c < 3; ++c) u[c] = Jx[c] = Jy[c] = Jz[c] = 0.0f;
     const float4 *plane = coef_cell(coef, i0);
     // the z loop stays rolled (bounds the live coefficient loads); its two
-    // weights are picked by selects, which keeps the arrays in registers
+    // weights are picked by selects, which keeps the arrays in registers.
+    // The y loop is unrolled: 16 independent float4 loads per plane.
 #pragma unroll 1
     for (int k = 0; k < 4; ++k, plane += CPAD * CPAD) {
         const float wzk = k == 0 ? wz[0] : (k == 1 ? wz[1] : (k == 2 ? wz[2] : wz[3]));
         const float dzk = k == 0 ? dz[0] : (k == 1 ? dz[1] : (k == 2 ? dz[2] : dz[3]));
         float a[3] = {0.f, 0.f, 0.f}, bx[3] = {0.f, 0.f, 0.f}, by[3] = {0.f, 0.f, 0.f};
         const float4 *row = plane;
-#pragma unroll 1
+#pragma unroll
         for (int j = 0; j < 4; ++j, row += CPAD) {
-            const float wyj = j == 0 ? wy[0] : (j == 1 ? wy[1] : (j == 2 ? wy[2] : wy[3]));
-            const float dyj = j == 0 ? dy[0] : (j == 1 ? dy[1] : (j == 2 ? dy[2] : dy[3]));
+            const float wyj = wy[j], dyj = dy[j];
             float sx[3] = {0.f, 0.f, 0.f}, tx[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
