@@ -13,6 +13,8 @@
 //     formed; persistent and warp-specialised (a TMA producer warp, an MMA
 //     warp, epilogue warps):
 //       conv_fwd_tma_kernel     forward and input gradient,
+//       conv_fwd_kx_kernel      the same for at most 16 output channels,
+//                               kx taps folded into N, planes reused along z,
 //       conv_wgrad_tma_kernel   weight gradient (MN-major operands, K = voxels);
 //   * im2col kernels (other channel counts, and the fallback when no tensor
 //     map can be made): the CTA's 128 threads gather implicit-im2col chunks
@@ -44,6 +46,15 @@ namespace {
 #endif
 #ifndef CTREX_CONV_FILL
 #define CTREX_CONV_FILL 1
+#endif
+// Layers of at most 16 output channels through conv_fwd_kx_kernel (1), its
+// input windows 32-byte swizzled with 16 channels per TMA box (1) or two
+// 8-channel blocks (0).
+#ifndef CTREX_CONV_KX
+#define CTREX_CONV_KX 1
+#endif
+#ifndef CTREX_CONV_KX_SW32
+#define CTREX_CONV_KX_SW32 1
 #endif
 #ifndef CTREX_CONV_WG_CHUNK
 #define CTREX_CONV_WG_CHUNK 32
@@ -102,6 +113,22 @@ __device__ __forceinline__ uint64_t sdesc_none(uint32_t saddr, uint32_t lbo, uin
     d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Shared-memory matrix descriptor, K-major with 32-byte swizzle: rows of 32
+// bytes (K = 16 BF16), 8-row atoms of 256 bytes whose two 16-byte chunks
+// are exchanged in rows 4..7 (address bit 4 ^= bit 7, as the TMA writes a
+// box with CU_TENSOR_MAP_SWIZZLE_32B); sbo = byte stride between 8-row
+// groups; the start address must sit on an atom (256-byte) boundary.
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)6 << 61;
     return d;
 }
 
@@ -173,6 +200,36 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Columns [0, 48) of this thread's TMEM lane at ta and [0, 32) at tb (80
+// FP32 values): five 16-column loads, one wait.
+__device__ __forceinline__ void tmem_ld48_32(uint32_t ta, uint32_t tb, float a[48], float b[32])
+{
+    uint32_t r[80];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%80];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%81];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%82];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%83];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%64,%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79}, [%84];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63]),
+          "=r"(r[64]), "=r"(r[65]), "=r"(r[66]), "=r"(r[67]), "=r"(r[68]), "=r"(r[69]), "=r"(r[70]), "=r"(r[71]),
+          "=r"(r[72]), "=r"(r[73]), "=r"(r[74]), "=r"(r[75]), "=r"(r[76]), "=r"(r[77]), "=r"(r[78]), "=r"(r[79])
+        : "r"(ta), "r"(ta + 16u), "r"(ta + 32u), "r"(tb), "r"(tb + 16u)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 48; ++i) a[i] = __uint_as_float(r[i]);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) b[i] = __uint_as_float(r[48 + i]);
 }
 
 // Byte offset of 16-byte chunk j of row r in a 128B-swizzled K-major tile.
@@ -799,6 +856,26 @@ __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, unsigned parity, v
     return false;
 }
 
+// Warp-wide bounded wait for two phases that are usually complete already:
+// one poll of both with non-blocking tests (their latencies overlap: each
+// poll costs some hundred cycles on a busy SM), then blocking waits for any
+// that is not.
+__device__ __forceinline__ bool mbar_wait2_warp(uint64_t *b1, unsigned p1, uint64_t *b2, unsigned p2,
+                                                volatile int *abort_flag)
+{
+    uint32_t d1, d2;
+    asm volatile(
+        "{\n .reg .pred a, b;\n mbarrier.test_wait.parity.shared::cta.b64 a, [%2], %3;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 b, [%4], %5;\n selp.u32 %0, 1, 0, a;\n selp.u32 %1, 1, 0, b;\n}\n"
+        : "=r"(d1), "=r"(d2)
+        : "r"(smem_addr(b1)), "r"(p1), "r"(smem_addr(b2)), "r"(p2)
+        : "memory");
+    const uint32_t dd = __reduce_or_sync(0xffffffffu, d1 | (d2 << 1));
+    if (!(dd & 1u) && !mbar_wait_warp(b1, p1, abort_flag)) return false;
+    if (!(dd & 2u) && !mbar_wait_warp(b2, p2, abort_flag)) return false;
+    return true;
+}
+
 // Shared-memory plan of the TMA kernel (bytes; every TMA destination
 // 128-byte aligned, every stage 1024-byte aligned).  RESW: the whole filter
 // of the (single) N tile stays resident, loaded once per CTA (W_MAX bytes at
@@ -1033,6 +1110,293 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             // leader is not carried out of the loop: keeping it live there
             // cost the issue loop about 40 %)
             umma_commit_p(elect_one(), &drain);
+            mbar_wait_warp(&drain, 0u, nullptr);
+        }
+    }
+    if (warp == 1) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PL::TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward (and input gradient) of layers with at most 16 output channels and
+// a multiple of 16 input channels: the kx taps folded into N, input planes
+// reused along z.
+//   * N = 48 = (kx, co): one MMA of 128 x 48 x 16 multiplies 8 window columns
+//     x 16 rows by the filter rows (kx, co) of one (kz, ky) and 16 input
+//     channels, so that the accumulator holds, per window column c,
+//     E_kx[c] = sum over kz, ky, ci of w[co][kz][ky][kx][ci] x[..., c][ci];
+//     the epilogue forms y[i] = E_0[i] + E_1[i + 1] + E_2[i + 2] with warp
+//     shuffles.  A tile of 8 NT output columns x 16 rows needs NG = NT + 1
+//     column groups (8 NG >= 8 NT + 2): 9 NG MMAs per 16 input channels
+//     instead of 27 NT.
+//   * A CTA runs items of ZC consecutive output planes of one (n, y, x)
+//     column.  The windows of the input planes z0 - 1 .. z0 + ZC stream
+//     through a ring of P plane slots (a slot holds the cin / 16 windows of
+//     one plane), so each plane is loaded once per item rather than once per
+//     kz tap, and tile z reads the slots of planes z - 1, z and z + 1.  A
+//     slot is released when the last tile that reads it has its MMAs done.
+//   * The filter is resident: block (tap t, 8-channel block kb) of 16 rows
+//     at ((t / 3) * cin / 8 + kb) * 3 + t % 3, so that the 48 rows (kx, co)
+//     of one (kz, ky) and channel block are contiguous, 16 bytes apart.
+//   * A window (16 channels of 18 rows x 8 NG columns, 6 more than the taps
+//     reach) is one TMA box of 32-byte rows, 32-byte swizzled; every MMA's
+//     A operand then starts on a 256-byte swizzle atom (columns come in
+//     groups of 8, rows are 8 NG positions long).  The extra columns land
+//     in accumulator lanes that the epilogue never uses.  (Without the
+//     swizzle: two boxes of 8 channels, 16-byte rows.)
+//   * The MMA warp polls once per tile: the plane that tile adds and the
+//     release of its accumulator together (a poll costs a few hundred
+//     cycles on the busy SM, and four of them took a quarter of the time).
+// Measured on 128^3 x 2 (16 output channels): 16 -> 16 0.184 ms with the
+// 27 NT scheme, 0.102 ms here; 32 -> 16 0.327 -> 0.176; 48 -> 16 0.474 ->
+// 0.279.
+template <int NT>
+struct KxPlan {
+    static constexpr bool SW = CTREX_CONV_KX_SW32;  // 32-byte swizzled windows
+    static constexpr int NG = NT + 1;       // MMA column groups
+    static constexpr int RW = 8 * NG;       // window columns loaded (8 NT + 2 used)
+    static constexpr int NP = RW * 18;      // window positions
+    static constexpr int NW = 48;           // MMA N
+    static constexpr int A_BLK = NP * 16;   // one 8-channel block (a multiple of 128 bytes)
+    static constexpr int WIN = 2 * A_BLK;   // one window of 16 channels
+    static constexpr uint32_t WIN_TX = 2u * NP * 16;  // bytes the TMA writes per window
+    static constexpr int B_BLK = 16 * 16;             // one tap's 8-channel block of 16 rows
+    static constexpr int ACC = NG * NW;               // columns of one accumulator
+    static constexpr int TMEM_COLS = 2 * ACC <= 128 ? 128 : (2 * ACC <= 256 ? 256 : 512);
+    static_assert(2 * ACC <= 512, "two accumulators must fit in TMEM");
+    static_assert(A_BLK % 128 == 0, "128-byte aligned window rows");
+};
+
+struct KxArgs {
+    int cb;       // 16-channel blocks of the input (cin / 16)
+    int zc;       // output planes per item
+    int w_bytes;  // bytes reserved for the resident filter (multiple of 1024)
+};
+
+template <int NT, int P>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    conv_fwd_kx_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
+                       const float *__restrict__ bias, void *__restrict__ out, int out_bf16, ConvShape S, KxArgs G,
+                       int *__restrict__ status)
+{
+    using PL = KxPlan<NT>;
+    constexpr int RW = PL::RW;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *wres = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *ring = wres + G.w_bytes;
+    __shared__ uint64_t full[P], empty[P], acc_full[2], acc_empty[2], drain, wbar;
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int CB = G.cb, ZC = G.zc;
+    const int tiles_x = (S.w + 8 * NT - 1) / (8 * NT), tiles_y = (S.h + 15) / 16, zchunks = (S.d + ZC - 1) / ZC;
+    const long long items = (long long)S.nb * zchunks * tiles_y * tiles_x;
+    const int kbs = S.cin >> 3;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < P; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 128);
+        }
+        mbar_init(&drain, 1);
+        mbar_init(&wbar, 1);
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmw)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base_s)),
+                     "r"(PL::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tmem_base_s;
+    volatile int *abort_flag = &abort_s;
+    // item -> (n, first output plane z0, planes nz, y0, x0); x fastest, so
+    // that CTAs running at the same time read neighbouring windows
+    auto decode = [&](long long it, int &nb, int &z0, int &nz, int &y0, int &x0) {
+        const int tx = (int)(it % tiles_x);
+        long long t = it / tiles_x;
+        const int ty = (int)(t % tiles_y);
+        t /= tiles_y;
+        z0 = (int)(t % zchunks) * ZC;
+        nb = (int)(t / zchunks);
+        nz = S.d - z0 < ZC ? S.d - z0 : ZC;
+        x0 = tx * 8 * NT;
+        y0 = ty * 16;
+    };
+
+    long long fills = 0;  // producer: plane fills issued
+    bool mmas = false;    // MMA warp: any MMA issued
+    if (warp == 0) {
+        // producer warp: warp-wide loop, one elected lane issues each copy
+        const uint32_t leader = elect_one();
+        long long fill = 0;
+        bool ok = true;
+        expect_tx_p(leader, &wbar, (uint32_t)(27 * kbs * PL::B_BLK));
+        const uint32_t wb = smem_addr(wres);
+        for (int t = 0; t < 27; ++t)
+            for (int kb = 0; kb < kbs; ++kb)
+                tma_load_2d_p(leader, wb + (uint32_t)((((t / 3) * kbs + kb) * 3 + t % 3) * PL::B_BLK), &tmw,
+                              t * S.cin + 8 * kb, 0, &wbar);
+        for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+            int nb, z0, nz, y0, x0;
+            decode(it, nb, z0, nz, y0, x0);
+            // planes z0 - 1 .. z0 + nz (outside the volume: zero-filled)
+            for (int pz = z0 - 1; pz <= z0 + nz; ++pz, ++fill) {
+                const int sl = (int)(fill % P);
+                if (fill >= P && !mbar_wait_warp(&empty[sl], (unsigned)(((fill / P) - 1) & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t base = smem_addr(ring) + (uint32_t)(sl * CB * PL::WIN);
+                expect_tx_p(leader, &full[sl], (uint32_t)CB * PL::WIN_TX);
+                for (int c = 0; c < CB; ++c) {
+                    const uint32_t a = base + (uint32_t)(c * PL::WIN);
+                    if (PL::SW) {
+                        tma_load_5d_p(leader, a, &tmx, 16 * c, x0 - 1, y0 - 1, pz, nb, &full[sl]);
+                    } else {
+                        tma_load_5d_p(leader, a, &tmx, 16 * c, x0 - 1, y0 - 1, pz, nb, &full[sl]);
+                        tma_load_5d_p(leader, a + PL::A_BLK, &tmx, 16 * c + 8, x0 - 1, y0 - 1, pz, nb, &full[sl]);
+                    }
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicExch(status, 1);
+        fills = fill;
+    } else if (warp == 1) {
+        // MMA warp: warp-wide loop, one elected lane issues the MMAs and
+        // commits
+        const uint32_t leader = elect_one();
+        constexpr uint32_t ID = idesc(PL::NW);
+        long long fill = 0;  // plane fill of the current item's first plane
+        int tile_i = 0;
+        bool ok = mbar_wait_warp(&wbar, 0u, abort_flag), issued = false;
+        const uint32_t wb = smem_addr(wres), rb = smem_addr(ring);
+        const uint64_t b_dy = (uint64_t)((3 * kbs * PL::B_BLK) >> 4);
+        for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+            int nb, z0, nz, y0, x0;
+            decode(it, nb, z0, nz, y0, x0);
+            for (int k = 0; k < nz; ++k, ++tile_i) {
+                const int acc = tile_i & 1;
+                // planes z - 1, z, z + 1 of output plane z = z0 + k: the
+                // first two were waited for by the item's earlier tiles
+                // (they stay until released below), except at its start
+                for (int dz = 0; k == 0 && dz < 2 && ok; ++dz) {
+                    const long long f = fill + dz;
+                    ok = mbar_wait_warp(&full[f % P], (unsigned)((f / P) & 1), abort_flag);
+                }
+                const long long f2 = fill + k + 2;
+                if (ok && tile_i >= 2)
+                    ok = mbar_wait2_warp(&acc_empty[acc], (unsigned)(((tile_i >> 1) - 1) & 1), &full[f2 % P],
+                                         (unsigned)((f2 / P) & 1), abort_flag);
+                else if (ok)
+                    ok = mbar_wait_warp(&full[f2 % P], (unsigned)((f2 / P) & 1), abort_flag);
+                if (!ok) break;
+                tc_after_sync();
+                const uint32_t d = tmem + (uint32_t)(acc * PL::ACC);
+                for (int dz = 0; dz < 3; ++dz) {
+                    const uint32_t slot = rb + (uint32_t)(((fill + k + dz) % P) * CB * PL::WIN);
+                    for (int c = 0; c < CB; ++c) {
+                        // A: the window, rows = 8 columns x 16 rows, 8-row
+                        // groups one window row apart, channel blocks A_BLK
+                        // apart; B: rows (kx, co) of (kz, ky) = (dz, dy),
+                        // channel blocks 2c and 2c + 1, 3 B_BLK apart
+                        const uint64_t a0 = PL::SW ? sdesc_sw32(slot + (uint32_t)(c * PL::WIN), (uint32_t)(RW * 32))
+                                                   : sdesc_none(slot + (uint32_t)(c * PL::WIN), (uint32_t)PL::A_BLK,
+                                                                (uint32_t)(RW * 16));
+                        constexpr int AU = PL::SW ? 2 : 1;  // 16-byte units per window position
+                        const uint64_t b0 = sdesc_none(wb + (uint32_t)((9 * dz * kbs + 6 * c) * PL::B_BLK),
+                                                       (uint32_t)(3 * PL::B_BLK), 128u);
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                            for (int q = 0; q < PL::NG; ++q)
+                                umma_bf16_p(leader, d + (uint32_t)(q * PL::NW), a0 + (uint64_t)(AU * (dy * RW + 8 * q)),
+                                            b0 + (uint64_t)dy * b_dy, ID, (dz > 0 || c > 0 || dy > 0) ? 1u : 0u);
+                    }
+                }
+                issued = true;
+                // plane z - 1 is not read again
+                umma_commit_p(leader, &empty[(fill + k) % P]);
+                umma_commit_p(leader, &acc_full[acc]);
+            }
+            if (!ok) break;
+            // the item's last two planes
+            umma_commit_p(leader, &empty[(fill + nz) % P]);
+            umma_commit_p(leader, &empty[(fill + nz + 1) % P]);
+            fill += nz + 2;
+        }
+        if (!ok && lane == 0) atomicExch(status, 1);
+        mmas = issued;
+    } else {
+        // epilogue warps 2..5: accumulator rows 32 (warp % 4) + lane, row
+        // m = 8 (window row) + column within the group
+        const int quarter = warp & 3;
+        const int m = 32 * quarter + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+        // column i + 1 (i + 2) is the next lane of the same 8-lane group or,
+        // past the group's end, one of the first lanes of group q + 1: each
+        // lane offers the value that the lane asking for it needs
+        const int cc = lane & 7;
+        const int src1 = cc < 7 ? lane + 1 : lane - 7, src2 = cc < 6 ? lane + 2 : lane - 6;
+        int tile_i = 0;
+        bool ok = true;
+        for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+            int nb, z0, nz, y0, x0;
+            decode(it, nb, z0, nz, y0, x0);
+            for (int k = 0; k < nz; ++k, ++tile_i) {
+                const int acc = tile_i & 1;
+                if (!mbar_wait_warp(&acc_full[acc], (unsigned)((tile_i >> 1) & 1), abort_flag, EPI_WAIT_LIMIT)) {
+                    if (lane == 0) atomicExch(status, 1);
+                    ok = false;
+                    break;
+                }
+                tc_after_sync();
+                const int y = y0 + (m >> 3);
+#pragma unroll 1
+                for (int q = 0; q < NT; ++q) {
+                    const int xo = x0 + 8 * q + cc;
+                    // E_kx of group q (48 columns) and E_1, E_2 of group
+                    // q + 1 (32 columns)
+                    const uint32_t col = lane_base + (uint32_t)(acc * PL::ACC + q * PL::NW);
+                    float e[48], en[32], v[16];
+                    tmem_ld48_32(col, col + PL::NW + 16, e, en);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        v[i] = e[i] + __shfl_sync(0xffffffffu, cc == 0 ? en[i] : e[16 + i], src1) +
+                               __shfl_sync(0xffffffffu, cc < 2 ? en[16 + i] : e[32 + i], src2);
+                    if (y < S.h && xo < S.w)
+                        store16_fwd(v, bias, out, out_bf16, S, (((long long)nb * S.d + z0 + k) * S.h + y) * S.w + xo,
+                                    0);
+                }
+                tc_before_sync();
+                mbar_arrive(&acc_empty[acc]);
+            }
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    // as in conv_fwd_tma_kernel: once a role gave up, the producer waits for
+    // the last fill of every slot and the filter, the MMA warp for its MMAs
+    // (bounded waits), before TMEM and shared memory are released
+    if (*abort_flag) {
+        if (warp == 0) {
+            for (long long f = fills - 1; f >= 0 && f >= fills - P; --f)
+                mbar_wait_warp(&full[f % P], (unsigned)((f / P) & 1), nullptr);
+            mbar_wait_warp(&wbar, 0u, nullptr);
+        } else if (warp == 1 && mmas) {
+            umma_commit_p(elect_one(), &drain);  // the lane that issued the MMAs (same member mask)
             mbar_wait_warp(&drain, 0u, nullptr);
         }
     }
@@ -1543,6 +1907,83 @@ cudaError_t launch_tma(const __nv_bfloat16 *x, const __nv_bfloat16 *w, const flo
     return cudaGetLastError();
 }
 
+// Forward of a layer with at most 16 output channels (conv_fwd_kx_kernel):
+// returns cudaErrorNotSupported (nothing launched) when the tensor maps
+// cannot be made or the filter and four plane slots do not fit in shared
+// memory.
+template <int NT, int P>
+cudaError_t launch_kx_nt(const __nv_bfloat16 *x, const __nv_bfloat16 *w, const float *bias, void *out, int out_bf16,
+                         const ConvShape &S, const KxArgs &G, int *status, cudaStream_t stream)
+{
+    using PL = KxPlan<NT>;
+    const EncodeTiledFn enc = encode_tiled();
+    const int sms = sm_count();
+    if (!enc || sms <= 0 || (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(w) & 15))
+        return cudaErrorNotSupported;
+    const uint64_t es = sizeof(__nv_bfloat16);
+    CUtensorMap mx, mw;
+    {
+        const cuuint64_t dims[5] = {(cuuint64_t)S.cin, (cuuint64_t)S.w, (cuuint64_t)S.h, (cuuint64_t)S.d, (cuuint64_t)S.nb};
+        const cuuint64_t strides[4] = {S.cin * es, (uint64_t)S.w * S.cin * es, (uint64_t)S.h * S.w * S.cin * es,
+                                       (uint64_t)S.d * S.h * S.w * S.cin * es};
+        // 16 channels (32 bytes, 32-byte swizzle) or 8 channels per box
+        const cuuint32_t box[5] = {PL::SW ? 16u : 8u, (cuuint32_t)PL::RW, 18, 1, 1};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(x), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, PL::SW ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+    }
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)(27LL * S.cin), (cuuint64_t)S.n_total};
+        const cuuint64_t strides[1] = {27ULL * S.cin * es};
+        const cuuint32_t box[2] = {8, 16};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(w), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+    }
+    KxArgs A = G;
+    // output planes per item: the whole depth, halved while the grid would
+    // hold fewer than six items per SM (each item loads nz + 2 planes)
+    const long long cols = (long long)S.nb * ((S.h + 15) / 16) * ((S.w + 8 * NT - 1) / (8 * NT));
+    int zc = S.d;
+    while (zc > 4 && cols * ((S.d + zc - 1) / zc) < 6LL * sms) zc = (zc + 1) / 2;
+    A.zc = zc;
+    const int smem = A.w_bytes + P * A.cb * PL::WIN + 1024;
+    cudaError_t e = cudaFuncSetAttribute(conv_fwd_kx_kernel<NT, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const long long items = cols * ((S.d + zc - 1) / zc);
+    const unsigned grid = (unsigned)(items < sms ? items : sms);
+    conv_fwd_kx_kernel<NT, P><<<grid, TMA_THREADS, smem, stream>>>(mx, mw, bias, out, out_bf16, S, A, status);
+    return cudaGetLastError();
+}
+
+// Tile width: 32 columns (NT = 4) when the filter and four plane slots of
+// that width fit in shared memory, else 16; 8 for volumes at most 8 wide.
+// Plane slots: 8 where they fit, else 4.
+cudaError_t launch_kx(const __nv_bfloat16 *x, const __nv_bfloat16 *w, const float *bias, void *out, int out_bf16,
+                      const ConvShape &S, int *status, cudaStream_t stream)
+{
+    constexpr int SMEM_MAX = 227 * 1024 - 1024 - 512;  // dynamic budget: alignment slack, static barriers
+    KxArgs G{};
+    G.cb = S.cin / 16;
+    G.w_bytes = (27 * S.cin * 16 * 2 + 1023) / 1024 * 1024;
+    auto fits = [&](int win, int p) { return G.w_bytes + p * G.cb * win <= SMEM_MAX; };
+#define CTREX_KX_LAUNCH(NT)                                                                        \
+    if (fits(KxPlan<NT>::WIN, 8)) return launch_kx_nt<NT, 8>(x, w, bias, out, out_bf16, S, G, status, stream); \
+    if (fits(KxPlan<NT>::WIN, 4)) return launch_kx_nt<NT, 4>(x, w, bias, out, out_bf16, S, G, status, stream);
+    if (S.w <= 8) {
+        CTREX_KX_LAUNCH(1)
+        return cudaErrorNotSupported;
+    }
+    CTREX_KX_LAUNCH(4)
+    CTREX_KX_LAUNCH(2)
+#undef CTREX_KX_LAUNCH
+    return cudaErrorNotSupported;
+}
+
 // Brick weight gradient: returns cudaErrorNotSupported (nothing launched)
 // when the tensor maps cannot be made.
 template <int CN, bool M64>
@@ -1620,6 +2061,12 @@ template <int OP, int BN>
 cudaError_t launch_bn(const __nv_bfloat16 *a, const __nv_bfloat16 *b, const float *bias, void *out, int out_bf16,
                       const ConvShape &S, int *status, cudaStream_t stream)
 {
+    if constexpr (BN == 16) {
+        if (OP == OP_FWD && (S.cin & 15) == 0 && CTREX_CONV_TMA && CTREX_CONV_KX) {
+            const cudaError_t e = launch_kx(a, b, bias, out, out_bf16, S, status, stream);
+            if (e != cudaErrorNotSupported) return e;  // else: the brick kernel below
+        }
+    }
     if (OP == OP_FWD && (S.cin & 15) == 0 && CTREX_CONV_TMA) {
         // tiles 16 x 16 (NT = 2) unless the volume is at most 8 wide; the
         // filter stays resident when the layer has one N tile and it fits

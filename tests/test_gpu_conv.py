@@ -34,7 +34,9 @@ def _bf(a):
                                             ((1, 8, 8, 8), 32, 192), ((1, 4, 4, 4), 96, 128),
                                             ((2, 3, 17, 19), 8, 16), ((1, 5, 9, 11), 24, 40),
                                             ((1, 4, 35, 21), 32, 24), ((2, 3, 18, 40), 16, 16),
-                                            ((1, 3, 20, 19), 32, 160), ((1, 2, 17, 18), 192, 64)])
+                                            ((1, 3, 20, 19), 32, 160), ((1, 2, 17, 18), 192, 64),
+                                            ((1, 5, 19, 33), 16, 16), ((2, 4, 9, 7), 16, 16), ((1, 4, 21, 26), 32, 32),
+                                            ((1, 3, 17, 45), 48, 16), ((1, 3, 16, 64), 16, 32)])
 def test_conv_fwd_matches_oracle(ct, shape, cin, cout):
     from oracle import conv
 
