@@ -110,7 +110,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -121,13 +121,17 @@ class ClockSampler:
                 smax.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                power.append(float(parts[3]))
+            except ValueError:
+                pass
             for name, val in zip(names, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(name)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w": statistics.median(power) if power else None}
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
@@ -485,7 +489,9 @@ def measure_rows(device, gather_peak, sm_count, sm_mhz):
     best = max(v["fwd_tflops"] for v in convs.values())
     rows["a12_conv3d_tcgen05"] = {"layers": convs, "best_fwd_tflops": best, "bf16_peak_tflops": bf16_peak,
                                   "best_fwd_frac": best / bf16_peak,
-                                  "kernels": {"fwd": "conv_fwd_tma_kernel (persistent, TMA, brick-staged input)",
+                                  "kernels": {"fwd": "conv_fwd_tma_kernel (persistent, TMA, brick-staged input); "
+                                                     "at most 16 output channels: conv_fwd_kx_kernel (kx taps "
+                                                     "folded into N, input planes reused along z)",
                                               "wgrad": "conv_wgrad_tma_kernel (MN-major brick, kx taps folded into N); "
                                                        "16 output channels: conv_wgrad_c16_kernel (mma.m16n8k16 "
                                                        "with register-resident operands)"}}
@@ -568,14 +574,20 @@ def run_ours(args):
         ph = p.cpu().pin_memory()
         ctx.sirt_host(xh, ph, 1)  # warm-up (allocates the context's host-path buffers)
         torch.cuda.synchronize(device)
+        clocks_e2e = ClockSampler(local)
+        clocks_e2e.start()
+        step_s = []
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
+            t1 = time.perf_counter()
             ctx.sirt_host(xh, ph, 1)
+            step_s.append(time.perf_counter() - t1)
         e2e_s = time.perf_counter() - t0
         elt = 2 if tdt == torch.bfloat16 else 4
         e2e = {"value": units * args.e2e_steps * world / e2e_s / 1e9, "unit": "GUPS",
                "h2d_bytes_per_step": int(xh.numel() * elt + ph.numel() * elt),
-               "d2h_bytes_per_step": int(xh.numel() * elt + 16)}
+               "d2h_bytes_per_step": int(xh.numel() * elt + 16),
+               "step_ms": [round(t * 1e3, 1) for t in step_s], "clocks": clocks_e2e.stop()}
         del ph, xh
 
     elt = 2 if tdt == torch.bfloat16 else 4
