@@ -142,11 +142,11 @@ class ClockSampler:
 # the two captures, evaluated at 720 views.  Valid only for the kernel
 # sources it was taken on (hash below) and for the FP32 workload; otherwise
 # null.
-_T16, _T180 = 585478400 + 33003264, 980367872 + 395119616
+_T16, _T180 = 585724416 + 33573888, 983185408 + 395431680
 FWD_TRAFFIC_BYTES = int(_T16 + (_T180 - _T16) * (720 - 16) / (180 - 16))
 FWD_TRAFFIC_SOURCES = ("project.cu", "atlas.cuh", "ray.cuh", "cylinder.cuh", "joseph.cuh", "roi.cuh", "fwd_common.cuh",
                        "ctrex_internal.cuh", "dyrect.cuh")
-FWD_TRAFFIC_HASH = "65167ed01d5f8c82"
+FWD_TRAFFIC_HASH = "7dff830989774c97"
 
 
 def fwd_traffic(dtype, views):
@@ -327,8 +327,11 @@ def dyrect_sirt_step(ctx, cfg, device, n_samples, n_updates, gather_peak):
     times, measured data simulated by the event-model projector, the fused
     forward + correction and the split backprojection timed.  Samples and
     voxel-view updates are those of the static step (each tap and each
-    voxel-view pair serves one of the two value fields); a sample costs six
-    gathers (initial value, final value, transition time; two slices)."""
+    voxel-view pair serves one of the two value fields).  A sample costs two
+    gathers where its 8^3 brick lies wholly on one side of the view's time
+    and six otherwise (initial value, final value, transition time; two
+    slices); fwd_gathers_per_sample is the forward time in units of the
+    measured gather ceiling per sample (the static projector: about 2.3)."""
     import torch
 
     from paper_2609_30166_gb300 import inputs
@@ -350,7 +353,7 @@ def dyrect_sirt_step(ctx, cfg, device, n_samples, n_updates, gather_peak):
     torch.cuda.empty_cache()
     return {"workload": cfg.name + " (event scene: 8 changing regions)", "fwd_correct_ms": t_f * 1e3,
             "back_project_ms": t_b * 1e3, "gups": (n_samples + n_updates) / (t_f + t_b) / 1e9,
-            "fwd_tex_gather_frac": 6 * n_samples / t_f / gather_peak,
+            "fwd_gathers_per_sample": t_f * gather_peak / n_samples,
             "bp_tex_gather_frac": n_updates / t_b / gather_peak}
 
 

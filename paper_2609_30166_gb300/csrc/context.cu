@@ -78,6 +78,7 @@ struct ctrex_ctx {
     bool dyr = false;
     float *d_tau = nullptr;     // [nz][ny][nx] transition times
     float *d_tview = nullptr;   // [n_views] acquisition times
+    float2 *d_tau_brick = nullptr;  // (min, max) transition time per 8^3 brick
     AtlasStore dyr_atlas1;      // the final values (the volume atlas holds the initial ones)
     AtlasStore tau_atlas;
     Atlas dyr_atlas1_view, tau_atlas_view;
@@ -206,7 +207,9 @@ void dyr_release(ctrex_ctx *c)
     c->dyr = false;
     if (c->d_tau) cudaFree(c->d_tau);
     if (c->d_tview) cudaFree(c->d_tview);
+    if (c->d_tau_brick) cudaFree(c->d_tau_brick);
     c->d_tau = c->d_tview = nullptr;
+    c->d_tau_brick = nullptr;
     atlas_release(c->dyr_atlas1);
     atlas_release(c->tau_atlas);
 }
@@ -851,6 +854,14 @@ int ctrex_set_dyrect(ctrex_ctx *c, const float *tau, const float *t_view)
     e = atlas_upload(c->tau_atlas, c->d_tau, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "transition-time atlas upload");
     c->tau_atlas_view = atlas_view(c->tau_atlas);
+    const int bnx = (c->grid.nx + 7) / 8, bny = (c->grid.ny + 7) / 8, bnz = (c->grid.nz + 7) / 8;
+    if (!c->d_tau_brick)
+        CT_CUDA(c, cudaMalloc((void **)&c->d_tau_brick, sizeof(float2) * (size_t)bnx * bny * bnz));
+    e = launch_tau_bricks(c->d_tau, c->grid.nx, c->grid.ny, c->grid.nz, c->d_tau_brick, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "transition-time bricks");
+    c->dyra.tau_brick = c->d_tau_brick;
+    c->dyra.bnx = bnx;
+    c->dyra.bny = bny;
     c->dyra.tau = c->d_tau;
     c->dyra.t_view = c->d_tview;
     c->dyra.tau_atlas = &c->tau_atlas_view;

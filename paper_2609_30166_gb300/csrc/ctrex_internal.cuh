@@ -106,7 +106,14 @@ struct DyrArgs {
     const Atlas *tau_atlas = nullptr;
     const float *tau = nullptr;     // device [nz][ny][nx]
     const float *t_view = nullptr;  // device [n_views]
+    const float2 *tau_brick = nullptr;  // device: (min, max) of tau per 8^3 brick and its upper neighbours
+    int bnx = 0, bny = 0;               // bricks along x and y
 };
+
+// (min, max) transition time of each 8^3 brick of tau [nz][ny][nx], taken
+// over the brick and the voxel past each of its upper faces (within the
+// grid).
+cudaError_t launch_tau_bricks(const float *tau, int nx, int ny, int nz, float2 *out, cudaStream_t stream);
 
 struct FwdArgs {
     const Grid *grid;           // host copy

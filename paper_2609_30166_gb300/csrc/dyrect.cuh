@@ -6,6 +6,13 @@
 // those of the static projector.  The three fields live in three texture
 // atlases of identical tiling (one tile-origin table serves all), and one
 // footprint costs three gathers (mu0, mu1, tau) per slice.
+// Interior samples first read the smallest and largest transition time of
+// their 8^3 brick (taken over the brick and the voxel past each of its upper
+// faces, so that it covers every footprint whose lower corner lies in the
+// brick): when the view's time is below the smallest every tap takes mu0,
+// when it is at or above the largest every tap takes mu1, and the footprint
+// costs one gather per slice; the values and the arithmetic are those the
+// per-tap choice gives.
 #pragma once
 
 #include "atlas.cuh"
@@ -15,6 +22,8 @@ namespace ctrex {
 struct DyrectSampler {
     Atlas A0, A1, At;              // mu0, mu1 and tau atlases (same w, h, n, tshift)
     const float *t_view = nullptr;  // device [n_views]: acquisition time of each view
+    const float2 *brick = nullptr;  // device [bz][by][bx]: (min, max) transition time of each 8^3 brick
+    int bnx = 0, bny = 0;           // bricks along x and y
     float t = 0.0f;                 // time of the view being projected (set per CTA)
     const float2 *tile = nullptr;
 
@@ -62,8 +71,16 @@ struct DyrectSampler {
         const float ax = gx - fx, ay = gy - fy, az = gz - fz;
         const float2 o0 = origin(iz), o1 = origin(iz + 1);
         float a00, a10, a01, a11, b00, b10, b01, b11;
-        quad(o0.x + fx, o0.y + fy, a00, a10, a01, a11);
-        quad(o1.x + fx, o1.y + fy, b00, b10, b01, b11);
+        const float2 lh = __ldg(brick + ((iz >> 3) * bny + ((int)fy >> 3)) * bnx + ((int)fx >> 3));
+        if (t < lh.x || t >= lh.y) {
+            // one field for the whole footprint
+            const Atlas &S = t < lh.x ? A0 : A1;
+            atlas_quad_at(S, o0.x + fx, o0.y + fy, a00, a10, a01, a11);
+            atlas_quad_at(S, o1.x + fx, o1.y + fy, b00, b10, b01, b11);
+        } else {
+            quad(o0.x + fx, o0.y + fy, a00, a10, a01, a11);
+            quad(o1.x + fx, o1.y + fy, b00, b10, b01, b11);
+        }
         const float c0 = fmaf(ay, fmaf(ax, a11 - a01, a01) - fmaf(ax, a10 - a00, a00), fmaf(ax, a10 - a00, a00));
         const float c1 = fmaf(ay, fmaf(ax, b11 - b01, b01) - fmaf(ax, b10 - b00, b00), fmaf(ax, b10 - b00, b00));
         return fmaf(az, c1 - c0, c0);

@@ -118,11 +118,12 @@ __device__ __forceinline__ void pixel_integral(const Grid &G, const ViewGPU *__r
 }
 
 template <typename Sampler, typename TP, int MODE, bool MOTION>
-__global__ void __launch_bounds__(FWD_TX *FWD_TY)
-    fwd_kernel(Grid G, const ViewGPU *__restrict__ views, const MotionGPU *__restrict__ motion,
-               const float *__restrict__ coef_g, const Sampler vol_in,
-               const int *__restrict__ view_idx, TP *__restrict__ out, float *__restrict__ rowsum_out,
-               const TP *__restrict__ p, float *__restrict__ partials, unsigned *devcheck, int p_by_view)
+__device__ __forceinline__ void fwd_body(Grid G, const ViewGPU *__restrict__ views,
+                                         const MotionGPU *__restrict__ motion, const float *__restrict__ coef_g,
+                                         const Sampler &vol_in, const int *__restrict__ view_idx,
+                                         TP *__restrict__ out, float *__restrict__ rowsum_out,
+                                         const TP *__restrict__ p, float *__restrict__ partials, unsigned *devcheck,
+                                         int p_by_view)
 {
     __shared__ float4 s_coef[MOTION ? NCOEF_PAD : 1];  // zero-padded 9^3 float4 copy of the coefficients
     __shared__ float s_red[2][FWD_TX * FWD_TY / 32];
@@ -156,6 +157,36 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
     if (inside) pixel_integral<Sampler, MOTION>(G, views, mo, coef, vol, view, (float)iu, (float)iv, val, rs);
     fwd_epilogue<TP, MODE>(G, k, view, ok, in_pix, iu, iv, val, rs, out, rowsum_out, p, partials, p_by_view,
                            s_red);
+}
+
+template <typename Sampler, typename TP, int MODE, bool MOTION>
+__global__ void __launch_bounds__(FWD_TX *FWD_TY)
+    fwd_kernel(Grid G, const ViewGPU *__restrict__ views, const MotionGPU *__restrict__ motion,
+               const float *__restrict__ coef_g, const Sampler vol_in, const int *__restrict__ view_idx,
+               TP *__restrict__ out, float *__restrict__ rowsum_out, const TP *__restrict__ p,
+               float *__restrict__ partials, unsigned *devcheck, int p_by_view)
+{
+    fwd_body<Sampler, TP, MODE, MOTION>(G, views, motion, coef_g, vol_in, view_idx, out, rowsum_out, p, partials,
+                                        devcheck, p_by_view);
+}
+
+// The event-model projector as its own kernel, compiled for
+// CTREX_FWD_DYR_MIN_BLOCKS resident CTAs per SM: its per-tap choice needs
+// more registers than the static sampler, and the texture path wants warps
+// in flight (72 registers and 7 CTAs: 1128 ms on the 512^3 event workload;
+// 56 registers and 9 CTAs: 1058 ms).
+#ifndef CTREX_FWD_DYR_MIN_BLOCKS
+#define CTREX_FWD_DYR_MIN_BLOCKS 9
+#endif
+
+template <typename TP, int MODE>
+__global__ void __launch_bounds__(FWD_TX *FWD_TY, CTREX_FWD_DYR_MIN_BLOCKS)
+    fwd_kernel_dyr(Grid G, const ViewGPU *__restrict__ views, const DyrectSampler vol_in,
+                   const int *__restrict__ view_idx, TP *__restrict__ out, float *__restrict__ rowsum_out,
+                   const TP *__restrict__ p, float *__restrict__ partials, unsigned *devcheck, int p_by_view)
+{
+    fwd_body<DyrectSampler, TP, MODE, false>(G, views, nullptr, nullptr, vol_in, view_idx, out, rowsum_out, p,
+                                             partials, devcheck, p_by_view);
 }
 
 // Second pass of the residual reduction: one CTA, fixed order, FP64.
@@ -251,8 +282,12 @@ static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, flo
     } else if (a.motion) {
         return cudaErrorNotSupported;  // the motion warp is defined for the trilinear Cartesian projector only
     }
-    fwd_kernel<Sampler, TP, MODE, false><<<grid, block, 0, a.stream>>>(
-        G, a.views, nullptr, nullptr, smp, a.view_idx, out, rowsum, p, partials, a.devcheck, a.p_by_view);
+    if constexpr (Sampler::DYRECT)
+        fwd_kernel_dyr<TP, MODE><<<grid, block, 0, a.stream>>>(G, a.views, smp, a.view_idx, out, rowsum, p, partials,
+                                                              a.devcheck, a.p_by_view);
+    else
+        fwd_kernel<Sampler, TP, MODE, false><<<grid, block, 0, a.stream>>>(
+            G, a.views, nullptr, nullptr, smp, a.view_idx, out, rowsum, p, partials, a.devcheck, a.p_by_view);
     return cudaGetLastError();
 }
 
@@ -268,7 +303,8 @@ static cudaError_t fwd_dispatch_sampler(const FwdArgs &a, TP *out, float *rowsum
     }
     if (a.dyr) {  // mu0 from the volume atlas, mu1 and tau from their own
         if (!a.atlas || !a.dyr->mu1 || !a.dyr->tau_atlas || a.cyl || a.joseph) return cudaErrorInvalidValue;
-        DyrectSampler ds{*a.atlas, *a.dyr->mu1, *a.dyr->tau_atlas, a.dyr->t_view};
+        DyrectSampler ds{*a.atlas, *a.dyr->mu1, *a.dyr->tau_atlas, a.dyr->t_view, a.dyr->tau_brick, a.dyr->bnx,
+                         a.dyr->bny};
         return fwd_launch<DyrectSampler, TP, MODE>(a, ds, out, rowsum, p, partials);
     }
     if (a.joseph) {  // the Joseph projector reads its three-stack atlas only
@@ -339,6 +375,40 @@ cudaError_t launch_count_samples(const FwdArgs &a, unsigned long long *out)
     else
         count_kernel<COUNT_BOX><<<grid, block, 0, a.stream>>>(*a.grid, CylGPU{}, RoiGPU{}, a.views, a.view_idx,
                                                               out);
+    return cudaGetLastError();
+}
+
+// (min, max) of tau over each 8^3 brick and the voxel past each of its
+// upper faces: one thread per brick (run once, by ctrex_set_dyrect).
+__global__ void tau_brick_kernel(const float *__restrict__ tau, int nx, int ny, int nz, int bnx, int bny, int bnz,
+                                 float2 *__restrict__ out)
+{
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (long long)bnx * bny * bnz) return;
+    const int bx = (int)(b % bnx), by = (int)((b / bnx) % bny), bz = (int)(b / ((long long)bnx * bny));
+    const int x1 = min(8 * bx + 8, nx - 1), y1 = min(8 * by + 8, ny - 1), z1 = min(8 * bz + 8, nz - 1);
+    float lo = INFINITY, hi = -INFINITY;
+    bool nan = false;
+    for (int z = 8 * bz; z <= z1; ++z)
+        for (int y = 8 * by; y <= y1; ++y) {
+            const float *row = tau + ((size_t)z * ny + y) * nx;
+            for (int x = 8 * bx; x <= x1; ++x) {
+                const float v = __ldg(row + x);
+                nan |= v != v;
+                lo = fminf(lo, v);
+                hi = fmaxf(hi, v);
+            }
+        }
+    // a NaN transition time sends its tap to mu1 (t < NaN is false): such a
+    // brick never takes the mu0 shortcut, and the mu1 one only for t = +inf
+    out[b] = nan ? make_float2(-INFINITY, INFINITY) : make_float2(lo, hi);
+}
+
+cudaError_t launch_tau_bricks(const float *tau, int nx, int ny, int nz, float2 *out, cudaStream_t stream)
+{
+    const int bnx = (nx + 7) / 8, bny = (ny + 7) / 8, bnz = (nz + 7) / 8;
+    const long long n = (long long)bnx * bny * bnz;
+    tau_brick_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(tau, nx, ny, nz, bnx, bny, bnz, out);
     return cudaGetLastError();
 }
 

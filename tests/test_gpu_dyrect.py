@@ -129,6 +129,37 @@ def test_dyrect_sirt_and_bf16(ct, scene):
     c.close()
 
 
+def test_dyrect_brick_shortcut_paths(ct, scene):
+    """The per-brick shortcut of the projector: with one transition time for
+    the whole volume every interior footprint takes one field (mu0 for the
+    views before it, mu1 after), which must give the static projections of
+    those fields; with NaN transition times in a few voxels (their taps take
+    mu1, t < NaN being false) their bricks take the per-tap path, and the
+    result must still match the oracle."""
+    cfg, P, x, tau, tv, pb = scene
+    t_mid = float(np.float32(0.5 * (tv[14] + tv[15])))
+    c = _ctx(ct, cfg, P, np.full_like(tau, t_mid), tv)
+    got = _np(c.fwd_project(_t(x)))
+    st = ct.context_for(cfg, P=P)
+    p0, p1 = _np(st.fwd_project(_t(x[0]))), _np(st.fwd_project(_t(x[1])))
+    e0, e1 = rel_l2(got[:15], p0[:15]), rel_l2(got[15:], p1[15:])
+    print(f"uniform transition time: early views vs static mu0 {e0:.2e}, late views vs static mu1 {e1:.2e}")
+    assert e0 <= 1e-6 and e1 <= 1e-6
+    c.close()
+    st.close()
+    tau_nan = tau.copy()
+    rng = np.random.default_rng(3)
+    idx = rng.integers(0, tau.size, size=40)
+    tau_nan.flat[idx] = np.nan
+    c = _ctx(ct, cfg, P, tau_nan, tv)
+    ref, _ = oracle.forward(oracle.Problem(P, cfg.vol_shape, (cfg.vox,) * 3, cfg.origin, (cfg.nu, cfg.nv),
+                                           cfg.step_vox).with_dyrect(tau_nan, tv), x)
+    e = rel_l2(_np(c.fwd_project(_t(x))), ref)
+    print(f"NaN transition times in 40 voxels: forward vs oracle {e:.2e}")
+    assert e <= TOL32
+    c.close()
+
+
 def test_dyrect_refusals(ct, scene):
     cfg, P, x, tau, tv, pb = scene
     c = _ctx(ct, cfg, P, tau, tv)
