@@ -684,6 +684,24 @@ def run_ours(args):
                         "fwd_tex_gather_frac": n_samples / t_bf / gather_peak,
                         "bp_tex_gather_frac": n_updates / t_bb / gather_peak}
             del x16, p16, r16
+        # ordered-subset SIRT (Sec. 2.3.2): one cycle over 10 interleaved
+        # subsets of 72 views (visited in bit-reversed order), each a fused
+        # forward + correction and a normalised backprojection of its views,
+        # with a host read of the subset's residual between them
+        subsets = inputs.subsets_cyclic(geo.n_views, 10)
+        xo = torch.zeros_like(x)
+        t_os = _time(lambda: ctx.os_sirt_iterate(xo, p, subsets, 1), reps=2)
+        os_row = {"workload": cfg.name, "subsets": len(subsets), "views_per_subset": geo.n_views // len(subsets),
+                  "cycle_ms": t_os * 1e3, "gups": units / t_os / 1e9, "sirt_step_ms": ms / args.steps}
+        # extended field of view (Sec. 3.6, 4.3.2): one SIRT iteration whose
+        # backprojector sees per-view detector windows, the inner edge drawn
+        # between column 0 and the detector centre
+        ctx.set_bp_window(inputs.efov_windows(geo, 0.5 * (geo.nu - 1), seed=7))
+        t_ef = _time(lambda: ctx.sirt_iterate(xo, p, 1), reps=2)
+        ctx.set_bp_window(None)
+        ef_row = {"workload": cfg.name + " (per-view BP windows)", "iteration_ms": t_ef * 1e3,
+                  "gups": units / t_ef / 1e9, "sirt_step_ms": ms / args.steps}
+        del xo
         del x, r
         torch.cuda.empty_cache()
         if args.accuracy and tdt == torch.float32:
@@ -698,6 +716,8 @@ def run_ours(args):
                                           "tex_gather_frac": sv_points / t_sv / gather_peak,
                                           "centre_bp_ms": statistics.mean(bp_ms)}
         out["rows"]["a16_joseph_sirt_step"] = joseph_row
+        out["rows"]["a19_os_sirt_cycle"] = os_row
+        out["rows"]["a20_efov_sirt_iteration"] = ef_row
         if bf16_row:
             out["rows"]["a11_bf16_sirt_step"] = bf16_row
     if rank == 0 and world == 1 and not args.no_rows and not args.views and not args.small and not cyl:

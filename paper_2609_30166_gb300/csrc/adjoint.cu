@@ -10,15 +10,19 @@
 // Motion gradient CTA: CTREX_MGRAD_WARPS warps, each on an 8 x 4 pixel
 // patch (the CTA covers 8 * warps detector columns x 4 rows), with
 // CTREX_MGRAD_MIN_BLOCKS resident CTAs per SM (two warps and six CTAs cap
-// the registers at 168, enough for the unrolled y loop of the spline without
-// spills; 5 or 4 CTAs with more registers, or 4-warp CTAs, were no faster).
-// Few warps per CTA shorten the wait of warps with short rays for the CTA's
-// final reduction.
+// the registers at 168; 5 or 4 CTAs with more registers, or 4-warp CTAs,
+// were no faster).  The spline's y and z loops are unrolled
+// (CTREX_MGRAD_UNROLL_Z): 616 -> 564 ms on the motion workload, with 4
+// bytes of spills.  Few warps per CTA shorten the wait of warps with short
+// rays for the CTA's final reduction.
 #ifndef CTREX_MGRAD_WARPS
 #define CTREX_MGRAD_WARPS 2
 #endif
 #ifndef CTREX_MGRAD_MIN_BLOCKS
 #define CTREX_MGRAD_MIN_BLOCKS (12 / CTREX_MGRAD_WARPS)
+#endif
+#ifndef CTREX_MGRAD_UNROLL_Z
+#define CTREX_MGRAD_UNROLL_Z 1
 #endif
 
 namespace ctrex {
@@ -259,10 +263,14 @@ __device__ __forceinline__ void spline_value_jacobian(const float4 *coef, const 
 #pragma unroll
     for (int c = 0; c < 3; ++c) u[c] = Jx[c] = Jy[c] = Jz[c] = 0.0f;
     const float4 *plane = coef_cell(coef, i0);
-    // the z loop stays rolled (bounds the live coefficient loads); its two
-    // weights are picked by selects, which keeps the arrays in registers.
-    // The y loop is unrolled: 16 independent float4 loads per plane.
+    // the z loop's two weights are picked by selects, which keeps the
+    // arrays in registers when the loop stays rolled (CTREX_MGRAD_UNROLL_Z
+    // 0); the y loop is unrolled: 16 independent float4 loads per plane.
+#if CTREX_MGRAD_UNROLL_Z
+#pragma unroll
+#else
 #pragma unroll 1
+#endif
     for (int k = 0; k < 4; ++k, plane += CPAD * CPAD) {
         const float wzk = k == 0 ? wz[0] : (k == 1 ? wz[1] : (k == 2 ? wz[2] : wz[3]));
         const float dzk = k == 0 ? dz[0] : (k == 1 ? dz[1] : (k == 2 ? dz[2] : dz[3]));
