@@ -405,6 +405,13 @@ int ctrex_os_sirt_iterate(ctrex_ctx *ctx, void *vol, int vol_dtype, const void *
  * Same as ctrex_sirt_iterate with HOST buffers: copies vol (x_0) and p to
  * device buffers owned by the context, iterates, and copies the volume back
  * into vol.  vol_dtype / p_dtype describe the host arrays.  Synchronous.
+ * With FP32 projections the first iteration overlaps the upload of p with
+ * the forward projection (a copy stream owned by the context; the
+ * correction waits for the upload), so the iterates equal those of
+ * ctrex_sirt_iterate bitwise and only the first residual norm is summed in
+ * another order.  Pinned host memory lets the copies run asynchronously;
+ * pageable memory works but the driver stages it.  The context then also
+ * holds two FP32 projection-sized scratch buffers.
  */
 int ctrex_sirt_host(ctrex_ctx *ctx, void *vol_host, int vol_dtype, const void *p_host, int p_dtype,
                     int max_iter, float alpha, const float *w_host, float tol,

@@ -92,6 +92,13 @@ struct ctrex_ctx {
     void *d_hvol = nullptr, *d_hp = nullptr;
     float *d_hw = nullptr;
     size_t hvol_bytes = 0, hp_bytes = 0, hw_bytes = 0;
+    // its first iteration overlaps the projections' upload with the forward
+    // projection: A x and the row sums (FP32), a copy stream, two events
+    void *d_hq = nullptr;
+    float *d_hrs = nullptr;
+    size_t hq_bytes = 0, hrs_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_vol = nullptr, ev_p = nullptr;
 };
 
 namespace {
@@ -399,6 +406,11 @@ int ctrex_destroy(ctrex_ctx *c)
         dfree(c->d_hvol);
         dfree(c->d_hp);
         dfree(c->d_hw);
+        dfree(c->d_hq);
+        dfree(c->d_hrs);
+        if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+        if (c->ev_vol) cudaEventDestroy(c->ev_vol);
+        if (c->ev_p) cudaEventDestroy(c->ev_p);
         dfree(c->d_subset_views);
         dfree(c->d_window);
         dfree(c->d_subset_sums);
@@ -1156,8 +1168,58 @@ int ctrex_sirt_host(ctrex_ctx *c, void *vol_h, int vdt, const void *p_h, int pdt
         dw = c->d_hw;
     }
     CT_CUDA(c, cudaMemcpyAsync(c->d_hvol, vol_h, vb, cudaMemcpyHostToDevice, c->stream));
-    CT_CUDA(c, cudaMemcpyAsync(c->d_hp, p_h, pb, cudaMemcpyHostToDevice, c->stream));
-    e = ctrex_sirt_iterate(c, c->d_hvol, vdt, c->d_hp, pdt, max_iter, alpha, dw, tol, hist, iters_done);
+    if (iters_done) *iters_done = 0;
+    int first = 0;  // iterations done here, before ctrex_sirt_iterate takes over
+    if (pdt == CTREX_F32 && max_iter >= 1) {
+        // First iteration: the projections (the larger upload) travel on a
+        // copy stream while the forward projection runs; the correction
+        // r = R (p - A x) waits for them.  Same arithmetic as the fused
+        // correction (A x and the row sums are FP32 either way); only the
+        // residual norms are summed in another order.
+        const size_t npix = (size_t)G.n_views * G.nu * G.nv;
+        e = ensure(c, &c->d_hq, &c->hq_bytes, npix * sizeof(float), "host-SIRT forward projection");
+        if (e) return e;
+        e = ensure(c, (void **)&c->d_hrs, &c->hrs_bytes, npix * sizeof(float), "host-SIRT row sums");
+        if (e) return e;
+        e = ensure(c, &c->d_r, &c->r_bytes, npix * sizeof(float), "SIRT correction images");
+        if (e) return e;
+        if (!c->copy_stream) CT_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        if (!c->ev_vol) CT_CUDA(c, cudaEventCreateWithFlags(&c->ev_vol, cudaEventDisableTiming));
+        if (!c->ev_p) CT_CUDA(c, cudaEventCreateWithFlags(&c->ev_p, cudaEventDisableTiming));
+        CT_CUDA(c, cudaEventRecord(c->ev_vol, c->stream));  // the volume's upload (and earlier work) first
+        CT_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_vol, 0));
+        CT_CUDA(c, cudaMemcpyAsync(c->d_hp, p_h, pb, cudaMemcpyHostToDevice, c->copy_stream));
+        CT_CUDA(c, cudaEventRecord(c->ev_p, c->copy_stream));
+        FwdArgs a = fwd_args(c, c->d_hvol, vdt, nullptr, G.n_views);
+        e = prepare_atlas(c, a, c->d_hvol, vdt);
+        if (e) return e;
+        cudaError_t ce = launch_forward(a, c->d_hq, CTREX_F32, c->d_hrs);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "sirt_host: forward projection");
+        CT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_p, 0));
+        e = ctrex_correct_static(c->d_hp, c->d_hq, c->d_hrs, c->d_r, CTREX_F32, (long long)npix, G.eps_R, c->d_sums,
+                                 c->stream);
+        if (e) return fail(c, e, "sirt_host: correction of the first iteration");
+        double s[2];
+        CT_CUDA(c, cudaMemcpyAsync(s, c->d_sums, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+        CT_CUDA(c, cudaStreamSynchronize(c->stream));
+        const double rho = s[1] > 0.0 ? sqrt(s[0] / s[1]) : sqrt(s[0]);
+        if (hist) hist[0] = (float)rho;
+        if (!isfinite(rho)) return fail(c, CTREX_E_DIVERGED, "sirt: residual not finite at iteration 0");
+        first = 1;
+        if (rho <= (double)tol) {
+            max_iter = first;  // converged before the first update
+        } else {
+            e = ctrex_back_project(c, c->d_r, CTREX_F32, c->d_hvol, vdt, dw, alpha, 1, 1, nullptr, G.n_views);
+            if (e) return e;
+            if (iters_done) *iters_done = 1;
+        }
+    } else {
+        CT_CUDA(c, cudaMemcpyAsync(c->d_hp, p_h, pb, cudaMemcpyHostToDevice, c->stream));
+    }
+    int rest = 0;
+    e = ctrex_sirt_iterate(c, c->d_hvol, vdt, c->d_hp, pdt, max_iter - first, alpha, dw, tol,
+                           hist ? hist + first : nullptr, &rest);
+    if (iters_done && max_iter - first > 0) *iters_done = first + rest;
     if (e) return e;
     CT_CUDA(c, cudaMemcpyAsync(vol_h, c->d_hvol, vb, cudaMemcpyDeviceToHost, c->stream));
     CT_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -209,8 +209,17 @@ def test_sirt_tolerance_stop_and_host_path(ct, c1):
     ph = torch.as_tensor(proj, dtype=torch.float32).pin_memory()
     xh, hist_h, done_h = c.sirt_host(xh, ph, 4)
     xd = torch.zeros(cfg.vol_shape, device="cuda")
-    xd, hist_d, _ = c.sirt_iterate(xd, _gpu(proj), 4)
-    assert torch.equal(xh, xd.cpu()) and np.array_equal(hist_h, hist_d)
+    xd, hist_d, done_d = c.sirt_iterate(xd, _gpu(proj), 4)
+    # the host path's first iteration projects while the projections upload
+    # and corrects afterwards: the same correction images (so the same
+    # iterates, bitwise), only that residual norm summed in another order
+    assert done_h == done_d == 4
+    assert torch.equal(xh, xd.cpu()) and np.array_equal(hist_h[1:], hist_d[1:])
+    assert np.allclose(hist_h[:1], hist_d[:1], rtol=1e-6, atol=0)
+    # stopping on the tolerance at the first residual: no update applied
+    xh0 = torch.zeros(cfg.vol_shape, dtype=torch.float32).pin_memory()
+    xh0, hist0, done0 = c.sirt_host(xh0, ph, 4, tol=10.0)
+    assert done0 == 0 and not xh0.any() and np.isclose(hist0[0], hist_d[0], rtol=1e-6)
 
 
 # ---------------------------------------------------------------------------
