@@ -411,7 +411,8 @@ int ctrex_os_sirt_iterate(ctrex_ctx *ctx, void *vol, int vol_dtype, const void *
  * ctrex_sirt_iterate bitwise and only the first residual norm is summed in
  * another order.  Pinned host memory lets the copies run asynchronously;
  * pageable memory works but the driver stages it.  The context then also
- * holds two FP32 projection-sized scratch buffers.
+ * holds two FP32 projection-sized scratch buffers and the correction's
+ * partial norms (its own, not ctrex_correct_static's shared array).
  */
 int ctrex_sirt_host(ctrex_ctx *ctx, void *vol_host, int vol_dtype, const void *p_host, int p_dtype,
                     int max_iter, float alpha, const float *w_host, float tol,

@@ -96,7 +96,8 @@ struct ctrex_ctx {
     // projection: A x and the row sums (FP32), a copy stream, two events
     void *d_hq = nullptr;
     float *d_hrs = nullptr;
-    size_t hq_bytes = 0, hrs_bytes = 0;
+    double *d_hcs = nullptr;  // the correction's partial norms
+    size_t hq_bytes = 0, hrs_bytes = 0, hcs_bytes = 0;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_vol = nullptr, ev_p = nullptr;
 };
@@ -408,6 +409,7 @@ int ctrex_destroy(ctrex_ctx *c)
         dfree(c->d_hw);
         dfree(c->d_hq);
         dfree(c->d_hrs);
+        dfree(c->d_hcs);
         if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
         if (c->ev_vol) cudaEventDestroy(c->ev_vol);
         if (c->ev_p) cudaEventDestroy(c->ev_p);
@@ -1173,15 +1175,19 @@ int ctrex_sirt_host(ctrex_ctx *c, void *vol_h, int vdt, const void *p_h, int pdt
     if (pdt == CTREX_F32 && max_iter >= 1) {
         // First iteration: the projections (the larger upload) travel on a
         // copy stream while the forward projection runs; the correction
-        // r = R (p - A x) waits for them.  Same arithmetic as the fused
-        // correction (A x and the row sums are FP32 either way); only the
-        // residual norms are summed in another order.
+        // r = R (p - A x) waits for them (the kernels of
+        // ctrex_correct_static with this context's own scratch).  Same
+        // arithmetic as the fused correction (A x and the row sums are FP32
+        // either way); only the residual norms are summed in another order.
         const size_t npix = (size_t)G.n_views * G.nu * G.nv;
         e = ensure(c, &c->d_hq, &c->hq_bytes, npix * sizeof(float), "host-SIRT forward projection");
         if (e) return e;
         e = ensure(c, (void **)&c->d_hrs, &c->hrs_bytes, npix * sizeof(float), "host-SIRT row sums");
         if (e) return e;
         e = ensure(c, &c->d_r, &c->r_bytes, npix * sizeof(float), "SIRT correction images");
+        if (e) return e;
+        const size_t pairs = (size_t)correct_scratch_pairs((long long)npix);
+        e = ensure(c, (void **)&c->d_hcs, &c->hcs_bytes, 2 * sizeof(double) * pairs, "host-SIRT correction partials");
         if (e) return e;
         if (!c->copy_stream) CT_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
         if (!c->ev_vol) CT_CUDA(c, cudaEventCreateWithFlags(&c->ev_vol, cudaEventDisableTiming));
@@ -1196,9 +1202,9 @@ int ctrex_sirt_host(ctrex_ctx *c, void *vol_h, int vdt, const void *p_h, int pdt
         cudaError_t ce = launch_forward(a, c->d_hq, CTREX_F32, c->d_hrs);
         if (ce != cudaSuccess) return cuda_fail(c, ce, "sirt_host: forward projection");
         CT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_p, 0));
-        e = ctrex_correct_static(c->d_hp, c->d_hq, c->d_hrs, c->d_r, CTREX_F32, (long long)npix, G.eps_R, c->d_sums,
-                                 c->stream);
-        if (e) return fail(c, e, "sirt_host: correction of the first iteration");
+        ce = launch_correct(c->d_hp, c->d_hq, c->d_hrs, c->d_r, CTREX_F32, (long long)npix, G.eps_R, c->d_sums,
+                            c->d_hcs, c->stream);
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "sirt_host: correction of the first iteration");
         double s[2];
         CT_CUDA(c, cudaMemcpyAsync(s, c->d_sums, sizeof s, cudaMemcpyDeviceToHost, c->stream));
         CT_CUDA(c, cudaStreamSynchronize(c->stream));

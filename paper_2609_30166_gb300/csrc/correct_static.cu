@@ -143,6 +143,20 @@ cudaError_t launch(const void *p, const void *q, const float *rowsum, void *r, l
 
 }  // namespace
 
+namespace ctrex {
+
+long long correct_scratch_pairs(long long n) { return (n + CS_PER_BLOCK - 1) / CS_PER_BLOCK; }
+
+cudaError_t launch_correct(const void *p, const void *q, const float *rowsum, void *r, int dtype, long long n,
+                           float eps_R, double *sums, double *scratch, cudaStream_t stream)
+{
+    if (n <= 0) return cudaSuccess;
+    return dtype == CTREX_F32 ? launch<float>(p, q, rowsum, r, n, eps_R, sums, scratch, stream)
+                              : launch<__nv_bfloat16>(p, q, rowsum, r, n, eps_R, sums, scratch, stream);
+}
+
+}  // namespace ctrex
+
 extern "C" int ctrex_correct_static(const void *p, const void *q, const float *rowsum, void *r, int dtype,
                                     long long n, float eps_R, double *sums, void *cuda_stream)
 {

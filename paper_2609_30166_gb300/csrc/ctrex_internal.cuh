@@ -110,6 +110,14 @@ struct DyrArgs {
     int bnx = 0, bny = 0;               // bricks along x and y
 };
 
+// The detector-space correction r = R (p - q) with the residual norms
+// (sum (p - q)^2, sum p^2) into sums (DEVICE double [2]; NULL: r only), as
+// ctrex_correct_static computes it but with caller-owned scratch of
+// correct_scratch_pairs(n) double pairs, for any n >= 0 (correct_static.cu).
+long long correct_scratch_pairs(long long n);
+cudaError_t launch_correct(const void *p, const void *q, const float *rowsum, void *r, int dtype, long long n,
+                           float eps_R, double *sums, double *scratch, cudaStream_t stream);
+
 // (min, max) transition time of each 8^3 brick of tau [nz][ny][nx], taken
 // over the brick and the voxel past each of its upper faces (within the
 // grid).
