@@ -41,18 +41,26 @@ constexpr int NCOEF = 8 * 8 * 8 * 3;
 // the neighbours x0, x0 + 1, consecutive floats.  When both lie in one
 // 16-byte-aligned quad of the volume (x0 % 4 != 3 in element terms; 3 cases
 // in 4), one vector reduction adds (.., w0, w1, ..) with zeros in the other
-// two lanes, so a sample issues about 5 reductions instead of 8 (the
-// reductions' L1/TEX path bounds the kernel without motion; with motion the
-// spline evaluation does).  The zero lanes belong to neighbouring voxels
-// (possibly of the adjacent row) inside the volume; adding +0 leaves them
-// unchanged.  vec: the volume is 16-byte aligned; nvox: its element count.
-__device__ __forceinline__ void scatter_trilinear(float *__restrict__ vol, int nx, int ny, int nz, const float c[3],
-                                                  const float gc[3], float val, bool vec, long long nvox)
+// two lanes, so a footprint issues about 5 reductions instead of 8 (the
+// reductions' L1/TEX path bounds the kernel).  The zero lanes belong to
+// neighbouring voxels (possibly of the adjacent row) inside the volume;
+// adding +0 leaves them unchanged.  vec: the volume is 16-byte aligned;
+// nvox: its element count.
+// A footprint waiting to be scattered: the lower corner (ix, iy, iz) in
+// voxel indices and the summed weight of each of its eight taps.  A ray's
+// samples lie half a voxel apart, so consecutive ones often share the
+// corner: their weights are added here and reduced into the volume once,
+// when the corner moves or the ray ends.
+struct Footprint {
+    int ix = 0, iy = 0, iz = 0;
+    bool live = false;
+    float w[2][2][2] = {{{0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}}};
+};
+
+__device__ __forceinline__ void scatter_footprint(float *__restrict__ vol, int nx, int ny, int nz,
+                                                  const Footprint &F, bool vec, long long nvox)
 {
-    const float fx = floorf(gc[0]), fy = floorf(gc[1]), fz = floorf(gc[2]);
-    const int ix = (int)fx + (int)c[0], iy = (int)fy + (int)c[1], iz = (int)fz + (int)c[2];
-    const float ax = gc[0] - fx, ay = gc[1] - fy, az = gc[2] - fz;
-    const float wx[2] = {1.0f - ax, ax}, wy[2] = {1.0f - ay, ay}, wz[2] = {1.0f - az, az};
+    const int ix = F.ix, iy = F.iy, iz = F.iz;
     const bool in0 = (unsigned)ix < (unsigned)nx, in1 = (unsigned)(ix + 1) < (unsigned)nx;
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz) {
@@ -62,12 +70,11 @@ __device__ __forceinline__ void scatter_trilinear(float *__restrict__ vol, int n
         for (int dy = 0; dy < 2; ++dy) {
             const int y = iy + dy;
             if ((unsigned)y >= (unsigned)ny) continue;
-            const float wzy = val * wz[dz] * wy[dy];
             const long long e = ((long long)z * ny + y) * nx + ix;  // element of tap x0 (x0 may be -1)
+            const float w0 = in0 ? F.w[dz][dy][0] : 0.0f, w1 = in1 ? F.w[dz][dy][1] : 0.0f;
             const int lane = (int)(e & 3);
             if (vec && lane != 3 && e >= 0 && (e | 3) < nvox) {
                 float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                const float w0 = in0 ? wzy * wx[0] : 0.0f, w1 = in1 ? wzy * wx[1] : 0.0f;
                 if (lane == 0) {
                     q.x = w0;
                     q.y = w1;
@@ -80,11 +87,47 @@ __device__ __forceinline__ void scatter_trilinear(float *__restrict__ vol, int n
                 }
                 atomicAdd(reinterpret_cast<float4 *>(vol + (e - lane)), q);
             } else {
-                if (in0) atomicAdd(vol + e, wzy * wx[0]);
-                if (in1) atomicAdd(vol + e + 1, wzy * wx[1]);
+                if (in0) atomicAdd(vol + e, w0);
+                if (in1) atomicAdd(vol + e + 1, w1);
             }
         }
     }
+}
+
+// Adds val at the point with centred index coordinates gc to the pending
+// footprint F, first scattering F if the point's corner differs.
+__device__ __forceinline__ void scatter_trilinear(float *__restrict__ vol, int nx, int ny, int nz, const float c[3],
+                                                  const float gc[3], float val, bool vec, long long nvox,
+                                                  Footprint &F)
+{
+    const float fx = floorf(gc[0]), fy = floorf(gc[1]), fz = floorf(gc[2]);
+    const int ix = (int)fx + (int)c[0], iy = (int)fy + (int)c[1], iz = (int)fz + (int)c[2];
+    const float ax = gc[0] - fx, ay = gc[1] - fy, az = gc[2] - fz;
+    const float wx[2] = {1.0f - ax, ax}, wy[2] = {1.0f - ay, ay}, wz[2] = {1.0f - az, az};
+    if (F.live && (ix != F.ix || iy != F.iy || iz != F.iz)) {
+        scatter_footprint(vol, nx, ny, nz, F, vec, nvox);
+        F.live = false;
+    }
+    if (!F.live) {
+        F.ix = ix;
+        F.iy = iy;
+        F.iz = iz;
+        F.live = true;
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) F.w[dz][dy][dx] = 0.0f;
+    }
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const float wzy = val * wz[dz] * wy[dy];
+            F.w[dz][dy][0] = fmaf(wzy, wx[0], F.w[dz][dy][0]);
+            F.w[dz][dy][1] = fmaf(wzy, wx[1], F.w[dz][dy][1]);
+        }
 }
 
 // Event-based 4D model (Sec. 3.3): the transpose sends each tap's share to
@@ -151,6 +194,7 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
     const float t = DYR ? __ldg(t_view + view) : 0.0f;
     float cen[3];
     grid_centre(G, cen);
+    Footprint F;  // the pending footprint of this thread's samples
     for (int s = 0; s < G.n_sub; ++s) {
         Ray R;  // sample positions relative to the grid centre
         if (!setup_ray(G, views[view * G.n_sub + s], (float)iu, (float)iv, R, cen)) continue;
@@ -183,9 +227,10 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
             if (DYR)
                 scatter_trilinear_dyrect(vol, G.nx, G.ny, G.nz, cen, gc, val, tau, t, nvox);
             else
-                scatter_trilinear(vol, G.nx, G.ny, G.nz, cen, gc, val, vec, nvox);
+                scatter_trilinear(vol, G.nx, G.ny, G.nz, cen, gc, val, vec, nvox, F);
         }
     }
+    if (!DYR && F.live) scatter_footprint(vol, G.nx, G.ny, G.nz, F, vec, nvox);
 }
 
 cudaError_t launch_adjoint(const FwdArgs &a, const float *proj, float *vol)
