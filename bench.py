@@ -421,7 +421,7 @@ def measure_rows(device, gather_peak, sm_count, sm_mhz):
                                    "alu_peak_ops_per_s": alu_peak,
                                    "ops_per_sample_est": MOTION_OPS_PER_SAMPLE}
     rows["a8_matched_adjoint"] = {"workload": cfg.name, "ms": t_a * 1e3, "gsamples_per_s": ns / t_a / 1e9,
-                                  "atomics_per_s": 8 * ns / t_a}
+                                  "tap_updates_per_s": 8 * ns / t_a}
     rows["a9_motion_gradient"] = {"workload": cfg.name, "ms": t_g * 1e3, "gsamples_per_s": ns / t_g / 1e9}
     del ctx, vol, proj, g, adj
     # cylindrical domain (Sec. 3.5): one SIRT step on the vial workload
