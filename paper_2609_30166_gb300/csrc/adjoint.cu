@@ -94,18 +94,50 @@ __device__ __forceinline__ void scatter_footprint(float *__restrict__ vol, int n
     }
 }
 
+// Event-based 4D model (Sec. 3.3): the transpose sends each tap's share to
+// mu0 (vol[j]) if the view's time t precedes the voxel's transition time
+// tau_j, else to mu1 (vol[nvox + j]); scalar reductions.  The choice is the
+// voxel's for the whole view, so merged weights route as their samples'.
+__device__ __forceinline__ void scatter_footprint_dyrect(float *__restrict__ vol, int nx, int ny, int nz,
+                                                         const Footprint &F, const float *__restrict__ tau, float t,
+                                                         long long nvox)
+{
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz) {
+        const int z = F.iz + dz;
+        if ((unsigned)z >= (unsigned)nz) continue;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const int y = F.iy + dy;
+            if ((unsigned)y >= (unsigned)ny) continue;
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int x = F.ix + dx;
+                if ((unsigned)x >= (unsigned)nx) continue;
+                const long long j = ((long long)z * ny + y) * nx + x;
+                atomicAdd(vol + (t < __ldg(tau + j) ? j : nvox + j), F.w[dz][dy][dx]);
+            }
+        }
+    }
+}
+
 // Adds val at the point with centred index coordinates gc to the pending
-// footprint F, first scattering F if the point's corner differs.
+// footprint F, first scattering F if the point's corner differs (DYR: into
+// the event model's two fields, by tau and the view's time t).
+template <bool DYR>
 __device__ __forceinline__ void scatter_trilinear(float *__restrict__ vol, int nx, int ny, int nz, const float c[3],
                                                   const float gc[3], float val, bool vec, long long nvox,
-                                                  Footprint &F)
+                                                  Footprint &F, const float *__restrict__ tau, float t)
 {
     const float fx = floorf(gc[0]), fy = floorf(gc[1]), fz = floorf(gc[2]);
     const int ix = (int)fx + (int)c[0], iy = (int)fy + (int)c[1], iz = (int)fz + (int)c[2];
     const float ax = gc[0] - fx, ay = gc[1] - fy, az = gc[2] - fz;
     const float wx[2] = {1.0f - ax, ax}, wy[2] = {1.0f - ay, ay}, wz[2] = {1.0f - az, az};
     if (F.live && (ix != F.ix || iy != F.iy || iz != F.iz)) {
-        scatter_footprint(vol, nx, ny, nz, F, vec, nvox);
+        if (DYR)
+            scatter_footprint_dyrect(vol, nx, ny, nz, F, tau, t, nvox);
+        else
+            scatter_footprint(vol, nx, ny, nz, F, vec, nvox);
         F.live = false;
     }
     if (!F.live) {
@@ -128,36 +160,6 @@ __device__ __forceinline__ void scatter_trilinear(float *__restrict__ vol, int n
             F.w[dz][dy][0] = fmaf(wzy, wx[0], F.w[dz][dy][0]);
             F.w[dz][dy][1] = fmaf(wzy, wx[1], F.w[dz][dy][1]);
         }
-}
-
-// Event-based 4D model (Sec. 3.3): the transpose sends each tap's share to
-// mu0 (vol[j]) if the view's time t precedes the voxel's transition time
-// tau_j, else to mu1 (vol[nvox + j]); scalar reductions.
-__device__ __forceinline__ void scatter_trilinear_dyrect(float *__restrict__ vol, int nx, int ny, int nz,
-                                                         const float c[3], const float gc[3], float val,
-                                                         const float *__restrict__ tau, float t, long long nvox)
-{
-    const float fx = floorf(gc[0]), fy = floorf(gc[1]), fz = floorf(gc[2]);
-    const int ix = (int)fx + (int)c[0], iy = (int)fy + (int)c[1], iz = (int)fz + (int)c[2];
-    const float ax = gc[0] - fx, ay = gc[1] - fy, az = gc[2] - fz;
-    const float wx[2] = {1.0f - ax, ax}, wy[2] = {1.0f - ay, ay}, wz[2] = {1.0f - az, az};
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz) {
-        const int z = iz + dz;
-        if ((unsigned)z >= (unsigned)nz) continue;
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-            const int y = iy + dy;
-            if ((unsigned)y >= (unsigned)ny) continue;
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const int x = ix + dx;
-                if ((unsigned)x >= (unsigned)nx) continue;
-                const long long j = ((long long)z * ny + y) * nx + x;
-                atomicAdd(vol + (t < __ldg(tau + j) ? j : nvox + j), val * wz[dz] * wy[dy] * wx[dx]);
-            }
-        }
-    }
 }
 
 template <bool MOTION, bool DYR>
@@ -224,13 +226,15 @@ __global__ void __launch_bounds__(ADJ_TX *ADJ_TY)
             if (!(gc[0] >= -1.0f - cen[0] && gc[0] < (float)G.nx - cen[0] && gc[1] >= -1.0f - cen[1] &&
                   gc[1] < (float)G.ny - cen[1] && gc[2] >= -1.0f - cen[2] && gc[2] < (float)G.nz - cen[2]))
                 continue;
-            if (DYR)
-                scatter_trilinear_dyrect(vol, G.nx, G.ny, G.nz, cen, gc, val, tau, t, nvox);
-            else
-                scatter_trilinear(vol, G.nx, G.ny, G.nz, cen, gc, val, vec, nvox, F);
+            scatter_trilinear<DYR>(vol, G.nx, G.ny, G.nz, cen, gc, val, vec, nvox, F, tau, t);
         }
     }
-    if (!DYR && F.live) scatter_footprint(vol, G.nx, G.ny, G.nz, F, vec, nvox);
+    if (F.live) {
+        if (DYR)
+            scatter_footprint_dyrect(vol, G.nx, G.ny, G.nz, F, tau, t, nvox);
+        else
+            scatter_footprint(vol, G.nx, G.ny, G.nz, F, vec, nvox);
+    }
 }
 
 cudaError_t launch_adjoint(const FwdArgs &a, const float *proj, float *vol)
