@@ -142,11 +142,11 @@ class ClockSampler:
 # the two captures, evaluated at 720 views.  Valid only for the kernel
 # sources it was taken on (hash below) and for the FP32 workload; otherwise
 # null.
-_T16, _T180 = 585724416 + 33573888, 983185408 + 395431680
+_T16, _T180 = 585831936 + 33430016, 982422528 + 395699200
 FWD_TRAFFIC_BYTES = int(_T16 + (_T180 - _T16) * (720 - 16) / (180 - 16))
 FWD_TRAFFIC_SOURCES = ("project.cu", "atlas.cuh", "ray.cuh", "cylinder.cuh", "joseph.cuh", "roi.cuh", "fwd_common.cuh",
                        "ctrex_internal.cuh", "dyrect.cuh")
-FWD_TRAFFIC_HASH = "7dff830989774c97"
+FWD_TRAFFIC_HASH = "ffcabe5e01f8bb0a"
 
 
 def fwd_traffic(dtype, views):

@@ -58,15 +58,19 @@ __device__ __forceinline__ void atlas_quad(const Atlas &A, int s, int x0, int y0
 
 // Zero-padded trilinear interpolation of a volume atlas at index coordinate
 // (gx, gy, gz); same weights as the row-major sampler, two gathers.
-struct AtlasSampler {
+// TT: slices whose tile origins the shared-memory table holds (origins of
+// later slices are computed on the fly).
+template <int TT>
+struct AtlasSamplerT {
     Atlas A;
     const float2 *tile = nullptr;  // shared-memory table: slice -> (atlas x, y of its tile) + 1
 
-    static constexpr int TILE_TABLE = 2048;
+    static constexpr int TILE_TABLE = TT;
     static constexpr bool CYLINDER = false;
     static constexpr bool JOSEPH = false;
     static constexpr bool ROI = false;
     static constexpr bool DYRECT = false;
+    static constexpr int MIN_BLOCKS = 0;  // 0: the shared forward kernel entry
     // Fills the per-CTA tile-origin table (all threads call; barrier inside).
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads)
     {
@@ -180,6 +184,8 @@ struct AtlasSampler {
     }
 };
 
+using AtlasSampler = AtlasSamplerT<2048>;
+
 // Row-major (linear memory) sampler with the same semantics.
 template <typename TV>
 struct LinearSampler {
@@ -190,6 +196,7 @@ struct LinearSampler {
     static constexpr bool JOSEPH = false;
     static constexpr bool ROI = false;
     static constexpr bool DYRECT = false;
+    static constexpr int MIN_BLOCKS = 0;  // 0: the shared forward kernel entry
     __device__ __forceinline__ void bind(float2 *, int, int) {}
     __device__ __forceinline__ float interior(float gx, float gy, float gz) const;
     __device__ __forceinline__ float operator()(float gx, float gy, float gz, float &wsum) const;

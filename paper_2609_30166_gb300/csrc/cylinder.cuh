@@ -99,6 +99,7 @@ struct CylSampler {
     static constexpr bool JOSEPH = false;
     static constexpr bool ROI = false;
     static constexpr bool DYRECT = false;
+    static constexpr int MIN_BLOCKS = 0;  // 0: the shared forward kernel entry
 
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads) { base.bind(table, tid, nthreads); }
 

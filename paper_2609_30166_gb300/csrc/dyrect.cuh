@@ -17,6 +17,13 @@
 
 #include "atlas.cuh"
 
+// Resident CTAs per SM the event-model projector is compiled for, through
+// its own kernel entry (its per-tap choice needs more registers than the
+// static sampler, and the texture path wants warps in flight).
+#ifndef CTREX_FWD_DYR_MIN_BLOCKS
+#define CTREX_FWD_DYR_MIN_BLOCKS 9
+#endif
+
 namespace ctrex {
 
 struct DyrectSampler {
@@ -32,6 +39,7 @@ struct DyrectSampler {
     static constexpr bool JOSEPH = false;
     static constexpr bool ROI = false;
     static constexpr bool DYRECT = true;
+    static constexpr int MIN_BLOCKS = CTREX_FWD_DYR_MIN_BLOCKS;  // own kernel entry, CTAs per SM
 
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads)
     {

@@ -26,6 +26,7 @@ struct JosephSampler {
     static constexpr bool JOSEPH = true;
     static constexpr bool ROI = false;
     static constexpr bool DYRECT = false;
+    static constexpr int MIN_BLOCKS = 0;  // 0: the shared forward kernel entry
 
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads) { base.bind(table, tid, nthreads); }
     // unused: the Joseph path never samples trilinearly

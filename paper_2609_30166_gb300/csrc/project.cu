@@ -170,23 +170,19 @@ __global__ void __launch_bounds__(FWD_TX *FWD_TY)
                                         devcheck, p_by_view);
 }
 
-// The event-model projector as its own kernel, compiled for
-// CTREX_FWD_DYR_MIN_BLOCKS resident CTAs per SM: its per-tap choice needs
-// more registers than the static sampler, and the texture path wants warps
-// in flight (72 registers and 7 CTAs: 1128 ms on the 512^3 event workload;
-// 56 registers and 9 CTAs: 1058 ms).
-#ifndef CTREX_FWD_DYR_MIN_BLOCKS
-#define CTREX_FWD_DYR_MIN_BLOCKS 9
-#endif
-
-template <typename TP, int MODE>
-__global__ void __launch_bounds__(FWD_TX *FWD_TY, CTREX_FWD_DYR_MIN_BLOCKS)
-    fwd_kernel_dyr(Grid G, const ViewGPU *__restrict__ views, const DyrectSampler vol_in,
-                   const int *__restrict__ view_idx, TP *__restrict__ out, float *__restrict__ rowsum_out,
-                   const TP *__restrict__ p, float *__restrict__ partials, unsigned *devcheck, int p_by_view)
+// Projectors whose sampler declares MIN_BLOCKS > 0 (the event model and
+// the multi-resolution ROI) run through this entry, compiled for that many
+// resident CTAs per SM; the others keep fwd_kernel's bounds.  Event model:
+// 72 registers and 7 CTAs gave 1128 ms on the 512^3 event workload, 56
+// registers and 9 CTAs 1058 ms.
+template <typename Sampler, typename TP, int MODE>
+__global__ void __launch_bounds__(FWD_TX *FWD_TY, Sampler::MIN_BLOCKS > 0 ? Sampler::MIN_BLOCKS : 1)
+    fwd_kernel_mb(Grid G, const ViewGPU *__restrict__ views, const Sampler vol_in, const int *__restrict__ view_idx,
+                  TP *__restrict__ out, float *__restrict__ rowsum_out, const TP *__restrict__ p,
+                  float *__restrict__ partials, unsigned *devcheck, int p_by_view)
 {
-    fwd_body<DyrectSampler, TP, MODE, false>(G, views, nullptr, nullptr, vol_in, view_idx, out, rowsum_out, p,
-                                             partials, devcheck, p_by_view);
+    fwd_body<Sampler, TP, MODE, false>(G, views, nullptr, nullptr, vol_in, view_idx, out, rowsum_out, p, partials,
+                                       devcheck, p_by_view);
 }
 
 // Second pass of the residual reduction: one CTA, fixed order, FP64.
@@ -282,9 +278,9 @@ static cudaError_t fwd_launch(const FwdArgs &a, const Sampler &smp, TP *out, flo
     } else if (a.motion) {
         return cudaErrorNotSupported;  // the motion warp is defined for the trilinear Cartesian projector only
     }
-    if constexpr (Sampler::DYRECT)
-        fwd_kernel_dyr<TP, MODE><<<grid, block, 0, a.stream>>>(G, a.views, smp, a.view_idx, out, rowsum, p, partials,
-                                                              a.devcheck, a.p_by_view);
+    if constexpr (Sampler::MIN_BLOCKS > 0)
+        fwd_kernel_mb<Sampler, TP, MODE><<<grid, block, 0, a.stream>>>(G, a.views, smp, a.view_idx, out, rowsum, p,
+                                                                      partials, a.devcheck, a.p_by_view);
     else
         fwd_kernel<Sampler, TP, MODE, false><<<grid, block, 0, a.stream>>>(
             G, a.views, nullptr, nullptr, smp, a.view_idx, out, rowsum, p, partials, a.devcheck, a.p_by_view);
@@ -298,7 +294,7 @@ static cudaError_t fwd_dispatch_sampler(const FwdArgs &a, TP *out, float *rowsum
 {
     if (a.roi) {  // context and ROI grids, each from its own atlas
         if (!a.atlas || !a.roi_atlas || a.cyl || a.joseph) return cudaErrorInvalidValue;
-        RoiSampler rs{AtlasSampler{*a.atlas}, AtlasSampler{*a.roi_atlas}, *a.roi};
+        RoiSampler rs{RoiAtlasSampler{*a.atlas}, RoiAtlasSampler{*a.roi_atlas}, *a.roi};
         return fwd_launch<RoiSampler, TP, MODE>(a, rs, out, rowsum, p, partials);
     }
     if (a.dyr) {  // mu0 from the volume atlas, mu1 and tau from their own

@@ -11,22 +11,34 @@
 #include "atlas.cuh"
 #include "ray.cuh"
 
+// Resident CTAs per SM the multi-resolution projector is compiled for,
+// through its own kernel entry (two grids' setup needs more registers than
+// the static sampler, and the texture path wants warps in flight).
+#ifndef CTREX_FWD_ROI_MIN_BLOCKS
+#define CTREX_FWD_ROI_MIN_BLOCKS 8
+#endif
+
 namespace ctrex {
 
+// Each grid's table holds 1024 slices (16 KB for both, so that the CTAs the
+// kernel is compiled for fit in shared memory).
+using RoiAtlasSampler = AtlasSamplerT<1024>;
+
 struct RoiSampler {
-    AtlasSampler ctx;  // context grid atlas (tile table: first half)
-    AtlasSampler roi;  // ROI grid atlas (tile table: second half)
+    RoiAtlasSampler ctx;  // context grid atlas (tile table: first half)
+    RoiAtlasSampler roi;  // ROI grid atlas (tile table: second half)
     RoiGPU R;
-    static constexpr int TILE_TABLE = 2 * AtlasSampler::TILE_TABLE;
+    static constexpr int TILE_TABLE = 2 * RoiAtlasSampler::TILE_TABLE;
     static constexpr bool CYLINDER = false;
     static constexpr bool JOSEPH = false;
     static constexpr bool ROI = true;
     static constexpr bool DYRECT = false;
+    static constexpr int MIN_BLOCKS = CTREX_FWD_ROI_MIN_BLOCKS;  // own kernel entry, CTAs per SM
 
     __device__ __forceinline__ void bind(float2 *table, int tid, int nthreads)
     {
         ctx.bind(table, tid, nthreads);
-        roi.bind(table + AtlasSampler::TILE_TABLE, tid, nthreads);
+        roi.bind(table + RoiAtlasSampler::TILE_TABLE, tid, nthreads);
     }
     // unused: the ROI path integrates piece by piece
     __device__ __forceinline__ float operator()(float, float, float, float &ws) const
@@ -66,7 +78,7 @@ __device__ __forceinline__ void piece_interior(const float X[3], const float dg[
 // Truncated-midpoint samples of the piece [a, b] (mm along the ray) of the
 // line g(t) = X + t dg in the index coordinates of grid `smp` (n voxels per
 // axis), step h (mm); samples with all taps inside take the short path.
-__device__ __forceinline__ void roi_piece(const AtlasSampler &smp, const int n[3], const float X[3],
+__device__ __forceinline__ void roi_piece(const RoiAtlasSampler &smp, const int n[3], const float X[3],
                                           const float dg[3], float a, float b, float h, float &val, float &rs)
 {
     if (!(b > a)) return;
