@@ -53,10 +53,11 @@ def test_expired_epilogue_wait_recovers(variant):
 
     dev = torch.device("cuda", torch.cuda.current_device())
     rng = np.random.default_rng(21)
-    # 2 x 64^3 x 16 channels: 2048 output tiles, several per CTA, so the MMA
-    # warp also reaches its accumulator-release waits.  The weight gradient
-    # takes 32 output channels: layers with 16 use the register-blocked kernel,
-    # which has no mbarrier waits.
+    # 2 x 64^3 x 16 channels: the forward runs the kx-folded kernel (1024
+    # output tiles of 16 x 32 in items of 4 planes, several tiles per CTA, so
+    # the MMA warp also reaches its accumulator-release waits).  The weight
+    # gradient takes 32 output channels: layers with 16 use the
+    # register-blocked kernel, which has no mbarrier waits.
     nb, d, h, w, cin, cout, cg = 2, 64, 64, 64, 16, 16, 32
     x = torch.as_tensor(rng.normal(size=(nb, d, h, w, cin)), dtype=torch.float32).to(torch.bfloat16).to(dev)
     wt = torch.as_tensor(rng.normal(size=(cout, 27, cin)) / 20.0, dtype=torch.float32).to(torch.bfloat16).to(dev)
