@@ -281,7 +281,12 @@ int ctrex_set_roi(ctrex_ctx *ctx, const ctrex_vol_grid *roi);
  *   t_view  DEVICE float [n_views] acquisition time of each view (same
  *           unit as tau).
  * Both are copied on the stream (the caller may free them once the stream
- * has passed this call).  Defined for the trilinear projector on the
+ * has passed this call).  The context also keeps tau as a texture atlas and
+ * the smallest and largest tau of each 8^3 brick (over the brick and the
+ * voxel past each upper face; 8 bytes per brick), with which the projector
+ * takes one field for a whole footprint when the view's time lies on one
+ * side of both (same result as the per-tap choice; a NaN tau keeps its
+ * brick on the per-tap path).  Defined for the trilinear projector on the
  * Cartesian grid without motion, ROI or sub-voxel backprojection:
  * CTREX_E_STATE otherwise (and set_motion, set_roi, set_projector(Joseph),
  * set_bp_subvoxel(s > 1) and motion_grad return CTREX_E_STATE while it is
