@@ -4,9 +4,9 @@
 // tensor memory (TMEM).  The paper has no such operator; it motivates learned
 // components combined with the physics operators (Sec. 5).
 //
-// All kernels compute C[M][N] = sum_k A[M][k] B[N][k] with tcgen05.mma
-// (kind::f16, M = 128, cta_group::1), accumulators in TMEM read back with
-// tcgen05.ld for the epilogue.  Two families:
+// The tcgen05 kernels compute C[M][N] = sum_k A[M][k] B[N][k] with
+// tcgen05.mma (kind::f16, M = 128, cta_group::1), accumulators in TMEM read
+// back with tcgen05.ld for the epilogue.  Two families, and one more kernel:
 //   * brick kernels (channel counts that are multiples of 16): TMA stages the
 //     input window a tile's taps reach once ("brick") and every tap's operand
 //     is the brick at a shifted descriptor start address, so no im2col is
@@ -21,7 +21,10 @@
 //     of 64 K elements into 128-byte-swizzled K-major tiles (16-byte cp.async
 //     copies for multiples of 8 channels: conv_fwd_async_kernel; loads and
 //     stores otherwise: conv_tc_kernel), one thread issues four MMAs per
-//     chunk.
+//     chunk;
+//   * conv_wgrad_c16_kernel: the weight gradient of layers with 16 output
+//     channels on mma.sync (m16n8k16, M = the 16 output channels, no padded
+//     rows; tcgen05 has no M below 64).
 // Operand layouts:
 //   FWD   A = im2col(x)[m][(tap, ci)], B = w[co][(tap, ci)], C -> y[m][co]
 //         (+ bias, optional ReLU);  m runs over N*D*H*W output voxels (NDHWC).
